@@ -1,0 +1,647 @@
+/*
+ * snn_oracle.c -- correctness oracle for the DPSNN per-timestep method
+ * (Pastorelli et al., PDP 2018).  TEST INFRASTRUCTURE ONLY: see snn_oracle.h.
+ *
+ * Plain single-threaded C, compiled with -ffp-contract=off so that every
+ * floating-point expression is evaluated exactly as written (no fused
+ * multiply-add on any host).  The method, in the paper's order:
+ *
+ *   construction (Sec. II-B, Sec. III-B): every neuron i projects K synapses;
+ *     synapse j gets a target K^{ij} drawn from the normalised lateral kernel,
+ *     a delay D^{ij} and a weight W^{ij};
+ *   simulation (Sec. II-A, steps 1-6 of the execution flow): each 1 ms step,
+ *     neurons integrate the inputs queued for this step (recurrent + external
+ *     Poisson synapses, Sec. III-A), spiking neurons are identified, and their
+ *     spikes are queued at the targets for the step given by each delay.
+ *
+ * Readings of the paper used here (where it is silent or ambiguous):
+ *   - Eq. 1 prints +(V-E)/tau_m; the leak is read as -(V-E)/tau_m (the
+ *     standard LIF of the cited Gigante et al. model).  E = 0 by default and
+ *     C_m is absorbed into g_c.
+ *   - The event-driven solver of flow step 6 is the exact propagator of
+ *     Eq. 1-2 over one step: with integer delays every input arrives on a step
+ *     boundary, so integrating each arrival exactly equals decaying V and c
+ *     over dt and then adding the step's summed jumps.
+ *   - "exceeds" the threshold is a strict >; after a spike V is held at V_r
+ *     for round(tau_arp/dt) steps, inputs arriving then are discarded, c keeps
+ *     decaying; c += alpha_c on a spike of an excitatory neuron (Sec. III-A:
+ *     the SFA term is zero for inhibitory neurons).
+ *   - The target module is drawn from one kernel normalised over all in-grid
+ *     modules within the cut-off radius, including the source (r = 0); open
+ *     grid boundaries; draws with replacement (autapses/multapses allowed).
+ *   - Flow step 5 (sorting the inputs) is replaced by an exact int32 fixed
+ *     point sum: integer addition does not depend on the order.
+ */
+#include "snn_oracle.h"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_TAG_GEN 0u
+#define OR_TAG_DRIVE 1u
+#define OR_TAG_INIT 2u
+
+static char g_err[256];
+
+static void set_err(const char* msg) {
+    snprintf(g_err, sizeof g_err, "%s", msg);
+}
+
+const char* or_error(void) { return g_err; }
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers:
+ * As Easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64 multiplications
+ * with the round key bumped by the Weyl constants between rounds. */
+void or_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void draw(const or_params* p, uint32_t a, uint32_t b, uint32_t tag, uint32_t out[4]) {
+    uint32_t ctr[4] = {a, b, tag, 0u};
+    uint32_t key[2] = {(uint32_t)p->seed, (uint32_t)(p->seed >> 32)};
+    or_philox(ctr, key, out);
+}
+
+/* 24-bit uniform in [0, 1): top 24 bits of a word times 2^-24 (exact). */
+static float unit24(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
+static double unit24d(uint32_t u) { return (double)(u >> 8) * (1.0 / 16777216.0); }
+
+/* Round-to-nearest-even to bfloat16 (the top 16 bits of an IEEE binary32). */
+uint16_t or_bf16_bits(float w) {
+    uint32_t bits;
+    memcpy(&bits, &w, 4);
+    if ((bits & 0x7F800000u) == 0x7F800000u && (bits & 0x007FFFFFu))
+        return (uint16_t)((bits >> 16) | 0x40u); /* quiet NaN */
+    uint32_t lsb = (bits >> 16) & 1u;
+    bits += 0x7FFFu + lsb;
+    return (uint16_t)(bits >> 16);
+}
+
+float or_bf16_to_float(uint16_t b) {
+    uint32_t bits = (uint32_t)b << 16;
+    float w;
+    memcpy(&w, &bits, 4);
+    return w;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Constants of the method, all derived here in FP64 and rounded once. */
+int or_constants(const or_params* p, or_consts* c) {
+    memset(c, 0, sizeof *c);
+    if (p->grid_w == 0 || p->grid_h == 0 || p->neurons_per_module == 0) {
+        set_err("empty grid");
+        return -1;
+    }
+    if (!(p->spacing_um > 0.0f) || !(p->dt > 0.0f) || !(p->tau_m > 0.0f) || !(p->tau_c > 0.0f)) {
+        set_err("spacing, dt, tau_m and tau_c must be positive");
+        return -1;
+    }
+    if (p->kernel != 0 && p->kernel != 1) {
+        set_err("kernel must be 0 (Gaussian) or 1 (exponential)");
+        return -1;
+    }
+    if ((p->kernel == 0 && !(p->sigma_um > 0.0)) || (p->kernel == 1 && !(p->lambda_um > 0.0))) {
+        set_err("kernel length scale must be positive");
+        return -1;
+    }
+    if (!(p->cutoff_um >= 0.0)) {
+        set_err("cutoff must be non-negative");
+        return -1;
+    }
+    if (p->d_exc_lo < 1 || p->d_exc_hi < p->d_exc_lo || p->d_inh < 1 || p->d_exc_hi > 255 ||
+        p->d_inh > 255) {
+        set_err("delays must satisfy 1 <= lo <= hi <= 255");
+        return -1;
+    }
+    if (p->fx_shift < 8 || p->fx_shift > 24) {
+        set_err("fx_shift must be in [8, 24]");
+        return -1;
+    }
+    uint64_t N = (uint64_t)p->grid_w * p->grid_h * p->neurons_per_module;
+    if (N > 0xFFFFFFF0ull) {
+        set_err("too many neurons");
+        return -1;
+    }
+    c->N = (uint32_t)N;
+    c->n_modules = p->grid_w * p->grid_h;
+    double ne = floor((double)p->exc_fraction * (double)p->neurons_per_module + 0.5);
+    if (ne < 0.0) ne = 0.0;
+    if (ne > (double)p->neurons_per_module) ne = (double)p->neurons_per_module;
+    c->n_exc = (uint32_t)ne;
+    uint32_t dmax = p->d_exc_hi > p->d_inh ? p->d_exc_hi : p->d_inh;
+    c->D = dmax + 1u;
+    c->ref_steps = (uint32_t)lround((double)p->t_ref / (double)p->dt);
+
+    double q = p->cutoff_um / (double)p->spacing_um;
+    c->R2 = (uint32_t)floor(q * q + 1e-9);
+    uint32_t R = 0;
+    while ((R + 1) * (R + 1) <= c->R2) ++R;
+    uint32_t cnt = 0;
+    for (int32_t dy = -(int32_t)R; dy <= (int32_t)R; ++dy)
+        for (int32_t dx = -(int32_t)R; dx <= (int32_t)R; ++dx)
+            if ((uint32_t)(dx * dx + dy * dy) <= c->R2) ++cnt;
+    c->max_offsets = cnt;
+
+    double dt = (double)p->dt, tm = (double)p->tau_m, tc = (double)p->tau_c;
+    double em = exp(-dt / tm);
+    double ec = exp(-dt / tc);
+    c->a_m = (float)em;
+    c->a_c = (float)ec;
+    double kc;
+    if (tc == tm)
+        kc = (double)p->g_c * dt * em;
+    else
+        kc = (double)p->g_c * (tm * tc / (tc - tm)) * (ec - em);
+    c->kc = (float)kc;
+
+    float scale = ldexpf(1.0f, (int)p->fx_shift);
+    c->J_ext_fx = (int32_t)lrintf(p->J_ext * scale);
+
+    double lam = (double)p->ext_rate_hz * dt / 1000.0;
+    c->pois_len = 0;
+    if (lam < 0.0) {
+        set_err("negative external rate");
+        return -1;
+    }
+    if (lam > 0.0) {
+        double pk = exp(-lam), cdf = 0.0;
+        for (uint32_t k = 0; k < 64; ++k) {
+            cdf = cdf + pk;
+            double x = floor(cdf * 4294967296.0);
+            if (x >= 4294967295.0) break;
+            c->pois[c->pois_len++] = (uint64_t)x;
+            pk = pk * lam / (double)(k + 1);
+        }
+        if (c->pois_len == 64) {
+            set_err("external rate too high for the Poisson table");
+            return -1;
+        }
+    }
+    double pf = (double)p->imposed_rate_hz * dt / 1000.0;
+    if (pf < 0.0) pf = 0.0;
+    if (pf > 1.0) pf = 1.0;
+    c->imposed_thresh = (uint64_t)floor(pf * 4294967296.0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lateral kernels (Sec. I and Sec. III-B): Gaussian B exp(-r^2 / 2 sigma^2),
+ * exponential A exp(-r / lambda); r = spacing * grid distance.  The
+ * normalisation constants A and B are 1 / (sum over the stencil). */
+static double kernel_value(const or_params* p, uint32_t d2) {
+    double s = (double)p->spacing_um;
+    if (p->kernel == 0) {
+        double num = (double)d2 * s * s;
+        double den = 2.0 * p->sigma_um * p->sigma_um;
+        return exp(-(num / den));
+    }
+    double r = s * sqrt((double)d2);
+    return exp(-(r / p->lambda_um));
+}
+
+int or_cdf_table(const or_params* p, uint32_t module, uint32_t* thresh, uint32_t* tgt_module,
+                 double* prob, uint32_t cap, uint32_t* n_out) {
+    or_consts c;
+    if (or_constants(p, &c)) return -1;
+    if (module >= c.n_modules) {
+        set_err("module out of range");
+        return -1;
+    }
+    double* pre = (double*)malloc(sizeof(double) * (c.max_offsets + 1));
+    double* f = (double*)malloc(sizeof(double) * (c.max_offsets + 1));
+    uint32_t* tg = (uint32_t*)malloc(sizeof(uint32_t) * (c.max_offsets + 1));
+    if (!pre || !f || !tg) {
+        free(pre); free(f); free(tg);
+        set_err("out of memory");
+        return -1;
+    }
+    int32_t sx = (int32_t)(module % p->grid_w), sy = (int32_t)(module / p->grid_w);
+    uint32_t R = 0;
+    while ((R + 1) * (R + 1) <= c.R2) ++R;
+    uint32_t n = 0;
+    double P = 0.0;
+    for (int32_t dy = -(int32_t)R; dy <= (int32_t)R; ++dy) {
+        for (int32_t dx = -(int32_t)R; dx <= (int32_t)R; ++dx) {
+            uint32_t d2 = (uint32_t)(dx * dx + dy * dy);
+            if (d2 > c.R2) continue;
+            int32_t tx = sx + dx, ty = sy + dy;
+            if (tx < 0 || ty < 0 || tx >= (int32_t)p->grid_w || ty >= (int32_t)p->grid_h) continue;
+            f[n] = kernel_value(p, d2);
+            P = P + f[n];
+            pre[n] = P;
+            tg[n] = (uint32_t)ty * p->grid_w + (uint32_t)tx;
+            ++n;
+        }
+    }
+    if (n > cap) {
+        free(pre); free(f); free(tg);
+        set_err("table capacity too small");
+        return -1;
+    }
+    double S = pre[n - 1];
+    for (uint32_t j = 0; j < n; ++j) {
+        uint32_t T = 0xFFFFFFFFu;
+        if (j + 1 < n) {
+            double x = floor(pre[j] / S * 4294967296.0);
+            T = x >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)x;
+        }
+        thresh[j] = T;
+        tgt_module[j] = tg[j];
+        if (prob) prob[j] = f[j] / S;
+    }
+    *n_out = n;
+    free(pre); free(f); free(tg);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+int or_lif_update(const or_consts* c, const or_params* p, float* V, float* cf, uint8_t* ref,
+                  int exc, int32_t I_fx, int forced) {
+    int was_ref = *ref > 0;
+    if (was_ref) {
+        *ref = (uint8_t)(*ref - 1);
+        *V = p->V_reset;
+    } else {
+        /* exact propagator of Eq. 1-2 over dt, then this step's jumps */
+        float v = *V - p->E;
+        v = v * c->a_m;
+        v = v + p->E;
+        float adapt = c->kc * *cf;
+        v = v - adapt;
+        float inp = (float)I_fx * ldexpf(1.0f, -(int)p->fx_shift);
+        v = v + inp;
+        *V = v;
+    }
+    *cf = *cf * c->a_c;
+    int spike = !was_ref && (*V > p->V_th || forced);
+    if (spike) {
+        *V = p->V_reset;
+        *ref = (uint8_t)c->ref_steps;
+        if (exc) *cf = *cf + p->alpha_c;
+    }
+    return spike;
+}
+
+uint32_t or_poisson_count(const or_consts* c, uint32_t u0) {
+    uint32_t n = 0;
+    for (uint32_t k = 0; k < c->pois_len; ++k)
+        if (c->pois[k] <= (uint64_t)u0) ++n;
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+struct or_net {
+    or_params p;
+    or_consts c;
+    int fp64;
+    uint32_t N, K, M;
+    uint64_t nsyn;
+    uint32_t* tgt;
+    float* w;
+    double* w64;
+    uint8_t* d;
+    float* V;
+    float* cf;
+    double* V64;
+    double* c64;
+    uint8_t* ref;
+    int64_t* ring;
+    double* ring64;
+    uint32_t t;
+    uint32_t* spk;
+    uint32_t* rst_t;
+    uint32_t* rst_id;
+    uint64_t rst_n, rst_cap;
+    uint64_t n_spikes, rec, ext;
+    uint64_t shuffle_seed;
+    double a_m64, a_c64, kc64;
+};
+
+static int is_exc(const or_net* n, uint32_t i) { return (i % n->M) < n->c.n_exc; }
+
+void or_destroy(or_net* n) {
+    if (!n) return;
+    free(n->tgt); free(n->w); free(n->w64); free(n->d);
+    free(n->V); free(n->cf); free(n->V64); free(n->c64); free(n->ref);
+    free(n->ring); free(n->ring64); free(n->spk); free(n->rst_t); free(n->rst_id);
+    free(n);
+}
+
+/* Synapse generation (Sec. II-B): synapse k of neuron i draws one Philox
+ * block (i, k, GEN); u0 picks the target module by inverse CDF, u1 the neuron
+ * inside it, u2 the weight and u3 the delay. */
+static int generate(or_net* n) {
+    const or_params* p = &n->p;
+    uint32_t cap = n->c.max_offsets;
+    uint32_t nm = n->c.n_modules;
+    uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
+    uint32_t* TM = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
+    uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * nm);
+    if (!T || !TM || !cnt) {
+        free(T); free(TM); free(cnt);
+        set_err("out of memory");
+        return -1;
+    }
+    for (uint32_t m = 0; m < nm; ++m) {
+        if (or_cdf_table(p, m, T + (size_t)m * cap, TM + (size_t)m * cap, NULL, cap, &cnt[m])) {
+            free(T); free(TM); free(cnt);
+            return -1;
+        }
+    }
+    float span = p->w_exc_hi - p->w_exc_lo;
+    uint32_t dspan = p->d_exc_hi - p->d_exc_lo + 1u;
+    for (uint32_t i = 0; i < n->N; ++i) {
+        uint32_t s = i / n->M;
+        const uint32_t* Ts = T + (size_t)s * cap;
+        const uint32_t* TMs = TM + (size_t)s * cap;
+        uint32_t ns = cnt[s];
+        int exc = is_exc(n, i);
+        for (uint32_t k = 0; k < n->K; ++k) {
+            uint32_t u[4];
+            draw(p, i, k, OR_TAG_GEN, u);
+            uint32_t j = 0;
+            while (j + 1 < ns && Ts[j] <= u[0]) ++j; /* first entry with u0 < T */
+            uint32_t tmod = TMs[j];
+            uint32_t tgt = tmod * n->M + (uint32_t)(((uint64_t)u[1] * n->M) >> 32);
+            size_t e = (size_t)i * n->K + k;
+            n->tgt[e] = tgt;
+            if (exc) {
+                n->d[e] = (uint8_t)(p->d_exc_lo + (uint32_t)(((uint64_t)u[3] * dspan) >> 32));
+                if (n->fp64) {
+                    double lo = (double)p->w_exc_lo, hi = (double)p->w_exc_hi;
+                    n->w64[e] = lo + (hi - lo) * unit24d(u[2]);
+                } else {
+                    float x = span * unit24(u[2]);
+                    n->w[e] = p->w_exc_lo + x;
+                }
+            } else {
+                n->d[e] = (uint8_t)p->d_inh;
+                if (n->fp64)
+                    n->w64[e] = (double)p->w_inh;
+                else
+                    n->w[e] = p->w_inh;
+            }
+            if (!n->fp64 && p->weight_bf16) n->w[e] = or_bf16_to_float(or_bf16_bits(n->w[e]));
+        }
+    }
+    free(T); free(TM); free(cnt);
+    return 0;
+}
+
+or_net* or_create(const or_params* p, int fp64) {
+    or_consts c;
+    if (or_constants(p, &c)) return NULL;
+    or_net* n = (or_net*)calloc(1, sizeof *n);
+    if (!n) {
+        set_err("out of memory");
+        return NULL;
+    }
+    n->p = *p;
+    n->c = c;
+    n->fp64 = fp64 ? 1 : 0;
+    n->N = c.N;
+    n->K = p->K;
+    n->M = p->neurons_per_module;
+    n->nsyn = (uint64_t)n->N * n->K;
+    size_t ns = (size_t)n->nsyn ? (size_t)n->nsyn : 1;
+    n->tgt = (uint32_t*)malloc(sizeof(uint32_t) * ns);
+    n->d = (uint8_t*)malloc(ns);
+    if (n->fp64)
+        n->w64 = (double*)malloc(sizeof(double) * ns);
+    else
+        n->w = (float*)malloc(sizeof(float) * ns);
+    n->ref = (uint8_t*)calloc(n->N, 1);
+    n->spk = (uint32_t*)malloc(sizeof(uint32_t) * n->N);
+    if (n->fp64) {
+        n->V64 = (double*)malloc(sizeof(double) * n->N);
+        n->c64 = (double*)calloc(n->N, sizeof(double));
+        n->ring64 = (double*)calloc((size_t)c.D * n->N, sizeof(double));
+    } else {
+        n->V = (float*)malloc(sizeof(float) * n->N);
+        n->cf = (float*)calloc(n->N, sizeof(float));
+        n->ring = (int64_t*)calloc((size_t)c.D * n->N, sizeof(int64_t));
+    }
+    if (!n->tgt || !n->d || (!n->w && !n->w64) || !n->ref || !n->spk ||
+        (n->fp64 ? (!n->V64 || !n->c64 || !n->ring64) : (!n->V || !n->cf || !n->ring))) {
+        or_destroy(n);
+        set_err("out of memory");
+        return NULL;
+    }
+    if (generate(n)) {
+        or_destroy(n);
+        return NULL;
+    }
+    /* initial state (the paper is silent): V0 = V_th * U[0,1), c = 0, ring = 0 */
+    for (uint32_t i = 0; i < n->N; ++i) {
+        uint32_t u[4];
+        draw(p, i, 0u, OR_TAG_INIT, u);
+        if (n->fp64)
+            n->V64[i] = (double)p->V_th * unit24d(u[0]);
+        else
+            n->V[i] = p->V_th * unit24(u[0]);
+    }
+    double dt = (double)p->dt, tm = (double)p->tau_m, tc = (double)p->tau_c;
+    n->a_m64 = exp(-dt / tm);
+    n->a_c64 = exp(-dt / tc);
+    n->kc64 = tc == tm ? (double)p->g_c * dt * n->a_m64
+                       : (double)p->g_c * (tm * tc / (tc - tm)) * (n->a_c64 - n->a_m64);
+    return n;
+}
+
+uint64_t or_n_synapses(const or_net* n) { return n->nsyn; }
+
+void or_get_csr(const or_net* n, uint32_t* tgt, float* w, uint8_t* d) {
+    if (tgt) memcpy(tgt, n->tgt, sizeof(uint32_t) * n->nsyn);
+    if (w && n->w) memcpy(w, n->w, sizeof(float) * n->nsyn);
+    if (d) memcpy(d, n->d, n->nsyn);
+}
+
+void or_get_csr_f64(const or_net* n, double* w) {
+    if (w && n->w64) memcpy(w, n->w64, sizeof(double) * n->nsyn);
+}
+
+void or_set_delivery_shuffle(or_net* n, uint64_t s) { n->shuffle_seed = s; }
+
+/* splitmix64: only used to permute the delivery order in the order-independence check */
+static uint64_t mix64(uint64_t* s) {
+    uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static int raster_push(or_net* n, uint32_t t, uint32_t id) {
+    if (n->rst_n == n->rst_cap) {
+        uint64_t nc = n->rst_cap ? n->rst_cap * 2 : 4096;
+        uint32_t* a = (uint32_t*)realloc(n->rst_t, sizeof(uint32_t) * nc);
+        if (!a) return -1;
+        n->rst_t = a;
+        uint32_t* b = (uint32_t*)realloc(n->rst_id, sizeof(uint32_t) * nc);
+        if (!b) return -1;
+        n->rst_id = b;
+        n->rst_cap = nc;
+    }
+    n->rst_t[n->rst_n] = t;
+    n->rst_id[n->rst_n] = id;
+    ++n->rst_n;
+    return 0;
+}
+
+static void deliver_one(or_net* n, uint32_t t, uint32_t src, uint32_t k) {
+    size_t e = (size_t)src * n->K + k;
+    uint32_t slot = (t + n->d[e]) % n->c.D;
+    size_t r = (size_t)slot * n->N + n->tgt[e];
+    if (n->fp64) {
+        n->ring64[r] += n->w64[e];
+    } else {
+        float scale = ldexpf(1.0f, (int)n->p.fx_shift);
+        n->ring[r] += (int64_t)lrintf(n->w[e] * scale);
+    }
+}
+
+static int step_once(or_net* n) {
+    const or_params* p = &n->p;
+    const or_consts* c = &n->c;
+    uint32_t t = n->t;
+    uint32_t slot = t % c->D;
+    uint32_t nspk = 0;
+    /* flow steps 4-6: inject the inputs queued for this step and integrate */
+    for (uint32_t i = 0; i < n->N; ++i) {
+        uint32_t u[4];
+        draw(p, i, t, OR_TAG_DRIVE, u);
+        uint32_t next = or_poisson_count(c, u[0]);
+        int forced = (uint64_t)u[1] < c->imposed_thresh;
+        int exc = is_exc(n, i);
+        int spike;
+        n->ext += next;
+        size_t r = (size_t)slot * n->N + i;
+        if (n->fp64) {
+            double I = n->ring64[r] + (double)next * (double)p->J_ext;
+            n->ring64[r] = 0.0;
+            int was_ref = n->ref[i] > 0;
+            if (was_ref) {
+                n->ref[i] = (uint8_t)(n->ref[i] - 1);
+                n->V64[i] = (double)p->V_reset;
+            } else {
+                double E = (double)p->E;
+                n->V64[i] = ((n->V64[i] - E) * n->a_m64 + E) - n->kc64 * n->c64[i] + I;
+            }
+            n->c64[i] = n->c64[i] * n->a_c64;
+            spike = !was_ref && (n->V64[i] > (double)p->V_th || forced);
+            if (spike) {
+                n->V64[i] = (double)p->V_reset;
+                n->ref[i] = (uint8_t)c->ref_steps;
+                if (exc) n->c64[i] = n->c64[i] + (double)p->alpha_c;
+            }
+        } else {
+            int64_t I = n->ring[r] + (int64_t)next * c->J_ext_fx;
+            n->ring[r] = 0;
+            if (I > INT32_MAX || I < INT32_MIN) {
+                set_err("int32 fixed-point input overflow");
+                return -1;
+            }
+            spike = or_lif_update(c, p, &n->V[i], &n->cf[i], &n->ref[i], exc, (int32_t)I, forced);
+        }
+        /* flow step 1: neurons that spiked in this step, in id order */
+        if (spike) {
+            n->spk[nspk++] = i;
+            if (raster_push(n, t, i)) {
+                set_err("out of memory");
+                return -1;
+            }
+        }
+    }
+    n->n_spikes += nspk;
+    n->rec += (uint64_t)nspk * n->K;
+    /* flow steps 2-3: queue every spike at its targets, in the slot of the
+     * step at which it arrives (t + delay) */
+    if (n->shuffle_seed == 0) {
+        for (uint32_t s = 0; s < nspk; ++s)
+            for (uint32_t k = 0; k < n->K; ++k) deliver_one(n, t, n->spk[s], k);
+    } else {
+        uint64_t st = n->shuffle_seed ^ ((uint64_t)t << 32);
+        uint64_t total = (uint64_t)nspk * n->K;
+        uint64_t* ord = (uint64_t*)malloc(sizeof(uint64_t) * (total ? total : 1));
+        if (!ord) {
+            set_err("out of memory");
+            return -1;
+        }
+        for (uint64_t e = 0; e < total; ++e) ord[e] = e;
+        for (uint64_t e = total; e > 1; --e) {
+            uint64_t j = mix64(&st) % e;
+            uint64_t tmp = ord[e - 1];
+            ord[e - 1] = ord[j];
+            ord[j] = tmp;
+        }
+        for (uint64_t e = 0; e < total; ++e)
+            deliver_one(n, t, n->spk[ord[e] / n->K], (uint32_t)(ord[e] % n->K));
+        free(ord);
+    }
+    n->t = t + 1;
+    return 0;
+}
+
+int or_step(or_net* n, uint32_t n_steps) {
+    for (uint32_t s = 0; s < n_steps; ++s)
+        if (step_once(n)) return -1;
+    return 0;
+}
+
+uint64_t or_raster_size(const or_net* n) { return n->rst_n; }
+
+void or_get_raster(const or_net* n, uint32_t* steps, uint32_t* ids) {
+    if (steps) memcpy(steps, n->rst_t, sizeof(uint32_t) * n->rst_n);
+    if (ids) memcpy(ids, n->rst_id, sizeof(uint32_t) * n->rst_n);
+}
+
+void or_clear_raster(or_net* n) { n->rst_n = 0; }
+
+uint32_t or_time(const or_net* n) { return n->t; }
+
+void or_get_state(const or_net* n, float* V, float* c, uint8_t* ref, int32_t* ring) {
+    if (V && n->V) memcpy(V, n->V, sizeof(float) * n->N);
+    if (c && n->cf) memcpy(c, n->cf, sizeof(float) * n->N);
+    if (ref) memcpy(ref, n->ref, n->N);
+    if (ring && n->ring) {
+        /* ring rows in absolute-slot order: row r holds inputs for steps with t % D == r */
+        size_t tot = (size_t)n->c.D * n->N;
+        for (size_t e = 0; e < tot; ++e) ring[e] = (int32_t)(uint32_t)(uint64_t)n->ring[e];
+    }
+}
+
+void or_get_state_f64(const or_net* n, double* V, double* c) {
+    if (V && n->V64) memcpy(V, n->V64, sizeof(double) * n->N);
+    if (c && n->c64) memcpy(c, n->c64, sizeof(double) * n->N);
+}
+
+void or_set_state(or_net* n, const float* V, const float* c, const uint8_t* ref) {
+    if (V && n->V) memcpy(n->V, V, sizeof(float) * n->N);
+    if (c && n->cf) memcpy(n->cf, c, sizeof(float) * n->N);
+    if (ref) memcpy(n->ref, ref, n->N);
+}
+
+void or_get_stats(const or_net* n, uint64_t* spikes, uint64_t* rec, uint64_t* ext) {
+    if (spikes) *spikes = n->n_spikes;
+    if (rec) *rec = n->rec;
+    if (ext) *ext = n->ext;
+}

@@ -1,0 +1,71 @@
+"""Seeded synthetic workloads: the parameter sets that both the CUDA path and
+the oracle are run on.  This module holds inputs only (numbers and seeds), none
+of the method's arithmetic.
+
+Every network here is synthetic, shaped like the paper's workloads: square grids
+of cortical modules at 100 um spacing, 80 % excitatory neurons per module, and
+a Gaussian (sigma = 100 um) or exponential (lambda = 290 um) lateral kernel
+(Sec. III-B, Table I).  The paper uses no public dataset.
+"""
+from __future__ import annotations
+
+import copy
+
+# Neuron model of Eq. 1-2 plus the external Poisson synapses (Sec. III-A).
+_NEURON = {
+    "tau_m_ms": 20.0, "E_mV": 0.0, "V_th_mV": 20.0, "V_reset_mV": 15.0, "t_ref_ms": 2.0,
+    "tau_c_ms": 500.0, "alpha_c": 0.05, "g_c_mV": 1.0, "dt_ms": 1.0,
+    "ext_rate_hz": 1500.0, "J_ext_mV": 0.2,
+}
+
+_SYNAPSES = {
+    "w_exc_lo": 0.1, "w_exc_hi": 0.3, "w_inh": -0.8,
+    "d_exc_lo": 1, "d_exc_hi": 20, "d_inh": 1,
+}
+
+_GAUSS = {"kernel": "gauss", "sigma_um": 100.0, "lambda_um": 290.0, "cutoff_um": 300.0}
+_EXP = {"kernel": "exp", "sigma_um": 100.0, "lambda_um": 290.0, "cutoff_um": 1200.0}
+
+
+def _make(grid, M, K, lateral, seed, weight_dtype="f32", imposed_rate_hz=0.0, **extra):
+    cfg = {
+        "grid_w": grid, "grid_h": grid, "neurons_per_module": M, "exc_fraction": 0.8,
+        "spacing_um": 100.0, "K": K, **lateral, **_SYNAPSES, **_NEURON,
+        "imposed_rate_hz": imposed_rate_hz, "weight_dtype": weight_dtype, "fx_shift": 16,
+        "seed": seed,
+    }
+    cfg.update(extra)
+    return cfg
+
+
+def gauss_4x4_k1000(seed=1, **kw):
+    """4x4 modules x 1,000 neurons (16k), K=1,000, Gaussian 3-sigma, FP32 weights."""
+    return _make(4, 1000, 1000, _GAUSS, seed, **kw)
+
+
+def gauss_24x24_k1125(seed=1, **kw):
+    """24x24 modules x 1,250 neurons (720k), K=1,125 (~810 M synapses), Gaussian 3-sigma."""
+    return _make(24, 1250, 1125, _GAUSS, seed, **kw)
+
+
+def exp_24x24_k2250(seed=1, weight_dtype="bf16", **kw):
+    """24x24 modules x 1,250 neurons, K=2,250 (~1.6 G synapses), exponential to 1.2 mm."""
+    return _make(24, 1250, 2250, _EXP, seed, weight_dtype=weight_dtype, **kw)
+
+
+def patch(cfg, grid, steps=None):
+    """The same model on a smaller grid (a bounded sample of a large workload)."""
+    c = copy.deepcopy(cfg)
+    c["grid_w"] = c["grid_h"] = grid
+    return c
+
+
+def small(grid=2, M=40, K=30, lateral="gauss", seed=3, **kw):
+    """Tiny networks for brute-force and edge-case checks."""
+    return _make(grid, M, K, _GAUSS if lateral == "gauss" else _EXP, seed, **kw)
+
+
+# Firing rates the paper observed (Sec. III-D): ~7.5 Hz with the Gaussian
+# kernel, 32-38 Hz with the exponential one.  Used as imposed rates.
+PAPER_RATE_GAUSS_HZ = 7.5
+PAPER_RATE_EXP_HZ = 35.0
