@@ -1,0 +1,193 @@
+/*
+ * snn.h -- C ABI of libsnn.so: the per-timestep hot path of the DPSNN cortical
+ * simulator (Pastorelli et al., "Gaussian and exponential lateral connectivity
+ * on distributed spiking neural network simulation", PDP 2018) on one GB300.
+ *
+ * Model.  LIF neurons with spike-frequency adaptation (Eq. 1-2, Sec. III-A),
+ * grouped in cortical modules of M neurons (80 % excitatory) on a 2-D grid
+ * with spacing alpha (Sec. III-B).  Every neuron i projects K synapses with
+ * target K^{ij}, delay D^{ij} and weight W^{ij} (Sec. II-B); the target module
+ * is drawn from a Gaussian B exp(-r^2/2 sigma^2) or exponential A exp(-r/lambda)
+ * lateral kernel (Sec. I, Sec. III-B) normalised over the in-grid modules
+ * within a cut-off radius.  External synapses are a Poisson process (Sec. III-A).
+ * Simulation is the mixed time/event-driven loop of Sec. II-A with a 1 ms
+ * exchange step: integrate, identify spikers, queue each spike at its targets
+ * for the step given by the synaptic delay.
+ *
+ * Conventions (every function):
+ *   - Returns an snn_status; nothing throws across the ABI.  On failure a
+ *     message is available from snn_last_error() (per calling thread).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Functions marked "async" only enqueue work on that stream.
+ *   - Device memory comes from the caller's allocator hook (alloc_fn/free_fn),
+ *     or from cudaMalloc/cudaFree when the hook is NULL.  Host buffers are
+ *     caller-owned and must hold the sizes stated.
+ *   - The network object is library-owned; destroy it with snn_destroy.
+ *   - One network must not be used from two host threads at once.
+ *
+ * Units: um, ms, mV, Hz.  Input to a neuron is accumulated in int32 fixed
+ * point with a quantum of 2^-fx_shift mV, so delivery order never changes a
+ * result (this replaces the sorting of inputs of flow step 5, Sec. II-A).
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SNN_API __attribute__((visibility("default")))
+#else
+#define SNN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum snn_status {
+    SNN_OK = 0,
+    SNN_EINVAL = -1,    /* invalid argument or network description */
+    SNN_ENOMEM = -2,    /* the allocator hook returned NULL */
+    SNN_ECUDA = -3,     /* a CUDA runtime call failed (message in snn_last_error) */
+    SNN_EOVERFLOW = -4, /* the device raster filled up; spikes past capacity were dropped */
+    SNN_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    SNN_EBUDGET = -6    /* a request does not fit the memory budget */
+} snn_status;
+
+enum { SNN_KERNEL_GAUSS = 0, SNN_KERNEL_EXP = 1 };
+enum { SNN_WEIGHT_F32 = 0, SNN_WEIGHT_BF16 = 1 };
+
+/* Network description; plain data, copied by snn_build_network. */
+typedef struct snn_config {
+    uint32_t grid_w, grid_h;     /* modules along x and y (Sec. III-B, Table I) */
+    uint32_t neurons_per_module; /* M; neuron i lives in module i / M */
+    float exc_fraction;          /* excitatory share; neuron i is excitatory if
+                                    i % M < floor(exc_fraction * M + 0.5) */
+    float spacing_um;            /* grid step alpha (Sec. III-B) */
+    uint32_t K;                  /* out-degree: synapses projected per neuron (Sec. II-B) */
+    int32_t kernel;              /* SNN_KERNEL_GAUSS or SNN_KERNEL_EXP */
+    double sigma_um;             /* Gaussian width */
+    double lambda_um;            /* exponential decay length */
+    double cutoff_um;            /* keep modules with dx^2 + dy^2 <= floor((cutoff/spacing)^2) */
+    float w_exc_lo, w_exc_hi;    /* excitatory weight: w_lo + (w_hi - w_lo) * U[0,1) (mV) */
+    float w_inh;                 /* inhibitory weight (mV) */
+    uint32_t d_exc_lo, d_exc_hi; /* excitatory delay: uniform integer in [lo, hi] steps */
+    uint32_t d_inh;              /* inhibitory delay (steps); all delays in [1, 255] */
+    float tau_m_ms, E_mV, V_th_mV, V_reset_mV, t_ref_ms; /* Eq. 1 and reset rules */
+    float tau_c_ms, alpha_c, g_c_mV;                     /* Eq. 2, SFA increment, coupling */
+    float dt_ms;                 /* time step (the paper's 1 ms exchange step) */
+    float ext_rate_hz, J_ext_mV; /* external Poisson synapses (Sec. III-A) */
+    float imposed_rate_hz;       /* extra Bernoulli spikes per neuron and step
+                                    (0 = off); a workload knob, not part of the model */
+    int32_t weight_dtype;        /* SNN_WEIGHT_F32 or SNN_WEIGHT_BF16 (stored weights) */
+    uint32_t fx_shift;           /* fixed-point quantum 2^-fx_shift mV, in [8, 24] */
+    uint64_t seed;               /* Philox4x32-10 key */
+    uint64_t raster_capacity;    /* device raster entries (spikes) kept before overflow */
+} snn_config;
+
+typedef struct snn_stats {
+    uint64_t steps;          /* time steps simulated so far */
+    uint64_t n_spikes;       /* spikes emitted (including any beyond raster capacity) */
+    uint64_t rec_events;     /* recurrent synaptic events delivered: sum over spikes of K */
+    uint64_t ext_events;     /* external Poisson events received */
+    uint64_t raster_count;   /* spikes recorded since the last snn_clear_raster */
+    uint64_t raster_capacity;
+} snn_stats;
+
+typedef struct snn_net snn_net; /* opaque, library-owned */
+
+typedef void* (*snn_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*snn_free_fn)(void* ptr, void* ctx);
+
+/* Construction phase (Sec. II-A phase 1; Sec. II-B; Sec. III-B).  Validates
+ * `cfg`, builds per source module the FP64 cumulative target-module table of
+ * the normalised lateral kernel, draws the N*K synapses with counter-based
+ * Philox into a row-per-neuron table (uint32 target, f32 or bf16 weight,
+ * uint8 delay), and sets the initial state: V = V_th * U[0,1), c = 0, empty
+ * delay ring.  Async on `stream` except for argument checks and allocation.
+ * Errors: SNN_EINVAL (bad description), SNN_ENOMEM, SNN_ECUDA.  *out is set
+ * only on success. */
+SNN_API snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
+                             void* alloc_ctx, void* stream, snn_net** out);
+
+/* Simulation phase (Sec. II-A, flow steps 1-6) for n_steps time steps.  Each
+ * step: every neuron reads and clears its ring slot for this step, adds its
+ * Poisson external input, integrates Eq. 1-2 exactly over dt, applies
+ * threshold / reset / refractory / adaptation, and the spikes of the step
+ * (ids in increasing order) are appended to the device raster; then every
+ * spike adds its K weights into ring[(t + delay) mod D][target].  Async.
+ * Errors: SNN_EINVAL (NULL net), SNN_ECUDA. */
+SNN_API snn_status snn_step(snn_net* net, uint32_t n_steps, void* stream);
+
+/* Copies the recorded spikes (AER events: step, neuron id; Sec. II-C),
+ * ordered by (step, id), into caller-owned host arrays of `cap` entries.
+ * *n_out = entries copied = min(recorded, raster capacity, cap).  Synchronises
+ * `stream`.  Returns SNN_EOVERFLOW (after copying) if the device raster had
+ * to drop spikes. */
+SNN_API snn_status snn_read_spikes(snn_net* net, uint32_t* steps, uint32_t* ids, size_t cap,
+                           size_t* n_out, void* stream);
+
+/* Empties the device raster (async). */
+SNN_API snn_status snn_clear_raster(snn_net* net, void* stream);
+
+/* Counters of Sec. III-D's normalised cost: spikes, recurrent and external
+ * ("total equivalent") synaptic events.  Synchronises `stream`. */
+SNN_API snn_status snn_get_stats(snn_net* net, snn_stats* out, void* stream);
+
+/* Dynamic state (V, c, refractory counters, delay ring, time, counters) as an
+ * opaque host blob; the synapse table is not included (it is a pure function
+ * of the description).  With host_buf == NULL, *n = bytes needed.  snn_restore
+ * takes a blob of the same network description.  Both synchronise `stream`. */
+SNN_API snn_status snn_snapshot(snn_net* net, void* host_buf, size_t cap, size_t* n, void* stream);
+SNN_API snn_status snn_restore(snn_net* net, const void* host_buf, size_t n, void* stream);
+
+/* Copies of device data for inspection (all synchronise `stream`; any
+ * pointer may be NULL to skip that array):
+ *   snn_get_table:  synapse table, row i of neuron i holds entries
+ *                   [i*K, (i+1)*K) (padding removed); weights as float.
+ *   snn_get_cdf:    per source module m, entries [m*max_offsets, ...):
+ *                   thresholds (uint32; target j = #{thresholds <= u}) and
+ *                   target modules, plus counts[m]; *max_offsets set.
+ *   snn_get_state:  V, c (float), ref (uint8) of N neurons; ring as D rows of
+ *                   N int32 (row r = inputs of steps t with t % D == r); *t.
+ *   snn_set_state:  overwrites V, c, ref (NULL keeps the current values). */
+SNN_API snn_status snn_get_table(snn_net* net, uint32_t* tgt, float* w, uint8_t* d, void* stream);
+/* Rows [first, first + count) of the synapse table, laid out as snn_get_table
+ * lays out the whole table.  Errors: SNN_EINVAL if the rows are out of range. */
+SNN_API snn_status snn_get_rows(snn_net* net, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
+                                uint8_t* d, void* stream);
+SNN_API snn_status snn_get_cdf(snn_net* net, uint32_t* thresh, uint32_t* tgt_module, uint32_t* counts,
+                       uint32_t* max_offsets, void* stream);
+SNN_API snn_status snn_get_state(snn_net* net, float* V, float* c, uint8_t* ref, int32_t* ring,
+                         uint32_t* t, void* stream);
+SNN_API snn_status snn_set_state(snn_net* net, const float* V, const float* c, const uint8_t* ref,
+                         void* stream);
+
+/* Sizes of the network: N neurons, K, D ring rows, bytes of device memory. */
+SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t* D, uint64_t* device_bytes);
+
+/* Delivery schedule.  schedule 0: one warp per (spike, 128-synapse chunk),
+ * 16-byte vector loads; 1: one thread per synapse over the flattened
+ * (spike, synapse) range.  block: threads per block (multiple of 32, <= 1024),
+ * 0 = default.  Errors: SNN_EINVAL. */
+SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
+
+/* Kernel timing: when enabled, every delivery launch is bracketed by CUDA
+ * events on the launching stream; snn_kernel_time returns the summed device
+ * time (ms) and the number of delivery launches timed, and the same for the
+ * neuron kernel.  Synchronises the stream of the last launch. */
+SNN_API snn_status snn_set_timing(snn_net* net, int32_t enable);
+SNN_API snn_status snn_kernel_time(snn_net* net, double* deliver_ms, uint64_t* deliver_launches,
+                           double* neuron_ms, uint64_t* neuron_launches);
+
+/* Number of this library's kernel launches issued so far (all networks). */
+SNN_API uint64_t snn_launch_count(void);
+
+SNN_API void snn_destroy(snn_net* net);
+SNN_API const char* snn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -134,6 +134,12 @@ def lib():
         L.or_get_state_f64.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2
         L.or_set_state.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 3
         L.or_get_stats.argtypes = [ctypes.c_void_p, u64p, u64p, u64p]
+        L.or_gen_rows.argtypes = [P(OrParams), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+        L.or_initial_V.argtypes = [P(OrParams), ctypes.c_uint32]
+        L.or_initial_V.restype = ctypes.c_float
+        L.or_drive.argtypes = [P(OrParams), P(OrConsts), ctypes.c_uint32, ctypes.c_uint32, u32p,
+                               P(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -195,6 +201,33 @@ def lif_update(cfg: dict, V: float, c: float, ref: int, exc: bool, I_fx: int, fo
     s = lib().or_lif_update(ctypes.byref(k), ctypes.byref(p), ctypes.byref(v), ctypes.byref(cf),
                             ctypes.byref(r), int(bool(exc)), int(I_fx), int(bool(forced)))
     return v.value, cf.value, r.value, bool(s)
+
+
+def gen_rows(cfg: dict, first: int, count: int):
+    """Synapse rows [first, first + count) without building the whole network."""
+    p = params(cfg)
+    K = int(cfg["K"])
+    tgt = np.empty(count * K, np.uint32)
+    w = np.empty(count * K, np.float32)
+    d = np.empty(count * K, np.uint8)
+    if lib().or_gen_rows(ctypes.byref(p), first, count, _ptr(tgt), _ptr(w), _ptr(d)):
+        raise ValueError(lib().or_error().decode())
+    return tgt, w, d
+
+
+def initial_V(cfg: dict, i: int) -> float:
+    return float(lib().or_initial_V(ctypes.byref(params(cfg)), i))
+
+
+def drive(cfg: dict, i: int, t: int):
+    """(external count, forced flag) of neuron i at step t."""
+    p = params(cfg)
+    k = OrConsts()
+    lib().or_constants(ctypes.byref(p), ctypes.byref(k))
+    n = ctypes.c_uint32()
+    f = ctypes.c_int()
+    lib().or_drive(ctypes.byref(p), ctypes.byref(k), i, t, ctypes.byref(n), ctypes.byref(f))
+    return int(n.value), bool(f.value)
 
 
 def poisson_count(cfg: dict, u0: int) -> int:

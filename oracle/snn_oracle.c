@@ -349,20 +349,24 @@ void or_destroy(or_net* n) {
 
 /* Synapse generation (Sec. II-B): synapse k of neuron i draws one Philox
  * block (i, k, GEN); u0 picks the target module by inverse CDF, u1 the neuron
- * inside it, u2 the weight and u3 the delay. */
-static int generate(or_net* n) {
-    const or_params* p = &n->p;
-    uint32_t cap = n->c.max_offsets;
-    uint32_t nm = n->c.n_modules;
+ * inside it, u2 the weight and u3 the delay.  Rows [first, first + count) are
+ * written from offset 0 of the output arrays; w (float) or w64 (double) is
+ * filled, whichever is non-NULL. */
+static int gen_rows(const or_params* p, const or_consts* c, uint32_t first, uint32_t count,
+                    uint32_t* tgt, float* w, double* w64, uint8_t* d) {
+    uint32_t cap = c->max_offsets;
+    uint32_t nm = c->n_modules;
+    uint32_t M = p->neurons_per_module;
     uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
     uint32_t* TM = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
-    uint32_t* cnt = (uint32_t*)malloc(sizeof(uint32_t) * nm);
+    uint32_t* cnt = (uint32_t*)calloc(nm, sizeof(uint32_t));
     if (!T || !TM || !cnt) {
         free(T); free(TM); free(cnt);
         set_err("out of memory");
         return -1;
     }
-    for (uint32_t m = 0; m < nm; ++m) {
+    uint32_t m0 = first / M, m1 = count ? (first + count - 1) / M : m0;
+    for (uint32_t m = m0; m <= m1 && m < nm; ++m) {
         if (or_cdf_table(p, m, T + (size_t)m * cap, TM + (size_t)m * cap, NULL, cap, &cnt[m])) {
             free(T); free(TM); free(cnt);
             return -1;
@@ -370,42 +374,71 @@ static int generate(or_net* n) {
     }
     float span = p->w_exc_hi - p->w_exc_lo;
     uint32_t dspan = p->d_exc_hi - p->d_exc_lo + 1u;
-    for (uint32_t i = 0; i < n->N; ++i) {
-        uint32_t s = i / n->M;
+    for (uint32_t r = 0; r < count; ++r) {
+        uint32_t i = first + r;
+        uint32_t s = i / M;
         const uint32_t* Ts = T + (size_t)s * cap;
         const uint32_t* TMs = TM + (size_t)s * cap;
         uint32_t ns = cnt[s];
-        int exc = is_exc(n, i);
-        for (uint32_t k = 0; k < n->K; ++k) {
+        int exc = (i % M) < c->n_exc;
+        for (uint32_t k = 0; k < p->K; ++k) {
             uint32_t u[4];
             draw(p, i, k, OR_TAG_GEN, u);
             uint32_t j = 0;
             while (j + 1 < ns && Ts[j] <= u[0]) ++j; /* first entry with u0 < T */
             uint32_t tmod = TMs[j];
-            uint32_t tgt = tmod * n->M + (uint32_t)(((uint64_t)u[1] * n->M) >> 32);
-            size_t e = (size_t)i * n->K + k;
-            n->tgt[e] = tgt;
+            size_t e = (size_t)r * p->K + k;
+            tgt[e] = tmod * M + (uint32_t)(((uint64_t)u[1] * M) >> 32);
             if (exc) {
-                n->d[e] = (uint8_t)(p->d_exc_lo + (uint32_t)(((uint64_t)u[3] * dspan) >> 32));
-                if (n->fp64) {
+                d[e] = (uint8_t)(p->d_exc_lo + (uint32_t)(((uint64_t)u[3] * dspan) >> 32));
+                if (w64) {
                     double lo = (double)p->w_exc_lo, hi = (double)p->w_exc_hi;
-                    n->w64[e] = lo + (hi - lo) * unit24d(u[2]);
+                    w64[e] = lo + (hi - lo) * unit24d(u[2]);
                 } else {
                     float x = span * unit24(u[2]);
-                    n->w[e] = p->w_exc_lo + x;
+                    w[e] = p->w_exc_lo + x;
                 }
             } else {
-                n->d[e] = (uint8_t)p->d_inh;
-                if (n->fp64)
-                    n->w64[e] = (double)p->w_inh;
+                d[e] = (uint8_t)p->d_inh;
+                if (w64)
+                    w64[e] = (double)p->w_inh;
                 else
-                    n->w[e] = p->w_inh;
+                    w[e] = p->w_inh;
             }
-            if (!n->fp64 && p->weight_bf16) n->w[e] = or_bf16_to_float(or_bf16_bits(n->w[e]));
+            if (!w64 && p->weight_bf16) w[e] = or_bf16_to_float(or_bf16_bits(w[e]));
         }
     }
     free(T); free(TM); free(cnt);
     return 0;
+}
+
+static int generate(or_net* n) {
+    return gen_rows(&n->p, &n->c, 0, n->N, n->tgt, n->w, n->w64, n->d);
+}
+
+int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
+                uint8_t* d) {
+    or_consts c;
+    if (or_constants(p, &c)) return -1;
+    if ((uint64_t)first + count > c.N) {
+        set_err("rows out of range");
+        return -1;
+    }
+    return gen_rows(p, &c, first, count, tgt, w, NULL, d);
+}
+
+float or_initial_V(const or_params* p, uint32_t i) {
+    uint32_t u[4];
+    draw(p, i, 0u, OR_TAG_INIT, u);
+    return p->V_th * unit24(u[0]);
+}
+
+void or_drive(const or_params* p, const or_consts* c, uint32_t i, uint32_t t, uint32_t* n_ext,
+              int* forced) {
+    uint32_t u[4];
+    draw(p, i, t, OR_TAG_DRIVE, u);
+    *n_ext = or_poisson_count(c, u[0]);
+    *forced = (uint64_t)u[1] < c->imposed_thresh;
 }
 
 or_net* or_create(const or_params* p, int fp64) {
@@ -453,12 +486,13 @@ or_net* or_create(const or_params* p, int fp64) {
     }
     /* initial state (the paper is silent): V0 = V_th * U[0,1), c = 0, ring = 0 */
     for (uint32_t i = 0; i < n->N; ++i) {
-        uint32_t u[4];
-        draw(p, i, 0u, OR_TAG_INIT, u);
-        if (n->fp64)
+        if (n->fp64) {
+            uint32_t u[4];
+            draw(p, i, 0u, OR_TAG_INIT, u);
             n->V64[i] = (double)p->V_th * unit24d(u[0]);
-        else
-            n->V[i] = p->V_th * unit24(u[0]);
+        } else {
+            n->V[i] = or_initial_V(p, i);
+        }
     }
     double dt = (double)p->dt, tm = (double)p->tau_m, tc = (double)p->tau_c;
     n->a_m64 = exp(-dt / tm);
@@ -527,10 +561,9 @@ static int step_once(or_net* n) {
     uint32_t nspk = 0;
     /* flow steps 4-6: inject the inputs queued for this step and integrate */
     for (uint32_t i = 0; i < n->N; ++i) {
-        uint32_t u[4];
-        draw(p, i, t, OR_TAG_DRIVE, u);
-        uint32_t next = or_poisson_count(c, u[0]);
-        int forced = (uint64_t)u[1] < c->imposed_thresh;
+        uint32_t next;
+        int forced;
+        or_drive(p, c, i, t, &next, &forced);
         int exc = is_exc(n, i);
         int spike;
         n->ext += next;

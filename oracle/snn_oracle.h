@@ -82,6 +82,17 @@ int or_lif_update(const or_consts* c, const or_params* p, float* V, float* cf,
                   uint8_t* ref, int exc, int32_t I_fx, int forced);
 uint32_t or_poisson_count(const or_consts* c, uint32_t u0);
 
+/* Synapse rows [first, first + count) of the network described by p, without
+ * building the rest of it (row i holds entries [i*K, (i+1)*K) of the output,
+ * counted from `first`).  For sampled checks of networks too large to build. */
+int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
+                uint8_t* d);
+/* Initial membrane potential of neuron i, and its external count / forced
+ * flag at step t. */
+float or_initial_V(const or_params* p, uint32_t i);
+void or_drive(const or_params* p, const or_consts* c, uint32_t i, uint32_t t, uint32_t* n_ext,
+              int* forced);
+
 /* fp64 != 0 builds the double-precision variant (double state, double
  * weights, no fixed point) used as the precision reference. */
 or_net* or_create(const or_params* p, int fp64);

@@ -1,0 +1,681 @@
+// snn_api.cu -- host runtime and C ABI of libsnn.so (declared in include/snn.h).
+//
+// The host side validates the network description, derives the constants of
+// the method once in FP64 (membrane and fatigue decay factors of Eq. 1-2, the
+// Poisson table of the external synapses, fixed-point scales), obtains device
+// memory from the caller's allocator, and enqueues the kernels.  Nothing of
+// the simulation itself runs on the host.
+#include "snn.h"
+#include "snn_internal.h"
+
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace snn;
+
+namespace {
+
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+
+snn_status fail(snn_status s, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+snn_status fail(snn_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(SNN_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                        __LINE__);                                                           \
+    } while (0)
+
+constexpr int TIMING_SLOTS = 256;
+
+struct EventRing {
+    cudaEvent_t a[TIMING_SLOTS] = {};
+    cudaEvent_t b[TIMING_SLOTS] = {};
+    bool pending[TIMING_SLOTS] = {};
+    uint64_t next = 0;
+    double total_ms = 0.0;
+    uint64_t count = 0;
+};
+
+}  // namespace
+
+namespace snn {
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace snn
+
+struct snn_net {
+    snn_config cfg;
+    snn_alloc_fn alloc_fn = nullptr;
+    snn_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<void*> blocks;
+    uint64_t device_bytes = 0;
+    int device = 0;
+
+    uint32_t N = 0, Npad = 0, M = 0, K = 0, Kpad = 0, n_modules = 0, n_exc = 0, D = 0;
+    uint32_t max_off = 0, nb = 0;
+    NetView v{};
+    uint32_t* cdf_T = nullptr;
+    uint32_t* cdf_mod = nullptr;
+    uint32_t* cdf_n = nullptr;
+
+    int schedule = 0;
+    int block = 256;
+    int grid = 0;
+    bool timing = false;
+    EventRing ev_deliver, ev_neuron;
+};
+
+namespace {
+
+void* dev_alloc(snn_net* n, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (n->alloc_fn) {
+        p = n->alloc_fn(bytes, n->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        n->blocks.push_back(p);
+        n->device_bytes += bytes;
+    }
+    return p;
+}
+
+void release_all(snn_net* n) {
+    for (void* p : n->blocks) {
+        if (n->free_fn)
+            n->free_fn(p, n->alloc_ctx);
+        else if (!n->alloc_fn)
+            cudaFree(p);
+    }
+    n->blocks.clear();
+}
+
+void destroy_events(EventRing& r) {
+    for (int i = 0; i < TIMING_SLOTS; ++i) {
+        if (r.a[i]) cudaEventDestroy(r.a[i]);
+        if (r.b[i]) cudaEventDestroy(r.b[i]);
+        r.a[i] = r.b[i] = nullptr;
+    }
+}
+
+snn_status validate(const snn_config* c) {
+    if (!c) return fail(SNN_EINVAL, "config is NULL");
+    if (c->grid_w == 0 || c->grid_h == 0 || c->neurons_per_module == 0)
+        return fail(SNN_EINVAL, "grid_w, grid_h and neurons_per_module must be positive");
+    const uint64_t N = (uint64_t)c->grid_w * c->grid_h * c->neurons_per_module;
+    if (N > (uint64_t)MAX_NEURON_BLOCKS * NEURONS_PER_BLOCK)
+        return fail(SNN_EINVAL, "too many neurons (%llu > %u)", (unsigned long long)N,
+                    MAX_NEURON_BLOCKS * NEURONS_PER_BLOCK);
+    if (c->K > 16384) return fail(SNN_EINVAL, "K must be <= 16384");
+    if (!(c->exc_fraction >= 0.0f && c->exc_fraction <= 1.0f))
+        return fail(SNN_EINVAL, "exc_fraction must be in [0, 1]");
+    if (!(c->spacing_um > 0.0f)) return fail(SNN_EINVAL, "spacing_um must be positive");
+    if (c->kernel != SNN_KERNEL_GAUSS && c->kernel != SNN_KERNEL_EXP)
+        return fail(SNN_EINVAL, "kernel must be SNN_KERNEL_GAUSS or SNN_KERNEL_EXP");
+    if (c->kernel == SNN_KERNEL_GAUSS && !(c->sigma_um > 0.0))
+        return fail(SNN_EINVAL, "sigma_um must be positive");
+    if (c->kernel == SNN_KERNEL_EXP && !(c->lambda_um > 0.0))
+        return fail(SNN_EINVAL, "lambda_um must be positive");
+    if (!(c->cutoff_um >= 0.0) || c->cutoff_um / c->spacing_um > 512.0)
+        return fail(SNN_EINVAL, "cutoff_um must be in [0, 512 * spacing_um]");
+    if (c->d_exc_lo < 1 || c->d_exc_hi < c->d_exc_lo || c->d_exc_hi > 255 || c->d_inh < 1 ||
+        c->d_inh > 255)
+        return fail(SNN_EINVAL, "delays must satisfy 1 <= d_exc_lo <= d_exc_hi <= 255, 1 <= d_inh <= 255");
+    if (!(c->tau_m_ms > 0.0f) || !(c->tau_c_ms > 0.0f) || !(c->dt_ms > 0.0f))
+        return fail(SNN_EINVAL, "tau_m_ms, tau_c_ms and dt_ms must be positive");
+    if (!(c->t_ref_ms >= 0.0f) || std::lround((double)c->t_ref_ms / c->dt_ms) > 255)
+        return fail(SNN_EINVAL, "t_ref_ms must be in [0, 255 dt]");
+    if (!(c->ext_rate_hz >= 0.0f)) return fail(SNN_EINVAL, "ext_rate_hz must be >= 0");
+    if (!(c->imposed_rate_hz >= 0.0f)) return fail(SNN_EINVAL, "imposed_rate_hz must be >= 0");
+    if (c->weight_dtype != SNN_WEIGHT_F32 && c->weight_dtype != SNN_WEIGHT_BF16)
+        return fail(SNN_EINVAL, "weight_dtype must be SNN_WEIGHT_F32 or SNN_WEIGHT_BF16");
+    if (c->fx_shift < 8 || c->fx_shift > 24) return fail(SNN_EINVAL, "fx_shift must be in [8, 24]");
+    if (!std::isfinite(c->w_exc_lo) || !std::isfinite(c->w_exc_hi) || !std::isfinite(c->w_inh) ||
+        !std::isfinite(c->V_th_mV) || !std::isfinite(c->V_reset_mV) || !std::isfinite(c->E_mV) ||
+        !std::isfinite(c->J_ext_mV) || !std::isfinite(c->g_c_mV) || !std::isfinite(c->alpha_c))
+        return fail(SNN_EINVAL, "non-finite parameter");
+    const float wmax = std::fmax(std::fabs(c->w_exc_lo), std::fmax(std::fabs(c->w_exc_hi), std::fabs(c->w_inh)));
+    if (std::ldexp((double)wmax, (int)c->fx_shift) > 1.0e9 ||
+        std::ldexp((double)std::fabs(c->J_ext_mV), (int)c->fx_shift) > 1.0e8)
+        return fail(SNN_EINVAL, "weights too large for the fixed-point scale");
+    return SNN_OK;
+}
+
+// Host-side constants of the method (FP64, rounded once to float).
+snn_status derive(snn_net* n) {
+    const snn_config& c = n->cfg;
+    n->M = c.neurons_per_module;
+    n->N = c.grid_w * c.grid_h * c.neurons_per_module;
+    n->nb = (n->N + NEURONS_PER_BLOCK - 1) / NEURONS_PER_BLOCK;
+    if (n->nb == 0) n->nb = 1;
+    n->Npad = n->nb * NEURONS_PER_BLOCK;
+    n->K = c.K;
+    n->Kpad = (c.K + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+    n->n_modules = c.grid_w * c.grid_h;
+    double ne = std::floor((double)c.exc_fraction * (double)c.neurons_per_module + 0.5);
+    if (ne > (double)c.neurons_per_module) ne = (double)c.neurons_per_module;
+    n->n_exc = (uint32_t)ne;
+    n->D = (c.d_exc_hi > c.d_inh ? c.d_exc_hi : c.d_inh) + 1u;
+
+    NetView& v = n->v;
+    v.N = n->N;
+    v.Npad = n->Npad;
+    v.M = n->M;
+    v.K = n->K;
+    v.Kpad = n->Kpad;
+    v.n_exc = n->n_exc;
+    v.D = n->D;
+    v.nb = n->nb;
+    v.key0 = (uint32_t)c.seed;
+    v.key1 = (uint32_t)(c.seed >> 32);
+    v.ref_steps = (uint32_t)std::lround((double)c.t_ref_ms / (double)c.dt_ms);
+
+    const double dt = c.dt_ms, tau_m = c.tau_m_ms, tau_c = c.tau_c_ms;
+    const double decay_m = std::exp(-dt / tau_m);
+    const double decay_c = std::exp(-dt / tau_c);
+    // Eq. 1 driven by c(s) = c0 exp(-s/tau_c): the adaptation term integrated
+    // over one step contributes -k_c c0, k_c = g_c int_0^dt exp(-(dt-s)/tau_m) exp(-s/tau_c) ds.
+    const double kc = (tau_c == tau_m) ? (double)c.g_c_mV * dt * decay_m
+                                       : (double)c.g_c_mV * (tau_m * tau_c / (tau_c - tau_m)) * (decay_c - decay_m);
+    v.a_m = (float)decay_m;
+    v.a_c = (float)decay_c;
+    v.kc = (float)kc;
+    v.E = c.E_mV;
+    v.V_th = c.V_th_mV;
+    v.V_reset = c.V_reset_mV;
+    v.alpha_c = c.alpha_c;
+    v.w_scale = std::ldexp(1.0f, (int)c.fx_shift);
+    v.in_scale = std::ldexp(1.0f, -(int)c.fx_shift);
+    v.J_ext_fx = (int32_t)std::lrintf(c.J_ext_mV * v.w_scale);
+    v.w_bf16 = c.weight_dtype == SNN_WEIGHT_BF16 ? 1 : 0;
+
+    // External Poisson synapses: P[k] = floor(F(k) 2^32), F the Poisson CDF of
+    // mean rate * dt; the count of a step is #{k : P[k] <= u} for a uniform
+    // 32-bit u.  The table stops before the first entry that reaches 2^32 - 1.
+    const double mean = (double)c.ext_rate_hz * dt / 1000.0;
+    v.pois_len = 0;
+    if (mean > 0.0) {
+        double pmf = std::exp(-mean), F = 0.0;
+        for (uint32_t k = 0;; ++k) {
+            F = F + pmf;
+            const double x = std::floor(F * 4294967296.0);
+            if (x >= 4294967295.0) break;
+            if (k >= (uint32_t)MAX_POIS) return fail(SNN_EINVAL, "ext_rate_hz * dt too large for the Poisson table");
+            v.pois[v.pois_len++] = (uint64_t)x;
+            pmf = pmf * mean / (double)(k + 1);
+        }
+    }
+    double pf = (double)c.imposed_rate_hz * dt / 1000.0;
+    if (pf > 1.0) pf = 1.0;
+    v.imposed_thresh = (uint64_t)std::floor(pf * 4294967296.0);
+    v.raster_cap = c.raster_capacity;
+    return SNN_OK;
+}
+
+// In-disc grid offsets (dx, dy) with dx^2 + dy^2 <= R2, in (dy, dx) raster order.
+std::vector<int16_t> disc_offsets(const snn_config& c, uint32_t* R2_out) {
+    const double q = c.cutoff_um / (double)c.spacing_um;
+    const uint32_t R2 = (uint32_t)std::floor(q * q + 1e-9);
+    int R = 0;
+    while ((uint32_t)((R + 1) * (R + 1)) <= R2) ++R;
+    std::vector<int16_t> off;
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx)
+            if ((uint32_t)(dx * dx + dy * dy) <= R2) {
+                off.push_back((int16_t)dx);
+                off.push_back((int16_t)dy);
+            }
+    *R2_out = R2;
+    return off;
+}
+
+snn_status build_impl(snn_net* n, cudaStream_t s) {
+    const snn_config& c = n->cfg;
+    snn_status st = derive(n);
+    if (st != SNN_OK) return st;
+    uint32_t R2 = 0;
+    std::vector<int16_t> off = disc_offsets(c, &R2);
+    n->max_off = (uint32_t)(off.size() / 2);
+
+    NetView& v = n->v;
+    const size_t nsyn = (size_t)n->N * n->Kpad;
+    const size_t wbytes = v.w_bf16 ? 2 : 4;
+    struct Req {
+        void** p;
+        size_t bytes;
+    } reqs[] = {
+        {(void**)&v.tgt, nsyn * 4},
+        {(void**)&v.w, nsyn * wbytes},
+        {(void**)&v.d, nsyn},
+        {(void**)&v.V, (size_t)n->Npad * 4},
+        {(void**)&v.c, (size_t)n->Npad * 4},
+        {(void**)&v.ref, (size_t)n->Npad},
+        {(void**)&v.ring, (size_t)n->D * n->Npad * 4},
+        {(void**)&v.seg, (size_t)n->Npad * 4},
+        {(void**)&v.blk_cnt, (size_t)n->nb * 4},
+        {(void**)&v.blk_off, (size_t)(n->nb + 1) * 4},
+        {(void**)&v.blk_ext, (size_t)n->nb * 8},
+        {(void**)&v.raster_t, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
+        {(void**)&v.raster_id, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
+        {(void**)&v.st, sizeof(DevState)},
+        {(void**)&n->cdf_T, (size_t)n->n_modules * n->max_off * 4},
+        {(void**)&n->cdf_mod, (size_t)n->n_modules * n->max_off * 4},
+        {(void**)&n->cdf_n, (size_t)n->n_modules * 4},
+    };
+    for (auto& r : reqs) {
+        *r.p = dev_alloc(n, r.bytes);
+        if (!*r.p) return fail(SNN_ENOMEM, "device allocation of %zu bytes failed", r.bytes);
+    }
+    // construction-only buffers (released at the end of the build)
+    const size_t scratch_bytes = (size_t)n->n_modules * n->max_off * sizeof(double);
+    const size_t off_bytes = off.size() * sizeof(int16_t);
+    void* scratch = dev_alloc(n, scratch_bytes);
+    void* doff = dev_alloc(n, off_bytes);
+    if (!scratch || !doff) return fail(SNN_ENOMEM, "device allocation of construction scratch failed");
+
+    CUDA_TRY(cudaMemcpyAsync(doff, off.data(), off_bytes, cudaMemcpyHostToDevice, s));
+
+    BuildView b{};
+    b.grid_w = c.grid_w;
+    b.grid_h = c.grid_h;
+    b.n_modules = n->n_modules;
+    b.max_off = n->max_off;
+    b.M = n->M;
+    b.N = n->N;
+    b.Npad = n->Npad;
+    b.K = n->K;
+    b.Kpad = n->Kpad;
+    b.n_exc = n->n_exc;
+    b.d_lo = c.d_exc_lo;
+    b.d_span = c.d_exc_hi - c.d_exc_lo + 1u;
+    b.d_inh = c.d_inh;
+    b.key0 = v.key0;
+    b.key1 = v.key1;
+    b.kernel = c.kernel;
+    b.spacing = (double)c.spacing_um;
+    b.sigma = c.sigma_um;
+    b.lambda = c.lambda_um;
+    b.w_lo = c.w_exc_lo;
+    b.w_span = c.w_exc_hi - c.w_exc_lo;
+    b.w_inh = c.w_inh;
+    b.V_th = c.V_th_mV;
+    b.w_bf16 = v.w_bf16;
+    b.offsets = (const int16_t*)doff;
+    b.scratch = (double*)scratch;
+    b.cdf_T = n->cdf_T;
+    b.cdf_mod = n->cdf_mod;
+    b.cdf_n = n->cdf_n;
+
+    CUDA_TRY(launch_build_cdf(b, s));
+    CUDA_TRY(launch_gen_synapses(b, v.tgt, v.w, v.d, s));
+    CUDA_TRY(launch_init_state(b, v.V, v.c, v.ref, s));
+    CUDA_TRY(cudaMemsetAsync(v.ring, 0, (size_t)n->D * n->Npad * 4, s));
+    CUDA_TRY(cudaMemsetAsync(v.seg, 0, (size_t)n->Npad * 4, s));
+    CUDA_TRY(cudaMemsetAsync(v.st, 0, sizeof(DevState), s));
+    CUDA_TRY(cudaMemsetAsync(v.blk_off, 0, (size_t)(n->nb + 1) * 4, s));
+    CUDA_TRY(prepare_deliver(n->nb));
+    // the scratch and offset list must outlive the kernels that read them
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (void* p : {scratch, doff}) {
+        for (size_t i = 0; i < n->blocks.size(); ++i)
+            if (n->blocks[i] == p) {
+                if (n->free_fn)
+                    n->free_fn(p, n->alloc_ctx);
+                else if (!n->alloc_fn)
+                    cudaFree(p);
+                n->blocks.erase(n->blocks.begin() + i);
+                break;
+            }
+    }
+    n->device_bytes -= ((scratch_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);
+    n->grid = deliver_default_grid(n->schedule, n->block, n->nb, v.w_bf16 != 0);
+    return SNN_OK;
+}
+
+snn_status timed_begin(EventRing& r, cudaStream_t s, int* slot) {
+    const int k = (int)(r.next % TIMING_SLOTS);
+    if (!r.a[k]) {
+        CUDA_TRY(cudaEventCreate(&r.a[k]));
+        CUDA_TRY(cudaEventCreate(&r.b[k]));
+    }
+    if (r.pending[k]) {
+        CUDA_TRY(cudaEventSynchronize(r.b[k]));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a[k], r.b[k]));
+        r.total_ms += ms;
+        r.count += 1;
+        r.pending[k] = false;
+    }
+    CUDA_TRY(cudaEventRecord(r.a[k], s));
+    *slot = k;
+    return SNN_OK;
+}
+
+snn_status timed_end(EventRing& r, cudaStream_t s, int k) {
+    CUDA_TRY(cudaEventRecord(r.b[k], s));
+    r.pending[k] = true;
+    r.next += 1;
+    return SNN_OK;
+}
+
+snn_status drain(EventRing& r) {
+    for (int k = 0; k < TIMING_SLOTS; ++k) {
+        if (!r.pending[k]) continue;
+        CUDA_TRY(cudaEventSynchronize(r.b[k]));
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, r.a[k], r.b[k]));
+        r.total_ms += ms;
+        r.count += 1;
+        r.pending[k] = false;
+    }
+    return SNN_OK;
+}
+
+struct SnapshotHeader {
+    uint64_t magic;
+    uint32_t version, N, Npad, D;
+    uint64_t seed;
+    uint32_t K, pad;
+};
+constexpr uint64_t SNAP_MAGIC = 0x31504E5350534E53ull;  // "SNSPSNP1"
+
+}  // namespace
+
+extern "C" {
+
+const char* snn_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t snn_launch_count(void) { return g_launches.load(); }
+
+snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
+                             void* alloc_ctx, void* stream, snn_net** out) {
+    if (!out) return fail(SNN_EINVAL, "out is NULL");
+    *out = nullptr;
+    snn_status st = validate(cfg);
+    if (st != SNN_OK) return st;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+    snn_net* n = new (std::nothrow) snn_net();
+    if (!n) return fail(SNN_ENOMEM, "host allocation failed");
+    n->cfg = *cfg;
+    n->alloc_fn = alloc_fn;
+    n->free_fn = free_fn;
+    n->alloc_ctx = alloc_ctx;
+    cudaGetDevice(&n->device);
+    st = build_impl(n, (cudaStream_t)stream);
+    if (st != SNN_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        release_all(n);
+        delete n;
+        return st;
+    }
+    *out = n;
+    return SNN_OK;
+}
+
+snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (uint32_t k = 0; k < n_steps; ++k) {
+        int slot = 0;
+        if (n->timing) {
+            snn_status st = timed_begin(n->ev_neuron, s, &slot);
+            if (st != SNN_OK) return st;
+        }
+        CUDA_TRY(launch_neuron_step(n->v, s));
+        if (n->timing) {
+            snn_status st = timed_end(n->ev_neuron, s, slot);
+            if (st == SNN_OK) st = timed_begin(n->ev_deliver, s, &slot);
+            if (st != SNN_OK) return st;
+        }
+        CUDA_TRY(launch_deliver(n->v, n->schedule, n->block, n->grid, s));
+        if (n->timing) {
+            snn_status st = timed_end(n->ev_deliver, s, slot);
+            if (st != SNN_OK) return st;
+        }
+    }
+    return SNN_OK;
+}
+
+snn_status snn_read_spikes(snn_net* n, uint32_t* steps, uint32_t* ids, size_t cap, size_t* n_out,
+                           void* stream) {
+    if (!n || !n_out) return fail(SNN_EINVAL, "net or n_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevState ds;
+    CUDA_TRY(cudaMemcpyAsync(&ds, n->v.st, sizeof ds, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    uint64_t avail = ds.raster_count < n->v.raster_cap ? ds.raster_count : n->v.raster_cap;
+    const size_t m = (size_t)(avail < cap ? avail : cap);
+    if (m && steps) CUDA_TRY(cudaMemcpyAsync(steps, n->v.raster_t, m * 4, cudaMemcpyDeviceToHost, s));
+    if (m && ids) CUDA_TRY(cudaMemcpyAsync(ids, n->v.raster_id, m * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *n_out = m;
+    if (ds.raster_count > n->v.raster_cap)
+        return fail(SNN_EOVERFLOW, "raster overflow: %llu spikes recorded, capacity %llu",
+                    (unsigned long long)ds.raster_count, (unsigned long long)n->v.raster_cap);
+    return SNN_OK;
+}
+
+snn_status snn_clear_raster(snn_net* n, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    CUDA_TRY(cudaMemsetAsync(&n->v.st->raster_count, 0, sizeof(uint64_t), (cudaStream_t)stream));
+    return SNN_OK;
+}
+
+snn_status snn_get_stats(snn_net* n, snn_stats* out, void* stream) {
+    if (!n || !out) return fail(SNN_EINVAL, "net or out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevState ds;
+    CUDA_TRY(cudaMemcpyAsync(&ds, n->v.st, sizeof ds, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    out->steps = ds.t;
+    out->n_spikes = ds.n_spikes;
+    out->rec_events = ds.rec_events;
+    out->ext_events = ds.ext_events;
+    out->raster_count = ds.raster_count;
+    out->raster_capacity = n->v.raster_cap;
+    return SNN_OK;
+}
+
+snn_status snn_get_dims(snn_net* n, uint32_t* N, uint32_t* K, uint32_t* D, uint64_t* bytes) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (N) *N = n->N;
+    if (K) *K = n->K;
+    if (D) *D = n->D;
+    if (bytes) *bytes = n->device_bytes;
+    return SNN_OK;
+}
+
+snn_status snn_get_rows(snn_net* n, uint32_t first, uint32_t count, uint32_t* tgt, float* w, uint8_t* d,
+                        void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if ((uint64_t)first + count > n->N) return fail(SNN_EINVAL, "rows [%u, %u) out of range", first, first + count);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t rows = count, K = n->K, Kp = n->Kpad;
+    const size_t e0 = (size_t)first * Kp;
+    if (tgt && K && rows)
+        CUDA_TRY(cudaMemcpy2DAsync(tgt, K * 4, n->v.tgt + e0, Kp * 4, K * 4, rows, cudaMemcpyDeviceToHost, s));
+    if (d && K && rows) CUDA_TRY(cudaMemcpy2DAsync(d, K, n->v.d + e0, Kp, K, rows, cudaMemcpyDeviceToHost, s));
+    if (w && K && rows) {
+        if (n->v.w_bf16) {
+            std::vector<uint16_t> tmp(rows * K);
+            CUDA_TRY(cudaMemcpy2DAsync(tmp.data(), K * 2, (const uint16_t*)n->v.w + e0, Kp * 2, K * 2, rows,
+                                       cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            for (size_t e = 0; e < tmp.size(); ++e) {
+                uint32_t bits = (uint32_t)tmp[e] << 16;
+                std::memcpy(&w[e], &bits, 4);
+            }
+        } else {
+            CUDA_TRY(cudaMemcpy2DAsync(w, K * 4, (const float*)n->v.w + e0, Kp * 4, K * 4, rows,
+                                       cudaMemcpyDeviceToHost, s));
+        }
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_get_table(snn_net* n, uint32_t* tgt, float* w, uint8_t* d, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    return snn_get_rows(n, 0, n->N, tgt, w, d, stream);
+}
+
+snn_status snn_get_cdf(snn_net* n, uint32_t* thresh, uint32_t* tgt_module, uint32_t* counts,
+                       uint32_t* max_offsets, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t tot = (size_t)n->n_modules * n->max_off;
+    if (max_offsets) *max_offsets = n->max_off;
+    if (thresh) CUDA_TRY(cudaMemcpyAsync(thresh, n->cdf_T, tot * 4, cudaMemcpyDeviceToHost, s));
+    if (tgt_module) CUDA_TRY(cudaMemcpyAsync(tgt_module, n->cdf_mod, tot * 4, cudaMemcpyDeviceToHost, s));
+    if (counts) CUDA_TRY(cudaMemcpyAsync(counts, n->cdf_n, (size_t)n->n_modules * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_get_state(snn_net* n, float* V, float* c, uint8_t* ref, int32_t* ring, uint32_t* t,
+                         void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = n->N;
+    if (V) CUDA_TRY(cudaMemcpyAsync(V, n->v.V, N * 4, cudaMemcpyDeviceToHost, s));
+    if (c) CUDA_TRY(cudaMemcpyAsync(c, n->v.c, N * 4, cudaMemcpyDeviceToHost, s));
+    if (ref) CUDA_TRY(cudaMemcpyAsync(ref, n->v.ref, N, cudaMemcpyDeviceToHost, s));
+    if (ring && N)
+        CUDA_TRY(cudaMemcpy2DAsync(ring, N * 4, n->v.ring, (size_t)n->Npad * 4, N * 4, n->D,
+                                   cudaMemcpyDeviceToHost, s));
+    DevState ds;
+    CUDA_TRY(cudaMemcpyAsync(&ds, n->v.st, sizeof ds, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (t) *t = ds.t;
+    return SNN_OK;
+}
+
+snn_status snn_set_state(snn_net* n, const float* V, const float* c, const uint8_t* ref, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t N = n->N;
+    if (V) CUDA_TRY(cudaMemcpyAsync(n->v.V, V, N * 4, cudaMemcpyHostToDevice, s));
+    if (c) CUDA_TRY(cudaMemcpyAsync(n->v.c, c, N * 4, cudaMemcpyHostToDevice, s));
+    if (ref) CUDA_TRY(cudaMemcpyAsync(n->v.ref, ref, N, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_snapshot(snn_net* n, void* host_buf, size_t cap, size_t* nbytes, void* stream) {
+    if (!n || !nbytes) return fail(SNN_EINVAL, "net or n is NULL");
+    const size_t N = n->Npad, D = n->D;
+    const size_t need = sizeof(SnapshotHeader) + sizeof(DevState) + N * 4 * 2 + N + D * N * 4;
+    *nbytes = need;
+    if (!host_buf) return SNN_OK;
+    if (cap < need) return fail(SNN_EINVAL, "snapshot buffer too small (%zu < %zu)", cap, need);
+    cudaStream_t s = (cudaStream_t)stream;
+    char* p = (char*)host_buf;
+    SnapshotHeader h{SNAP_MAGIC, 1u, n->N, n->Npad, n->D, n->cfg.seed, n->K, 0u};
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    CUDA_TRY(cudaMemcpyAsync(p, n->v.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    p += sizeof(DevState);
+    CUDA_TRY(cudaMemcpyAsync(p, n->v.V, N * 4, cudaMemcpyDeviceToHost, s));
+    p += N * 4;
+    CUDA_TRY(cudaMemcpyAsync(p, n->v.c, N * 4, cudaMemcpyDeviceToHost, s));
+    p += N * 4;
+    CUDA_TRY(cudaMemcpyAsync(p, n->v.ref, N, cudaMemcpyDeviceToHost, s));
+    p += N;
+    CUDA_TRY(cudaMemcpyAsync(p, n->v.ring, D * N * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_restore(snn_net* n, const void* host_buf, size_t nbytes, void* stream) {
+    if (!n || !host_buf) return fail(SNN_EINVAL, "net or buffer is NULL");
+    const size_t N = n->Npad, D = n->D;
+    const size_t need = sizeof(SnapshotHeader) + sizeof(DevState) + N * 4 * 2 + N + D * N * 4;
+    if (nbytes != need) return fail(SNN_EINVAL, "snapshot size mismatch (%zu != %zu)", nbytes, need);
+    const char* p = (const char*)host_buf;
+    SnapshotHeader h;
+    std::memcpy(&h, p, sizeof h);
+    if (h.magic != SNAP_MAGIC || h.version != 1u || h.N != n->N || h.Npad != n->Npad || h.D != n->D ||
+        h.seed != n->cfg.seed || h.K != n->K)
+        return fail(SNN_EINVAL, "snapshot was taken from a different network");
+    p += sizeof h;
+    DevState ds;
+    std::memcpy(&ds, p, sizeof ds);
+    ds.done = 0;
+    ds.raster_count = 0;  // recorded spikes are not part of the state
+    ds.raster_base = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(n->v.st, &ds, sizeof ds, cudaMemcpyHostToDevice, s));
+    p += sizeof(DevState);
+    CUDA_TRY(cudaMemcpyAsync(n->v.V, p, N * 4, cudaMemcpyHostToDevice, s));
+    p += N * 4;
+    CUDA_TRY(cudaMemcpyAsync(n->v.c, p, N * 4, cudaMemcpyHostToDevice, s));
+    p += N * 4;
+    CUDA_TRY(cudaMemcpyAsync(n->v.ref, p, N, cudaMemcpyHostToDevice, s));
+    p += N;
+    CUDA_TRY(cudaMemcpyAsync(n->v.ring, p, D * N * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (schedule != 0 && schedule != 1) return fail(SNN_EINVAL, "schedule must be 0 or 1");
+    if (block == 0) block = 256;
+    if (block < 32 || block > 256 || block % 32) return fail(SNN_EINVAL, "block must be a multiple of 32 in [32, 256]");
+    n->schedule = schedule;
+    n->block = block;
+    n->grid = deliver_default_grid(schedule, block, n->nb, n->v.w_bf16 != 0);
+    return SNN_OK;
+}
+
+snn_status snn_set_timing(snn_net* n, int32_t enable) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    n->timing = enable != 0;
+    return SNN_OK;
+}
+
+snn_status snn_kernel_time(snn_net* n, double* deliver_ms, uint64_t* deliver_launches, double* neuron_ms,
+                           uint64_t* neuron_launches) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    snn_status st = drain(n->ev_deliver);
+    if (st == SNN_OK) st = drain(n->ev_neuron);
+    if (st != SNN_OK) return st;
+    if (deliver_ms) *deliver_ms = n->ev_deliver.total_ms;
+    if (deliver_launches) *deliver_launches = n->ev_deliver.count;
+    if (neuron_ms) *neuron_ms = n->ev_neuron.total_ms;
+    if (neuron_launches) *neuron_launches = n->ev_neuron.count;
+    return SNN_OK;
+}
+
+void snn_destroy(snn_net* n) {
+    if (!n) return;
+    cudaDeviceSynchronize();
+    destroy_events(n->ev_deliver);
+    destroy_events(n->ev_neuron);
+    release_all(n);
+    delete n;
+}
+
+}  // extern "C"

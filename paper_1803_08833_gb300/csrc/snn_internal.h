@@ -1,0 +1,93 @@
+// snn_internal.h -- shared declarations of libsnn.so's host runtime and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace snn {
+
+// Philox counter layout (c0, c1, c2, c3) = (a, b, tag, 0).
+constexpr uint32_t TAG_GEN = 0u;    // (neuron i, synapse k): target, weight, delay
+constexpr uint32_t TAG_DRIVE = 1u;  // (neuron i, step t): external Poisson count, forced spike
+constexpr uint32_t TAG_INIT = 2u;   // (neuron i, 0): initial membrane potential
+
+constexpr int NEURON_THREADS = 256;
+constexpr int NEURONS_PER_THREAD = 4;
+constexpr int NEURONS_PER_BLOCK = NEURON_THREADS * NEURONS_PER_THREAD;  // 1024
+constexpr int MAX_POIS = 48;
+constexpr uint32_t K_ALIGN = 8;  // rows padded to 8 synapses: 32 B f32 / 16 B bf16 / 8 B delay
+constexpr uint32_t MAX_NEURON_BLOCKS = 16384;
+
+// Device-resident simulation state shared by consecutive kernels of one network.
+struct DevState {
+    uint32_t t;          // next step the neuron kernel integrates
+    uint32_t t_deliver;  // step whose spikes are staged for the delivery kernel
+    uint32_t n_spk;      // spikes staged
+    uint32_t done;       // arrival ticket of the neuron kernel's blocks
+    uint64_t raster_count;  // spikes recorded since the raster was cleared
+    uint64_t raster_base;   // raster index of the first staged spike
+    uint64_t n_spikes, rec_events, ext_events;
+    uint32_t err;
+    uint32_t pad;
+};
+
+// Everything a kernel needs, passed by value (kernel parameter space).
+struct NetView {
+    uint32_t N, Npad, M, K, Kpad, n_exc, D, ref_steps, nb;
+    uint32_t key0, key1;
+    float a_m, a_c, kc, E, V_th, V_reset, alpha_c, in_scale, w_scale;
+    int32_t J_ext_fx;
+    uint32_t pois_len;
+    uint64_t imposed_thresh;
+    uint64_t pois[MAX_POIS];
+    int32_t w_bf16;
+    // synapse table, rows of Kpad entries per neuron
+    uint32_t* tgt;
+    void* w;
+    uint8_t* d;
+    // neuron state (Npad entries) and delay ring (D rows of Npad)
+    float* V;
+    float* c;
+    uint8_t* ref;
+    int32_t* ring;
+    // per-step spike staging
+    uint32_t* seg;      // nb segments of NEURONS_PER_BLOCK ids
+    uint32_t* blk_cnt;  // spikes per neuron block
+    uint32_t* blk_off;  // exclusive prefix of blk_cnt, nb + 1 entries
+    uint64_t* blk_ext;  // external events per neuron block
+    uint32_t* raster_t;
+    uint32_t* raster_id;
+    uint64_t raster_cap;
+    DevState* st;
+};
+
+// Parameters of the construction kernels.
+struct BuildView {
+    uint32_t grid_w, grid_h, n_modules, max_off, M, N, Npad, K, Kpad, n_exc;
+    uint32_t d_lo, d_span, d_inh;
+    uint32_t key0, key1;
+    int32_t kernel;
+    double spacing, sigma, lambda;
+    float w_lo, w_span, w_inh, V_th;
+    int32_t w_bf16;
+    const int16_t* offsets;  // max_off (dx, dy) pairs in (dy, dx) raster order
+    double* scratch;         // n_modules * max_off doubles
+    uint32_t* cdf_T;
+    uint32_t* cdf_mod;
+    uint32_t* cdf_n;
+};
+
+// Launch wrappers (return the launch error).
+cudaError_t launch_build_cdf(const BuildView& b, cudaStream_t s);
+cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d,
+                                cudaStream_t s);
+cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* ref,
+                              cudaStream_t s);
+cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);
+cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s);
+int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16);
+cudaError_t prepare_deliver(uint32_t nb);
+
+void count_launch(uint64_t n);
+
+}  // namespace snn

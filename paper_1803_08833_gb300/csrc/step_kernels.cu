@@ -1,0 +1,410 @@
+// step_kernels.cu -- one simulation time step (Sec. II-A, flow steps 1-6).
+//
+//   k_neuron_step  flow steps 1, 4-6 for every neuron: read and clear this step's
+//                  delay-ring slot, add the external Poisson input, integrate
+//                  Eq. 1-2 exactly over dt, threshold / reset / refractory /
+//                  adaptation; the block's spikes are compacted in id order.
+//                  The last block to finish turns the per-block spike counts
+//                  into offsets, so spikes have a global (step, id) order
+//                  without any inter-block waiting.
+//   k_deliver      flow steps 2-4: every spike of the step adds its K weights,
+//                  in int32 fixed point, into ring[(t + delay) mod D][target]
+//                  with fire-and-forget L2 reductions; it also writes the
+//                  (step, id) raster entries.
+#include "philox.cuh"
+#include "snn_internal.h"
+
+#include <cuda_bf16.h>
+
+namespace snn {
+
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Streaming 16 B load that does not allocate in L1 and marks the L2 line
+// evict-first: the synapse table is read once per spike and must not push
+// the delay ring out of L2.
+__device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
+    uint4 r;
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], pol;\n\t}"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const void* p) {
+    uint2 r;
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], pol;\n\t}"
+        : "=r"(r.x), "=r"(r.y)
+        : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_stream_u1(const void* p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .b64 pol;\n\t"
+        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
+        "ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], pol;\n\t}"
+        : "=r"(r)
+        : "l"(p));
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Neuron update (Eq. 1-2).  Exact propagator over dt with the input of the step
+// added after the decay:
+//   V <- ((V - E) a_m + E) - k_c c + I 2^-fx,   c <- c a_c,
+// a_m = exp(-dt/tau_m), a_c = exp(-dt/tau_c),
+// k_c = g_c tau_m tau_c / (tau_c - tau_m) (exp(-dt/tau_c) - exp(-dt/tau_m)).
+// While refractory V is held at V_r and the input is discarded.  A spike
+// (V > V_th, or a forced spike) resets V, starts the refractory count and,
+// for excitatory neurons, adds alpha_c to c.
+__device__ __forceinline__ bool lif_update(const NetView& v, float& V, float& c, uint32_t& ref,
+                                           bool exc, int32_t I, bool forced) {
+    const bool was_ref = ref > 0;
+    if (was_ref) {
+        ref -= 1;
+        V = v.V_reset;
+    } else {
+        float x = __fsub_rn(V, v.E);
+        x = __fmul_rn(x, v.a_m);
+        x = __fadd_rn(x, v.E);
+        x = __fsub_rn(x, __fmul_rn(v.kc, c));
+        x = __fadd_rn(x, __fmul_rn(__int2float_rn(I), v.in_scale));
+        V = x;
+    }
+    c = __fmul_rn(c, v.a_c);
+    const bool spike = !was_ref && (V > v.V_th || forced);
+    if (spike) {
+        V = v.V_reset;
+        ref = v.ref_steps;
+        if (exc) c = __fadd_rn(c, v.alpha_c);
+    }
+    return spike;
+}
+
+__global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
+    DevState* st = v.st;
+    const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&st->t);
+    const uint32_t slot = t % v.D;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t base = blockIdx.x * NEURONS_PER_BLOCK + tid * NEURONS_PER_THREAD;
+
+    int4* ring4 = reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base);
+    const int4 I4 = *ring4;
+    *ring4 = make_int4(0, 0, 0, 0);
+    float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
+    float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
+    uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
+
+    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
+    float Cq[4] = {C4.x, C4.y, C4.z, C4.w};
+    const int32_t Iq[4] = {I4.x, I4.y, I4.z, I4.w};
+    uint32_t spk = 0, next_sum = 0, Rout = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t i = base + q;
+        uint32_t r = (R4 >> (8 * q)) & 0xFFu;
+        if (i < v.N) {
+            const U4 u = philox4x32_10(i, t, TAG_DRIVE, 0u, v.key0, v.key1);
+            uint32_t n_ext = 0;
+            for (uint32_t k = 0; k < v.pois_len; ++k) n_ext += (v.pois[k] <= (uint64_t)u.x) ? 1u : 0u;
+            next_sum += n_ext;
+            const bool forced = (uint64_t)u.y < v.imposed_thresh;
+            const bool exc = (i % v.M) < v.n_exc;
+            const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
+            if (lif_update(v, Vq[q], Cq[q], r, exc, I, forced)) spk |= 1u << q;
+        }
+        Rout |= r << (8 * q);
+    }
+    *reinterpret_cast<float4*>(v.V + base) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+    *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
+    *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
+
+    // Block-ordered compaction: exclusive prefix of per-thread spike counts.
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    const uint32_t cnt = __popc(spk);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += x;
+    }
+    uint32_t ext_w = next_sum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ext_w += __shfl_xor_sync(0xFFFFFFFFu, ext_w, o);
+    __shared__ uint32_t s_wsum[NEURON_THREADS / 32];
+    __shared__ uint32_t s_wext[NEURON_THREADS / 32];
+    __shared__ bool s_last;
+    if (lane == 31) s_wsum[warp] = incl;
+    if (lane == 0) s_wext[warp] = ext_w;
+    __syncthreads();
+    uint32_t woff = 0, btot = 0, bext = 0;
+#pragma unroll
+    for (int w = 0; w < NEURON_THREADS / 32; ++w) {
+        const uint32_t x = s_wsum[w];
+        if (w < (int)warp) woff += x;
+        btot += x;
+        bext += s_wext[w];
+    }
+    uint32_t pos = woff + incl - cnt;
+    uint32_t* seg = v.seg + (size_t)blockIdx.x * NEURONS_PER_BLOCK;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (spk & (1u << q)) seg[pos++] = base + q;
+
+    if (tid == 0) {
+        v.blk_cnt[blockIdx.x] = btot;
+        v.blk_ext[blockIdx.x] = bext;
+        __threadfence();
+        const uint32_t ticket = atomicAdd(&st->done, 1u);
+        s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+
+    // Last block: offsets of every block's spikes (exclusive prefix) and the
+    // bookkeeping of the step.  All other blocks have published their counts.
+    __threadfence();
+    const uint32_t nb = v.nb;
+    const uint32_t per = (nb + NEURON_THREADS - 1) / NEURON_THREADS;
+    const uint32_t b0 = tid * per;
+    const uint32_t b1 = min(b0 + per, nb);
+    uint32_t local = 0;
+    unsigned long long lext = 0;
+    for (uint32_t b = b0; b < b1; ++b) {
+        local += __ldcg(v.blk_cnt + b);
+        lext += __ldcg(reinterpret_cast<const unsigned long long*>(v.blk_ext) + b);
+    }
+    uint32_t li = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, li, o);
+        if (lane >= (uint32_t)o) li += x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lext += __shfl_xor_sync(0xFFFFFFFFu, lext, o);
+    __shared__ uint32_t s_tsum[NEURON_THREADS / 32];
+    __shared__ unsigned long long s_text[NEURON_THREADS / 32];
+    __syncthreads();
+    if (lane == 31) s_tsum[warp] = li;
+    if (lane == 0) s_text[warp] = lext;
+    __syncthreads();
+    uint32_t toff = 0, total = 0;
+    unsigned long long ext_total = 0;
+#pragma unroll
+    for (int w = 0; w < NEURON_THREADS / 32; ++w) {
+        if (w < (int)warp) toff += s_tsum[w];
+        total += s_tsum[w];
+        ext_total += s_text[w];
+    }
+    uint32_t run = toff + li - local;
+    for (uint32_t b = b0; b < b1; ++b) {
+        v.blk_off[b] = run;
+        run += __ldcg(v.blk_cnt + b);
+    }
+    if (tid == 0) {
+        v.blk_off[nb] = total;
+        st->n_spk = total;
+        st->t_deliver = t;
+        st->raster_base = st->raster_count;
+        st->raster_count += total;
+        st->n_spikes += total;
+        st->rec_events += (uint64_t)total * v.K;
+        st->ext_events += ext_total;
+        st->t = t + 1;
+        st->done = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Delivery.  The staged spikes of the step are addressed by their global
+// index j; the owning neuron block is found by binary search over the block
+// offsets (held in shared memory).
+
+__device__ __forceinline__ uint32_t find_block(const uint32_t* s_off, uint32_t nb, uint32_t j) {
+    // largest b with s_off[b] <= j (s_off[0] = 0, s_off[nb] = n_spk > j)
+    uint32_t lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_off[mid] <= j)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// AER raster (Sec. II-C): entry rbase + j = (step, id of staged spike j).
+__device__ __forceinline__ void write_raster(const NetView& v, const uint32_t* s_off, uint32_t n_spk,
+                                             uint32_t t, uint64_t rbase) {
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_spk; j += stride) {
+        const uint64_t r = rbase + j;
+        if (r >= v.raster_cap) break;
+        const uint32_t b = find_block(s_off, v.nb, j);
+        v.raster_t[r] = t;
+        v.raster_id[r] = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
+    }
+}
+
+__device__ __forceinline__ int32_t fx_weight(const NetView& v, float w) {
+    return __float2int_rn(__fmul_rn(w, v.w_scale));
+}
+
+__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
+
+// Schedule 0: one warp per (spike, 128-synapse chunk); each lane handles 4
+// consecutive synapses with one 16 B target load, one 16 B (f32) or 8 B (bf16)
+// weight load and one 4 B delay load.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_deliver_warp(NetView v) {
+    extern __shared__ uint32_t s_off[];
+    const DevState* st = v.st;
+    const uint32_t n_spk = *reinterpret_cast<const volatile uint32_t*>(&st->n_spk);
+    if (n_spk == 0) return;
+    const uint32_t nb = v.nb;
+    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) s_off[b] = v.blk_off[b];
+    const uint32_t t = st->t_deliver;
+    const uint64_t rbase = st->raster_base;
+    __syncthreads();
+
+    write_raster(v, s_off, n_spk, t, rbase);
+    const uint32_t slot0 = t % v.D;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t chunks = (v.K + 127) >> 7;
+    const uint32_t n_tasks = n_spk * chunks;
+    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < n_tasks; task += warps) {
+        const uint32_t j = task / chunks;
+        const uint32_t ch = task - j * chunks;
+        const uint32_t b = find_block(s_off, nb, j);
+        const uint32_t id = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
+        const uint32_t k0 = (ch << 7) + (lane << 2);
+        if (k0 >= v.K) continue;
+        const size_t e = (size_t)id * v.Kpad + k0;
+        const uint4 tg = ld_stream_u4(v.tgt + e);
+        float w[4];
+        if (BF16) {
+            const uint2 wb = ld_stream_u2(reinterpret_cast<const uint16_t*>(v.w) + e);
+            w[0] = bf16_lo(wb.x);
+            w[1] = bf16_hi(wb.x);
+            w[2] = bf16_lo(wb.y);
+            w[3] = bf16_hi(wb.y);
+        } else {
+            const uint4 wf = ld_stream_u4(reinterpret_cast<const float*>(v.w) + e);
+            w[0] = __uint_as_float(wf.x);
+            w[1] = __uint_as_float(wf.y);
+            w[2] = __uint_as_float(wf.z);
+            w[3] = __uint_as_float(wf.w);
+        }
+        const uint32_t dd = ld_stream_u1(v.d + e);
+        const uint32_t tq[4] = {tg.x, tg.y, tg.z, tg.w};
+        const uint32_t nvalid = min(4u, v.K - k0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if ((uint32_t)q < nvalid) {
+                uint32_t s = slot0 + ((dd >> (8 * q)) & 0xFFu);
+                if (s >= v.D) s -= v.D;
+                red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[q]));
+            }
+        }
+    }
+}
+
+// Schedule 1: one thread per synapse over the flattened (spike, synapse)
+// range, scalar loads.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_deliver_thread(NetView v) {
+    extern __shared__ uint32_t s_off[];
+    const DevState* st = v.st;
+    const uint32_t n_spk = *reinterpret_cast<const volatile uint32_t*>(&st->n_spk);
+    if (n_spk == 0) return;
+    const uint32_t nb = v.nb;
+    for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) s_off[b] = v.blk_off[b];
+    const uint32_t t = st->t_deliver;
+    const uint64_t rbase = st->raster_base;
+    __syncthreads();
+    write_raster(v, s_off, n_spk, t, rbase);
+    const uint32_t slot0 = t % v.D;
+    const uint64_t total = (uint64_t)n_spk * v.K;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint32_t cached_j = 0xFFFFFFFFu, id = 0;
+    for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const uint32_t j = (uint32_t)(g / v.K);
+        const uint32_t k = (uint32_t)(g - (uint64_t)j * v.K);
+        if (j != cached_j) {
+            const uint32_t b = find_block(s_off, nb, j);
+            id = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
+            cached_j = j;
+        }
+        const size_t e = (size_t)id * v.Kpad + k;
+        const uint32_t tg = __ldg(v.tgt + e);
+        const float w = BF16 ? __uint_as_float((uint32_t)__ldg(reinterpret_cast<const uint16_t*>(v.w) + e) << 16)
+                             : __ldg(reinterpret_cast<const float*>(v.w) + e);
+        uint32_t s = slot0 + __ldg(v.d + e);
+        if (s >= v.D) s -= v.D;
+        red_add(v.ring + (size_t)s * v.Npad + tg, fx_weight(v, w));
+    }
+}
+
+cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s) {
+    k_neuron_step<<<v.nb, NEURON_THREADS, 0, s>>>(v);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+static const void* deliver_fn(int schedule, bool bf16) {
+    if (schedule == 1) return bf16 ? (const void*)k_deliver_thread<true> : (const void*)k_deliver_thread<false>;
+    return bf16 ? (const void*)k_deliver_warp<true> : (const void*)k_deliver_warp<false>;
+}
+
+// Persistent grid: as many blocks as fit on all SMs at once.
+int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)(nb + 1) * sizeof(uint32_t);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_fn(schedule, bf16), block, smem);
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+cudaError_t prepare_deliver(uint32_t nb) {
+    const size_t smem = (size_t)(nb + 1) * sizeof(uint32_t);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    for (int sch = 0; sch < 2; ++sch)
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = cudaFuncSetAttribute(deliver_fn(sch, b != 0),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s) {
+    const size_t smem = (size_t)(v.nb + 1) * sizeof(uint32_t);
+    const bool bf16 = v.w_bf16 != 0;
+    if (schedule == 1) {
+        if (bf16)
+            k_deliver_thread<true><<<grid, block, smem, s>>>(v);
+        else
+            k_deliver_thread<false><<<grid, block, smem, s>>>(v);
+    } else {
+        if (bf16)
+            k_deliver_warp<true><<<grid, block, smem, s>>>(v);
+        else
+            k_deliver_warp<false><<<grid, block, smem, s>>>(v);
+    }
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+}  // namespace snn

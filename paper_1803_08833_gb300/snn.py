@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libsnn.so (C ABI in include/snn.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels.  PyTorch supplies the device memory (its caching allocator, via
+the library's allocator hook) and the CUDA stream.  There is no fallback: if
+libsnn.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsnn.so")
+
+SNN_OK, SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_EOVERFLOW, SNN_ETIMEOUT, SNN_EBUDGET = 0, -1, -2, -3, -4, -5, -6
+_STATUS = {0: "SNN_OK", -1: "SNN_EINVAL", -2: "SNN_ENOMEM", -3: "SNN_ECUDA", -4: "SNN_EOVERFLOW",
+           -5: "SNN_ETIMEOUT", -6: "SNN_EBUDGET"}
+
+
+class SnnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class SnnConfig(ctypes.Structure):
+    _fields_ = [
+        ("grid_w", ctypes.c_uint32), ("grid_h", ctypes.c_uint32),
+        ("neurons_per_module", ctypes.c_uint32),
+        ("exc_fraction", ctypes.c_float), ("spacing_um", ctypes.c_float),
+        ("K", ctypes.c_uint32), ("kernel", ctypes.c_int32),
+        ("sigma_um", ctypes.c_double), ("lambda_um", ctypes.c_double), ("cutoff_um", ctypes.c_double),
+        ("w_exc_lo", ctypes.c_float), ("w_exc_hi", ctypes.c_float), ("w_inh", ctypes.c_float),
+        ("d_exc_lo", ctypes.c_uint32), ("d_exc_hi", ctypes.c_uint32), ("d_inh", ctypes.c_uint32),
+        ("tau_m_ms", ctypes.c_float), ("E_mV", ctypes.c_float), ("V_th_mV", ctypes.c_float),
+        ("V_reset_mV", ctypes.c_float), ("t_ref_ms", ctypes.c_float),
+        ("tau_c_ms", ctypes.c_float), ("alpha_c", ctypes.c_float), ("g_c_mV", ctypes.c_float),
+        ("dt_ms", ctypes.c_float),
+        ("ext_rate_hz", ctypes.c_float), ("J_ext_mV", ctypes.c_float),
+        ("imposed_rate_hz", ctypes.c_float),
+        ("weight_dtype", ctypes.c_int32), ("fx_shift", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("raster_capacity", ctypes.c_uint64),
+    ]
+
+
+class SnnStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("steps", "n_spikes", "rec_events", "ext_events", "raster_count", "raster_capacity")]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+
+
+def load():
+    """Load the in-tree libsnn.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsnn.so not found at %s: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, P = ctypes.c_void_p, ctypes.POINTER
+    st = ctypes.c_int
+    sig = {
+        "snn_build_network": (st, [P(SnnConfig), ALLOC_FN, FREE_FN, vp, vp, P(vp)]),
+        "snn_step": (st, [vp, ctypes.c_uint32, vp]),
+        "snn_read_spikes": (st, [vp, vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]),
+        "snn_clear_raster": (st, [vp, vp]),
+        "snn_get_stats": (st, [vp, P(SnnStats), vp]),
+        "snn_snapshot": (st, [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]),
+        "snn_restore": (st, [vp, vp, ctypes.c_size_t, vp]),
+        "snn_get_table": (st, [vp, vp, vp, vp, vp]),
+        "snn_get_rows": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp, vp]),
+        "snn_get_cdf": (st, [vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
+        "snn_get_state": (st, [vp, vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
+        "snn_set_state": (st, [vp, vp, vp, vp, vp]),
+        "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
+                              P(ctypes.c_uint64)]),
+        "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_set_timing": (st, [vp, ctypes.c_int32]),
+        "snn_kernel_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_double),
+                                 P(ctypes.c_uint64)]),
+        "snn_launch_count": (ctypes.c_uint64, []),
+        "snn_destroy": (None, [vp]),
+        "snn_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != SNN_OK:
+        raise SnnError(status, load().snn_last_error().decode(errors="replace"))
+    return status
+
+
+def config(cfg: dict, raster_capacity: int = 0) -> SnnConfig:
+    """Marshal a workload dictionary (keys = snn_config field names) into snn_config."""
+    c = SnnConfig()
+    names = {f[0] for f in SnnConfig._fields_}
+    for k, v in cfg.items():
+        if k == "kernel":
+            v = {"gauss": 0, "exp": 1}.get(v, v)
+        elif k == "weight_dtype":
+            v = {"f32": 0, "bf16": 1}.get(v, v)
+        if k not in names:
+            raise KeyError("unknown snn_config field %r" % k)
+        setattr(c, k, v)
+    if raster_capacity:
+        c.raster_capacity = raster_capacity
+    return c
+
+
+def launch_count() -> int:
+    return int(load().snn_launch_count())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _TorchAllocator:
+    """Allocator hook backed by PyTorch's caching allocator on one device/stream."""
+
+    def __init__(self, device, stream):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, size, ctx):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(size), self.device, self.stream)
+        except Exception:  # out of memory: the library reports SNN_ENOMEM
+            return None
+
+    def _free(self, ptr, ctx):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+class Network:
+    """One simulated network resident on the current CUDA device."""
+
+    def __init__(self, cfg: dict, raster_capacity: int = 1 << 20, stream=None, allocator="torch"):
+        import torch
+        L = load()
+        self.cfg = dict(cfg)
+        self._torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._s = ctypes.c_void_p(self.stream.cuda_stream)
+        self._c = config(cfg, raster_capacity)
+        self._alloc = _TorchAllocator(self.device, self.stream) if allocator == "torch" else None
+        h = ctypes.c_void_p()
+        if self._alloc is not None:
+            st = L.snn_build_network(ctypes.byref(self._c), self._alloc.alloc, self._alloc.free, None,
+                                     self._s, ctypes.byref(h))
+        else:
+            st = L.snn_build_network(ctypes.byref(self._c), ALLOC_FN(), FREE_FN(), None, self._s,
+                                     ctypes.byref(h))
+        check(st)
+        self._h = h
+        N, K, D = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        nbytes = ctypes.c_uint64()
+        check(L.snn_get_dims(h, ctypes.byref(N), ctypes.byref(K), ctypes.byref(D), ctypes.byref(nbytes)))
+        self.N, self.K, self.D, self.device_bytes = N.value, K.value, D.value, nbytes.value
+        self.raster_capacity = raster_capacity
+        self.n_modules = int(cfg["grid_w"]) * int(cfg["grid_h"])
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().snn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- simulation ------------------------------------------------------
+    def step(self, n: int = 1):
+        check(load().snn_step(self._h, int(n), self._s))
+
+    def read_spikes(self, cap=None, allow_overflow=False):
+        cap = self.raster_capacity if cap is None else cap
+        steps = np.empty(cap, np.uint32)
+        ids = np.empty(cap, np.uint32)
+        n = ctypes.c_size_t()
+        st = load().snn_read_spikes(self._h, _ptr(steps), _ptr(ids), cap, ctypes.byref(n), self._s)
+        if not (allow_overflow and st == SNN_EOVERFLOW):
+            check(st)
+        return steps[: n.value], ids[: n.value]
+
+    def read_spikes_into(self, steps: np.ndarray, ids: np.ndarray) -> int:
+        """Copy the raster into caller-owned (e.g. pinned) host arrays; returns the count."""
+        n = ctypes.c_size_t()
+        check(load().snn_read_spikes(self._h, _ptr(steps), _ptr(ids), min(len(steps), len(ids)),
+                                     ctypes.byref(n), self._s))
+        return n.value
+
+    def clear_raster(self):
+        check(load().snn_clear_raster(self._h, self._s))
+
+    def stats(self) -> dict:
+        s = SnnStats()
+        check(load().snn_get_stats(self._h, ctypes.byref(s), self._s))
+        return {f[0]: int(getattr(s, f[0])) for f in SnnStats._fields_}
+
+    # -- inspection --------------------------------------------------------
+    def csr(self, first: int = 0, count=None):
+        """Synapse rows [first, first + count) as flat (target, weight, delay) arrays."""
+        count = self.N - first if count is None else count
+        ns = count * self.K
+        tgt = np.empty(ns, np.uint32)
+        w = np.empty(ns, np.float32)
+        d = np.empty(ns, np.uint8)
+        check(load().snn_get_rows(self._h, first, count, _ptr(tgt), _ptr(w), _ptr(d), self._s))
+        return tgt, w, d
+
+    def cdf(self):
+        mo = ctypes.c_uint32()
+        check(load().snn_get_cdf(self._h, None, None, None, ctypes.byref(mo), self._s))
+        m = mo.value
+        T = np.empty(self.n_modules * m, np.uint32)
+        TM = np.empty(self.n_modules * m, np.uint32)
+        cnt = np.empty(self.n_modules, np.uint32)
+        check(load().snn_get_cdf(self._h, _ptr(T), _ptr(TM), _ptr(cnt), ctypes.byref(mo), self._s))
+        return T.reshape(self.n_modules, m), TM.reshape(self.n_modules, m), cnt
+
+    def state(self):
+        V = np.empty(self.N, np.float32)
+        c = np.empty(self.N, np.float32)
+        ref = np.empty(self.N, np.uint8)
+        ring = np.empty(self.D * self.N, np.int32)
+        t = ctypes.c_uint32()
+        check(load().snn_get_state(self._h, _ptr(V), _ptr(c), _ptr(ref), _ptr(ring), ctypes.byref(t), self._s))
+        return {"V": V, "c": c, "ref": ref, "ring": ring.reshape(self.D, self.N), "t": t.value}
+
+    def set_state(self, V=None, c=None, ref=None):
+        V = None if V is None else np.ascontiguousarray(V, np.float32)
+        c = None if c is None else np.ascontiguousarray(c, np.float32)
+        ref = None if ref is None else np.ascontiguousarray(ref, np.uint8)
+        check(load().snn_set_state(self._h, _ptr(V), _ptr(c), _ptr(ref), self._s))
+
+    def snapshot(self) -> bytes:
+        n = ctypes.c_size_t()
+        check(load().snn_snapshot(self._h, None, 0, ctypes.byref(n), self._s))
+        buf = ctypes.create_string_buffer(n.value)
+        check(load().snn_snapshot(self._h, buf, n.value, ctypes.byref(n), self._s))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        check(load().snn_restore(self._h, buf, len(blob), self._s))
+
+    # -- tuning / timing ---------------------------------------------------
+    def set_schedule(self, schedule: int, block: int = 0):
+        check(load().snn_set_schedule(self._h, int(schedule), int(block)))
+
+    def set_timing(self, enable: bool):
+        check(load().snn_set_timing(self._h, 1 if enable else 0))
+
+    def kernel_time(self) -> dict:
+        dm, nm = ctypes.c_double(), ctypes.c_double()
+        dl, nl = ctypes.c_uint64(), ctypes.c_uint64()
+        check(load().snn_kernel_time(self._h, ctypes.byref(dm), ctypes.byref(dl), ctypes.byref(nm),
+                                     ctypes.byref(nl)))
+        return {"deliver_ms": dm.value, "deliver_launches": dl.value,
+                "neuron_ms": nm.value, "neuron_launches": nl.value}

@@ -1,0 +1,261 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Integer work (target tables, synapse tables, spike rasters, ring contents) must
+be bit-exact; with FP32 and BF16 weights the neuron state (V, c) is bit-exact
+too, because both sides evaluate the same IEEE expressions in the same order
+with no fused multiply-add.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_08833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    from paper_1803_08833_gb300 import _build
+    from paper_1803_08833_gb300 import snn as S
+    _build.build()
+    S.load()
+    return S
+
+
+def _cdf_case(name):
+    if name == "gauss4":
+        return W.gauss_4x4_k1000()
+    if name == "gauss24":
+        return W.gauss_24x24_k1125()
+    if name == "exp24":
+        return W.exp_24x24_k2250()
+    if name == "exp_rect":
+        return dict(W.small(lateral="exp"), grid_w=13, grid_h=5)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["gauss4", "gauss24", "exp24", "exp_rect"])
+def test_target_tables_equal_oracle(snn, name):
+    cfg = dict(_cdf_case(name), neurons_per_module=2, K=8)  # the tables depend on the grid only
+    with snn.Network(cfg) as net:
+        T, TM, cnt = net.cdf()
+    for m in range(cfg["grid_w"] * cfg["grid_h"]):
+        oT, oTM, _ = oracle.cdf_table(cfg, m)
+        n = len(oT)
+        assert cnt[m] == n
+        assert np.array_equal(T[m, :n], oT), m
+        assert np.array_equal(TM[m, :n], oTM), m
+
+
+CSR_CASES = {
+    "gauss_4x4_k1000": lambda: W.gauss_4x4_k1000(seed=3),
+    "ragged_k37": lambda: dict(W.small(grid=3, M=77, K=37, seed=12), grid_h=2),
+    "exp_bf16": lambda: W.small(grid=6, M=50, K=203, lateral="exp", seed=4, weight_dtype="bf16"),
+    "k1": lambda: W.small(grid=2, M=5, K=1, seed=2),
+    "k0": lambda: W.small(grid=2, M=5, K=0, seed=2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CSR_CASES))
+def test_synapse_table_equals_oracle(snn, name):
+    cfg = CSR_CASES[name]()
+    with snn.Network(cfg) as net:
+        tgt, w, d = net.csr()
+    ref = oracle.OracleNet(cfg)
+    rt, rw, rd = ref.csr()
+    assert np.array_equal(tgt, rt)
+    assert np.array_equal(w.view(np.uint32), rw.view(np.uint32))
+    assert np.array_equal(d, rd)
+
+
+SIM_CASES = {
+    # the plain 4x4 workload as specified (it falls nearly silent after the initial transient)
+    "gauss4_seed1": (lambda: W.gauss_4x4_k1000(seed=1), 1000),
+    "gauss4_seed2": (lambda: W.gauss_4x4_k1000(seed=2), 1000),
+    "gauss4_seed3": (lambda: W.gauss_4x4_k1000(seed=3), 1000),
+    # the same network at the paper's Gaussian rate (imposed) and under a stronger drive
+    "gauss4_imposed7.5": (lambda: W.gauss_4x4_k1000(seed=1, imposed_rate_hz=7.5), 300),
+    "gauss4_drive5k": (lambda: W.gauss_4x4_k1000(seed=2, ext_rate_hz=5000.0), 300),
+    # long-range kernel, bf16 weights, the paper's exponential rate
+    "exp_bf16_35hz": (lambda: W.small(grid=7, M=150, K=400, lateral="exp", seed=5, weight_dtype="bf16",
+                                      imposed_rate_hz=35.0), 200),
+    # ragged sizes: N not a multiple of the block, K not a multiple of the vector width
+    "ragged": (lambda: dict(W.small(grid=3, M=333, K=37, seed=9, imposed_rate_hz=40.0), grid_h=2), 150),
+    # adaptation and E != 0 exercised under strong drive
+    "adapt_E": (lambda: W.small(grid=4, M=100, K=90, seed=6, ext_rate_hz=6000.0, E_mV=-1.5, alpha_c=0.2), 250),
+}
+
+
+def _compare(net, ref):
+    st, ids = net.read_spikes()
+    rs, ri = ref.raster()
+    assert np.array_equal(st, rs) and np.array_equal(ids, ri), (len(st), len(rs))
+    s, o = net.state(), ref.state()
+    assert s["t"] == ref.t
+    assert np.array_equal(s["V"].view(np.uint32), o["V"].view(np.uint32))
+    assert np.array_equal(s["c"].view(np.uint32), o["c"].view(np.uint32))
+    assert np.array_equal(s["ref"], o["ref"])
+    assert np.array_equal(s["ring"], o["ring"])
+    a, b = net.stats(), ref.stats()
+    assert a["n_spikes"] == b["spikes"] and a["rec_events"] == b["rec_events"]
+    assert a["ext_events"] == b["ext_events"]
+    return len(st)
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("name", sorted(SIM_CASES))
+def test_simulation_bit_exact(snn, name, schedule):
+    make, steps = SIM_CASES[name]
+    cfg = make()
+    with snn.Network(cfg, raster_capacity=1 << 22) as net:
+        net.set_schedule(schedule)
+        net.step(steps)
+        ref = oracle.OracleNet(cfg)
+        ref.step(steps)
+        n = _compare(net, ref)
+    if "imposed" in name or "35hz" in name or "drive" in name:
+        assert n > 1000
+
+
+def test_block_sizes_agree(snn):
+    cfg = W.small(grid=3, M=200, K=150, seed=3, imposed_rate_hz=50.0)
+    ref = oracle.OracleNet(cfg)
+    ref.step(80)
+    for schedule, block in ((0, 32), (0, 128), (1, 64), (1, 256)):
+        with snn.Network(cfg) as net:
+            net.set_schedule(schedule, block)
+            net.step(80)
+            _compare(net, ref)
+
+
+def test_steps_in_pieces_equal_one_call(snn):
+    cfg = W.small(grid=3, M=100, K=60, seed=8, imposed_rate_hz=30.0)
+    with snn.Network(cfg) as a, snn.Network(cfg) as b:
+        a.step(90)
+        for n in (1, 2, 30, 57):
+            b.step(n)
+        sa, sb = a.state(), b.state()
+        for k in ("V", "c", "ref", "ring"):
+            assert np.array_equal(sa[k], sb[k])
+        assert all(np.array_equal(x, y) for x, y in zip(a.read_spikes(), b.read_spikes()))
+
+
+def test_snapshot_restore_resumes_bit_exact(snn):
+    cfg = W.small(grid=3, M=120, K=80, seed=14, imposed_rate_hz=25.0, ext_rate_hz=4000.0)
+    with snn.Network(cfg) as a, snn.Network(cfg) as b:
+        a.step(120)
+        st_a, id_a = a.read_spikes()
+        a.step(0)
+        b.step(60)
+        blob = b.snapshot()
+        with snn.Network(cfg) as c:
+            c.restore(blob)
+            c.step(60)
+            st_c, id_c = c.read_spikes()
+            late = st_a >= 60
+            assert np.array_equal(st_c, st_a[late]) and np.array_equal(id_c, id_a[late])
+            sa, sc = a.state(), c.state()
+            for k in ("V", "c", "ref", "ring", "t"):
+                assert np.array_equal(sa[k], sc[k]), k
+            assert c.stats()["n_spikes"] == a.stats()["n_spikes"]
+
+
+def test_snapshot_of_another_network_is_rejected(snn):
+    with snn.Network(W.small(seed=1)) as a, snn.Network(W.small(seed=2)) as b:
+        blob = a.snapshot()
+        with pytest.raises(snn.SnnError, match="different network"):
+            b.restore(blob)
+
+
+def test_raster_overflow_is_reported(snn):
+    cfg = W.small(grid=3, M=100, K=20, seed=4, imposed_rate_hz=100.0)
+    with snn.Network(cfg, raster_capacity=500) as net:
+        net.step(40)
+        with pytest.raises(snn.SnnError, match="SNN_EOVERFLOW"):
+            net.read_spikes()
+        st, ids = net.read_spikes(allow_overflow=True)
+        assert len(st) == 500
+        ref = oracle.OracleNet(cfg)
+        ref.step(40)
+        rs, ri = ref.raster()
+        assert np.array_equal(st, rs[:500]) and np.array_equal(ids, ri[:500])
+        assert net.stats()["n_spikes"] == len(rs)
+        net.clear_raster()
+        net.step(1)
+        st2, _ = net.read_spikes()
+        assert np.all(st2 == 40)
+
+
+def test_empty_steps_and_silent_network(snn):
+    cfg = W.small(grid=2, M=64, K=10, seed=1, ext_rate_hz=0.0)
+    with snn.Network(cfg) as net:
+        net.step(0)
+        V0 = net.state()["V"]
+        net.step(50)
+        st, _ = net.read_spikes()
+        assert len(st) == 0 and net.stats()["rec_events"] == 0
+        ref = oracle.OracleNet(cfg)
+        ref.step(50)
+        assert np.array_equal(net.state()["V"], ref.state()["V"])
+        assert V0.max() < cfg["V_th_mV"]
+
+
+def _full_size_check(snn, cfg, n_rows=1500, seed=0):
+    """At the full configuration: sampled synapse rows, the first step of sampled
+    neurons, the exact ring after the first delivery, and invariants."""
+    rng = np.random.default_rng(seed)
+    with snn.Network(cfg, raster_capacity=1 << 24) as net:
+        N, K, M = net.N, net.K, cfg["neurons_per_module"]
+        rows = np.unique(np.concatenate([
+            rng.integers(0, N, n_rows), [0, 1, M - 1, M, N // 2, N - 2, N - 1]]))
+        for r in rows.tolist():
+            tgt, w, d = net.csr(r, 1)
+            ot, ow, od = oracle.gen_rows(cfg, r, 1)
+            assert np.array_equal(tgt, ot), r
+            assert np.array_equal(w.view(np.uint32), ow.view(np.uint32)), r
+            assert np.array_equal(d, od), r
+        net.step(1)
+        st, ids = net.read_spikes()
+        s = net.state()
+        spiked = set(ids.tolist())
+        k = oracle.constants(cfg)
+        sample = rng.integers(0, N, 3000)
+        for i in sample.tolist():
+            n_ext, forced = oracle.drive(cfg, i, 0)
+            V, c, ref, sp = oracle.lif_update(cfg, oracle.initial_V(cfg, i), 0.0, 0,
+                                              (i % M) < k["n_exc"], n_ext * k["J_ext_fx"], forced)
+            assert np.float32(V) == s["V"][i] and np.float32(c) == s["c"][i] and ref == s["ref"][i], i
+            assert sp == (i in spiked), i
+        assert np.all(st == 0) and np.all(np.diff(ids.astype(np.int64)) > 0)
+        # the ring after delivering every spike of step 0, recomputed from oracle rows
+        expect = np.zeros((net.D, N), np.int64)
+        scale = float(2 ** cfg["fx_shift"])
+        for i in ids.tolist():
+            ot, ow, od = oracle.gen_rows(cfg, i, 1)
+            np.add.at(expect, (od.astype(np.int64) % net.D, ot.astype(np.int64)),
+                      np.rint(ow.astype(np.float64) * scale).astype(np.int64))
+        ring = s["ring"].astype(np.int64)
+        expect[0] = 0  # slot 0 was consumed by step 0
+        assert np.array_equal(ring, expect)
+        # a longer run keeps the invariants
+        net.clear_raster()
+        net.step(200)
+        st, ids = net.read_spikes()
+        stats = net.stats()
+        assert stats["rec_events"] == stats["n_spikes"] * K
+        key = st.astype(np.int64) * N + ids
+        assert np.all(np.diff(key) > 0)
+        rate = len(st) / (N * 200) * 1000.0
+        assert 0.5 * cfg["imposed_rate_hz"] < rate < 2.0 * cfg["imposed_rate_hz"] + 5.0
+
+
+def test_full_size_gauss_24x24_k1125(snn):
+    _full_size_check(snn, W.gauss_24x24_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ))
+
+
+def test_full_size_exp_24x24_k2250_bf16(snn):
+    _full_size_check(snn, W.exp_24x24_k2250(seed=2, imposed_rate_hz=W.PAPER_RATE_EXP_HZ), n_rows=600)
