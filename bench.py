@@ -1,0 +1,420 @@
+"""Benchmark of the per-timestep hot path: synaptic events per second on one GB300.
+
+Workload: the 24x24-module Gaussian network (720,000 LIF-SFA neurons, K = 1,125,
+810 M synapses, FP32 weights), spiking at the paper's Gaussian rate of 7.5 Hz
+(imposed Bernoulli spikes on top of the model's own dynamics, whose specified
+drive alone leaves the network nearly silent).  One benchmark step = 1,000
+simulated 1 ms time steps (one simulated second): for every time step the fused
+neuron kernel and the delivery kernel, through the C ABI.  The synapse table
+(7.3 GB) is far larger than L2, so every step streams it from HBM.
+
+value       recurrent synaptic events / s (events = spikes x out-degree, from the
+            device counters), device-timed with CUDA events over K steps.
+e2e         the same metric for whole jobs through the public API: build the
+            network from the host description, simulate 10,000 steps reading
+            the raster into pinned host memory every 1,000 steps, destroy.
+roofline    the delivery kernel: algorithmic bytes (9 B per recurrent event:
+            uint32 target + f32 weight + uint8 delay) / its summed CUDA-event
+            time, against the measured HBM copy bandwidth.
+cpu_baseline  the oracle (single-threaded C) on a bounded sample of the same
+            model, simulation phase only, like `value`.
+
+--impl reference runs the oracle arm on the host cores (this project's
+reference is the CPU oracle; the paper's own simulator is not available).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "synaptic events/s on 1 GB300, % of HBM roofline; served p50/p99 latency"
+UNIT = "synaptic events/s"
+BYTES_PER_EVENT = {"f32": 9, "bf16": 7}
+TIMESTEPS_PER_STEP = 1000
+JOB_TIMESTEPS = 10000
+
+# DRAM traffic of one delivery launch from an ncu capture of the same kernel
+# source (dram__bytes_read.sum + dram__bytes_write.sum, per recurrent event).
+# Reported only while the kernel source is unchanged since the capture.
+NCU_TRAFFIC = {"source_sha256": None, "bytes_per_event": None, "capture": None}
+
+
+def _log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def _kernel_source_sha():
+    p = os.path.join(ROOT, "paper_1803_08833_gb300", "csrc", "step_kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "snn_clocks_%d_%d.csv" % (os.getpid(), gpu_index))
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, local, dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _reduce(dist, value, op):
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def workload(seed=1, grid=24):
+    from paper_1803_08833_gb300 import workloads as W
+    cfg = W.gauss_24x24_k1125(seed=seed, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ)
+    return W.patch(cfg, grid) if grid != 24 else cfg
+
+
+def config_block(cfg, extra=None):
+    g = cfg["grid_w"]
+    n = g * g * cfg["neurons_per_module"]
+    d = {
+        "workload": "gauss_%dx%d_k1125: %dx%d modules x 1250 LIF-SFA neurons (%s), K=1125 "
+                    "(%dM synapses), Gaussian sigma=100um cut at 3 sigma, FP32 weights, dt=1 ms"
+                    % (g, g, g, g, format(n, ","), round(n * 1125 / 1e6)),
+        "imposed_rate_hz": cfg["imposed_rate_hz"],
+        "ext_drive": "%.0f Hz x %.1f mV Poisson" % (cfg["ext_rate_hz"], cfg["J_ext_mV"]),
+        "timesteps_per_step": TIMESTEPS_PER_STEP,
+        "l2": "inputs larger than L2 (129 MB): the %.1f GB synapse table is streamed every step"
+              % (n * 1128 * 9 / 1e9),
+        "parallelism": "replicas",
+    }
+    if extra:
+        d.update(extra)
+    return d
+
+
+# --------------------------------------------------------------------------
+def cpu_oracle_rate(cfg, grid, min_seconds, max_steps, warm_steps=20):
+    """Oracle simulation-phase throughput on a grid x grid patch of the model."""
+    import oracle
+    from paper_1803_08833_gb300 import workloads as W
+    sample = W.patch(cfg, grid)
+    net = oracle.OracleNet(sample)
+    net.step(warm_steps)
+    s0 = net.stats()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (time.perf_counter() - t0 < min_seconds or steps < 5):
+        net.step(10)
+        steps += 10
+    dt = time.perf_counter() - t0
+    s1 = net.stats()
+    net.close()
+    ev = s1["rec_events"] - s0["rec_events"]
+    return ev / dt, {"steps": steps, "seconds": dt, "events": ev, "neurons": sample["grid_w"] ** 2 * sample[
+        "neurons_per_module"]}
+
+
+def run_reference(args):
+    rank, ws, local, dist = _dist()
+    if rank != 0:
+        return 0
+    cfg = workload()
+    import oracle
+    from paper_1803_08833_gb300 import workloads as W
+    grid = 6
+    sample = W.patch(cfg, grid)
+    steps_per = 100
+    net = oracle.OracleNet(sample)
+    for _ in range(args.warmup):
+        net.step(steps_per)
+    s0 = net.stats()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        net.step(steps_per)
+    dt = time.perf_counter() - t0
+    s1 = net.stats()
+    value = (s1["rec_events"] - s0["rec_events"]) / dt
+    desc = ("oracle (single-threaded C) on a %dx%d-module patch of the workload (%d neurons, K=%d, "
+            "imposed %.1f Hz), %d simulated 1 ms steps per bench step, simulation phase only"
+            % (grid, grid, grid * grid * sample["neurons_per_module"], sample["K"], sample["imposed_rate_hz"],
+               steps_per))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0 / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_block(cfg, {"sample": desc}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+def run_gpu(args):
+    rank, ws, local, dist = _dist()
+    import numpy as np
+    import torch
+
+    from paper_1803_08833_gb300 import _build, snn
+
+    if rank == 0 or dist is None:
+        _build.build()
+    _barrier(dist)
+    torch.cuda.set_device(local)
+    cfg = workload(seed=1 + rank, grid=args.grid)
+    T = args.timesteps
+    peak, peak_kind = _peaks()
+    stream = torch.cuda.current_stream()
+
+    t_build = time.perf_counter()
+    net = snn.Network(cfg, raster_capacity=T * 20000)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    if args.schedule is not None:
+        net.set_schedule(args.schedule, args.block)
+    net.set_timing(args.timing_every)
+
+    for _ in range(args.warmup):
+        net.step(T)
+        net.clear_raster()
+    torch.cuda.synchronize()
+    kt0 = net.kernel_time()
+    s0 = net.stats()
+    l0 = snn.launch_count()
+
+    ev_a = torch.cuda.Event(enable_timing=True)
+    ev_b = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        _barrier(dist)
+        torch.cuda.synchronize()
+        ev_a.record(stream)
+        for _ in range(args.steps):
+            net.step(T)
+            net.clear_raster()
+        ev_b.record(stream)
+        torch.cuda.synchronize()
+        _barrier(dist)
+    launches = snn.launch_count() - l0
+    ms = ev_a.elapsed_time(ev_b)
+    s1 = net.stats()
+    kt1 = net.kernel_time()
+    rec = s1["rec_events"] - s0["rec_events"]
+    ext = s1["ext_events"] - s0["ext_events"]
+    spikes = s1["n_spikes"] - s0["n_spikes"]
+
+    ms_max = _reduce(dist, ms, _max_op(dist))
+    rec_all = _reduce(dist, rec, _sum_op(dist))
+    value = rec_all / (ms_max / 1000.0)
+
+    dl = kt1["deliver_launches"] - kt0["deliver_launches"]
+    dms = kt1["deliver_ms"] - kt0["deliver_ms"]
+    nms = kt1["neuron_ms"] - kt0["neuron_ms"]
+    # algorithmic bytes per timed launch: events of the timed region / timesteps x 9 B
+    ev_per_launch = rec / (args.steps * T)
+    achieved = BYTES_PER_EVENT["f32"] * ev_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
+    traffic = None
+    if NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() and NCU_TRAFFIC["bytes_per_event"]:
+        traffic = NCU_TRAFFIC["bytes_per_event"] * ev_per_launch
+    net.set_timing(0)
+
+    # end-to-end jobs through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(snn, cfg, args.e2e_jobs, stream)
+    net.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, info = cpu_oracle_rate(cfg, args.cpu_grid, args.cpu_seconds, 100000)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle (single-threaded C) on a %dx%d-module patch of the workload (%d neurons, "
+                         "K=1125, imposed 7.5 Hz), %d simulated steps after 20 warm-up steps, %.1f s, "
+                         "simulation phase only" % (args.cpu_grid, args.cpu_grid, info["neurons"], info["steps"],
+                                                    info["seconds"])}
+
+    if rank != 0:
+        return 0
+    ck = clocks.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_block(cfg, {"build_ms": round(t_build * 1000.0, 1),
+                                     "timesteps_per_step": T,
+                                     "spikes_per_timestep": spikes / (args.steps * T),
+                                     "rate_hz": spikes / (args.steps * T) / net.N * 1000.0,
+                                     "equivalent_events_per_s": (rec + ext) / (ms / 1000.0),
+                                     "neuron_kernel_us": 1000.0 * nms / max(dl, 1),
+                                     "deliver_kernel_us": 1000.0 * dms / max(dl, 1),
+                                     "kernel_timing": "CUDA events around the kernels of every %d-th "
+                                                      "simulated step of the timed region" % args.timing_every}),
+        "roofline": {"bound": "hbm", "kernel": "k_deliver_warp<f32>", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "bytes_per_event": BYTES_PER_EVENT["f32"],
+                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "launches_timed": dl},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_e2e(snn, cfg, jobs, stream):
+    """Whole jobs through the public API: build from the host description,
+    simulate JOB_TIMESTEPS reading the raster into pinned host memory after
+    every 1,000 steps, destroy.  Device-side inputs are never reused."""
+    import ctypes
+
+    import numpy as np
+    import torch
+    cap = TIMESTEPS_PER_STEP * 20000
+    h_steps = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    h_ids = torch.empty(cap, dtype=torch.int32, pin_memory=True)
+    a_steps = h_steps.numpy().view(np.uint32)
+    a_ids = h_ids.numpy().view(np.uint32)
+    total_ev, total_t, d2h = 0, 0.0, 0
+    for j in range(jobs + 1):  # the first job warms the allocator and is not counted
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net = snn.Network(dict(cfg, seed=100 + j), raster_capacity=cap, stream=stream)
+        got = 0
+        for _ in range(JOB_TIMESTEPS // TIMESTEPS_PER_STEP):
+            net.step(TIMESTEPS_PER_STEP)
+            got += net.read_spikes_into(a_steps, a_ids)
+            net.clear_raster()
+        st = net.stats()
+        net.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if j > 0:
+            total_ev += st["rec_events"]
+            total_t += dt
+            d2h += got * 8 + ctypes.sizeof(snn.SnnStats)
+    h2d = ctypes.sizeof(snn.SnnConfig)
+    return {"value": total_ev / total_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": int(d2h / max(jobs, 1)),
+            "step": "one job: build + %d timesteps + raster readout every %d steps" % (JOB_TIMESTEPS,
+                                                                                       TIMESTEPS_PER_STEP),
+            "jobs": jobs}
+
+
+def _max_op(dist):
+    return None if dist is None else dist.ReduceOp.MAX
+
+
+def _sum_op(dist):
+    return None if dist is None else dist.ReduceOp.SUM
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--schedule", type=int, default=None)
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--e2e-jobs", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-grid", type=int, default=6)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--timing-every", type=int, default=10,
+                    help="time the kernels of every n-th simulated step with CUDA events")
+    ap.add_argument("--grid", type=int, default=24, help="modules per side (24 = the benchmark workload)")
+    ap.add_argument("--timesteps", type=int, default=TIMESTEPS_PER_STEP, help="simulated steps per bench step")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300":
+        _log("note: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

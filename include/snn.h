@@ -173,11 +173,12 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  * 0 = default.  Errors: SNN_EINVAL. */
 SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
 
-/* Kernel timing: when enabled, every delivery launch is bracketed by CUDA
- * events on the launching stream; snn_kernel_time returns the summed device
- * time (ms) and the number of delivery launches timed, and the same for the
- * neuron kernel.  Synchronises the stream of the last launch. */
-SNN_API snn_status snn_set_timing(snn_net* net, int32_t enable);
+/* Kernel timing: with every = n >= 1, the neuron and delivery launches of
+ * every n-th time step are bracketed by CUDA events on the launching stream
+ * (0 = off).  snn_kernel_time returns the summed device time (ms) and the
+ * number of timed launches of each kernel.  Synchronises the stream of the
+ * timed launches. */
+SNN_API snn_status snn_set_timing(snn_net* net, int32_t every);
 SNN_API snn_status snn_kernel_time(snn_net* net, double* deliver_ms, uint64_t* deliver_launches,
                            double* neuron_ms, uint64_t* neuron_launches);
 

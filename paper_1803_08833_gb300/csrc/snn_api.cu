@@ -78,7 +78,8 @@ struct snn_net {
     int schedule = 0;
     int block = 256;
     int grid = 0;
-    bool timing = false;
+    int timing_every = 0;
+    uint64_t step_calls = 0;
     EventRing ev_deliver, ev_neuron;
 };
 
@@ -439,18 +440,19 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     for (uint32_t k = 0; k < n_steps; ++k) {
         int slot = 0;
-        if (n->timing) {
+        const bool timed = n->timing_every > 0 && (n->step_calls++ % (uint64_t)n->timing_every) == 0;
+        if (timed) {
             snn_status st = timed_begin(n->ev_neuron, s, &slot);
             if (st != SNN_OK) return st;
         }
         CUDA_TRY(launch_neuron_step(n->v, s));
-        if (n->timing) {
+        if (timed) {
             snn_status st = timed_end(n->ev_neuron, s, slot);
             if (st == SNN_OK) st = timed_begin(n->ev_deliver, s, &slot);
             if (st != SNN_OK) return st;
         }
         CUDA_TRY(launch_deliver(n->v, n->schedule, n->block, n->grid, s));
-        if (n->timing) {
+        if (timed) {
             snn_status st = timed_end(n->ev_deliver, s, slot);
             if (st != SNN_OK) return st;
         }
@@ -650,9 +652,11 @@ snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
     return SNN_OK;
 }
 
-snn_status snn_set_timing(snn_net* n, int32_t enable) {
+snn_status snn_set_timing(snn_net* n, int32_t every) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
-    n->timing = enable != 0;
+    if (every < 0) return fail(SNN_EINVAL, "every must be >= 0");
+    n->timing_every = every;
+    n->step_calls = 0;
     return SNN_OK;
 }
 

@@ -22,40 +22,6 @@ __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Streaming 16 B load that does not allocate in L1 and marks the L2 line
-// evict-first: the synapse table is read once per spike and must not push
-// the delay ring out of L2.
-__device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
-    uint4 r;
-    asm volatile(
-        "{\n\t.reg .b64 pol;\n\t"
-        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
-        "ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], pol;\n\t}"
-        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-        : "l"(p));
-    return r;
-}
-__device__ __forceinline__ uint2 ld_stream_u2(const void* p) {
-    uint2 r;
-    asm volatile(
-        "{\n\t.reg .b64 pol;\n\t"
-        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
-        "ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], pol;\n\t}"
-        : "=r"(r.x), "=r"(r.y)
-        : "l"(p));
-    return r;
-}
-__device__ __forceinline__ uint32_t ld_stream_u1(const void* p) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .b64 pol;\n\t"
-        "createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n\t"
-        "ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], pol;\n\t}"
-        : "=r"(r)
-        : "l"(p));
-    return r;
-}
-
 // ---------------------------------------------------------------------------
 // Neuron update (Eq. 1-2).  Exact propagator over dt with the input of the step
 // added after the decay:
@@ -89,9 +55,75 @@ __device__ __forceinline__ bool lif_update(const NetView& v, float& V, float& c,
     return spike;
 }
 
+// Last block of the neuron kernel: exclusive prefix of the per-block spike
+// counts (block offsets) and the bookkeeping of the step.  Each warp scans a
+// contiguous range of blocks in 32-wide coalesced chunks.
+__device__ __forceinline__ void finish_step(const NetView& v, uint32_t t) {
+    constexpr int W = NEURON_THREADS / 32;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nb = v.nb;
+    const uint32_t range = (((nb + W - 1) / W) + 31) & ~31u;
+    const uint32_t b0 = warp * range, b1 = min(b0 + range, nb);
+    __shared__ uint32_t s_wtot[W];
+    __shared__ unsigned long long s_wext[W];
+    uint32_t tot = 0;
+    unsigned long long ext = 0;
+#pragma unroll 4
+    for (uint32_t b = b0 + lane; b < b1; b += 32) {
+        tot += __ldcg(v.blk_cnt + b);
+        ext += __ldcg(reinterpret_cast<const unsigned long long*>(v.blk_ext) + b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+        ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
+    }
+    if (lane == 0) {
+        s_wtot[warp] = tot;
+        s_wext[warp] = ext;
+    }
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    unsigned long long ext_total = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        if (w < (int)warp) base += s_wtot[w];
+        total += s_wtot[w];
+        ext_total += s_wext[w];
+    }
+    for (uint32_t c = b0; c < b1; c += 32) {
+        const uint32_t b = c + lane;
+        const uint32_t x = b < b1 ? __ldcg(v.blk_cnt + b) : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (b < b1) v.blk_off[b] = base + incl - x;
+        base += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    if (threadIdx.x == 0) {
+        DevState* st = v.st;
+        v.blk_off[nb] = total;
+        st->n_spk = total;
+        st->t_deliver = t;
+        st->raster_base = st->raster_count;
+        st->raster_count += total;
+        st->n_spikes += total;
+        st->rec_events += (uint64_t)total * v.K;
+        st->ext_events += ext_total;
+        st->t = t + 1;
+        st->done = 0;
+    }
+}
+
 __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
-    DevState* st = v.st;
-    const uint32_t t = *reinterpret_cast<volatile uint32_t*>(&st->t);
+    __shared__ uint32_t s_t;
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) s_t = v.st->t;  // one read per block, not per thread
+    __syncthreads();
+    const uint32_t t = s_t;
     const uint32_t slot = t % v.D;
     const uint32_t tid = threadIdx.x;
     const uint32_t base = blockIdx.x * NEURONS_PER_BLOCK + tid * NEURONS_PER_THREAD;
@@ -99,14 +131,15 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     int4* ring4 = reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base);
     const int4 I4 = *ring4;
     *ring4 = make_int4(0, 0, 0, 0);
-    float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
-    float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
-    uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
+    const float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
+    const float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
+    const uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
 
     float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
     float Cq[4] = {C4.x, C4.y, C4.z, C4.w};
     const int32_t Iq[4] = {I4.x, I4.y, I4.z, I4.w};
     uint32_t spk = 0, next_sum = 0, Rout = 0;
+    const uint32_t m0 = base % v.M;  // position of the first neuron inside its module
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t i = base + q;
@@ -117,7 +150,10 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
             for (uint32_t k = 0; k < v.pois_len; ++k) n_ext += (v.pois[k] <= (uint64_t)u.x) ? 1u : 0u;
             next_sum += n_ext;
             const bool forced = (uint64_t)u.y < v.imposed_thresh;
-            const bool exc = (i % v.M) < v.n_exc;
+            uint32_t mi = m0 + q;
+            if (mi >= v.M) mi -= v.M;  // M >= 1, so at most one wrap within 4 neurons unless M < 4
+            if (mi >= v.M) mi %= v.M;
+            const bool exc = mi < v.n_exc;
             const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
             if (lif_update(v, Vq[q], Cq[q], r, exc, I, forced)) spk |= 1u << q;
         }
@@ -141,7 +177,6 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     for (int o = 16; o > 0; o >>= 1) ext_w += __shfl_xor_sync(0xFFFFFFFFu, ext_w, o);
     __shared__ uint32_t s_wsum[NEURON_THREADS / 32];
     __shared__ uint32_t s_wext[NEURON_THREADS / 32];
-    __shared__ bool s_last;
     if (lane == 31) s_wsum[warp] = incl;
     if (lane == 0) s_wext[warp] = ext_w;
     __syncthreads();
@@ -163,64 +198,14 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
         v.blk_cnt[blockIdx.x] = btot;
         v.blk_ext[blockIdx.x] = bext;
         __threadfence();
-        const uint32_t ticket = atomicAdd(&st->done, 1u);
+        const uint32_t ticket = atomicAdd(&v.st->done, 1u);
         s_last = (ticket == gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
-
-    // Last block: offsets of every block's spikes (exclusive prefix) and the
-    // bookkeeping of the step.  All other blocks have published their counts.
+    // All other blocks have published their counts (each fenced before its ticket).
     __threadfence();
-    const uint32_t nb = v.nb;
-    const uint32_t per = (nb + NEURON_THREADS - 1) / NEURON_THREADS;
-    const uint32_t b0 = tid * per;
-    const uint32_t b1 = min(b0 + per, nb);
-    uint32_t local = 0;
-    unsigned long long lext = 0;
-    for (uint32_t b = b0; b < b1; ++b) {
-        local += __ldcg(v.blk_cnt + b);
-        lext += __ldcg(reinterpret_cast<const unsigned long long*>(v.blk_ext) + b);
-    }
-    uint32_t li = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, li, o);
-        if (lane >= (uint32_t)o) li += x;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lext += __shfl_xor_sync(0xFFFFFFFFu, lext, o);
-    __shared__ uint32_t s_tsum[NEURON_THREADS / 32];
-    __shared__ unsigned long long s_text[NEURON_THREADS / 32];
-    __syncthreads();
-    if (lane == 31) s_tsum[warp] = li;
-    if (lane == 0) s_text[warp] = lext;
-    __syncthreads();
-    uint32_t toff = 0, total = 0;
-    unsigned long long ext_total = 0;
-#pragma unroll
-    for (int w = 0; w < NEURON_THREADS / 32; ++w) {
-        if (w < (int)warp) toff += s_tsum[w];
-        total += s_tsum[w];
-        ext_total += s_text[w];
-    }
-    uint32_t run = toff + li - local;
-    for (uint32_t b = b0; b < b1; ++b) {
-        v.blk_off[b] = run;
-        run += __ldcg(v.blk_cnt + b);
-    }
-    if (tid == 0) {
-        v.blk_off[nb] = total;
-        st->n_spk = total;
-        st->t_deliver = t;
-        st->raster_base = st->raster_count;
-        st->raster_count += total;
-        st->n_spikes += total;
-        st->rec_events += (uint64_t)total * v.K;
-        st->ext_events += ext_total;
-        st->t = t + 1;
-        st->done = 0;
-    }
+    finish_step(v, t);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,61 +246,136 @@ __device__ __forceinline__ int32_t fx_weight(const NetView& v, float w) {
 __device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
 
-// Schedule 0: one warp per (spike, 128-synapse chunk); each lane handles 4
-// consecutive synapses with one 16 B target load, one 16 B (f32) or 8 B (bf16)
-// weight load and one 4 B delay load.
+// Per-launch header of the delivery kernels, read once per block.
+struct StepHeader {
+    uint32_t n_spk, t;
+    uint64_t rbase;
+};
+
+__device__ __forceinline__ StepHeader read_header(const NetView& v) {
+    __shared__ StepHeader s_h;
+    if (threadIdx.x == 0) {
+        s_h.n_spk = v.st->n_spk;
+        s_h.t = v.st->t_deliver;
+        s_h.rbase = v.st->raster_base;
+    }
+    __syncthreads();
+    return s_h;
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_u4(const void* p, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_u2(const void* p, uint64_t pol) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_u1(const void* p, uint64_t pol) {
+    uint32_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+constexpr int DELIVER_UNROLL = 4;
+
+// Schedule 0: warps over (spike, 128-synapse chunk) tasks; each lane handles 4
+// consecutive synapses (one 16 B target load, one 16 B f32 / 8 B bf16 weight
+// load, one 4 B delay load).  The task range is split statically over the
+// blocks (every chunk but a row's last has 128 synapses, so the split is even);
+// a block first stages the ids of its spikes in shared memory, then each warp
+// issues the loads of DELIVER_UNROLL tasks before their reductions, so several
+// independent table reads are in flight per warp.
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_deliver_warp(NetView v) {
-    extern __shared__ uint32_t s_off[];
-    const DevState* st = v.st;
-    const uint32_t n_spk = *reinterpret_cast<const volatile uint32_t*>(&st->n_spk);
-    if (n_spk == 0) return;
+    extern __shared__ uint32_t s_off[];  // nb + 1 block offsets, then blockDim.x staged ids
+    const StepHeader h = read_header(v);
+    if (h.n_spk == 0) return;
     const uint32_t nb = v.nb;
     for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) s_off[b] = v.blk_off[b];
-    const uint32_t t = st->t_deliver;
-    const uint64_t rbase = st->raster_base;
     __syncthreads();
+    write_raster(v, s_off, h.n_spk, h.t, h.rbase);
 
-    write_raster(v, s_off, n_spk, t, rbase);
-    const uint32_t slot0 = t % v.D;
-    const uint32_t lane = threadIdx.x & 31;
     const uint32_t chunks = (v.K + 127) >> 7;
-    const uint32_t n_tasks = n_spk * chunks;
-    const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < n_tasks; task += warps) {
-        const uint32_t j = task / chunks;
-        const uint32_t ch = task - j * chunks;
-        const uint32_t b = find_block(s_off, nb, j);
-        const uint32_t id = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
-        const uint32_t k0 = (ch << 7) + (lane << 2);
-        if (k0 >= v.K) continue;
-        const size_t e = (size_t)id * v.Kpad + k0;
-        const uint4 tg = ld_stream_u4(v.tgt + e);
-        float w[4];
-        if (BF16) {
-            const uint2 wb = ld_stream_u2(reinterpret_cast<const uint16_t*>(v.w) + e);
-            w[0] = bf16_lo(wb.x);
-            w[1] = bf16_hi(wb.x);
-            w[2] = bf16_lo(wb.y);
-            w[3] = bf16_hi(wb.y);
-        } else {
-            const uint4 wf = ld_stream_u4(reinterpret_cast<const float*>(v.w) + e);
-            w[0] = __uint_as_float(wf.x);
-            w[1] = __uint_as_float(wf.y);
-            w[2] = __uint_as_float(wf.z);
-            w[3] = __uint_as_float(wf.w);
+    if (chunks == 0) return;
+    const uint64_t n_tasks = (uint64_t)h.n_spk * chunks;
+    const uint64_t t0 = n_tasks * blockIdx.x / gridDim.x;
+    const uint64_t t1 = n_tasks * (blockIdx.x + 1) / gridDim.x;
+    if (t0 >= t1) return;
+    uint32_t* s_id = s_off + nb + 1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    const uint32_t slot0 = h.t % v.D;
+    const uint64_t pol = evict_first_policy();
+    const uint32_t j_last = (uint32_t)((t1 - 1) / chunks);
+
+    for (uint32_t jb = (uint32_t)(t0 / chunks); jb <= j_last; jb += blockDim.x) {
+        const uint32_t j = jb + threadIdx.x;
+        if (j <= j_last) {
+            const uint32_t b = find_block(s_off, nb, j);
+            s_id[threadIdx.x] = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
         }
-        const uint32_t dd = ld_stream_u1(v.d + e);
-        const uint32_t tq[4] = {tg.x, tg.y, tg.z, tg.w};
-        const uint32_t nvalid = min(4u, v.K - k0);
+        __syncthreads();
+        const uint64_t lo = max(t0, (uint64_t)jb * chunks);
+        const uint64_t hi = min(t1, (uint64_t)(jb + blockDim.x) * chunks);
+        for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)nwarps * DELIVER_UNROLL) {
+            uint4 tg[DELIVER_UNROLL];
+            float w[DELIVER_UNROLL][4];
+            uint32_t dd[DELIVER_UNROLL], nv[DELIVER_UNROLL];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if ((uint32_t)q < nvalid) {
-                uint32_t s = slot0 + ((dd >> (8 * q)) & 0xFFu);
-                if (s >= v.D) s -= v.D;
-                red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[q]));
+            for (int u = 0; u < DELIVER_UNROLL; ++u) {
+                const uint64_t task = tk + (uint64_t)u * nwarps;
+                nv[u] = 0;
+                if (task < hi) {
+                    const uint32_t jj = (uint32_t)(task / chunks);
+                    const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
+                    const uint32_t k0 = (ch << 7) + (lane << 2);
+                    if (k0 < v.K) {
+                        nv[u] = min(4u, v.K - k0);
+                        const size_t e = (size_t)s_id[jj - jb] * v.Kpad + k0;
+                        tg[u] = ld_u4(v.tgt + e, pol);
+                        if (BF16) {
+                            const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
+                            w[u][0] = bf16_lo(wb.x);
+                            w[u][1] = bf16_hi(wb.x);
+                            w[u][2] = bf16_lo(wb.y);
+                            w[u][3] = bf16_hi(wb.y);
+                        } else {
+                            const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
+                            w[u][0] = __uint_as_float(wf.x);
+                            w[u][1] = __uint_as_float(wf.y);
+                            w[u][2] = __uint_as_float(wf.z);
+                            w[u][3] = __uint_as_float(wf.w);
+                        }
+                        dd[u] = ld_u1(v.d + e, pol);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < DELIVER_UNROLL; ++u) {
+                const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if ((uint32_t)q < nv[u]) {
+                        uint32_t s = slot0 + ((dd[u] >> (8 * q)) & 0xFFu);
+                        if (s >= v.D) s -= v.D;
+                        red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[u][q]));
+                    }
+                }
             }
         }
+        __syncthreads();
     }
 }
 
@@ -324,17 +384,14 @@ __global__ void __launch_bounds__(256) k_deliver_warp(NetView v) {
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_deliver_thread(NetView v) {
     extern __shared__ uint32_t s_off[];
-    const DevState* st = v.st;
-    const uint32_t n_spk = *reinterpret_cast<const volatile uint32_t*>(&st->n_spk);
-    if (n_spk == 0) return;
+    const StepHeader h = read_header(v);
+    if (h.n_spk == 0) return;
     const uint32_t nb = v.nb;
     for (uint32_t b = threadIdx.x; b <= nb; b += blockDim.x) s_off[b] = v.blk_off[b];
-    const uint32_t t = st->t_deliver;
-    const uint64_t rbase = st->raster_base;
     __syncthreads();
-    write_raster(v, s_off, n_spk, t, rbase);
-    const uint32_t slot0 = t % v.D;
-    const uint64_t total = (uint64_t)n_spk * v.K;
+    write_raster(v, s_off, h.n_spk, h.t, h.rbase);
+    const uint32_t slot0 = h.t % v.D;
+    const uint64_t total = (uint64_t)h.n_spk * v.K;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     uint32_t cached_j = 0xFFFFFFFFu, id = 0;
     for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
@@ -361,6 +418,9 @@ cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of a delivery block: block offsets + staged spike ids.
+static size_t deliver_smem(uint32_t nb, int block) { return (size_t)(nb + 1 + block) * sizeof(uint32_t); }
+
 static const void* deliver_fn(int schedule, bool bf16) {
     if (schedule == 1) return bf16 ? (const void*)k_deliver_thread<true> : (const void*)k_deliver_thread<false>;
     return bf16 ? (const void*)k_deliver_warp<true> : (const void*)k_deliver_warp<false>;
@@ -371,14 +431,14 @@ int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)(nb + 1) * sizeof(uint32_t);
+    const size_t smem = deliver_smem(nb, block);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, deliver_fn(schedule, bf16), block, smem);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
 
 cudaError_t prepare_deliver(uint32_t nb) {
-    const size_t smem = (size_t)(nb + 1) * sizeof(uint32_t);
+    const size_t smem = deliver_smem(nb, 1024);
     if (smem <= 48 * 1024) return cudaSuccess;
     for (int sch = 0; sch < 2; ++sch)
         for (int b = 0; b < 2; ++b) {
@@ -390,7 +450,7 @@ cudaError_t prepare_deliver(uint32_t nb) {
 }
 
 cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s) {
-    const size_t smem = (size_t)(v.nb + 1) * sizeof(uint32_t);
+    const size_t smem = deliver_smem(v.nb, block);
     const bool bf16 = v.w_bf16 != 0;
     if (schedule == 1) {
         if (bf16)

@@ -278,8 +278,9 @@ class Network:
     def set_schedule(self, schedule: int, block: int = 0):
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
 
-    def set_timing(self, enable: bool):
-        check(load().snn_set_timing(self._h, 1 if enable else 0))
+    def set_timing(self, every: int):
+        """Bracket the kernels of every n-th step with CUDA events (0 = off)."""
+        check(load().snn_set_timing(self._h, int(every)))
 
     def kernel_time(self) -> dict:
         dm, nm = ctypes.c_double(), ctypes.c_double()

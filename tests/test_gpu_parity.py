@@ -259,3 +259,16 @@ def test_full_size_gauss_24x24_k1125(snn):
 
 def test_full_size_exp_24x24_k2250_bf16(snn):
     _full_size_check(snn, W.exp_24x24_k2250(seed=2, imposed_rate_hz=W.PAPER_RATE_EXP_HZ), n_rows=600)
+
+
+def test_kernel_timing_counts_sampled_launches(snn):
+    cfg = W.small(grid=3, M=100, K=60, seed=8, imposed_rate_hz=30.0)
+    with snn.Network(cfg) as net:
+        net.set_timing(3)
+        net.step(30)
+        kt = net.kernel_time()
+        assert kt["deliver_launches"] == 10 and kt["neuron_launches"] == 10
+        assert kt["deliver_ms"] > 0 and kt["neuron_ms"] > 0
+        net.set_timing(0)
+        net.step(5)
+        assert net.kernel_time()["deliver_launches"] == 10
