@@ -185,6 +185,32 @@ SNN_API snn_status snn_kernel_time(snn_net* net, double* deliver_ms, uint64_t* d
 /* Number of this library's kernel launches issued so far (all networks). */
 SNN_API uint64_t snn_launch_count(void);
 
+/* Target-module tables without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot let the library allocate
+ * device memory -- a process whose device memory belongs to a pool or arena
+ * that must not be fragmented behind its back, or a latency-critical loop
+ * that cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * It writes the same tables snn_build_network builds (see snn_get_cdf) into
+ * caller-owned DEVICE buffers: thresh and tgt_module of n_modules *
+ * max_offsets uint32 each (row m = source module m, entries j < counts[m]
+ * valid) and counts of n_modules uint32.  With all three NULL it only sets
+ * *max_offsets (host) and returns.  Async on `stream`.
+ * Scratch: a fixed array inside the library image (4 MiB of FP64 plus a
+ * 16 KiB offset list) that every GPU loading the library holds until the
+ * process exits; n_modules * max_offsets must be <= 524,288 and
+ * max_offsets <= 4,096, else SNN_EINVAL.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ * The first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress, with that device current); make it before any stream
+ * capture.  Calls share the scratch, so calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.  The scratch needs no clearing: every entry read is first
+ * written by the same call.
+ * Errors: SNN_EINVAL (bad description, sizes over the limit, partial
+ * outputs), SNN_ECUDA. */
+SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh, uint32_t* tgt_module,
+                                        uint32_t* counts, uint32_t* max_offsets, void* stream);
+
 SNN_API void snn_destroy(snn_net* net);
 SNN_API const char* snn_last_error(void);
 

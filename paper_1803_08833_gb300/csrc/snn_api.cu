@@ -57,6 +57,7 @@ struct EventRing {
 
 namespace snn {
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace snn
 
 struct snn_net {

@@ -89,5 +89,6 @@ int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16);
 cudaError_t prepare_deliver(uint32_t nb);
 
 void count_launch(uint64_t n);
+void set_last_error(const char* msg);  // message returned by snn_last_error()
 
 }  // namespace snn

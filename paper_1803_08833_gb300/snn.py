@@ -87,6 +87,7 @@ def load():
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
         "snn_kernel_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_double),
                                  P(ctypes.c_uint64)]),
+        "snn_build_cdf_static": (st, [P(SnnConfig), vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_launch_count": (ctypes.c_uint64, []),
         "snn_destroy": (None, [vp]),
         "snn_last_error": (ctypes.c_char_p, []),
