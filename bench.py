@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 METRIC = "synaptic events/s on 1 GB300, % of HBM roofline; served p50/p99 latency"
 UNIT = "synaptic events/s"
 BYTES_PER_EVENT = {"f32": 9, "bf16": 7}
+# neuron update: V, c (f32) and ref (u8) read and written, ring slot read and cleared
+NEURON_BYTES = 2 * (4 + 4 + 1) + 2 * 4
 TIMESTEPS_PER_STEP = 1000
 JOB_TIMESTEPS = 10000
 
@@ -147,9 +149,11 @@ def _reduce(dist, value, op):
     return float(t.item())
 
 
-def workload(seed=1, grid=24):
+def workload(seed=1, grid=24, K=None, layout="draw"):
     from paper_1803_08833_gb300 import workloads as W
-    cfg = W.gauss_24x24_k1125(seed=seed, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ)
+    cfg = W.gauss_24x24_k1125(seed=seed, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout=layout)
+    if K is not None:
+        cfg["K"] = K
     return W.patch(cfg, grid) if grid != 24 else cfg
 
 
@@ -242,7 +246,8 @@ def run_gpu(args):
         _build.build()
     _barrier(dist)
     torch.cuda.set_device(local)
-    cfg = workload(seed=1 + rank, grid=args.grid)
+    schedule = 3 if args.schedule is None else args.schedule
+    cfg = workload(seed=1 + rank, grid=args.grid, K=args.K, layout="grouped" if schedule == 3 else "draw")
     T = args.timesteps
     peak, peak_kind = _peaks()
     stream = torch.cuda.current_stream()
@@ -251,8 +256,7 @@ def run_gpu(args):
     net = snn.Network(cfg, raster_capacity=T * 20000)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t_build
-    if args.schedule is not None:
-        net.set_schedule(args.schedule, args.block)
+    net.set_schedule(schedule, args.block)
     net.set_timing(args.timing_every)
 
     for _ in range(args.warmup):
@@ -290,18 +294,32 @@ def run_gpu(args):
     dl = kt1["deliver_launches"] - kt0["deliver_launches"]
     dms = kt1["deliver_ms"] - kt0["deliver_ms"]
     nms = kt1["neuron_ms"] - kt0["neuron_ms"]
-    # algorithmic bytes per timed launch: events of the timed region / timesteps x 9 B
-    ev_per_launch = rec / (args.steps * T)
-    achieved = BYTES_PER_EVENT["f32"] * ev_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
+    pl = kt1["persistent_launches"] - kt0["persistent_launches"]
+    pms = kt1["persistent_ms"] - kt0["persistent_ms"]
+    # algorithmic bytes of the dominant kernel per launch / its mean CUDA-event duration
+    steps_timed = args.steps * T
     traffic = None
-    if NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() and NCU_TRAFFIC["bytes_per_event"]:
-        traffic = NCU_TRAFFIC["bytes_per_event"] * ev_per_launch
+    if pl > 0:  # persistent schedule: one launch = T steps of neuron update + delivery
+        kernel = ("%s<f32> (persistent: neuron update + delivery, %d steps per launch)"
+                  % ("k_run_steps_tiled" if schedule == 3 else "k_run_steps", T))
+        launches_timed = pl
+        alg_per_launch = (BYTES_PER_EVENT["f32"] * rec + NEURON_BYTES * net.N * steps_timed) / max(args.steps, 1)
+        achieved = alg_per_launch / (pms / pl / 1000.0) / 1e9 if pms > 0 else None
+        bytes_note = "9 B per recurrent event + %d B per neuron per step" % NEURON_BYTES
+    else:
+        kernel = "k_deliver_warp<f32>"
+        launches_timed = dl
+        alg_per_launch = BYTES_PER_EVENT["f32"] * rec / steps_timed
+        achieved = alg_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
+        bytes_note = "9 B per recurrent event"
+        if NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() and NCU_TRAFFIC["bytes_per_event"]:
+            traffic = NCU_TRAFFIC["bytes_per_event"] * rec / steps_timed
     net.set_timing(0)
 
     # end-to-end jobs through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(snn, cfg, args.e2e_jobs, stream)
+        e2e = run_e2e(snn, cfg, args.e2e_jobs, stream, schedule)
     net.close()
 
     cpu = None
@@ -325,16 +343,23 @@ def run_gpu(args):
                                      "spikes_per_timestep": spikes / (args.steps * T),
                                      "rate_hz": spikes / (args.steps * T) / net.N * 1000.0,
                                      "equivalent_events_per_s": (rec + ext) / (ms / 1000.0),
-                                     "neuron_kernel_us": 1000.0 * nms / max(dl, 1),
-                                     "deliver_kernel_us": 1000.0 * dms / max(dl, 1),
+                                     "schedule": schedule,
+                                     "table_layout": cfg["table_layout"],
+                                     "neuron_kernel_us": 1000.0 * nms / max(dl, 1) if dl else None,
+                                     "deliver_kernel_us": 1000.0 * dms / max(dl, 1) if dl else None,
+                                     "persistent_us_per_step": 1000.0 * pms / steps_timed if pl else None,
+                                     "neuron_phase_us": (s1["neuron_phase_ns"] - s0["neuron_phase_ns"]) / 1e3 / steps_timed
+                                     if pl else None,
+                                     "deliver_phase_us": (s1["deliver_phase_ns"] - s0["deliver_phase_ns"]) / 1e3 / steps_timed
+                                     if pl else None,
                                      "kernel_timing": "CUDA events around the kernels of every %d-th "
                                                       "simulated step of the timed region" % args.timing_every}),
-        "roofline": {"bound": "hbm", "kernel": "k_deliver_warp<f32>", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "bytes_per_event": BYTES_PER_EVENT["f32"],
+                     "algorithmic_bytes": bytes_note, "bytes_per_launch": alg_per_launch,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
-                     "launches_timed": dl},
+                     "launches_timed": launches_timed},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -344,7 +369,7 @@ def run_gpu(args):
     return 0
 
 
-def run_e2e(snn, cfg, jobs, stream):
+def run_e2e(snn, cfg, jobs, stream, schedule):
     """Whole jobs through the public API: build from the host description,
     simulate JOB_TIMESTEPS reading the raster into pinned host memory after
     every 1,000 steps, destroy.  Device-side inputs are never reused."""
@@ -362,6 +387,7 @@ def run_e2e(snn, cfg, jobs, stream):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         net = snn.Network(dict(cfg, seed=100 + j), raster_capacity=cap, stream=stream)
+        net.set_schedule(schedule)
         got = 0
         for _ in range(JOB_TIMESTEPS // TIMESTEPS_PER_STEP):
             net.step(TIMESTEPS_PER_STEP)
@@ -407,6 +433,7 @@ def main(argv=None):
     ap.add_argument("--timing-every", type=int, default=10,
                     help="time the kernels of every n-th simulated step with CUDA events")
     ap.add_argument("--grid", type=int, default=24, help="modules per side (24 = the benchmark workload)")
+    ap.add_argument("--K", type=int, default=None, help="out-degree override (profiling of the neuron update only)")
     ap.add_argument("--timesteps", type=int, default=TIMESTEPS_PER_STEP, help="simulated steps per bench step")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":

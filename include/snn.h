@@ -57,6 +57,7 @@ typedef enum snn_status {
 
 enum { SNN_KERNEL_GAUSS = 0, SNN_KERNEL_EXP = 1 };
 enum { SNN_WEIGHT_F32 = 0, SNN_WEIGHT_BF16 = 1 };
+enum { SNN_LAYOUT_DRAW = 0, SNN_LAYOUT_GROUPED = 1 };
 
 /* Network description; plain data, copied by snn_build_network. */
 typedef struct snn_config {
@@ -84,6 +85,10 @@ typedef struct snn_config {
     uint32_t fx_shift;           /* fixed-point quantum 2^-fx_shift mV, in [8, 24] */
     uint64_t seed;               /* Philox4x32-10 key */
     uint64_t raster_capacity;    /* device raster entries (spikes) kept before overflow */
+    int32_t table_layout;        /* SNN_LAYOUT_DRAW: row i holds synapses k = 0..K-1 in draw order;
+                                    SNN_LAYOUT_GROUPED: the same synapses stably grouped by target
+                                    module (stencil order), plus a per-row segment index; needed
+                                    by schedule 3 */
 } snn_config;
 
 typedef struct snn_stats {
@@ -93,6 +98,8 @@ typedef struct snn_stats {
     uint64_t ext_events;     /* external Poisson events received */
     uint64_t raster_count;   /* spikes recorded since the last snn_clear_raster */
     uint64_t raster_capacity;
+    uint64_t neuron_phase_ns;  /* schedule 2: GPU-timer time of the neuron phases (with their barrier) */
+    uint64_t deliver_phase_ns; /* schedule 2: same for the delivery phases */
 } snn_stats;
 
 typedef struct snn_net snn_net; /* opaque, library-owned */
@@ -132,7 +139,8 @@ SNN_API snn_status snn_read_spikes(snn_net* net, uint32_t* steps, uint32_t* ids,
 SNN_API snn_status snn_clear_raster(snn_net* net, void* stream);
 
 /* Counters of Sec. III-D's normalised cost: spikes, recurrent and external
- * ("total equivalent") synaptic events.  Synchronises `stream`. */
+ * ("total equivalent") synaptic events.  Synchronises `stream`.  Returns
+ * SNN_ETIMEOUT (after filling *out) if a device-side wait ran out. */
 SNN_API snn_status snn_get_stats(snn_net* net, snn_stats* out, void* stream);
 
 /* Dynamic state (V, c, refractory counters, delay ring, time, counters) as an
@@ -153,6 +161,13 @@ SNN_API snn_status snn_restore(snn_net* net, const void* host_buf, size_t n, voi
  *                   N int32 (row r = inputs of steps t with t % D == r); *t.
  *   snn_set_state:  overwrites V, c, ref (NULL keeps the current values). */
 SNN_API snn_status snn_get_table(snn_net* net, uint32_t* tgt, float* w, uint8_t* d, void* stream);
+/* Grouped layout only: segment starts of rows [first, first + count), each
+ * row `*stride` uint16 entries (stride = stencil size + 1): entry j is the
+ * position in the row of the first synapse to the source module's j-th
+ * in-grid stencil module (stencil order as in snn_get_cdf); entries from the
+ * module's stencil count on equal K.  With seg == NULL only *stride is set. */
+SNN_API snn_status snn_get_segments(snn_net* net, uint32_t first, uint32_t count, uint16_t* seg, uint32_t* stride,
+                                    void* stream);
 /* Rows [first, first + count) of the synapse table, laid out as snn_get_table
  * lays out the whole table.  Errors: SNN_EINVAL if the rows are out of range. */
 SNN_API snn_status snn_get_rows(snn_net* net, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
@@ -167,20 +182,50 @@ SNN_API snn_status snn_set_state(snn_net* net, const float* V, const float* c, c
 /* Sizes of the network: N neurons, K, D ring rows, bytes of device memory. */
 SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t* D, uint64_t* device_bytes);
 
-/* Delivery schedule.  schedule 0: one warp per (spike, 128-synapse chunk),
- * 16-byte vector loads; 1: one thread per synapse over the flattened
- * (spike, synapse) range.  block: threads per block (multiple of 32, <= 1024),
- * 0 = default.  Errors: SNN_EINVAL. */
+/* Execution schedule of snn_step.
+ *   0: two launches per time step (neuron kernel, then delivery kernel); the
+ *      delivery walks each spike's synapses one warp per 128-synapse chunk
+ *      with 16-byte vector loads.
+ *   1: as 0, but one thread per synapse over the flattened (spike, synapse)
+ *      range.
+ *   2: one cooperative (persistent) launch per snn_step call that runs all
+ *      n_steps time steps, with two grid barriers per step; the delivery is
+ *      that of schedule 0.  Every barrier wait is bounded (snn_set_wait_limit);
+ *      if one runs out the launch stops and later calls report SNN_ETIMEOUT.
+ *   3: as 2, but target-owned delivery: each CTA gathers, for a target module,
+ *      the row segments of the step's spikes that target it, accumulates them
+ *      in a shared-memory tile of (D - 1) x M int32 and adds the tile into the
+ *      ring with plain coalesced writes.  Needs table_layout =
+ *      SNN_LAYOUT_GROUPED and a tile that fits in shared memory.
+ * All schedules give bit-identical results.  block: threads per block of the
+ * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
+ * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
 SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
 
-/* Kernel timing: with every = n >= 1, the neuron and delivery launches of
- * every n-th time step are bracketed by CUDA events on the launching stream
- * (0 = off).  snn_kernel_time returns the summed device time (ms) and the
- * number of timed launches of each kernel.  Synchronises the stream of the
- * timed launches. */
+/* Kernel timing: with every = n >= 1, the launches of every n-th snn_step
+ * time step (schedules 0, 1) or every persistent launch (schedule 2) are
+ * bracketed by CUDA events on the launching stream (0 = off).
+ * snn_kernel_time returns, for `which` (SNN_TIMER_NEURON, SNN_TIMER_DELIVER,
+ * SNN_TIMER_PERSISTENT), the summed device time in ms and the number of timed
+ * launches.  Synchronises the stream of the timed launches. */
+enum { SNN_TIMER_NEURON = 0, SNN_TIMER_DELIVER = 1, SNN_TIMER_PERSISTENT = 2 };
 SNN_API snn_status snn_set_timing(snn_net* net, int32_t every);
-SNN_API snn_status snn_kernel_time(snn_net* net, double* deliver_ms, uint64_t* deliver_launches,
-                           double* neuron_ms, uint64_t* neuron_launches);
+SNN_API snn_status snn_kernel_time(snn_net* net, int32_t which, double* ms, uint64_t* launches);
+
+/* Bound of every device-side wait (the persistent kernel's grid barriers),
+ * in ns of the GPU's global timer; default 2e9 (2 s).  Errors: SNN_EINVAL
+ * for 0. */
+SNN_API snn_status snn_set_wait_limit(snn_net* net, uint64_t ns);
+
+/* Testing aid for the failure path: the persistent kernel's barriers expect
+ * `extra` arrivals beyond the grid, which never come, so every wait runs out
+ * after the wait limit and the launch reports SNN_ETIMEOUT.  0 = normal.
+ * Nothing faults or hangs: the waits are bounded. */
+SNN_API snn_status snn_set_barrier_extra(snn_net* net, uint32_t extra);
+
+/* Clears the sticky device error state (after SNN_ETIMEOUT).  The network's
+ * dynamic state is then undefined until snn_restore.  Synchronises. */
+SNN_API snn_status snn_clear_error(snn_net* net, void* stream);
 
 /* Number of this library's kernel launches issued so far (all networks). */
 SNN_API uint64_t snn_launch_count(void);

@@ -74,7 +74,7 @@ _MAP = {
     "t_ref_ms": "t_ref", "tau_c_ms": "tau_c", "g_c_mV": "g_c", "dt_ms": "dt",
     "J_ext_mV": "J_ext",
 }
-_IGNORED = {"raster_capacity", "weight_dtype"}
+_IGNORED = {"raster_capacity", "weight_dtype", "table_layout"}
 
 
 def params(cfg: dict) -> OrParams:

@@ -145,6 +145,104 @@ __global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __r
     *reinterpret_cast<uint32_t*>(dout + e) = d[0] | (d[1] << 8) | (d[2] << 16) | (d[3] << 24);
 }
 
+// Synapse (i, k): target, weight, delay and stencil index j of its target module.
+struct Draw {
+    uint32_t tgt, j, d;
+    float w;
+};
+
+__device__ __forceinline__ Draw draw_synapse(const BuildView& b, uint32_t i, uint32_t k, bool exc, const uint32_t* T,
+                                             const uint32_t* TM, uint32_t n) {
+    const U4 u = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
+    Draw r;
+    r.j = upper_index(T, n, u.x);
+    r.tgt = __ldg(TM + r.j) * b.M + __umulhi(u.y, b.M);
+    if (exc) {
+        r.w = __fadd_rn(b.w_lo, __fmul_rn(b.w_span, unit24(u.z)));
+        r.d = b.d_lo + __umulhi(u.w, b.d_span);
+    } else {
+        r.w = b.w_inh;
+        r.d = b.d_inh;
+    }
+    return r;
+}
+
+// Grouped layout: one warp per row.  Pass 1 counts the row's synapses per
+// stencil entry j (shared-memory histogram) and writes the segment index
+// (exclusive prefix; entry n_s = K).  Pass 2 redraws the synapses in k order,
+// 32 at a time, and scatters each to cursor[j] + (its rank among the lanes of
+// the same j), so every segment keeps the draw order: the row is the stable
+// sort of the draw-order row by stencil index (= by target module).
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __restrict__ tgt,
+                                                     void* __restrict__ wout, uint8_t* __restrict__ dout) {
+    extern __shared__ uint32_t s_cur[];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* cur = s_cur + warp * (b.max_off + 1);
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (i >= b.N) return;  // warp-uniform
+    const uint32_t s = i / b.M;
+    const bool exc = (i - s * b.M) < b.n_exc;
+    const uint32_t* T = b.cdf_T + (size_t)s * b.max_off;
+    const uint32_t* TM = b.cdf_mod + (size_t)s * b.max_off;
+    const uint32_t n = __ldg(b.cdf_n + s);
+    for (uint32_t j = lane; j <= b.max_off; j += 32) cur[j] = 0;
+    __syncwarp();
+    for (uint32_t k = lane; k < b.K; k += 32) {
+        const U4 u = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
+        atomicAdd(&cur[upper_index(T, n, u.x)], 1u);
+    }
+    __syncwarp();
+    // exclusive prefix over the n bins, 32 at a time
+    uint16_t* seg = b.segidx + (size_t)i * (b.max_off + 1);
+    uint32_t run = 0;
+    for (uint32_t j0 = 0; j0 < n; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        const uint32_t x = j < n ? cur[j] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (j < n) {
+            cur[j] = run + incl - x;
+            seg[j] = (uint16_t)(run + incl - x);
+        }
+        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    for (uint32_t j = n + lane; j <= b.max_off; j += 32) seg[j] = (uint16_t)b.K;
+    __syncwarp();
+    const size_t row = (size_t)i * b.Kpad;
+    for (uint32_t k0 = 0; k0 < b.K; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        const bool active = k < b.K;
+        Draw r{0u, 0xFFFFFFFFu, 0u, 0.0f};
+        if (active) r = draw_synapse(b, i, k, exc, T, TM, n);
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, r.j);
+        if (active) {
+            const uint32_t pos = cur[r.j] + __popc(peers & ((1u << lane) - 1u));
+            tgt[row + pos] = r.tgt;
+            if (BF16)
+                reinterpret_cast<__nv_bfloat16*>(wout)[row + pos] = __float2bfloat16_rn(r.w);
+            else
+                reinterpret_cast<float*>(wout)[row + pos] = r.w;
+            dout[row + pos] = (uint8_t)r.d;
+        }
+        __syncwarp();
+        if (active && lane == (uint32_t)(__ffs(peers) - 1)) cur[r.j] += __popc(peers);
+        __syncwarp();
+    }
+    for (uint32_t k = b.K + lane; k < b.Kpad; k += 32) {  // padding entries
+        tgt[row + k] = 0u;
+        if (BF16)
+            reinterpret_cast<__nv_bfloat16*>(wout)[row + k] = __float2bfloat16_rn(0.0f);
+        else
+            reinterpret_cast<float*>(wout)[row + k] = 0.0f;
+        dout[row + k] = 0u;
+    }
+}
+
 __global__ void k_init_state(BuildView b, float* __restrict__ V, float* __restrict__ c,
                              uint8_t* __restrict__ ref) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,6 +271,24 @@ cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint
         k_gen_synapses<true><<<(unsigned)blocks, 256, 0, s>>>(b, tgt, w, d);
     else
         k_gen_synapses<false><<<(unsigned)blocks, 256, 0, s>>>(b, tgt, w, d);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s) {
+    if (b.N == 0 || b.Kpad == 0) return cudaSuccess;
+    const int warps = 8;
+    const size_t smem = (size_t)warps * (b.max_off + 1) * sizeof(uint32_t);
+    const void* fn = b.w_bf16 ? (const void*)k_gen_grouped<true> : (const void*)k_gen_grouped<false>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (b.N + warps - 1) / warps;
+    if (b.w_bf16)
+        k_gen_grouped<true><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
+    else
+        k_gen_grouped<false><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -1,0 +1,208 @@
+// device_common.cuh -- device functions shared by the per-step kernels and
+// the persistent multi-step kernel.
+#pragma once
+
+#include "philox.cuh"
+#include "snn_internal.h"
+
+namespace snn {
+
+__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Neuron update (Eq. 1-2).  Exact propagator over dt with the input of the step
+// added after the decay:
+//   V <- ((V - E) a_m + E) - k_c c + I 2^-fx,   c <- c a_c,
+// a_m = exp(-dt/tau_m), a_c = exp(-dt/tau_c),
+// k_c = g_c tau_m tau_c / (tau_c - tau_m) (exp(-dt/tau_c) - exp(-dt/tau_m)).
+// While refractory V is held at V_r and the input is discarded.  A spike
+// (V > V_th, or a forced spike) resets V, starts the refractory count and,
+// for excitatory neurons, adds alpha_c to c.
+__device__ __forceinline__ bool lif_update(const NetView& v, float& V, float& c, uint32_t& ref, bool exc,
+                                           int32_t I, bool forced) {
+    const bool was_ref = ref > 0;
+    if (was_ref) {
+        ref -= 1;
+        V = v.V_reset;
+    } else {
+        float x = __fsub_rn(V, v.E);
+        x = __fmul_rn(x, v.a_m);
+        x = __fadd_rn(x, v.E);
+        x = __fsub_rn(x, __fmul_rn(v.kc, c));
+        x = __fadd_rn(x, __fmul_rn(__int2float_rn(I), v.in_scale));
+        V = x;
+    }
+    c = __fmul_rn(c, v.a_c);
+    const bool spike = !was_ref && (V > v.V_th || forced);
+    if (spike) {
+        V = v.V_reset;
+        ref = v.ref_steps;
+        if (exc) c = __fadd_rn(c, v.alpha_c);
+    }
+    return spike;
+}
+
+// External Poisson count: #{k : P[k] <= u}.  `tab` (shared memory) holds the
+// stored thresholds (all <= 2^32 - 2) padded to `pad` (a power of two, 0 if
+// there is no drive) with 0xFFFFFFFF; with u clamped to 2^32 - 2 the padding
+// never counts.  Branch-free binary search; the table sits in shared memory
+// because lanes index it divergently.
+__device__ __forceinline__ uint32_t poisson_count(const uint32_t* tab, uint32_t pad, uint32_t u) {
+    const uint32_t x = min(u, 0xFFFFFFFEu);
+    uint32_t pos = 0;
+    for (uint32_t step = pad >> 1; step >= 1; step >>= 1)
+        if (tab[pos + step - 1] <= x) pos += step;
+    if (pad && tab[pos] <= x) pos += 1;
+    return pos;
+}
+
+// Copies the Poisson table into shared memory (call from every thread, then sync).
+__device__ __forceinline__ void load_poisson_table(const NetView& v, uint32_t* s_pois) {
+    for (uint32_t k = threadIdx.x; k < (uint32_t)MAX_POIS; k += blockDim.x) s_pois[k] = v.pois32[k];
+}
+
+// Updates neurons base .. base+3 (base a multiple of 4, < Npad) for step t:
+// reads and clears their ring slot, draws their external input, integrates.
+// Returns a 4-bit spike mask; adds the external events to `ext`.  The four
+// Philox draws are computed first, unconditionally (neurons past N are
+// padding and are not updated), so their dependency chains interleave.
+__device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
+                                                uint32_t slot, uint32_t& ext) {
+    // The slot was last written by other SMs' L2 reductions: read it at L2 (.cg).
+    int4* ring4 = reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base);
+    const int4 I4 = __ldcg(ring4);
+    const float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
+    const float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
+    const uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
+    U4 u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = philox4x32_10(base + q, t, TAG_DRIVE, 0u, v.key0, v.key1);
+    *ring4 = make_int4(0, 0, 0, 0);
+    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
+    float Cq[4] = {C4.x, C4.y, C4.z, C4.w};
+    const int32_t Iq[4] = {I4.x, I4.y, I4.z, I4.w};
+    uint32_t spk = 0, Rout = 0;
+    uint32_t mi = base % v.M;  // position of neuron `base` inside its module
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t i = base + q;
+        uint32_t r = (R4 >> (8 * q)) & 0xFFu;
+        const uint32_t n_ext = poisson_count(s_pois, v.pois_pad, u[q].x);
+        const bool forced = (uint64_t)u[q].y < v.imposed_thresh;
+        const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
+        float Vn = Vq[q], Cn = Cq[q];
+        uint32_t rn = r;
+        const bool s = lif_update(v, Vn, Cn, rn, mi < v.n_exc, I, forced);
+        if (i < v.N) {
+            ext += n_ext;
+            Vq[q] = Vn;
+            Cq[q] = Cn;
+            r = rn;
+            if (s) spk |= 1u << q;
+        }
+        Rout |= r << (8 * q);
+        mi += 1;
+        if (mi >= v.M) mi = 0;
+    }
+    *reinterpret_cast<float4*>(v.V + base) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+    *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
+    *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
+    return spk;
+}
+
+// ---------------------------------------------------------------------------
+// Delivery helpers.
+
+__device__ __forceinline__ int32_t fx_weight(const NetView& v, float w) {
+    return __float2int_rn(__fmul_rn(w, v.w_scale));
+}
+__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
+
+// The synapse table is read once per spike: no L1 allocation, and an L2
+// evict-first policy so the streamed table does not push the ring out of L2.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_u4(const void* p, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint2 ld_u2(const void* p, uint64_t pol) {
+    uint2 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+__device__ __forceinline__ uint32_t ld_u1(const void* p, uint64_t pol) {
+    uint32_t r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+    return r;
+}
+
+constexpr int DELIVER_UNROLL = 4;
+
+// One warp delivers up to DELIVER_UNROLL tasks (spike, 128-synapse chunk):
+// task tk + u * tstride for u < DELIVER_UNROLL, each below `hi`.  ids[j - j0]
+// gives the neuron of staged spike j.  Each lane loads 4 consecutive synapses
+// of every task first (16 B targets, 16 B f32 or 8 B bf16 weights, 4 B
+// delays), then issues the reductions.
+template <bool BF16>
+__device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
+                                              uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
+                                              uint32_t lane, uint64_t pol) {
+    uint4 tg[DELIVER_UNROLL];
+    float w[DELIVER_UNROLL][4];
+    uint32_t dd[DELIVER_UNROLL], nv[DELIVER_UNROLL];
+#pragma unroll
+    for (int u = 0; u < DELIVER_UNROLL; ++u) {
+        const uint64_t task = tk + (uint64_t)u * tstride;
+        nv[u] = 0;
+        if (task < hi) {
+            const uint32_t jj = (uint32_t)(task / chunks);
+            const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
+            const uint32_t k0 = (ch << 7) + (lane << 2);
+            if (k0 < v.K) {
+                nv[u] = min(4u, v.K - k0);
+                const size_t e = (size_t)ids[jj - j0] * v.Kpad + k0;
+                tg[u] = ld_u4(v.tgt + e, pol);
+                if (BF16) {
+                    const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
+                    w[u][0] = bf16_lo(wb.x);
+                    w[u][1] = bf16_hi(wb.x);
+                    w[u][2] = bf16_lo(wb.y);
+                    w[u][3] = bf16_hi(wb.y);
+                } else {
+                    const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
+                    w[u][0] = __uint_as_float(wf.x);
+                    w[u][1] = __uint_as_float(wf.y);
+                    w[u][2] = __uint_as_float(wf.z);
+                    w[u][3] = __uint_as_float(wf.w);
+                }
+                dd[u] = ld_u1(v.d + e, pol);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < DELIVER_UNROLL; ++u) {
+        const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if ((uint32_t)q < nv[u]) {
+                uint32_t s = slot0 + ((dd[u] >> (8 * q)) & 0xFFu);
+                if (s >= v.D) s -= v.D;
+                red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[u][q]));
+            }
+        }
+    }
+}
+
+}  // namespace snn

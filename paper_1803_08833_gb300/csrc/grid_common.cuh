@@ -1,0 +1,140 @@
+// grid_common.cuh -- grid-wide helpers of the persistent (cooperative) kernels.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace snn {
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t x;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(x) : "l"(p) : "memory");
+    return x;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Returns
+// false if this CTA's wait ran out or another CTA reported an error.
+__device__ inline bool grid_barrier(const NetView& v, uint32_t& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DevState* st = v.st;
+        int ok = 1;
+        __threadfence();  // publish this CTA's writes before arriving
+        const uint32_t expected = gridDim.x + v.barrier_extra;
+        const uint32_t arrived = atomicAdd(&st->bar_count, 1u);
+        if (arrived == expected - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            const uint64_t start = global_ns();
+            while (ld_acquire(&st->bar_gen) == gen) {
+                if (global_ns() - start > v.wait_limit_ns) {
+                    atomicOr(&st->err, ERR_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        gen += 1;
+        if (ld_acquire(&st->err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Exclusive prefix of cnt[0..n) into out[0..n], out[n] = total (one block of
+// at most 1024 threads).
+__device__ inline void block_exclusive_scan(const uint32_t* cnt, uint32_t n, uint32_t* out) {
+    __shared__ uint32_t s_w[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = min(threadIdx.x * per, n), b = min(a + per, n);
+    uint32_t local = 0;
+    for (uint32_t i = a; i < b; ++i) local += __ldcg(cnt + i);
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+        if (w < warp) base += s_w[w];
+        total += s_w[w];
+    }
+    uint32_t run = base + incl - local;
+    for (uint32_t i = a; i < b; ++i) {
+        out[i] = run;
+        run += __ldcg(cnt + i);
+    }
+    if (threadIdx.x == 0) out[n] = total;
+    __syncthreads();
+}
+
+// Neuron id of staged spike j: CTA by binary search over the CTA offsets,
+// warp by a scan of that CTA's W warp offsets, then the warp's segment.
+template <int W>
+__device__ __forceinline__ uint32_t spike_id(const NetView& v, const uint32_t* s_cta, const uint32_t* s_woff,
+                                             uint32_t j, uint32_t Q, uint32_t TW) {
+    uint32_t lo = 0, hi = gridDim.x;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_cta[mid] <= j)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const uint32_t jl = j - s_cta[lo];
+    uint32_t w = 0;
+#pragma unroll
+    for (uint32_t k = 1; k < (uint32_t)W; ++k)
+        if (s_woff[lo * W + k] <= jl) w = k;
+    const uint32_t wg = lo * W + w;
+    const uint32_t qa = (uint32_t)((uint64_t)Q * wg / TW);
+    return __ldcg(v.seg + ((size_t)qa << 2) + (jl - s_woff[wg]));
+}
+
+// In-place exclusive prefix of s[0..n) in shared memory, s[n] = total.
+__device__ inline void block_scan_inplace(uint32_t* s, uint32_t n) {
+    __shared__ uint32_t s_w2[32];
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = min(threadIdx.x * per, n), b = min(a + per, n);
+    uint32_t local = 0;
+    for (uint32_t i = a; i < b; ++i) local += s[i];
+    uint32_t incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) s_w2[warp] = incl;
+    __syncthreads();
+    uint32_t base = 0, total = 0;
+    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
+        if (w < warp) base += s_w2[w];
+        total += s_w2[w];
+    }
+    uint32_t run = base + incl - local;
+    for (uint32_t i = a; i < b; ++i) {
+        const uint32_t x = s[i];
+        s[i] = run;
+        run += x;
+    }
+    if (threadIdx.x == 0) s[n] = total;
+    __syncthreads();
+}
+
+}  // namespace snn

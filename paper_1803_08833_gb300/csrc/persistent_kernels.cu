@@ -1,0 +1,199 @@
+// persistent_kernels.cu -- many simulation time steps in one cooperative launch.
+//
+// The per-step kernels pay, every 1 ms step, two launches and the latency
+// chains of their prologue/epilogue.  k_run_steps keeps one resident grid for
+// n steps: phase N (flow steps 1, 4-6: every neuron integrates, spikes are
+// compacted in id order per warp-owned neuron range), a grid barrier, phase D
+// (flow steps 2-4: the spikes' synapses are added into the delay ring, raster
+// entries written), a grid barrier.  Results are identical to the per-step
+// kernels: the same update, the same (step, id) spike order, the same integer
+// sums.
+//
+// Every barrier wait is bounded by v.wait_limit_ns of %globaltimer: a CTA that
+// waits longer sets ERR_BARRIER_TIMEOUT in the device state and returns, and
+// every CTA stops at its next barrier once the flag is set; the host reports
+// SNN_ETIMEOUT.
+#include "grid_common.cuh"
+
+namespace snn {
+
+template <bool BF16>
+__global__ void __launch_bounds__(PERSIST_THREADS) k_run_steps(NetView v, uint32_t n_steps) {
+    extern __shared__ uint32_t smem[];
+    const uint32_t G = gridDim.x, TW = G * PERSIST_WARPS;
+    uint32_t* s_cta = smem;             // G + 1 CTA offsets
+    uint32_t* s_woff = smem + G + 1;    // TW warp offsets (CTA-local)
+    uint32_t* s_id = s_woff + TW;       // staged spike ids
+    __shared__ uint32_t s_t0, s_wcnt[PERSIST_WARPS];
+    __shared__ unsigned long long s_rc0;
+    __shared__ uint32_t s_ext[PERSIST_WARPS];
+    __shared__ uint32_t s_pois[MAX_POIS];
+    load_poisson_table(v, s_pois);
+    uint32_t gen = 0;
+    if (threadIdx.x == 0) {
+        s_t0 = v.st->t;
+        s_rc0 = v.st->raster_count;
+        gen = v.st->bar_gen;
+    }
+    __syncthreads();
+    const uint32_t t0 = s_t0;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wg = blockIdx.x * PERSIST_WARPS + warp;
+    const uint32_t Q = v.Npad >> 2;
+    const uint32_t qa = (uint32_t)((uint64_t)Q * wg / TW);
+    const uint32_t qb = (uint32_t)((uint64_t)Q * (wg + 1) / TW);
+    const uint64_t pol = evict_first_policy();
+    const uint32_t chunks = (v.K + 127) >> 7;
+    uint64_t rc = s_rc0;
+    uint64_t spikes = 0;
+    uint32_t ext = 0;
+    uint32_t done = 0;
+
+    uint64_t ph_n = 0, ph_d = 0, stamp = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) stamp = global_ns();
+    for (uint32_t step = 0; step < n_steps; ++step) {
+        const uint32_t t = t0 + step;
+        const uint32_t slot = t % v.D;
+        // ---- phase N: this warp's neurons, 4 per lane, spikes compacted in id order
+        uint32_t run = 0;
+        for (uint32_t qc = qa; qc < qb; qc += 32) {
+            const uint32_t q = qc + lane;
+            uint32_t spk = 0;
+            if (q < qb) spk = update_quad(v, s_pois, q << 2, t, slot, ext);
+            const uint32_t cnt = __popc(spk);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            uint32_t pos = (qa << 2) + run + incl - cnt;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (spk & (1u << b)) v.seg[pos++] = (q << 2) + b;
+            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+        if (lane == 0) s_wcnt[warp] = run;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int w = 0; w < PERSIST_WARPS; ++w) {
+                v.woff[blockIdx.x * PERSIST_WARPS + w] = acc;
+                acc += s_wcnt[w];
+            }
+            v.cta_cnt[blockIdx.x] = acc;
+        }
+        if (!grid_barrier(v, gen)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint64_t now = global_ns();
+            ph_n += now - stamp;
+            stamp = now;
+        }
+
+        // ---- phase D: global offsets, raster, delivery
+        block_exclusive_scan(v.cta_cnt, G, s_cta);
+        for (uint32_t i = threadIdx.x; i < TW; i += blockDim.x) s_woff[i] = __ldcg(v.woff + i);
+        __syncthreads();
+        const uint32_t total = s_cta[G];
+        for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
+            const uint64_t r = rc + j;
+            if (r >= v.raster_cap) break;
+            v.raster_t[r] = t;
+            v.raster_id[r] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW);
+        }
+        if (chunks > 0 && total > 0) {
+            const uint64_t n_tasks = (uint64_t)total * chunks;
+            const uint64_t ta = n_tasks * blockIdx.x / G;
+            const uint64_t tb = n_tasks * (blockIdx.x + 1) / G;
+            if (ta < tb) {
+                const uint32_t slot0 = t % v.D;
+                const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
+                for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
+                    const uint32_t j = jb + threadIdx.x;
+                    if (j <= j_last) s_id[threadIdx.x] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW);
+                    __syncthreads();
+                    const uint64_t lo = max(ta, (uint64_t)jb * chunks);
+                    const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
+                    for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
+                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol);
+                    __syncthreads();
+                }
+            }
+        }
+        rc += total;
+        spikes += total;
+        if (!grid_barrier(v, gen)) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const uint64_t now = global_ns();
+            ph_d += now - stamp;
+            stamp = now;
+        }
+        done = step + 1;
+    }
+
+    // ---- epilogue: counters of the launch
+    uint32_t e = ext;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    if (lane == 0) s_ext[warp] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long be = 0;
+        for (int w = 0; w < PERSIST_WARPS; ++w) be += s_ext[w];
+        atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->ext_events), be);
+        if (blockIdx.x == 0 && done == n_steps) {
+            DevState* st = v.st;
+            st->t = t0 + n_steps;
+            st->raster_count = rc;
+            st->n_spikes += spikes;
+            st->rec_events += spikes * v.K;
+            st->n_spk = 0;
+            st->phase_ns[0] += ph_n;
+            st->phase_ns[1] += ph_d;
+        }
+    }
+}
+
+static const void* persistent_fn(bool bf16) {
+    return bf16 ? (const void*)k_run_steps<true> : (const void*)k_run_steps<false>;
+}
+
+static size_t persistent_smem(int grid) {
+    return (size_t)(grid + 1 + grid * PERSIST_WARPS + PERSIST_THREADS) * sizeof(uint32_t);
+}
+
+// Co-resident grid: occupancy per SM x SMs, with the grid-dependent shared
+// memory accounted for (largest grid that still fits).
+int persistent_grid(bool bf16) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int per_sm = 8; per_sm >= 1; --per_sm) {
+        const int grid = per_sm * sms;
+        int fit = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persistent_fn(bf16), PERSIST_THREADS,
+                                                          persistent_smem(grid)) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (fit >= per_sm) return grid;
+    }
+    return sms;
+}
+
+cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {
+    const size_t smem = persistent_smem(grid);
+    const void* fn = persistent_fn(v.w_bf16 != 0);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    NetView vv = v;
+    uint32_t ns = n_steps;
+    void* args[] = {&vv, &ns};
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
+    count_launch(1);
+    return e;
+}
+
+}  // namespace snn

@@ -8,6 +8,7 @@
 #include "snn.h"
 #include "snn_internal.h"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -78,10 +79,12 @@ struct snn_net {
 
     int schedule = 0;
     int block = 256;
-    int grid = 0;
+    int grid = 0;       // delivery grid of schedules 0 and 1
+    int pgrid = 0;      // persistent grid (schedule 2)
+    int tgrid = 0;      // tiled persistent grid (schedule 3), 0 if unavailable
     int timing_every = 0;
     uint64_t step_calls = 0;
-    EventRing ev_deliver, ev_neuron;
+    EventRing ev_deliver, ev_neuron, ev_persist;
 };
 
 namespace {
@@ -153,6 +156,8 @@ snn_status validate(const snn_config* c) {
     if (c->weight_dtype != SNN_WEIGHT_F32 && c->weight_dtype != SNN_WEIGHT_BF16)
         return fail(SNN_EINVAL, "weight_dtype must be SNN_WEIGHT_F32 or SNN_WEIGHT_BF16");
     if (c->fx_shift < 8 || c->fx_shift > 24) return fail(SNN_EINVAL, "fx_shift must be in [8, 24]");
+    if (c->table_layout != SNN_LAYOUT_DRAW && c->table_layout != SNN_LAYOUT_GROUPED)
+        return fail(SNN_EINVAL, "table_layout must be SNN_LAYOUT_DRAW or SNN_LAYOUT_GROUPED");
     if (!std::isfinite(c->w_exc_lo) || !std::isfinite(c->w_exc_hi) || !std::isfinite(c->w_inh) ||
         !std::isfinite(c->V_th_mV) || !std::isfinite(c->V_reset_mV) || !std::isfinite(c->E_mV) ||
         !std::isfinite(c->J_ext_mV) || !std::isfinite(c->g_c_mV) || !std::isfinite(c->alpha_c))
@@ -224,14 +229,22 @@ snn_status derive(snn_net* n) {
             const double x = std::floor(F * 4294967296.0);
             if (x >= 4294967295.0) break;
             if (k >= (uint32_t)MAX_POIS) return fail(SNN_EINVAL, "ext_rate_hz * dt too large for the Poisson table");
-            v.pois[v.pois_len++] = (uint64_t)x;
+            v.pois32[v.pois_len++] = (uint32_t)x;
             pmf = pmf * mean / (double)(k + 1);
         }
     }
+    v.pois_pad = 0;
+    if (v.pois_len) {
+        v.pois_pad = 1;
+        while (v.pois_pad < v.pois_len) v.pois_pad <<= 1;
+    }
+    for (uint32_t k = v.pois_len; k < (uint32_t)MAX_POIS; ++k) v.pois32[k] = 0xFFFFFFFFu;
     double pf = (double)c.imposed_rate_hz * dt / 1000.0;
     if (pf > 1.0) pf = 1.0;
     v.imposed_thresh = (uint64_t)std::floor(pf * 4294967296.0);
     v.raster_cap = c.raster_capacity;
+    v.wait_limit_ns = 2000000000ull;
+    v.barrier_extra = 0;
     return SNN_OK;
 }
 
@@ -261,6 +274,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     n->max_off = (uint32_t)(off.size() / 2);
 
     NetView& v = n->v;
+    n->pgrid = persistent_grid(v.w_bf16 != 0);
     const size_t nsyn = (size_t)n->N * n->Kpad;
     const size_t wbytes = v.w_bf16 ? 2 : 4;
     struct Req {
@@ -281,13 +295,51 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         {(void**)&v.raster_t, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.raster_id, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.st, sizeof(DevState)},
+        {(void**)&v.woff, (size_t)n->pgrid * PERSIST_WARPS * 4},
+        {(void**)&v.cta_cnt, (size_t)n->pgrid * 4},
         {(void**)&n->cdf_T, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_mod, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_n, (size_t)n->n_modules * 4},
+        {(void**)&v.mod_cnt, (size_t)n->n_modules * 2 * 4},
+        {(void**)&v.seg_mod, (size_t)n->Npad * 4},
     };
     for (auto& r : reqs) {
         *r.p = dev_alloc(n, r.bytes);
         if (!*r.p) return fail(SNN_ENOMEM, "device allocation of %zu bytes failed", r.bytes);
+    }
+    const bool grouped = c.table_layout == SNN_LAYOUT_GROUPED;
+    uint16_t* segidx = nullptr;
+    v.n_modules = n->n_modules;
+    v.max_off = n->max_off;
+    v.seg_stride = n->max_off + 1;
+    if (grouped) {
+        // per-row segment index and, per target module, its incoming (source, stencil index) list
+        segidx = (uint16_t*)dev_alloc(n, (size_t)n->N * v.seg_stride * sizeof(uint16_t));
+        uint32_t* in_src = (uint32_t*)dev_alloc(n, (size_t)n->n_modules * n->max_off * 4);
+        uint32_t* in_j = (uint32_t*)dev_alloc(n, (size_t)n->n_modules * n->max_off * 4);
+        uint32_t* in_cnt = (uint32_t*)dev_alloc(n, (size_t)n->n_modules * 4);
+        if (!segidx || !in_src || !in_j || !in_cnt) return fail(SNN_ENOMEM, "device allocation of the segment index failed");
+        std::vector<uint32_t> h_src((size_t)n->n_modules * n->max_off, 0), h_j(h_src.size(), 0), h_cnt(n->n_modules, 0);
+        for (uint32_t sm = 0; sm < n->n_modules; ++sm) {
+            const int sx = (int)(sm % c.grid_w), sy = (int)(sm / c.grid_w);
+            uint32_t j = 0;
+            for (size_t o = 0; o < off.size(); o += 2) {
+                const int tx = sx + off[o], ty = sy + off[o + 1];
+                if (tx < 0 || ty < 0 || tx >= (int)c.grid_w || ty >= (int)c.grid_h) continue;
+                const uint32_t tm = (uint32_t)ty * c.grid_w + (uint32_t)tx;
+                const size_t slot = (size_t)tm * n->max_off + h_cnt[tm]++;
+                h_src[slot] = sm;
+                h_j[slot] = j++;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(in_src, h_src.data(), h_src.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(in_j, h_j.data(), h_j.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(in_cnt, h_cnt.data(), h_cnt.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+        v.segidx = segidx;
+        v.in_src = in_src;
+        v.in_j = in_j;
+        v.in_cnt = in_cnt;
     }
     // construction-only buffers (released at the end of the build)
     const size_t scratch_bytes = (size_t)n->n_modules * n->max_off * sizeof(double);
@@ -328,9 +380,13 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     b.cdf_T = n->cdf_T;
     b.cdf_mod = n->cdf_mod;
     b.cdf_n = n->cdf_n;
+    b.segidx = segidx;
 
     CUDA_TRY(launch_build_cdf(b, s));
-    CUDA_TRY(launch_gen_synapses(b, v.tgt, v.w, v.d, s));
+    if (grouped)
+        CUDA_TRY(launch_gen_grouped(b, v.tgt, v.w, v.d, s));
+    else
+        CUDA_TRY(launch_gen_synapses(b, v.tgt, v.w, v.d, s));
     CUDA_TRY(launch_init_state(b, v.V, v.c, v.ref, s));
     CUDA_TRY(cudaMemsetAsync(v.ring, 0, (size_t)n->D * n->Npad * 4, s));
     CUDA_TRY(cudaMemsetAsync(v.seg, 0, (size_t)n->Npad * 4, s));
@@ -352,6 +408,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     }
     n->device_bytes -= ((scratch_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);
     n->grid = deliver_default_grid(n->schedule, n->block, n->nb, v.w_bf16 != 0);
+    n->tgrid = grouped ? tiled_grid(v) : 0;
     return SNN_OK;
 }
 
@@ -439,6 +496,31 @@ snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_f
 snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     cudaStream_t s = (cudaStream_t)stream;
+    if (n->schedule >= 2) {
+        // one cooperative launch per call (in pieces of at most 2^20 steps)
+        for (uint32_t done = 0; done < n_steps;) {
+            const uint32_t m = std::min<uint32_t>(n_steps - done, 1u << 20);
+            CUDA_TRY(cudaMemsetAsync(&n->v.st->bar_count, 0, sizeof(uint32_t), s));
+            if (n->schedule == 3)
+                CUDA_TRY(cudaMemsetAsync(n->v.mod_cnt, 0, (size_t)n->n_modules * 2 * 4, s));
+            int slot = 0;
+            const bool timed = n->timing_every > 0;
+            if (timed) {
+                snn_status st = timed_begin(n->ev_persist, s, &slot);
+                if (st != SNN_OK) return st;
+            }
+            if (n->schedule == 3)
+                CUDA_TRY(launch_tiled(n->v, m, n->tgrid, s));
+            else
+                CUDA_TRY(launch_persistent(n->v, m, n->pgrid, s));
+            if (timed) {
+                snn_status st = timed_end(n->ev_persist, s, slot);
+                if (st != SNN_OK) return st;
+            }
+            done += m;
+        }
+        return SNN_OK;
+    }
     for (uint32_t k = 0; k < n_steps; ++k) {
         int slot = 0;
         const bool timed = n->timing_every > 0 && (n->step_calls++ % (uint64_t)n->timing_every) == 0;
@@ -474,6 +556,7 @@ snn_status snn_read_spikes(snn_net* n, uint32_t* steps, uint32_t* ids, size_t ca
     if (m && ids) CUDA_TRY(cudaMemcpyAsync(ids, n->v.raster_id, m * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     *n_out = m;
+    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out (error bits 0x%x)", ds.err);
     if (ds.raster_count > n->v.raster_cap)
         return fail(SNN_EOVERFLOW, "raster overflow: %llu spikes recorded, capacity %llu",
                     (unsigned long long)ds.raster_count, (unsigned long long)n->v.raster_cap);
@@ -498,6 +581,9 @@ snn_status snn_get_stats(snn_net* n, snn_stats* out, void* stream) {
     out->ext_events = ds.ext_events;
     out->raster_count = ds.raster_count;
     out->raster_capacity = n->v.raster_cap;
+    out->neuron_phase_ns = ds.phase_ns[0];
+    out->deliver_phase_ns = ds.phase_ns[1];
+    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out (error bits 0x%x)", ds.err);
     return SNN_OK;
 }
 
@@ -535,6 +621,20 @@ snn_status snn_get_rows(snn_net* n, uint32_t first, uint32_t count, uint32_t* tg
                                        cudaMemcpyDeviceToHost, s));
         }
     }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_get_segments(snn_net* n, uint32_t first, uint32_t count, uint16_t* seg, uint32_t* stride,
+                            void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (stride) *stride = n->v.seg_stride;
+    if (!seg) return SNN_OK;
+    if (!n->v.segidx) return fail(SNN_EINVAL, "the network was not built with the grouped layout");
+    if ((uint64_t)first + count > n->N) return fail(SNN_EINVAL, "rows out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(seg, n->v.segidx + (size_t)first * n->v.seg_stride,
+                             (size_t)count * n->v.seg_stride * sizeof(uint16_t), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SNN_OK;
 }
@@ -644,12 +744,18 @@ snn_status snn_restore(snn_net* n, const void* host_buf, size_t nbytes, void* st
 
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
-    if (schedule != 0 && schedule != 1) return fail(SNN_EINVAL, "schedule must be 0 or 1");
+    if (schedule < 0 || schedule > 3) return fail(SNN_EINVAL, "schedule must be 0, 1, 2 or 3");
+    if (schedule == 3 && n->cfg.table_layout != SNN_LAYOUT_GROUPED)
+        return fail(SNN_EINVAL, "schedule 3 needs a network built with table_layout = SNN_LAYOUT_GROUPED");
+    if (schedule == 3 && n->tgrid == 0)
+        return fail(SNN_EINVAL, "schedule 3: the (D - 1) x M delivery tile does not fit in shared memory");
     if (block == 0) block = 256;
     if (block < 32 || block > 256 || block % 32) return fail(SNN_EINVAL, "block must be a multiple of 32 in [32, 256]");
     n->schedule = schedule;
-    n->block = block;
-    n->grid = deliver_default_grid(schedule, block, n->nb, n->v.w_bf16 != 0);
+    if (schedule < 2) {
+        n->block = block;
+        n->grid = deliver_default_grid(schedule, block, n->nb, n->v.w_bf16 != 0);
+    }
     return SNN_OK;
 }
 
@@ -661,16 +767,38 @@ snn_status snn_set_timing(snn_net* n, int32_t every) {
     return SNN_OK;
 }
 
-snn_status snn_kernel_time(snn_net* n, double* deliver_ms, uint64_t* deliver_launches, double* neuron_ms,
-                           uint64_t* neuron_launches) {
+snn_status snn_kernel_time(snn_net* n, int32_t which, double* ms, uint64_t* launches) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
-    snn_status st = drain(n->ev_deliver);
-    if (st == SNN_OK) st = drain(n->ev_neuron);
+    EventRing* r = which == SNN_TIMER_NEURON ? &n->ev_neuron
+                 : which == SNN_TIMER_DELIVER ? &n->ev_deliver
+                 : which == SNN_TIMER_PERSISTENT ? &n->ev_persist : nullptr;
+    if (!r) return fail(SNN_EINVAL, "unknown timer %d", which);
+    snn_status st = drain(*r);
     if (st != SNN_OK) return st;
-    if (deliver_ms) *deliver_ms = n->ev_deliver.total_ms;
-    if (deliver_launches) *deliver_launches = n->ev_deliver.count;
-    if (neuron_ms) *neuron_ms = n->ev_neuron.total_ms;
-    if (neuron_launches) *neuron_launches = n->ev_neuron.count;
+    if (ms) *ms = r->total_ms;
+    if (launches) *launches = r->count;
+    return SNN_OK;
+}
+
+snn_status snn_set_wait_limit(snn_net* n, uint64_t ns) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (ns == 0) return fail(SNN_EINVAL, "the wait limit must be positive");
+    n->v.wait_limit_ns = ns;
+    return SNN_OK;
+}
+
+snn_status snn_set_barrier_extra(snn_net* n, uint32_t extra) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    n->v.barrier_extra = extra;
+    return SNN_OK;
+}
+
+snn_status snn_clear_error(snn_net* n, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemsetAsync(&n->v.st->err, 0, sizeof(uint32_t), s));
+    CUDA_TRY(cudaMemsetAsync(&n->v.st->bar_count, 0, sizeof(uint32_t), s));
+    CUDA_TRY(cudaStreamSynchronize(s));
     return SNN_OK;
 }
 
@@ -679,6 +807,7 @@ void snn_destroy(snn_net* n) {
     cudaDeviceSynchronize();
     destroy_events(n->ev_deliver);
     destroy_events(n->ev_neuron);
+    destroy_events(n->ev_persist);
     release_all(n);
     delete n;
 }

@@ -12,9 +12,12 @@ constexpr uint32_t TAG_DRIVE = 1u;  // (neuron i, step t): external Poisson coun
 constexpr uint32_t TAG_INIT = 2u;   // (neuron i, 0): initial membrane potential
 
 constexpr int NEURON_THREADS = 256;
+constexpr int PERSIST_THREADS = 256;                 // threads per CTA of the persistent kernel
+constexpr int PERSIST_WARPS = PERSIST_THREADS / 32;
+constexpr uint32_t ERR_BARRIER_TIMEOUT = 1u;         // DevState::err bits
 constexpr int NEURONS_PER_THREAD = 4;
 constexpr int NEURONS_PER_BLOCK = NEURON_THREADS * NEURONS_PER_THREAD;  // 1024
-constexpr int MAX_POIS = 48;
+constexpr int MAX_POIS = 64;  // Poisson table entries (padded to a power of two)
 constexpr uint32_t K_ALIGN = 8;  // rows padded to 8 synapses: 32 B f32 / 16 B bf16 / 8 B delay
 constexpr uint32_t MAX_NEURON_BLOCKS = 16384;
 
@@ -27,8 +30,11 @@ struct DevState {
     uint64_t raster_count;  // spikes recorded since the raster was cleared
     uint64_t raster_base;   // raster index of the first staged spike
     uint64_t n_spikes, rec_events, ext_events;
-    uint32_t err;
+    uint32_t err;        // sticky error bits (ERR_*)
+    uint32_t bar_count;  // grid-barrier arrivals (persistent kernel)
+    uint32_t bar_gen;    // grid-barrier generation
     uint32_t pad;
+    uint64_t phase_ns[2];  // persistent kernel, CTA 0: neuron phase + barrier, delivery phase + barrier
 };
 
 // Everything a kernel needs, passed by value (kernel parameter space).
@@ -37,9 +43,10 @@ struct NetView {
     uint32_t key0, key1;
     float a_m, a_c, kc, E, V_th, V_reset, alpha_c, in_scale, w_scale;
     int32_t J_ext_fx;
-    uint32_t pois_len;
+    uint32_t pois_len;  // stored thresholds
+    uint32_t pois_pad;  // pois_len rounded up to a power of two (0 if no drive)
     uint64_t imposed_thresh;
-    uint64_t pois[MAX_POIS];
+    uint32_t pois32[MAX_POIS];  // thresholds, then 0xFFFFFFFF padding
     int32_t w_bf16;
     // synapse table, rows of Kpad entries per neuron
     uint32_t* tgt;
@@ -59,6 +66,19 @@ struct NetView {
     uint32_t* raster_id;
     uint64_t raster_cap;
     DevState* st;
+    // persistent kernel: per-warp spike offsets within the CTA, per-CTA counts
+    uint32_t* woff;
+    uint32_t* cta_cnt;
+    uint64_t wait_limit_ns;   // bound of every grid-barrier wait
+    uint32_t barrier_extra;   // test knob: arrivals expected beyond the grid (never satisfied)
+    // tiled delivery (grouped layout): per-row segment starts, incoming stencil lists
+    uint32_t n_modules, max_off, seg_stride;
+    const uint16_t* segidx;   // N x seg_stride: start of the synapses to stencil entry j
+    const uint32_t* in_src;   // n_modules x max_off: source modules of target module m
+    const uint32_t* in_j;     // ... and the stencil index of m in each source's list
+    const uint32_t* in_cnt;   // n_modules
+    uint32_t* mod_cnt;        // 2 x n_modules spike counts (double-buffered by step parity)
+    uint32_t* seg_mod;        // Npad: spikes of module m at [m M, m M + mod_cnt)
 };
 
 // Parameters of the construction kernels.
@@ -75,17 +95,23 @@ struct BuildView {
     uint32_t* cdf_T;
     uint32_t* cdf_mod;
     uint32_t* cdf_n;
+    uint16_t* segidx;  // grouped layout: per neuron max_off + 1 segment starts
 };
 
 // Launch wrappers (return the launch error).
 cudaError_t launch_build_cdf(const BuildView& b, cudaStream_t s);
 cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d,
                                 cudaStream_t s);
+cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s);
 cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* ref,
                               cudaStream_t s);
 cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);
 cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s);
 int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16);
+int persistent_grid(bool bf16);
+int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
+cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
+cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t prepare_deliver(uint32_t nb);
 
 void count_launch(uint64_t n);

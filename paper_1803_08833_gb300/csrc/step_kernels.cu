@@ -11,49 +11,11 @@
 //                  in int32 fixed point, into ring[(t + delay) mod D][target]
 //                  with fire-and-forget L2 reductions; it also writes the
 //                  (step, id) raster entries.
-#include "philox.cuh"
-#include "snn_internal.h"
+#include "device_common.cuh"
 
 #include <cuda_bf16.h>
 
 namespace snn {
-
-__device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
-    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// ---------------------------------------------------------------------------
-// Neuron update (Eq. 1-2).  Exact propagator over dt with the input of the step
-// added after the decay:
-//   V <- ((V - E) a_m + E) - k_c c + I 2^-fx,   c <- c a_c,
-// a_m = exp(-dt/tau_m), a_c = exp(-dt/tau_c),
-// k_c = g_c tau_m tau_c / (tau_c - tau_m) (exp(-dt/tau_c) - exp(-dt/tau_m)).
-// While refractory V is held at V_r and the input is discarded.  A spike
-// (V > V_th, or a forced spike) resets V, starts the refractory count and,
-// for excitatory neurons, adds alpha_c to c.
-__device__ __forceinline__ bool lif_update(const NetView& v, float& V, float& c, uint32_t& ref,
-                                           bool exc, int32_t I, bool forced) {
-    const bool was_ref = ref > 0;
-    if (was_ref) {
-        ref -= 1;
-        V = v.V_reset;
-    } else {
-        float x = __fsub_rn(V, v.E);
-        x = __fmul_rn(x, v.a_m);
-        x = __fadd_rn(x, v.E);
-        x = __fsub_rn(x, __fmul_rn(v.kc, c));
-        x = __fadd_rn(x, __fmul_rn(__int2float_rn(I), v.in_scale));
-        V = x;
-    }
-    c = __fmul_rn(c, v.a_c);
-    const bool spike = !was_ref && (V > v.V_th || forced);
-    if (spike) {
-        V = v.V_reset;
-        ref = v.ref_steps;
-        if (exc) c = __fadd_rn(c, v.alpha_c);
-    }
-    return spike;
-}
 
 // Last block of the neuron kernel: exclusive prefix of the per-block spike
 // counts (block offsets) and the bookkeeping of the step.  Each warp scans a
@@ -121,47 +83,17 @@ __device__ __forceinline__ void finish_step(const NetView& v, uint32_t t) {
 __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     __shared__ uint32_t s_t;
     __shared__ bool s_last;
+    __shared__ uint32_t s_pois[MAX_POIS];
     if (threadIdx.x == 0) s_t = v.st->t;  // one read per block, not per thread
+    load_poisson_table(v, s_pois);
     __syncthreads();
     const uint32_t t = s_t;
     const uint32_t slot = t % v.D;
     const uint32_t tid = threadIdx.x;
     const uint32_t base = blockIdx.x * NEURONS_PER_BLOCK + tid * NEURONS_PER_THREAD;
 
-    int4* ring4 = reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base);
-    const int4 I4 = *ring4;
-    *ring4 = make_int4(0, 0, 0, 0);
-    const float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
-    const float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
-    const uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
-
-    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
-    float Cq[4] = {C4.x, C4.y, C4.z, C4.w};
-    const int32_t Iq[4] = {I4.x, I4.y, I4.z, I4.w};
-    uint32_t spk = 0, next_sum = 0, Rout = 0;
-    const uint32_t m0 = base % v.M;  // position of the first neuron inside its module
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t i = base + q;
-        uint32_t r = (R4 >> (8 * q)) & 0xFFu;
-        if (i < v.N) {
-            const U4 u = philox4x32_10(i, t, TAG_DRIVE, 0u, v.key0, v.key1);
-            uint32_t n_ext = 0;
-            for (uint32_t k = 0; k < v.pois_len; ++k) n_ext += (v.pois[k] <= (uint64_t)u.x) ? 1u : 0u;
-            next_sum += n_ext;
-            const bool forced = (uint64_t)u.y < v.imposed_thresh;
-            uint32_t mi = m0 + q;
-            if (mi >= v.M) mi -= v.M;  // M >= 1, so at most one wrap within 4 neurons unless M < 4
-            if (mi >= v.M) mi %= v.M;
-            const bool exc = mi < v.n_exc;
-            const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
-            if (lif_update(v, Vq[q], Cq[q], r, exc, I, forced)) spk |= 1u << q;
-        }
-        Rout |= r << (8 * q);
-    }
-    *reinterpret_cast<float4*>(v.V + base) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
-    *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
-    *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
+    uint32_t next_sum = 0;
+    const uint32_t spk = update_quad(v, s_pois, base, t, slot, next_sum);
 
     // Block-ordered compaction: exclusive prefix of per-thread spike counts.
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -239,13 +171,6 @@ __device__ __forceinline__ void write_raster(const NetView& v, const uint32_t* s
     }
 }
 
-__device__ __forceinline__ int32_t fx_weight(const NetView& v, float w) {
-    return __float2int_rn(__fmul_rn(w, v.w_scale));
-}
-
-__device__ __forceinline__ float bf16_lo(uint32_t x) { return __uint_as_float(x << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t x) { return __uint_as_float(x & 0xFFFF0000u); }
-
 // Per-launch header of the delivery kernels, read once per block.
 struct StepHeader {
     uint32_t n_spk, t;
@@ -262,33 +187,6 @@ __device__ __forceinline__ StepHeader read_header(const NetView& v) {
     __syncthreads();
     return s_h;
 }
-
-__device__ __forceinline__ uint64_t evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ uint4 ld_u4(const void* p, uint64_t pol) {
-    uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p), "l"(pol));
-    return r;
-}
-__device__ __forceinline__ uint2 ld_u2(const void* p, uint64_t pol) {
-    uint2 r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
-                 : "=r"(r.x), "=r"(r.y)
-                 : "l"(p), "l"(pol));
-    return r;
-}
-__device__ __forceinline__ uint32_t ld_u1(const void* p, uint64_t pol) {
-    uint32_t r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
-    return r;
-}
-
-constexpr int DELIVER_UNROLL = 4;
 
 // Schedule 0: warps over (spike, 128-synapse chunk) tasks; each lane handles 4
 // consecutive synapses (one 16 B target load, one 16 B f32 / 8 B bf16 weight
@@ -329,52 +227,8 @@ __global__ void __launch_bounds__(256) k_deliver_warp(NetView v) {
         __syncthreads();
         const uint64_t lo = max(t0, (uint64_t)jb * chunks);
         const uint64_t hi = min(t1, (uint64_t)(jb + blockDim.x) * chunks);
-        for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)nwarps * DELIVER_UNROLL) {
-            uint4 tg[DELIVER_UNROLL];
-            float w[DELIVER_UNROLL][4];
-            uint32_t dd[DELIVER_UNROLL], nv[DELIVER_UNROLL];
-#pragma unroll
-            for (int u = 0; u < DELIVER_UNROLL; ++u) {
-                const uint64_t task = tk + (uint64_t)u * nwarps;
-                nv[u] = 0;
-                if (task < hi) {
-                    const uint32_t jj = (uint32_t)(task / chunks);
-                    const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
-                    const uint32_t k0 = (ch << 7) + (lane << 2);
-                    if (k0 < v.K) {
-                        nv[u] = min(4u, v.K - k0);
-                        const size_t e = (size_t)s_id[jj - jb] * v.Kpad + k0;
-                        tg[u] = ld_u4(v.tgt + e, pol);
-                        if (BF16) {
-                            const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
-                            w[u][0] = bf16_lo(wb.x);
-                            w[u][1] = bf16_hi(wb.x);
-                            w[u][2] = bf16_lo(wb.y);
-                            w[u][3] = bf16_hi(wb.y);
-                        } else {
-                            const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
-                            w[u][0] = __uint_as_float(wf.x);
-                            w[u][1] = __uint_as_float(wf.y);
-                            w[u][2] = __uint_as_float(wf.z);
-                            w[u][3] = __uint_as_float(wf.w);
-                        }
-                        dd[u] = ld_u1(v.d + e, pol);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < DELIVER_UNROLL; ++u) {
-                const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if ((uint32_t)q < nv[u]) {
-                        uint32_t s = slot0 + ((dd[u] >> (8 * q)) & 0xFFu);
-                        if (s >= v.D) s -= v.D;
-                        red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[u][q]));
-                    }
-                }
-            }
-        }
+        for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)nwarps * DELIVER_UNROLL)
+            deliver_tasks<BF16>(v, tk, nwarps, hi, chunks, s_id, jb, slot0, lane, pol);
         __syncthreads();
     }
 }

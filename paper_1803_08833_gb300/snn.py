@@ -43,12 +43,14 @@ class SnnConfig(ctypes.Structure):
         ("imposed_rate_hz", ctypes.c_float),
         ("weight_dtype", ctypes.c_int32), ("fx_shift", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("raster_capacity", ctypes.c_uint64),
+        ("table_layout", ctypes.c_int32),
     ]
 
 
 class SnnStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
-                ("steps", "n_spikes", "rec_events", "ext_events", "raster_count", "raster_capacity")]
+                ("steps", "n_spikes", "rec_events", "ext_events", "raster_count", "raster_capacity",
+                 "neuron_phase_ns", "deliver_phase_ns")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -78,6 +80,7 @@ def load():
         "snn_restore": (st, [vp, vp, ctypes.c_size_t, vp]),
         "snn_get_table": (st, [vp, vp, vp, vp, vp]),
         "snn_get_rows": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp, vp]),
+        "snn_get_segments": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, P(ctypes.c_uint32), vp]),
         "snn_get_cdf": (st, [vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_get_state": (st, [vp, vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_set_state": (st, [vp, vp, vp, vp, vp]),
@@ -85,8 +88,10 @@ def load():
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
-        "snn_kernel_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_double),
-                                 P(ctypes.c_uint64)]),
+        "snn_kernel_time": (st, [vp, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_uint64)]),
+        "snn_set_wait_limit": (st, [vp, ctypes.c_uint64]),
+        "snn_set_barrier_extra": (st, [vp, ctypes.c_uint32]),
+        "snn_clear_error": (st, [vp, vp]),
         "snn_build_cdf_static": (st, [P(SnnConfig), vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_launch_count": (ctypes.c_uint64, []),
         "snn_destroy": (None, [vp]),
@@ -115,6 +120,8 @@ def config(cfg: dict, raster_capacity: int = 0) -> SnnConfig:
             v = {"gauss": 0, "exp": 1}.get(v, v)
         elif k == "weight_dtype":
             v = {"f32": 0, "bf16": 1}.get(v, v)
+        elif k == "table_layout":
+            v = {"draw": 0, "grouped": 1}.get(v, v)
         if k not in names:
             raise KeyError("unknown snn_config field %r" % k)
         setattr(c, k, v)
@@ -239,6 +246,15 @@ class Network:
         check(load().snn_get_rows(self._h, first, count, _ptr(tgt), _ptr(w), _ptr(d), self._s))
         return tgt, w, d
 
+    def segments(self, first: int = 0, count=None):
+        """Grouped layout: segment starts, shape (count, stride)."""
+        count = self.N - first if count is None else count
+        stride = ctypes.c_uint32()
+        check(load().snn_get_segments(self._h, 0, 0, None, ctypes.byref(stride), self._s))
+        out = np.empty(count * stride.value, np.uint16)
+        check(load().snn_get_segments(self._h, first, count, _ptr(out), ctypes.byref(stride), self._s))
+        return out.reshape(count, stride.value)
+
     def cdf(self):
         mo = ctypes.c_uint32()
         check(load().snn_get_cdf(self._h, None, None, None, ctypes.byref(mo), self._s))
@@ -284,9 +300,20 @@ class Network:
         check(load().snn_set_timing(self._h, int(every)))
 
     def kernel_time(self) -> dict:
-        dm, nm = ctypes.c_double(), ctypes.c_double()
-        dl, nl = ctypes.c_uint64(), ctypes.c_uint64()
-        check(load().snn_kernel_time(self._h, ctypes.byref(dm), ctypes.byref(dl), ctypes.byref(nm),
-                                     ctypes.byref(nl)))
-        return {"deliver_ms": dm.value, "deliver_launches": dl.value,
-                "neuron_ms": nm.value, "neuron_launches": nl.value}
+        """Summed CUDA-event time (ms) and timed launches per kernel."""
+        out = {}
+        for name, which in (("neuron", 0), ("deliver", 1), ("persistent", 2)):
+            ms, n = ctypes.c_double(), ctypes.c_uint64()
+            check(load().snn_kernel_time(self._h, which, ctypes.byref(ms), ctypes.byref(n)))
+            out[name + "_ms"] = ms.value
+            out[name + "_launches"] = n.value
+        return out
+
+    def set_wait_limit(self, ns: int):
+        check(load().snn_set_wait_limit(self._h, int(ns)))
+
+    def set_barrier_extra(self, extra: int):
+        check(load().snn_set_barrier_extra(self._h, int(extra)))
+
+    def clear_error(self):
+        check(load().snn_clear_error(self._h, self._s))

@@ -72,6 +72,39 @@ def test_synapse_table_equals_oracle(snn, name):
     assert np.array_equal(d, rd)
 
 
+def _grouped_rows(cfg, tgt, w, d):
+    """The oracle's draw-order rows, stably sorted by target module (per row)."""
+    K, M = cfg["K"], cfg["neurons_per_module"]
+    N = len(tgt) // K if K else 0
+    tm = (tgt // M).reshape(N, K).astype(np.int64)
+    order = np.argsort(tm, axis=1, kind="stable")
+    take = lambda a: np.take_along_axis(a.reshape(N, K), order, axis=1).reshape(-1)
+    return take(tgt), take(w), take(d)
+
+
+@pytest.mark.parametrize("name", sorted(CSR_CASES))
+def test_grouped_table_and_segments_equal_oracle(snn, name):
+    cfg = dict(CSR_CASES[name](), table_layout="grouped")
+    with snn.Network(cfg) as net:
+        tgt, w, d = net.csr()
+        seg = net.segments() if cfg["K"] else None
+    ref = oracle.OracleNet(cfg)
+    rt, rw, rd = _grouped_rows(cfg, *ref.csr())
+    assert np.array_equal(tgt, rt) and np.array_equal(d, rd)
+    assert np.array_equal(w.view(np.uint32), rw.view(np.uint32))
+    if seg is None:
+        return
+    K, M = cfg["K"], cfg["neurons_per_module"]
+    for i in range(0, ref.N, max(1, ref.N // 97)):
+        _, TM, _ = oracle.cdf_table(cfg, i // M)
+        pos = {int(m): j for j, m in enumerate(TM.tolist())}
+        js = np.array([pos[int(x) // M] for x in rt[i * K:(i + 1) * K]])
+        counts = np.bincount(js, minlength=len(TM))
+        expect = np.concatenate([[0], np.cumsum(counts)])[:len(TM)]
+        assert np.array_equal(seg[i, :len(TM)], expect), i
+        assert np.all(seg[i, len(TM):] == K)
+
+
 SIM_CASES = {
     # the plain 4x4 workload as specified (it falls nearly silent after the initial transient)
     "gauss4_seed1": (lambda: W.gauss_4x4_k1000(seed=1), 1000),
@@ -106,11 +139,13 @@ def _compare(net, ref):
     return len(st)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", sorted(SIM_CASES))
 def test_simulation_bit_exact(snn, name, schedule):
     make, steps = SIM_CASES[name]
     cfg = make()
+    if schedule == 3:
+        cfg["table_layout"] = "grouped"
     with snn.Network(cfg, raster_capacity=1 << 22) as net:
         net.set_schedule(schedule)
         net.step(steps)
@@ -132,11 +167,15 @@ def test_block_sizes_agree(snn):
             _compare(net, ref)
 
 
-def test_steps_in_pieces_equal_one_call(snn):
+@pytest.mark.parametrize("schedule_b", [0, 2])
+def test_steps_in_pieces_equal_one_call(snn, schedule_b):
     cfg = W.small(grid=3, M=100, K=60, seed=8, imposed_rate_hz=30.0)
     with snn.Network(cfg) as a, snn.Network(cfg) as b:
         a.step(90)
-        for n in (1, 2, 30, 57):
+        b.set_schedule(schedule_b)
+        for i, n in enumerate((1, 2, 30, 57)):
+            if i == 2:
+                b.set_schedule(2 - schedule_b)  # switching schedules mid-run changes nothing
             b.step(n)
         sa, sb = a.state(), b.state()
         for k in ("V", "c", "ref", "ring"):
@@ -147,6 +186,7 @@ def test_steps_in_pieces_equal_one_call(snn):
 def test_snapshot_restore_resumes_bit_exact(snn):
     cfg = W.small(grid=3, M=120, K=80, seed=14, imposed_rate_hz=25.0, ext_rate_hz=4000.0)
     with snn.Network(cfg) as a, snn.Network(cfg) as b:
+        a.set_schedule(2)
         a.step(120)
         st_a, id_a = a.read_spikes()
         a.step(0)
@@ -204,7 +244,7 @@ def test_empty_steps_and_silent_network(snn):
         assert V0.max() < cfg["V_th_mV"]
 
 
-def _full_size_check(snn, cfg, n_rows=1500, seed=0):
+def _full_size_check(snn, cfg, n_rows=1500, seed=0, schedule=0):
     """At the full configuration: sampled synapse rows, the first step of sampled
     neurons, the exact ring after the first delivery, and invariants."""
     rng = np.random.default_rng(seed)
@@ -243,6 +283,7 @@ def _full_size_check(snn, cfg, n_rows=1500, seed=0):
         assert np.array_equal(ring, expect)
         # a longer run keeps the invariants
         net.clear_raster()
+        net.set_schedule(schedule)
         net.step(200)
         st, ids = net.read_spikes()
         stats = net.stats()
@@ -254,11 +295,34 @@ def _full_size_check(snn, cfg, n_rows=1500, seed=0):
 
 
 def test_full_size_gauss_24x24_k1125(snn):
-    _full_size_check(snn, W.gauss_24x24_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ))
+    _full_size_check(snn, W.gauss_24x24_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), schedule=2)
+
+
+def test_full_size_schedules_agree(snn):
+    """The 24x24 Gaussian network run 60 steps with each schedule: identical state."""
+    cfg = W.gauss_24x24_k1125(seed=3, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped")
+    out = []
+    for schedule in (0, 2, 3):
+        with snn.Network(cfg, raster_capacity=1 << 20) as net:
+            net.set_schedule(schedule)
+            net.step(60)
+            st = net.state()
+            out.append((net.read_spikes(), st["V"], st["ring"], net.stats()))
+    (ra, Va, ga, sa) = out[0]
+    for (rb, Vb, gb, sb) in out[1:]:
+        assert np.array_equal(ra[0], rb[0]) and np.array_equal(ra[1], rb[1])
+        assert np.array_equal(Va, Vb) and np.array_equal(ga, gb)
+        assert all(sa[k] == sb[k] for k in ("n_spikes", "rec_events", "ext_events", "steps"))
 
 
 def test_full_size_exp_24x24_k2250_bf16(snn):
     _full_size_check(snn, W.exp_24x24_k2250(seed=2, imposed_rate_hz=W.PAPER_RATE_EXP_HZ), n_rows=600)
+
+
+def test_schedule_3_needs_the_grouped_layout(snn):
+    with snn.Network(W.small()) as net:
+        with pytest.raises(snn.SnnError, match="GROUPED"):
+            net.set_schedule(3)
 
 
 def test_kernel_timing_counts_sampled_launches(snn):
@@ -272,3 +336,30 @@ def test_kernel_timing_counts_sampled_launches(snn):
         net.set_timing(0)
         net.step(5)
         assert net.kernel_time()["deliver_launches"] == 10
+        net.set_schedule(2)
+        net.set_timing(1)
+        net.step(20)
+        net.step(7)
+        kt = net.kernel_time()
+        assert kt["persistent_launches"] == 2 and kt["persistent_ms"] > 0
+
+
+def test_bounded_barrier_wait_reports_timeout(snn):
+    """A grid-barrier arrival that never comes: every wait runs out after the
+    limit, the launch returns, the host reads SNN_ETIMEOUT, the context stays usable."""
+    cfg = W.small(grid=2, M=64, K=10, seed=1, imposed_rate_hz=50.0)
+    with snn.Network(cfg) as net:
+        net.set_schedule(2)
+        net.set_wait_limit(2_000_000)  # 2 ms
+        net.set_barrier_extra(1)
+        net.step(5)
+        with pytest.raises(snn.SnnError, match="SNN_ETIMEOUT"):
+            net.stats()
+        net.clear_error()
+        net.set_barrier_extra(0)
+    with snn.Network(cfg) as net2:
+        net2.set_schedule(2)
+        net2.step(10)
+        ref = oracle.OracleNet(cfg)
+        ref.step(10)
+        _compare(net2, ref)
