@@ -246,7 +246,7 @@ def run_gpu(args):
         _build.build()
     _barrier(dist)
     torch.cuda.set_device(local)
-    schedule = 3 if args.schedule is None else args.schedule
+    schedule = 2 if args.schedule is None else args.schedule
     cfg = workload(seed=1 + rank, grid=args.grid, K=args.K, layout="grouped" if schedule == 3 else "draw")
     T = args.timesteps
     peak, peak_kind = _peaks()

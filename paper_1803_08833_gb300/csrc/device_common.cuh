@@ -63,32 +63,43 @@ __device__ __forceinline__ void load_poisson_table(const NetView& v, uint32_t* s
     for (uint32_t k = threadIdx.x; k < (uint32_t)MAX_POIS; k += blockDim.x) s_pois[k] = v.pois32[k];
 }
 
-// Updates neurons base .. base+3 (base a multiple of 4, < Npad) for step t:
-// reads and clears their ring slot, draws their external input, integrates.
-// Returns a 4-bit spike mask; adds the external events to `ext`.  The four
-// Philox draws are computed first, unconditionally (neurons past N are
+// State of four consecutive neurons as loaded from memory.
+struct QuadIn {
+    int4 I;
+    float4 V, C;
+    uint32_t R;
+};
+
+// Loads neurons base .. base+3 (base a multiple of 4, < Npad) and their ring
+// slot.  The slot was last written by other SMs' L2 reductions: read at L2 (.cg).
+__device__ __forceinline__ QuadIn load_quad(const NetView& v, uint32_t base, uint32_t slot) {
+    QuadIn in;
+    in.I = __ldcg(reinterpret_cast<const int4*>(v.ring + (size_t)slot * v.Npad + base));
+    in.V = *reinterpret_cast<const float4*>(v.V + base);
+    in.C = *reinterpret_cast<const float4*>(v.c + base);
+    in.R = *reinterpret_cast<const uint32_t*>(v.ref + base);
+    return in;
+}
+
+// Integrates the loaded quad for step t, stores the new state, clears the ring
+// slot.  Returns a 4-bit spike mask; adds the external events to `ext`.  The
+// four Philox draws are computed first, unconditionally (neurons past N are
 // padding and are not updated), so their dependency chains interleave.
-__device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
-                                                uint32_t slot, uint32_t& ext) {
-    // The slot was last written by other SMs' L2 reductions: read it at L2 (.cg).
-    int4* ring4 = reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base);
-    const int4 I4 = __ldcg(ring4);
-    const float4 V4 = *reinterpret_cast<const float4*>(v.V + base);
-    const float4 C4 = *reinterpret_cast<const float4*>(v.c + base);
-    const uint32_t R4 = *reinterpret_cast<const uint32_t*>(v.ref + base);
+__device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
+                                                 uint32_t slot, const QuadIn& in, uint32_t& ext) {
     U4 u[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = philox4x32_10(base + q, t, TAG_DRIVE, 0u, v.key0, v.key1);
-    *ring4 = make_int4(0, 0, 0, 0);
-    float Vq[4] = {V4.x, V4.y, V4.z, V4.w};
-    float Cq[4] = {C4.x, C4.y, C4.z, C4.w};
-    const int32_t Iq[4] = {I4.x, I4.y, I4.z, I4.w};
+    *reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base) = make_int4(0, 0, 0, 0);
+    float Vq[4] = {in.V.x, in.V.y, in.V.z, in.V.w};
+    float Cq[4] = {in.C.x, in.C.y, in.C.z, in.C.w};
+    const int32_t Iq[4] = {in.I.x, in.I.y, in.I.z, in.I.w};
     uint32_t spk = 0, Rout = 0;
     uint32_t mi = base % v.M;  // position of neuron `base` inside its module
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t i = base + q;
-        uint32_t r = (R4 >> (8 * q)) & 0xFFu;
+        uint32_t r = (in.R >> (8 * q)) & 0xFFu;
         const uint32_t n_ext = poisson_count(s_pois, v.pois_pad, u[q].x);
         const bool forced = (uint64_t)u[q].y < v.imposed_thresh;
         const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
@@ -110,6 +121,11 @@ __device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t
     *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
     *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
     return spk;
+}
+
+__device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
+                                                uint32_t slot, uint32_t& ext) {
+    return compute_quad(v, s_pois, base, t, slot, load_quad(v, base, slot), ext);
 }
 
 // ---------------------------------------------------------------------------
@@ -148,7 +164,10 @@ __device__ __forceinline__ uint32_t ld_u1(const void* p, uint64_t pol) {
     return r;
 }
 
-constexpr int DELIVER_UNROLL = 4;
+#ifndef SNN_DELIVER_UNROLL
+#define SNN_DELIVER_UNROLL 4
+#endif
+constexpr int DELIVER_UNROLL = SNN_DELIVER_UNROLL;
 
 // One warp delivers up to DELIVER_UNROLL tasks (spike, 128-synapse chunk):
 // task tk + u * tstride for u < DELIVER_UNROLL, each below `hi`.  ids[j - j0]

@@ -17,8 +17,12 @@
 
 namespace snn {
 
+#ifndef SNN_PERSIST_MIN_BLOCKS
+#define SNN_PERSIST_MIN_BLOCKS 2
+#endif
+
 template <bool BF16>
-__global__ void __launch_bounds__(PERSIST_THREADS) k_run_steps(NetView v, uint32_t n_steps) {
+__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_steps(NetView v, uint32_t n_steps) {
     extern __shared__ uint32_t smem[];
     const uint32_t G = gridDim.x, TW = G * PERSIST_WARPS;
     uint32_t* s_cta = smem;             // G + 1 CTA offsets
@@ -56,10 +60,14 @@ __global__ void __launch_bounds__(PERSIST_THREADS) k_run_steps(NetView v, uint32
         const uint32_t slot = t % v.D;
         // ---- phase N: this warp's neurons, 4 per lane, spikes compacted in id order
         uint32_t run = 0;
+        QuadIn nxt;  // the next chunk's loads are issued before this chunk is integrated
+        if (qa + lane < qb) nxt = load_quad(v, (qa + lane) << 2, slot);
         for (uint32_t qc = qa; qc < qb; qc += 32) {
             const uint32_t q = qc + lane;
+            const QuadIn cur = nxt;
+            if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = update_quad(v, s_pois, q << 2, t, slot, ext);
+            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll

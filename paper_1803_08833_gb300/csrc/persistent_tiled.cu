@@ -19,6 +19,7 @@ constexpr int TILE_THREADS = 512;
 constexpr int TILE_WARPS = TILE_THREADS / 32;
 constexpr uint32_t PAIR_CAP = 1024;  // (spike, segment) pairs staged per batch
 constexpr int EV_UNROLL = 8;         // events in flight per lane
+constexpr int FLUSH_UNROLL = 8;      // ring read-modify-writes in flight per thread
 
 __device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p, uint64_t pol) {
     uint32_t r;
@@ -243,16 +244,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
                 }
                 __syncthreads();
             }
-            // flush: ring[(t + d) mod D][m M + n] += tile[d - 1][n]
-            for (uint32_t d = 1; d <= Dm1; ++d) {
-                uint32_t sl = slot + d;
-                if (sl >= v.D) sl -= v.D;
-                int32_t* dst = v.ring + (size_t)sl * v.Npad + (size_t)m * M;
-                const int32_t* src = tile + (size_t)(d - 1) * M;
-                for (uint32_t x = threadIdx.x; x < M; x += blockDim.x) {
-                    const int32_t a = src[x];
-                    if (a != 0) dst[x] = __ldcg(dst + x) + a;
+            // flush: ring[(t + d) mod D][m M + n] += tile[d - 1][n]; eight independent
+            // read-modify-writes in flight per thread
+            const uint32_t cells = Dm1 * M;
+            for (uint32_t x0 = threadIdx.x; x0 < cells; x0 += FLUSH_UNROLL * blockDim.x) {
+                int32_t add[FLUSH_UNROLL], old[FLUSH_UNROLL];
+                int32_t* dst[FLUSH_UNROLL];
+#pragma unroll
+                for (int u = 0; u < FLUSH_UNROLL; ++u) {
+                    const uint32_t x = x0 + u * blockDim.x;
+                    add[u] = 0;
+                    dst[u] = nullptr;
+                    if (x < cells) {
+                        add[u] = tile[x];
+                        const uint32_t row = x / M, col = x - row * M;
+                        uint32_t sl = slot + row + 1;
+                        if (sl >= v.D) sl -= v.D;
+                        dst[u] = v.ring + (size_t)sl * v.Npad + (size_t)m * M + col;
+                    }
                 }
+#pragma unroll
+                for (int u = 0; u < FLUSH_UNROLL; ++u) old[u] = add[u] != 0 ? __ldcg(dst[u]) : 0;
+#pragma unroll
+                for (int u = 0; u < FLUSH_UNROLL; ++u)
+                    if (add[u] != 0) *dst[u] = old[u] + add[u];
             }
             __syncthreads();
         }
