@@ -256,6 +256,68 @@ SNN_API uint64_t snn_launch_count(void);
 SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh, uint32_t* tgt_module,
                                         uint32_t* counts, uint32_t* max_offsets, void* stream);
 
+/* ---- Batched execution: many independent networks in one persistent launch.
+ * Network i is simulated by its own group of CTAs (sized in proportion to its
+ * estimated work per step, or set with snn_batch_set_groups), with its own
+ * grid barriers, for steps[i] time steps; results are bit-identical to
+ * running each network alone.  The nets stay owned by the caller and must
+ * outlive the batch.  Errors: SNN_EINVAL (NULL or repeated nets, more nets
+ * than co-resident CTAs), SNN_ENOMEM, SNN_ECUDA. */
+typedef struct snn_batch snn_batch;
+SNN_API snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
+                                    void* alloc_ctx, snn_batch** out);
+/* Runs network i for steps[i] (host array of n; 0 = idle) time steps.  Async. */
+SNN_API snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream);
+/* CTAs per network (host array of n, each >= 1, sum <= snn_batch_capacity). */
+SNN_API snn_status snn_batch_set_groups(snn_batch* b, const uint32_t* ctas);
+SNN_API snn_status snn_batch_get_groups(snn_batch* b, uint32_t* ctas, uint32_t* capacity);
+/* enable != 0: snn_batch_step replays a CUDA graph holding the launch
+ * (captured on first use; re-captured when the groups change). */
+SNN_API snn_status snn_batch_set_graph(snn_batch* b, int32_t enable);
+/* CUDA-event time (ms) and count of the batch launches since creation. */
+SNN_API snn_status snn_batch_time(snn_batch* b, double* ms, uint64_t* launches);
+SNN_API void snn_batch_destroy(snn_batch* b);
+
+/* ---- Serving: a continuous-batching loop over simulation requests.
+ * snn_server_submit queues a request (description, number of time steps,
+ * arrival time in ns of the host's monotonic clock, 0 = now); it is rejected
+ * with SNN_EBUDGET if it could never fit the device-memory budget.  Each
+ * snn_server_tick admits queued requests in arrival order while their
+ * estimated footprint (snn_estimate_bytes) fits the budget and a slot is
+ * free, advances every resident network by up to `chunk_steps` steps in one
+ * batched persistent launch (snn_batch_*), synchronises, and retires the
+ * finished networks: their results (counters, hashes of raster and final V,
+ * queueing and total latency) become available to snn_server_poll and their
+ * memory returns to the budget.  Results do not depend on which other
+ * requests shared a launch. */
+typedef struct snn_server snn_server;
+typedef struct snn_request_result {
+    uint64_t request_id;
+    uint64_t steps, n_spikes, rec_events, ext_events;
+    uint64_t raster_hash; /* FNV-1a over the (step, id) raster arrays */
+    uint64_t state_hash;  /* FNV-1a over the final membrane potentials */
+    double queue_ms;      /* arrival -> admission */
+    double latency_ms;    /* arrival -> completion */
+    int32_t status;       /* snn_status of the request */
+    int32_t pad;
+} snn_request_result;
+typedef struct snn_server_stats_t {
+    uint64_t ticks, launches, rec_events, ext_events, steps, busy_ns, used_bytes;
+    uint32_t active, queued;
+} snn_server_stats_t;
+SNN_API uint64_t snn_estimate_bytes(const snn_config* cfg);
+SNN_API snn_status snn_server_create(uint64_t budget_bytes, uint32_t chunk_steps, uint32_t max_slots,
+                                     snn_alloc_fn alloc_fn, snn_free_fn free_fn, void* alloc_ctx, void* stream,
+                                     snn_server** out);
+SNN_API snn_status snn_server_submit(snn_server* s, const snn_config* cfg, uint32_t n_steps, uint64_t arrival_ns,
+                                     uint64_t* request_id);
+SNN_API snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued);
+SNN_API snn_status snn_server_poll(snn_server* s, snn_request_result* out, uint32_t cap, uint32_t* n_out);
+SNN_API snn_status snn_server_stats(snn_server* s, snn_server_stats_t* out);
+/* Host monotonic clock in ns (the time base of arrival_ns). */
+SNN_API uint64_t snn_now_ns(void);
+SNN_API void snn_server_destroy(snn_server* s);
+
 SNN_API void snn_destroy(snn_net* net);
 SNN_API const char* snn_last_error(void);
 

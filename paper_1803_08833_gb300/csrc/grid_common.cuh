@@ -17,16 +17,17 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Returns
-// false if this CTA's wait ran out or another CTA reported an error.
-__device__ inline bool grid_barrier(const NetView& v, uint32_t& gen) {
+// Barrier over the G CTAs that simulate network v (all co-resident:
+// cooperative launch).  Returns false if this CTA's wait ran out or another
+// CTA of the network reported an error.
+__device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         DevState* st = v.st;
         int ok = 1;
         __threadfence();  // publish this CTA's writes before arriving
-        const uint32_t expected = gridDim.x + v.barrier_extra;
+        const uint32_t expected = G + v.barrier_extra;
         const uint32_t arrived = atomicAdd(&st->bar_count, 1u);
         if (arrived == expected - 1) {
             atomicExch(&st->bar_count, 0u);
@@ -87,8 +88,8 @@ __device__ inline void block_exclusive_scan(const uint32_t* cnt, uint32_t n, uin
 // warp by a scan of that CTA's W warp offsets, then the warp's segment.
 template <int W>
 __device__ __forceinline__ uint32_t spike_id(const NetView& v, const uint32_t* s_cta, const uint32_t* s_woff,
-                                             uint32_t j, uint32_t Q, uint32_t TW) {
-    uint32_t lo = 0, hi = gridDim.x;
+                                             uint32_t j, uint32_t Q, uint32_t TW, uint32_t G) {
+    uint32_t lo = 0, hi = G;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
         if (s_cta[mid] <= j)

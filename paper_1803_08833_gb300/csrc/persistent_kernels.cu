@@ -21,10 +21,12 @@ namespace snn {
 #define SNN_PERSIST_MIN_BLOCKS 2
 #endif
 
+// n_steps time steps of network v on a group of G CTAs; `bid` is this CTA's
+// index in the group.  smem: G + 1 + G * PERSIST_WARPS + PERSIST_THREADS words.
 template <bool BF16>
-__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_steps(NetView v, uint32_t n_steps) {
-    extern __shared__ uint32_t smem[];
-    const uint32_t G = gridDim.x, TW = G * PERSIST_WARPS;
+__device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, uint32_t G, uint32_t bid,
+                                          uint32_t* smem) {
+    const uint32_t TW = G * PERSIST_WARPS;
     uint32_t* s_cta = smem;             // G + 1 CTA offsets
     uint32_t* s_woff = smem + G + 1;    // TW warp offsets (CTA-local)
     uint32_t* s_id = s_woff + TW;       // staged spike ids
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     __syncthreads();
     const uint32_t t0 = s_t0;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t wg = blockIdx.x * PERSIST_WARPS + warp;
+    const uint32_t wg = bid * PERSIST_WARPS + warp;
     const uint32_t Q = v.Npad >> 2;
     const uint32_t qa = (uint32_t)((uint64_t)Q * wg / TW);
     const uint32_t qb = (uint32_t)((uint64_t)Q * (wg + 1) / TW);
@@ -54,7 +56,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     uint32_t done = 0;
 
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
-    if (blockIdx.x == 0 && threadIdx.x == 0) stamp = global_ns();
+    if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
     for (uint32_t step = 0; step < n_steps; ++step) {
         const uint32_t t = t0 + step;
         const uint32_t slot = t % v.D;
@@ -86,13 +88,13 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
         if (threadIdx.x == 0) {
             uint32_t acc = 0;
             for (int w = 0; w < PERSIST_WARPS; ++w) {
-                v.woff[blockIdx.x * PERSIST_WARPS + w] = acc;
+                v.woff[bid * PERSIST_WARPS + w] = acc;
                 acc += s_wcnt[w];
             }
-            v.cta_cnt[blockIdx.x] = acc;
+            v.cta_cnt[bid] = acc;
         }
-        if (!grid_barrier(v, gen)) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!grid_barrier(v, G, gen)) break;
+        if (bid == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_n += now - stamp;
             stamp = now;
@@ -103,22 +105,22 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
         for (uint32_t i = threadIdx.x; i < TW; i += blockDim.x) s_woff[i] = __ldcg(v.woff + i);
         __syncthreads();
         const uint32_t total = s_cta[G];
-        for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
+        for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
             const uint64_t r = rc + j;
             if (r >= v.raster_cap) break;
             v.raster_t[r] = t;
-            v.raster_id[r] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW);
+            v.raster_id[r] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW, G);
         }
         if (chunks > 0 && total > 0) {
             const uint64_t n_tasks = (uint64_t)total * chunks;
-            const uint64_t ta = n_tasks * blockIdx.x / G;
-            const uint64_t tb = n_tasks * (blockIdx.x + 1) / G;
+            const uint64_t ta = n_tasks * bid / G;
+            const uint64_t tb = n_tasks * (bid + 1) / G;
             if (ta < tb) {
                 const uint32_t slot0 = t % v.D;
                 const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
                 for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
                     const uint32_t j = jb + threadIdx.x;
-                    if (j <= j_last) s_id[threadIdx.x] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW);
+                    if (j <= j_last) s_id[threadIdx.x] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW, G);
                     __syncthreads();
                     const uint64_t lo = max(ta, (uint64_t)jb * chunks);
                     const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
@@ -130,8 +132,8 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
         }
         rc += total;
         spikes += total;
-        if (!grid_barrier(v, gen)) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!grid_barrier(v, G, gen)) break;
+        if (bid == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_d += now - stamp;
             stamp = now;
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
         unsigned long long be = 0;
         for (int w = 0; w < PERSIST_WARPS; ++w) be += s_ext[w];
         atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->ext_events), be);
-        if (blockIdx.x == 0 && done == n_steps) {
+        if (bid == 0 && done == n_steps) {
             DevState* st = v.st;
             st->t = t0 + n_steps;
             st->raster_count = rc;
@@ -160,6 +162,50 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
             st->phase_ns[1] += ph_d;
         }
     }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_steps(NetView v, uint32_t n_steps) {
+    extern __shared__ uint32_t smem[];
+    run_steps<BF16>(v, n_steps, gridDim.x, blockIdx.x, smem);
+}
+
+// Many independent networks in one cooperative launch: network i runs on CTAs
+// [cta_first[i], cta_first[i + 1]) for steps[i] time steps, with its own
+// barriers; networks with different weight types share the launch.
+__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS)
+    k_run_batch(const NetView* __restrict__ views, const uint32_t* __restrict__ cta_first,
+                const uint32_t* __restrict__ steps, uint32_t n_inst) {
+    extern __shared__ uint32_t smem[];
+    __shared__ NetView s_v;
+    __shared__ uint32_t s_i;
+    if (threadIdx.x == 0) {
+        uint32_t lo = 0, hi = n_inst;  // largest i with cta_first[i] <= blockIdx.x
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cta_first[mid] <= blockIdx.x)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        s_i = lo;
+    }
+    __syncthreads();
+    const uint32_t i = s_i;
+    const uint32_t first = cta_first[i], G = cta_first[i + 1] - first;
+    if (blockIdx.x >= cta_first[n_inst] || G == 0) return;
+    {  // the network's view, copied to shared memory word by word
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(views + i);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_v);
+        for (uint32_t k = threadIdx.x; k < sizeof(NetView) / 4; k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const uint32_t n = steps[i];
+    if (n == 0) return;
+    if (s_v.w_bf16)
+        run_steps<true>(s_v, n, G, blockIdx.x - first, smem);
+    else
+        run_steps<false>(s_v, n, G, blockIdx.x - first, smem);
 }
 
 static const void* persistent_fn(bool bf16) {
@@ -187,6 +233,32 @@ int persistent_grid(bool bf16) {
         if (fit >= per_sm) return grid;
     }
     return sms;
+}
+
+int batch_grid(uint32_t max_group) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int fit = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_batch, PERSIST_THREADS,
+                                                      persistent_smem((int)max_group)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return fit * sms;
+}
+
+cudaError_t launch_batch(const NetView* views, const uint32_t* cta_first, const uint32_t* steps, uint32_t n_inst,
+                         int grid, uint32_t max_group, cudaStream_t s) {
+    const size_t smem = persistent_smem((int)max_group);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_run_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    void* args[] = {(void*)&views, (void*)&cta_first, (void*)&steps, (void*)&n_inst};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_run_batch, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
+    count_launch(1);
+    return e;
 }
 
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
             }
             v.cta_cnt[blockIdx.x] = acc;
         }
-        if (!grid_barrier(v, gen)) break;
+        if (!grid_barrier(v, G, gen)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_n += now - stamp;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
             const uint64_t r = rc + j;
             if (r >= v.raster_cap) break;
             v.raster_t[r] = t;
-            v.raster_id[r] = spike_id<TILE_WARPS>(v, s_cta, s_woff, j, Q, TW);
+            v.raster_id[r] = spike_id<TILE_WARPS>(v, s_cta, s_woff, j, Q, TW, G);
         }
         // the other parity's counters were last used by the previous step
         for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += G * blockDim.x)
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
         }
         rc += total;
         spikes += total;
-        if (!grid_barrier(v, gen)) break;
+        if (!grid_barrier(v, G, gen)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_d += now - stamp;

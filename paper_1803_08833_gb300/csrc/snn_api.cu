@@ -812,4 +812,210 @@ void snn_destroy(snn_net* n) {
     delete n;
 }
 
+// ---------------------------------------------------------------------------
+// Batched execution.
+
+struct snn_batch {
+    std::vector<snn_net*> nets;
+    snn_alloc_fn alloc_fn = nullptr;
+    snn_free_fn free_fn = nullptr;
+    void* alloc_ctx = nullptr;
+    std::vector<void*> blocks;
+    NetView* d_views = nullptr;
+    uint32_t* d_first = nullptr;
+    uint32_t* d_steps = nullptr;
+    uint32_t* h_steps = nullptr;  // pinned staging of the per-network steps
+    std::vector<uint32_t> groups;
+    int capacity = 0;
+    bool use_graph = false;
+    bool graph_valid = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    EventRing ev;
+};
+
+namespace {
+
+void* batch_alloc(snn_batch* b, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (b->alloc_fn) {
+        p = b->alloc_fn(bytes, b->alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) b->blocks.push_back(p);
+    return p;
+}
+
+// Estimated work per step: neuron updates plus synaptic events at the
+// imposed rate (1 Hz when none is set), an event weighing half an update.
+double batch_cost(const snn_net* n) {
+    const double rate = std::max(1.0, (double)n->cfg.imposed_rate_hz) * n->cfg.dt_ms / 1000.0;
+    return (double)n->N * (1.0 + 0.5 * rate * n->K) + 1.0;
+}
+
+snn_status batch_upload(snn_batch* b, cudaStream_t s) {
+    const uint32_t n = (uint32_t)b->nets.size();
+    std::vector<NetView> views(n);
+    std::vector<uint32_t> first(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) {
+        views[i] = b->nets[i]->v;
+        first[i + 1] = first[i] + b->groups[i];
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->d_views, views.data(), n * sizeof(NetView), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(b->d_first, first.data(), (n + 1) * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+}  // namespace
+
+snn_status snn_batch_set_groups(snn_batch* b, const uint32_t* ctas) {
+    if (!b || !ctas) return fail(SNN_EINVAL, "batch or ctas is NULL");
+    uint64_t sum = 0;
+    for (size_t i = 0; i < b->nets.size(); ++i) {
+        if (ctas[i] < 1 || (int)ctas[i] > b->nets[i]->pgrid)
+            return fail(SNN_EINVAL, "network %zu: %u CTAs outside [1, %d]", i, ctas[i], b->nets[i]->pgrid);
+        sum += ctas[i];
+    }
+    if (sum > (uint64_t)b->capacity) return fail(SNN_EINVAL, "%llu CTAs exceed the co-resident capacity %d",
+                                                  (unsigned long long)sum, b->capacity);
+    b->groups.assign(ctas, ctas + b->nets.size());
+    b->graph_valid = false;
+    return batch_upload(b, nullptr);
+}
+
+snn_status snn_batch_get_groups(snn_batch* b, uint32_t* ctas, uint32_t* capacity) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    if (ctas) std::copy(b->groups.begin(), b->groups.end(), ctas);
+    if (capacity) *capacity = (uint32_t)b->capacity;
+    return SNN_OK;
+}
+
+snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
+                            void* alloc_ctx, snn_batch** out) {
+    if (!out || !nets || n == 0) return fail(SNN_EINVAL, "nets, n and out must be set");
+    *out = nullptr;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!nets[i]) return fail(SNN_EINVAL, "network %u is NULL", i);
+        for (uint32_t j = 0; j < i; ++j)
+            if (nets[j] == nets[i]) return fail(SNN_EINVAL, "network %u appears twice", i);
+    }
+    int max_group = 0;
+    for (uint32_t i = 0; i < n; ++i) max_group = std::max(max_group, nets[i]->pgrid);
+    const int capacity = batch_grid((uint32_t)max_group);
+    if (capacity < (int)n) return fail(SNN_EINVAL, "%u networks exceed the %d co-resident CTAs", n, capacity);
+    snn_batch* b = new (std::nothrow) snn_batch();
+    if (!b) return fail(SNN_ENOMEM, "host allocation failed");
+    b->nets.assign(nets, nets + n);
+    b->alloc_fn = alloc_fn;
+    b->free_fn = free_fn;
+    b->alloc_ctx = alloc_ctx;
+    b->capacity = capacity;
+    b->d_views = (NetView*)batch_alloc(b, n * sizeof(NetView));
+    b->d_first = (uint32_t*)batch_alloc(b, (n + 1) * 4);
+    b->d_steps = (uint32_t*)batch_alloc(b, n * 4);
+    if (!b->d_views || !b->d_first || !b->d_steps || cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        snn_batch_destroy(b);
+        return fail(SNN_ENOMEM, "batch allocation failed");
+    }
+    // CTAs in proportion to the estimated work, at least one each
+    std::vector<double> cost(n);
+    double total = 0.0;
+    for (uint32_t i = 0; i < n; ++i) total += cost[i] = batch_cost(nets[i]);
+    std::vector<uint32_t> g(n, 1);
+    int left = capacity - (int)n;
+    for (uint32_t i = 0; i < n; ++i) {
+        const int extra = std::min((int)std::floor(cost[i] / total * left), nets[i]->pgrid - 1);
+        g[i] += (uint32_t)std::max(extra, 0);
+    }
+    snn_status st = snn_batch_set_groups(b, g.data());
+    if (st != SNN_OK) {
+        snn_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return SNN_OK;
+}
+
+snn_status snn_batch_set_graph(snn_batch* b, int32_t enable) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    b->use_graph = enable != 0;
+    return SNN_OK;
+}
+
+snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
+    if (!b || !steps) return fail(SNN_EINVAL, "batch or steps is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n = (uint32_t)b->nets.size();
+    // the pinned staging buffer may still feed the previous call's copy
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::copy(steps, steps + n, b->h_steps);
+    CUDA_TRY(cudaMemcpyAsync(b->d_steps, b->h_steps, n * 4, cudaMemcpyHostToDevice, s));
+    uint32_t max_group = 0;
+    for (uint32_t gi : b->groups) max_group = std::max(max_group, gi);
+    int total = 0;
+    for (uint32_t gi : b->groups) total += (int)gi;
+    int slot = 0;
+    snn_status st = timed_begin(b->ev, s, &slot);
+    if (st != SNN_OK) return st;
+    if (b->use_graph) {
+        if (!b->graph_valid) {
+            if (b->exec) {
+                cudaGraphExecDestroy(b->exec);
+                b->exec = nullptr;
+            }
+            if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+            CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t le = launch_batch(b->d_views, b->d_first, b->d_steps, n, total, max_group, b->cap_stream);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+            if (le != cudaSuccess || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                return fail(SNN_ECUDA, "graph capture of the batch launch failed: %s",
+                            cudaGetErrorString(le != cudaSuccess ? le : ce));
+            }
+            cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ie != cudaSuccess) return fail(SNN_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+            b->graph_valid = true;
+        }
+        CUDA_TRY(cudaGraphLaunch(b->exec, s));
+        count_launch(1);
+    } else {
+        CUDA_TRY(launch_batch(b->d_views, b->d_first, b->d_steps, n, total, max_group, s));
+    }
+    return timed_end(b->ev, s, slot);
+}
+
+snn_status snn_batch_time(snn_batch* b, double* ms, uint64_t* launches) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    snn_status st = drain(b->ev);
+    if (st != SNN_OK) return st;
+    if (ms) *ms = b->ev.total_ms;
+    if (launches) *launches = b->ev.count;
+    return SNN_OK;
+}
+
+void snn_batch_destroy(snn_batch* b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->h_steps) cudaFreeHost(b->h_steps);
+    destroy_events(b->ev);
+    for (void* p : b->blocks) {
+        if (b->free_fn)
+            b->free_fn(p, b->alloc_ctx);
+        else if (!b->alloc_fn)
+            cudaFree(p);
+    }
+    delete b;
+}
+
 }  // extern "C"

@@ -109,6 +109,9 @@ cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);
 cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s);
 int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16);
 int persistent_grid(bool bf16);
+int batch_grid(uint32_t max_group);
+cudaError_t launch_batch(const NetView* views, const uint32_t* cta_first, const uint32_t* steps, uint32_t n_inst,
+                         int grid, uint32_t max_group, cudaStream_t s);
 int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);

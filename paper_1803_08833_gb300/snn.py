@@ -94,6 +94,13 @@ def load():
         "snn_clear_error": (st, [vp, vp]),
         "snn_build_cdf_static": (st, [P(SnnConfig), vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_launch_count": (ctypes.c_uint64, []),
+        "snn_batch_create": (st, [P(vp), ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, P(vp)]),
+        "snn_batch_step": (st, [vp, P(ctypes.c_uint32), vp]),
+        "snn_batch_set_groups": (st, [vp, P(ctypes.c_uint32)]),
+        "snn_batch_get_groups": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32)]),
+        "snn_batch_set_graph": (st, [vp, ctypes.c_int32]),
+        "snn_batch_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64)]),
+        "snn_batch_destroy": (None, [vp]),
         "snn_destroy": (None, [vp]),
         "snn_last_error": (ctypes.c_char_p, []),
     }
@@ -317,3 +324,65 @@ class Network:
 
     def clear_error(self):
         check(load().snn_clear_error(self._h, self._s))
+
+
+class Batch:
+    """Independent networks advanced together in one persistent launch."""
+
+    def __init__(self, nets, stream=None):
+        import torch
+        L = load()
+        self.nets = list(nets)
+        n = len(self.nets)
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._s = ctypes.c_void_p(self.stream.cuda_stream)
+        self._alloc = _TorchAllocator(dev, self.stream)
+        arr = (ctypes.c_void_p * n)(*[net._h.value for net in self.nets])
+        h = ctypes.c_void_p()
+        check(L.snn_batch_create(arr, n, self._alloc.alloc, self._alloc.free, None, ctypes.byref(h)))
+        self._h = h
+
+    def step(self, steps):
+        """steps: one count per network (0 = idle)."""
+        n = len(self.nets)
+        if isinstance(steps, int):
+            steps = [steps] * n
+        arr = (ctypes.c_uint32 * n)(*[int(x) for x in steps])
+        check(load().snn_batch_step(self._h, arr, self._s))
+
+    def groups(self):
+        n = len(self.nets)
+        arr = (ctypes.c_uint32 * n)()
+        cap = ctypes.c_uint32()
+        check(load().snn_batch_get_groups(self._h, arr, ctypes.byref(cap)))
+        return list(arr), cap.value
+
+    def set_groups(self, ctas):
+        arr = (ctypes.c_uint32 * len(self.nets))(*[int(x) for x in ctas])
+        check(load().snn_batch_set_groups(self._h, arr))
+
+    def set_graph(self, enable: bool):
+        check(load().snn_batch_set_graph(self._h, 1 if enable else 0))
+
+    def time(self):
+        ms, n = ctypes.c_double(), ctypes.c_uint64()
+        check(load().snn_batch_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().snn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

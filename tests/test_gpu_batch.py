@@ -1,0 +1,91 @@
+"""Batched execution: independent networks advanced in one persistent launch
+must each equal the network run alone (here: the oracle), bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_08833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    from paper_1803_08833_gb300 import _build
+    from paper_1803_08833_gb300 import snn as S
+    _build.build()
+    S.load()
+    return S
+
+
+def _cases():
+    return [
+        W.small(grid=2, M=120, K=77, seed=5, imposed_rate_hz=30.0, ext_rate_hz=3000.0),
+        W.small(grid=3, M=100, K=200, lateral="exp", seed=6, weight_dtype="bf16", imposed_rate_hz=35.0),
+        W.small(grid=4, M=50, K=150, seed=7, ext_rate_hz=5000.0),
+        dict(W.small(grid=3, M=333, K=37, seed=9, imposed_rate_hz=40.0), grid_h=2),
+        W.small(grid=2, M=64, K=10, seed=1, ext_rate_hz=0.0),
+        W.gauss_4x4_k1000(seed=2, imposed_rate_hz=7.5),
+    ]
+
+
+def _check(net, ref):
+    st, ids = net.read_spikes()
+    rs, ri = ref.raster()
+    assert np.array_equal(st, rs) and np.array_equal(ids, ri)
+    a, b = net.state(), ref.state()
+    for k in ("V", "c", "ref", "ring"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["t"] == ref.t
+    s = net.stats()
+    assert s["n_spikes"] == ref.stats()["spikes"] and s["ext_events"] == ref.stats()["ext_events"]
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_each_network_alone(snn, graph):
+    cfgs = _cases()
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_graph(graph)
+        groups, cap = batch.groups()
+        assert all(g >= 1 for g in groups) and sum(groups) <= cap
+        plans = [[60, 45, 60, 0, 30, 50], [10, 10, 0, 25, 10, 10], [10, 10, 0, 25, 10, 10]]
+        for steps in plans:
+            batch.step(steps)
+            for r, n in zip(refs, steps):
+                r.step(n)
+        for net, ref in zip(nets, refs):
+            _check(net, ref)
+        ms, launches = batch.time()
+        assert launches == len(plans) and ms > 0
+    for n in nets:
+        n.close()
+
+
+def test_batch_groups_can_be_set_and_are_validated(snn):
+    cfgs = _cases()[:3]
+    nets = [snn.Network(c) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_groups([1, 2, 3])
+        assert batch.groups()[0] == [1, 2, 3]
+        with pytest.raises(snn.SnnError):
+            batch.set_groups([0, 1, 1])
+        batch.step(40)
+        for r in refs:
+            r.step(40)
+        for net, ref in zip(nets, refs):
+            _check(net, ref)
+    for n in nets:
+        n.close()
+
+
+def test_batch_rejects_repeated_networks(snn):
+    net = snn.Network(W.small())
+    with pytest.raises(snn.SnnError, match="twice"):
+        snn.Batch([net, net])
+    net.close()
