@@ -322,6 +322,9 @@ def run_gpu(args):
         e2e = run_e2e(snn, cfg, args.e2e_jobs, stream, schedule)
     net.close()
 
+    batched = None if args.no_batched else run_batched(snn, args, stream)
+    served = None if args.no_served else run_served(snn, args, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         rate, info = cpu_oracle_rate(cfg, args.cpu_grid, args.cpu_seconds, 100000)
@@ -362,6 +365,8 @@ def run_gpu(args):
                      "launches_timed": launches_timed},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "batched": batched,
+        "served": served,
         "gpu_launches": launches,
         "clocks": ck,
     }
@@ -409,12 +414,117 @@ def run_e2e(snn, cfg, jobs, stream, schedule):
             "jobs": jobs}
 
 
+def run_batched(snn, args, stream):
+    """64 independent instances (grid side 4..16, Gaussian or exponential,
+    f32 or bf16) advanced 2,000 steps in one persistent launch, against the
+    same instances run one per launch (each its own persistent launch)."""
+    import torch
+    from paper_1803_08833_gb300 import workloads as W
+    inst = W.batched_instances(n=args.batch_n, steps=args.batch_steps)
+    nets = [snn.Network(c, raster_capacity=1) for c, _ in inst]
+    for n in nets:
+        n.set_schedule(2)
+    steps = [s for _, s in inst]
+
+    def events():
+        return sum(n.stats()["rec_events"] for n in nets)
+
+    with snn.Batch(nets, stream=stream) as batch:
+        batch.set_graph(True)
+        batch.step([20] * len(nets))  # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        e0, l0 = events(), snn.launch_count()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.step(steps)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_batched = a.elapsed_time(b)
+        ev_batched = events() - e0
+        launches_batched = snn.launch_count() - l0
+    # plain: one instance per launch, back to back on the same stream
+    e0 = events()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for n, s in zip(nets, steps):
+        n.step(s)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(b)
+    ev_plain = events() - e0
+    neurons = sum(n.N for n in nets)
+    for n in nets:
+        n.close()
+    v_b = ev_batched / (ms_batched / 1e3)
+    v_p = ev_plain / (ms_plain / 1e3)
+    return {"value": v_b, "unit": UNIT, "plain_value": v_p, "speedup_vs_plain": v_b / v_p,
+            "instances": len(inst), "neurons": neurons, "steps_each": args.batch_steps,
+            "ms_batched": ms_batched, "ms_plain": ms_plain, "launches": launches_batched,
+            "workload": "64 instances, grid side U{4..16} x 1250 neurons, K=1125, Gaussian (even seed, 7.5 Hz) / "
+                        "exponential (odd seed, 35 Hz), bf16 weights when seed bit 1 is set, one persistent "
+                        "launch replayed from a CUDA graph vs one persistent launch per instance"}
+
+
+def run_served(snn, args, stream):
+    """Poisson stream of requests into the continuous-batching server."""
+    import time as _t
+
+    import numpy as np
+    from paper_1803_08833_gb300 import workloads as W
+    stream_reqs = W.served_stream(seconds=args.served_seconds, rate_hz=20.0, seed=7)
+    budget = 150 << 30
+    results = []
+    with snn.Server(budget, chunk_steps=args.served_chunk, max_slots=args.served_slots, stream=stream) as srv:
+        start = snn.now_ns()
+        i = 0
+        peak = 0
+        while True:
+            now_s = (snn.now_ns() - start) / 1e9
+            while i < len(stream_reqs) and stream_reqs[i][0] <= now_s:
+                t, cfg, steps = stream_reqs[i]
+                srv.submit(cfg, steps, arrival_ns=start + int(t * 1e9), raster_capacity=1 << 10)
+                i += 1
+            a, q = srv.tick()
+            peak = max(peak, a)
+            results += srv.poll()
+            if i == len(stream_reqs) and a == 0 and q == 0:
+                break
+            if a == 0 and q == 0 and i < len(stream_reqs):
+                _t.sleep(max(0.0, stream_reqs[i][0] - (snn.now_ns() - start) / 1e9))
+        wall = (snn.now_ns() - start) / 1e9
+        st = srv.stats()
+    lat = np.array([r["latency_ms"] for r in results])
+    qms = np.array([r["queue_ms"] for r in results])
+    ok = sum(1 for r in results if r["status"] == 0)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_queue_ms": float(qms.mean()), "requests": len(results), "ok": ok,
+            "value": st["rec_events"] / wall, "unit": UNIT, "wall_s": wall, "arrival_window_s": args.served_seconds,
+            "gpu_busy_frac": st["busy_ns"] / 1e9 / wall, "peak_active": peak, "launches": st["launches"],
+            "budget_gb": 150, "chunk_steps": args.served_chunk,
+            "workload": "Poisson arrivals at 20 req/s (seed 7), grid side U{4..32} x 1250 neurons, K U{500..2250}, "
+                        "Gaussian or exponential, every network spiking at %.1f Hz (imposed background rate), "
+                        "duration U{500..5000} steps, bf16 weights, 150 GB budget, continuous batching in chunks "
+                        "of %d steps" % (W.SERVED_RATE_HZ, args.served_chunk)}
+
+
 def _max_op(dist):
     return None if dist is None else dist.ReduceOp.MAX
 
 
 def _sum_op(dist):
     return None if dist is None else dist.ReduceOp.SUM
+
+
+def run_calibration():
+    """Compile and run the memory-system calibration (calibration/l2_rates.cu)."""
+    from paper_1803_08833_gb300 import _build
+    src = os.path.join(ROOT, "paper_1803_08833_gb300", "calibration", "l2_rates.cu")
+    exe = os.path.join(_build.BUILD, "l2_rates")
+    os.makedirs(_build.BUILD, exist_ok=True)
+    subprocess.check_call([_build.nvcc(), *_build.ARCH, "-O3", "-o", exe, src])
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.strip()
+    print(out, flush=True)
+    return 0
 
 
 def main(argv=None):
@@ -428,6 +538,14 @@ def main(argv=None):
     ap.add_argument("--e2e-jobs", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--calibrate", action="store_true", help="measure L2 reduction and stream rates, then exit")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--served-seconds", type=float, default=60.0)
+    ap.add_argument("--served-chunk", type=int, default=250)
+    ap.add_argument("--served-slots", type=int, default=64)
     ap.add_argument("--cpu-grid", type=int, default=6)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--timing-every", type=int, default=10,
@@ -438,6 +556,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "gb300":
         _log("note: fewer than 3 warm-up steps")
+    if args.calibrate:
+        return run_calibration()
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

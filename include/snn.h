@@ -202,6 +202,18 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
 SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
 
+/* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
+ * per delivery block, 2, and 3 if the network has the grouped layout and its
+ * tile fits) for trial_steps steps from the same snapshot of the dynamic
+ * state, times each with CUDA events, restores the state (the raster and the
+ * counters are as before the call) and selects the fastest.  If cache_path
+ * is not NULL the choice is looked up there first and appended after
+ * tuning; the key holds the network's shape, weight type, layout, rates and
+ * the GPU name.  Outputs (may be NULL): the chosen schedule and block, and
+ * the measured ms per step (-1 on a cache hit).  Synchronises `stream`. */
+SNN_API snn_status snn_autotune(snn_net* net, uint32_t trial_steps, const char* cache_path, int32_t* schedule,
+                                int32_t* block, double* best_ms_per_step, void* stream);
+
 /* Kernel timing: with every = n >= 1, the launches of every n-th snn_step
  * time step (schedules 0, 1) or every persistent launch (schedule 2) are
  * bracketed by CUDA events on the launching stream (0 = off).
@@ -257,22 +269,22 @@ SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh,
                                         uint32_t* counts, uint32_t* max_offsets, void* stream);
 
 /* ---- Batched execution: many independent networks in one persistent launch.
- * Network i is simulated by its own group of CTAs (sized in proportion to its
- * estimated work per step, or set with snn_batch_set_groups), with its own
- * grid barriers, for steps[i] time steps; results are bit-identical to
+ * All networks share one global space of neurons and, every step, one global
+ * space of delivery tasks, each split evenly over every warp of the grid,
+ * with one pair of grid barriers per step for the whole batch; network i is
+ * advanced steps[i] time steps per call.  Results are bit-identical to
  * running each network alone.  The nets stay owned by the caller and must
- * outlive the batch.  Errors: SNN_EINVAL (NULL or repeated nets, more nets
- * than co-resident CTAs), SNN_ENOMEM, SNN_ECUDA. */
+ * outlive the batch; the batch uses their wait limit (smallest) and barrier
+ * test knob (largest).  Errors: SNN_EINVAL (NULL or repeated nets, a batch
+ * too large), SNN_ENOMEM, SNN_ECUDA.  A barrier wait that runs out marks
+ * every network of the batch (their snn_get_stats returns SNN_ETIMEOUT). */
 typedef struct snn_batch snn_batch;
 SNN_API snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
                                     void* alloc_ctx, snn_batch** out);
 /* Runs network i for steps[i] (host array of n; 0 = idle) time steps.  Async. */
 SNN_API snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream);
-/* CTAs per network (host array of n, each >= 1, sum <= snn_batch_capacity). */
-SNN_API snn_status snn_batch_set_groups(snn_batch* b, const uint32_t* ctas);
-SNN_API snn_status snn_batch_get_groups(snn_batch* b, uint32_t* ctas, uint32_t* capacity);
 /* enable != 0: snn_batch_step replays a CUDA graph holding the launch
- * (captured on first use; re-captured when the groups change). */
+ * (captured on first use, and again when the longest step count changes). */
 SNN_API snn_status snn_batch_set_graph(snn_batch* b, int32_t enable);
 /* CUDA-event time (ms) and count of the batch launches since creation. */
 SNN_API snn_status snn_batch_time(snn_batch* b, double* ms, uint64_t* launches);
@@ -298,8 +310,8 @@ typedef struct snn_request_result {
     uint64_t state_hash;  /* FNV-1a over the final membrane potentials */
     double queue_ms;      /* arrival -> admission */
     double latency_ms;    /* arrival -> completion */
-    int32_t status;       /* snn_status of the request */
-    int32_t pad;
+    int32_t status;          /* snn_status of the request */
+    int32_t raster_overflow; /* 1 if the request's raster capacity was exceeded (hash over the kept part) */
 } snn_request_result;
 typedef struct snn_server_stats_t {
     uint64_t ticks, launches, rec_events, ext_events, steps, busy_ns, used_bytes;

@@ -1,0 +1,129 @@
+// l2_rates.cu -- memory-system rates that bound spike delivery on this GPU.
+//
+// Measures, with CUDA events: (1) random 4-byte red.global.add.s32 into
+// buffers of several sizes (the delay ring takes one such reduction per
+// synaptic event), (2) the same with the 32 lanes of a warp on consecutive
+// words, (3) a streaming 16-byte read of a 4 GB table (the synapse table
+// stream), (4) the stream with one random reduction per loaded word.
+// Prints one JSON object.  Every address is inside its buffer.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+__global__ void k_red_random(int* buf, uint32_t n, uint32_t R, uint32_t salt) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t r = 0; r < R; ++r) {
+        const uint32_t a = mix32(g * 977u + r * 131071u + salt) % n;
+        asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(buf + a), "r"(1) : "memory");
+    }
+}
+
+__global__ void k_red_coalesced(int* buf, uint32_t n, uint32_t R, uint32_t salt) {
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31, w = g >> 5;
+    for (uint32_t r = 0; r < R; ++r) {
+        const uint32_t a = (mix32(w * 977u + r * 131071u + salt) % (n / 32)) * 32 + lane;
+        asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(buf + a), "r"(1) : "memory");
+    }
+}
+
+__global__ void k_stream(const uint4* tab, size_t n16, uint32_t* sink) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint4 v = __ldcs(tab + i);
+        acc += v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x12345678u) sink[0] = acc;
+}
+
+__global__ void k_stream_red(const uint4* tab, size_t n16, int* buf, uint32_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint4 v = __ldcs(tab + i);
+        const uint32_t t[4] = {v.x % n, v.y % n, v.z % n, v.w % n};
+        for (int q = 0; q < 4; ++q)
+            asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(buf + t[q]), "r"(1) : "memory");
+    }
+}
+
+__global__ void k_fill(uint4* tab, size_t n16) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride)
+        tab[i] = make_uint4(mix32((uint32_t)i * 4), mix32((uint32_t)i * 4 + 1), mix32((uint32_t)i * 4 + 2),
+                            mix32((uint32_t)i * 4 + 3));
+}
+
+int main() {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const uint32_t sizes_mb[] = {4, 16, 60, 256, 1024};
+    const uint32_t max_words = 1024u << 18;  // 1 GiB of int32
+    int* buf = nullptr;
+    uint4* tab = nullptr;
+    uint32_t* sink = nullptr;
+    const size_t tab_bytes = (size_t)4 << 30;
+    if (cudaMalloc(&buf, (size_t)max_words * 4) != cudaSuccess || cudaMalloc(&tab, tab_bytes) != cudaSuccess ||
+        cudaMalloc(&sink, 64) != cudaSuccess) {
+        printf("{\"error\": \"allocation failed\"}\n");
+        return 1;
+    }
+    cudaMemset(buf, 0, (size_t)max_words * 4);
+    k_fill<<<sms * 8, 256>>>(tab, tab_bytes / 16);
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float ms = 0.0f;
+    const int grid = sms * 16;
+    const uint32_t R = 32;
+    const double total = (double)grid * 256 * R;
+    printf("{\"sms\": %d, \"random_red_per_s\": {", sms);
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t n = sizes_mb[k] << 18;
+        k_red_random<<<grid, 256>>>(buf, n, R, 1);
+        cudaEventRecord(a);
+        for (int it = 0; it < 5; ++it) k_red_random<<<grid, 256>>>(buf, n, R, 7 + it);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        printf("%s\"%u MB\": %.4g", k ? ", " : "", sizes_mb[k], 5.0 * total / (ms * 1e-3));
+    }
+    printf("}, \"coalesced_red_per_s\": {");
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t n = sizes_mb[k] << 18;
+        cudaEventRecord(a);
+        for (int it = 0; it < 5; ++it) k_red_coalesced<<<grid, 256>>>(buf, n, R, 7 + it);
+        cudaEventRecord(b);
+        cudaEventSynchronize(b);
+        cudaEventElapsedTime(&ms, a, b);
+        printf("%s\"%u MB\": %.4g", k ? ", " : "", sizes_mb[k], 5.0 * total / (ms * 1e-3));
+    }
+    cudaEventRecord(a);
+    for (int it = 0; it < 3; ++it) k_stream<<<sms * 8, 256>>>(tab, tab_bytes / 16, sink);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    printf("}, \"stream_read_gb_per_s\": %.1f", 3.0 * tab_bytes / (ms * 1e-3) / 1e9);
+    const size_t part = tab_bytes / 16 / 16;
+    const uint32_t n60 = 60u << 18;
+    cudaEventRecord(a);
+    k_stream_red<<<sms * 16, 256>>>(tab, part, buf, n60);
+    cudaEventRecord(b);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&ms, a, b);
+    printf(", \"stream_plus_random_red\": {\"red_per_s\": %.4g, \"table_gb_per_s\": %.1f}", part * 4.0 / (ms * 1e-3),
+           part * 16.0 / (ms * 1e-3) / 1e9);
+    const cudaError_t e = cudaGetLastError();
+    printf(", \"status\": \"%s\"}\n", cudaGetErrorString(e));
+    return e == cudaSuccess ? 0 : 1;
+}

@@ -17,17 +17,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Barrier over the G CTAs that simulate network v (all co-resident:
-// cooperative launch).  Returns false if this CTA's wait ran out or another
-// CTA of the network reported an error.
-__device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen) {
+// Barrier over `expected` CTAs on the counters of `st` (all CTAs are
+// co-resident: cooperative launch).  Returns false if this CTA's wait ran out
+// (after limit_ns of the global timer; it then sets ERR_BARRIER_TIMEOUT) or
+// another CTA reported an error.
+__device__ inline bool grid_barrier_on(DevState* st, uint32_t expected, uint64_t limit_ns, uint32_t& gen) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        DevState* st = v.st;
         int ok = 1;
         __threadfence();  // publish this CTA's writes before arriving
-        const uint32_t expected = G + v.barrier_extra;
         const uint32_t arrived = atomicAdd(&st->bar_count, 1u);
         if (arrived == expected - 1) {
             atomicExch(&st->bar_count, 0u);
@@ -36,7 +35,7 @@ __device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen)
         } else {
             const uint64_t start = global_ns();
             while (ld_acquire(&st->bar_gen) == gen) {
-                if (global_ns() - start > v.wait_limit_ns) {
+                if (global_ns() - start > limit_ns) {
                     atomicOr(&st->err, ERR_BARRIER_TIMEOUT);
                     ok = 0;
                     break;
@@ -51,6 +50,11 @@ __device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen)
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Barrier over the G CTAs that simulate network v.
+__device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen) {
+    return grid_barrier_on(v.st, G + v.barrier_extra, v.wait_limit_ns, gen);
 }
 
 // Exclusive prefix of cnt[0..n) into out[0..n], out[n] = total (one block of

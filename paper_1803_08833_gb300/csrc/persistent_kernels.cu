@@ -170,44 +170,6 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     run_steps<BF16>(v, n_steps, gridDim.x, blockIdx.x, smem);
 }
 
-// Many independent networks in one cooperative launch: network i runs on CTAs
-// [cta_first[i], cta_first[i + 1]) for steps[i] time steps, with its own
-// barriers; networks with different weight types share the launch.
-__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS)
-    k_run_batch(const NetView* __restrict__ views, const uint32_t* __restrict__ cta_first,
-                const uint32_t* __restrict__ steps, uint32_t n_inst) {
-    extern __shared__ uint32_t smem[];
-    __shared__ NetView s_v;
-    __shared__ uint32_t s_i;
-    if (threadIdx.x == 0) {
-        uint32_t lo = 0, hi = n_inst;  // largest i with cta_first[i] <= blockIdx.x
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (cta_first[mid] <= blockIdx.x)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        s_i = lo;
-    }
-    __syncthreads();
-    const uint32_t i = s_i;
-    const uint32_t first = cta_first[i], G = cta_first[i + 1] - first;
-    if (blockIdx.x >= cta_first[n_inst] || G == 0) return;
-    {  // the network's view, copied to shared memory word by word
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(views + i);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_v);
-        for (uint32_t k = threadIdx.x; k < sizeof(NetView) / 4; k += blockDim.x) dst[k] = src[k];
-    }
-    __syncthreads();
-    const uint32_t n = steps[i];
-    if (n == 0) return;
-    if (s_v.w_bf16)
-        run_steps<true>(s_v, n, G, blockIdx.x - first, smem);
-    else
-        run_steps<false>(s_v, n, G, blockIdx.x - first, smem);
-}
-
 static const void* persistent_fn(bool bf16) {
     return bf16 ? (const void*)k_run_steps<true> : (const void*)k_run_steps<false>;
 }
@@ -233,32 +195,6 @@ int persistent_grid(bool bf16) {
         if (fit >= per_sm) return grid;
     }
     return sms;
-}
-
-int batch_grid(uint32_t max_group) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int fit = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_batch, PERSIST_THREADS,
-                                                      persistent_smem((int)max_group)) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return fit * sms;
-}
-
-cudaError_t launch_batch(const NetView* views, const uint32_t* cta_first, const uint32_t* steps, uint32_t n_inst,
-                         int grid, uint32_t max_group, cudaStream_t s) {
-    const size_t smem = persistent_smem((int)max_group);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_run_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    void* args[] = {(void*)&views, (void*)&cta_first, (void*)&steps, (void*)&n_inst};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_run_batch, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
-    count_launch(1);
-    return e;
 }
 
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {

@@ -149,7 +149,10 @@ static snn_status retire(snn_server* s, Active& a, uint64_t t_ns) {
     std::vector<uint32_t> steps(cap), ids(cap);
     size_t got = 0;
     e = snn_read_spikes(a.net, steps.data(), ids.data(), cap, &got, s->stream);
-    if (e != SNN_OK && r.status == SNN_OK) r.status = e;
+    if (e == SNN_EOVERFLOW)
+        r.raster_overflow = 1;  // the raster kept its first `cap` spikes; the counters are complete
+    else if (e != SNN_OK && r.status == SNN_OK)
+        r.status = e;
     uint64_t h = 1469598103934665603ull;
     h = fnv(steps.data(), got * 4, h);
     h = fnv(ids.data(), got * 4, h);

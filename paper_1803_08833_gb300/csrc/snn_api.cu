@@ -461,6 +461,16 @@ constexpr uint64_t SNAP_MAGIC = 0x31504E5350534E53ull;  // "SNSPSNP1"
 
 }  // namespace
 
+const snn_config* snn_config_of(const snn_net* net) { return &net->cfg; }
+
+cudaError_t snn_set_raster_count(snn_net* net, uint64_t count, cudaStream_t s) {
+    static thread_local uint64_t staged;  // pageable source: copied before the call returns
+    staged = count;
+    cudaError_t e = cudaMemcpyAsync(&net->v.st->raster_count, &staged, sizeof staged, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
 extern "C" {
 
 const char* snn_last_error(void) { return g_last_error.c_str(); }
@@ -821,16 +831,16 @@ struct snn_batch {
     snn_free_fn free_fn = nullptr;
     void* alloc_ctx = nullptr;
     std::vector<void*> blocks;
+    BatchMeta meta{};
     NetView* d_views = nullptr;
-    uint32_t* d_first = nullptr;
     uint32_t* d_steps = nullptr;
     uint32_t* h_steps = nullptr;  // pinned staging of the per-network steps
-    std::vector<uint32_t> groups;
-    int capacity = 0;
+    int grid = 0;
     bool use_graph = false;
     bool graph_valid = false;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    uint32_t graph_steps = 0;
     EventRing ev;
 };
 
@@ -849,50 +859,7 @@ void* batch_alloc(snn_batch* b, size_t bytes) {
     return p;
 }
 
-// Estimated work per step: neuron updates plus synaptic events at the
-// imposed rate (1 Hz when none is set), an event weighing half an update.
-double batch_cost(const snn_net* n) {
-    const double rate = std::max(1.0, (double)n->cfg.imposed_rate_hz) * n->cfg.dt_ms / 1000.0;
-    return (double)n->N * (1.0 + 0.5 * rate * n->K) + 1.0;
-}
-
-snn_status batch_upload(snn_batch* b, cudaStream_t s) {
-    const uint32_t n = (uint32_t)b->nets.size();
-    std::vector<NetView> views(n);
-    std::vector<uint32_t> first(n + 1, 0);
-    for (uint32_t i = 0; i < n; ++i) {
-        views[i] = b->nets[i]->v;
-        first[i + 1] = first[i] + b->groups[i];
-    }
-    CUDA_TRY(cudaMemcpyAsync(b->d_views, views.data(), n * sizeof(NetView), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(b->d_first, first.data(), (n + 1) * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    return SNN_OK;
-}
-
 }  // namespace
-
-snn_status snn_batch_set_groups(snn_batch* b, const uint32_t* ctas) {
-    if (!b || !ctas) return fail(SNN_EINVAL, "batch or ctas is NULL");
-    uint64_t sum = 0;
-    for (size_t i = 0; i < b->nets.size(); ++i) {
-        if (ctas[i] < 1 || (int)ctas[i] > b->nets[i]->pgrid)
-            return fail(SNN_EINVAL, "network %zu: %u CTAs outside [1, %d]", i, ctas[i], b->nets[i]->pgrid);
-        sum += ctas[i];
-    }
-    if (sum > (uint64_t)b->capacity) return fail(SNN_EINVAL, "%llu CTAs exceed the co-resident capacity %d",
-                                                  (unsigned long long)sum, b->capacity);
-    b->groups.assign(ctas, ctas + b->nets.size());
-    b->graph_valid = false;
-    return batch_upload(b, nullptr);
-}
-
-snn_status snn_batch_get_groups(snn_batch* b, uint32_t* ctas, uint32_t* capacity) {
-    if (!b) return fail(SNN_EINVAL, "batch is NULL");
-    if (ctas) std::copy(b->groups.begin(), b->groups.end(), ctas);
-    if (capacity) *capacity = (uint32_t)b->capacity;
-    return SNN_OK;
-}
 
 snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
                             void* alloc_ctx, snn_batch** out) {
@@ -900,45 +867,92 @@ snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc
     *out = nullptr;
     if ((alloc_fn == nullptr) != (free_fn == nullptr))
         return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+    uint64_t Qtot = 0, tasks = 0;
     for (uint32_t i = 0; i < n; ++i) {
         if (!nets[i]) return fail(SNN_EINVAL, "network %u is NULL", i);
         for (uint32_t j = 0; j < i; ++j)
             if (nets[j] == nets[i]) return fail(SNN_EINVAL, "network %u appears twice", i);
+        Qtot += nets[i]->Npad / 4;
+        tasks += (uint64_t)nets[i]->N * ((nets[i]->K + 127) / 128);
     }
-    int max_group = 0;
-    for (uint32_t i = 0; i < n; ++i) max_group = std::max(max_group, nets[i]->pgrid);
-    const int capacity = batch_grid((uint32_t)max_group);
-    if (capacity < (int)n) return fail(SNN_EINVAL, "%u networks exceed the %d co-resident CTAs", n, capacity);
+    if (Qtot >= (1ull << 32) || tasks >= (1ull << 32)) return fail(SNN_EINVAL, "the batch is too large");
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = batch_grid(n, (uint32_t)(8 * PERSIST_WARPS * sms) + n);
+    if (grid <= 0) return fail(SNN_EINVAL, "the batch kernel does not fit on this device (n = %u)", n);
     snn_batch* b = new (std::nothrow) snn_batch();
     if (!b) return fail(SNN_ENOMEM, "host allocation failed");
     b->nets.assign(nets, nets + n);
     b->alloc_fn = alloc_fn;
     b->free_fn = free_fn;
     b->alloc_ctx = alloc_ctx;
-    b->capacity = capacity;
+    b->grid = grid;
+    // global quad offsets; first and last warp overlapping each network
+    const uint64_t TW = (uint64_t)grid * PERSIST_WARPS;
+    std::vector<uint32_t> qoff(n + 1, 0), wlo(n, 0), cbase(n + 1, 0);
+    for (uint32_t i = 0; i < n; ++i) qoff[i + 1] = qoff[i] + nets[i]->Npad / 4;
+    auto owner = [&](uint64_t q) {  // the warp whose range [Qtot w / TW, Qtot (w+1) / TW) holds quad q
+        uint64_t lo = 0, hi = TW;
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (Qtot * mid / TW <= q)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        return (uint32_t)lo;
+    };
+    for (uint32_t i = 0; i < n; ++i) {
+        wlo[i] = owner(qoff[i]);
+        const uint32_t whi = owner(qoff[i + 1] - 1);
+        cbase[i + 1] = cbase[i] + (whi - wlo[i] + 1);
+    }
+    const uint32_t n_seg = cbase[n];
     b->d_views = (NetView*)batch_alloc(b, n * sizeof(NetView));
-    b->d_first = (uint32_t*)batch_alloc(b, (n + 1) * 4);
     b->d_steps = (uint32_t*)batch_alloc(b, n * 4);
-    if (!b->d_views || !b->d_first || !b->d_steps || cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
+    uint32_t* d_qoff = (uint32_t*)batch_alloc(b, (n + 1) * 4);
+    uint32_t* d_cbase = (uint32_t*)batch_alloc(b, (n + 1) * 4);
+    uint32_t* d_wlo = (uint32_t*)batch_alloc(b, n * 4);
+    uint32_t* d_wcnt = (uint32_t*)batch_alloc(b, (size_t)n_seg * 4);
+    DevState* d_st = (DevState*)batch_alloc(b, sizeof(DevState));
+    if (!b->d_views || !b->d_steps || !d_qoff || !d_cbase || !d_wlo || !d_wcnt || !d_st ||
+        cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
         cudaGetLastError();
         snn_batch_destroy(b);
         return fail(SNN_ENOMEM, "batch allocation failed");
     }
-    // CTAs in proportion to the estimated work, at least one each
-    std::vector<double> cost(n);
-    double total = 0.0;
-    for (uint32_t i = 0; i < n; ++i) total += cost[i] = batch_cost(nets[i]);
-    std::vector<uint32_t> g(n, 1);
-    int left = capacity - (int)n;
+    std::vector<NetView> views(n);
+    uint64_t limit = ~0ull;
+    uint32_t extra = 0;
     for (uint32_t i = 0; i < n; ++i) {
-        const int extra = std::min((int)std::floor(cost[i] / total * left), nets[i]->pgrid - 1);
-        g[i] += (uint32_t)std::max(extra, 0);
+        views[i] = nets[i]->v;
+        limit = std::min(limit, nets[i]->v.wait_limit_ns);
+        extra = std::max(extra, nets[i]->v.barrier_extra);
     }
-    snn_status st = snn_batch_set_groups(b, g.data());
-    if (st != SNN_OK) {
+    cudaError_t e = cudaMemcpy(b->d_views, views.data(), n * sizeof(NetView), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_qoff, qoff.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_cbase, cbase.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_wlo, wlo.data(), n * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_wcnt, 0, (size_t)n_seg * 4);
+    if (e == cudaSuccess) e = cudaMemset(d_st, 0, sizeof(DevState));
+    if (e != cudaSuccess) {
         snn_batch_destroy(b);
-        return st;
+        return fail(SNN_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
     }
+    BatchMeta& m = b->meta;
+    m.views = b->d_views;
+    m.qoff = d_qoff;
+    m.cbase = d_cbase;
+    m.wlo = d_wlo;
+    m.wcnt = d_wcnt;
+    m.steps = b->d_steps;
+    m.bst = d_st;
+    m.wait_limit_ns = limit;
+    m.barrier_extra = extra;
+    m.n = n;
+    m.n_seg = n_seg;
+    m.Qtot = (uint32_t)Qtot;
     *out = b;
     return SNN_OK;
 }
@@ -955,24 +969,24 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     const uint32_t n = (uint32_t)b->nets.size();
     // the pinned staging buffer may still feed the previous call's copy
     CUDA_TRY(cudaStreamSynchronize(s));
+    uint32_t max_steps = 0;
+    for (uint32_t i = 0; i < n; ++i) max_steps = std::max(max_steps, steps[i]);
+    if (max_steps == 0) return SNN_OK;
     std::copy(steps, steps + n, b->h_steps);
     CUDA_TRY(cudaMemcpyAsync(b->d_steps, b->h_steps, n * 4, cudaMemcpyHostToDevice, s));
-    uint32_t max_group = 0;
-    for (uint32_t gi : b->groups) max_group = std::max(max_group, gi);
-    int total = 0;
-    for (uint32_t gi : b->groups) total += (int)gi;
+    CUDA_TRY(cudaMemsetAsync(&b->meta.bst->bar_count, 0, sizeof(uint32_t), s));
     int slot = 0;
     snn_status st = timed_begin(b->ev, s, &slot);
     if (st != SNN_OK) return st;
     if (b->use_graph) {
-        if (!b->graph_valid) {
+        if (!b->graph_valid || b->graph_steps != max_steps) {
             if (b->exec) {
                 cudaGraphExecDestroy(b->exec);
                 b->exec = nullptr;
             }
             if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
             CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = launch_batch(b->d_views, b->d_first, b->d_steps, n, total, max_group, b->cap_stream);
+            cudaError_t le = launch_batch(b->meta, max_steps, b->grid, b->cap_stream);
             cudaGraph_t graph = nullptr;
             cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
             if (le != cudaSuccess || ce != cudaSuccess) {
@@ -984,11 +998,12 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
             cudaGraphDestroy(graph);
             if (ie != cudaSuccess) return fail(SNN_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
             b->graph_valid = true;
+            b->graph_steps = max_steps;
         }
         CUDA_TRY(cudaGraphLaunch(b->exec, s));
         count_launch(1);
     } else {
-        CUDA_TRY(launch_batch(b->d_views, b->d_first, b->d_steps, n, total, max_group, s));
+        CUDA_TRY(launch_batch(b->meta, max_steps, b->grid, s));
     }
     return timed_end(b->ev, s, slot);
 }

@@ -109,9 +109,21 @@ cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);
 cudaError_t launch_deliver(const NetView& v, int schedule, int block, int grid, cudaStream_t s);
 int deliver_default_grid(int schedule, int block, uint32_t nb, bool bf16);
 int persistent_grid(bool bf16);
-int batch_grid(uint32_t max_group);
-cudaError_t launch_batch(const NetView* views, const uint32_t* cta_first, const uint32_t* steps, uint32_t n_inst,
-                         int grid, uint32_t max_group, cudaStream_t s);
+// Batched execution: n networks in one global quad / task space.
+struct BatchMeta {
+    const NetView* views;   // n
+    const uint32_t* qoff;   // n + 1: global quad offsets of the networks
+    const uint32_t* cbase;  // n + 1: first (network, warp) segment of each network
+    const uint32_t* wlo;    // n: first warp whose quads overlap the network
+    uint32_t* wcnt;         // n_seg spike counts of the (network, warp) segments
+    const uint32_t* steps;  // n: steps of this launch per network
+    DevState* bst;          // barrier state of the batch
+    uint64_t wait_limit_ns;
+    uint32_t barrier_extra;
+    uint32_t n, n_seg, Qtot;
+};
+int batch_grid(uint32_t n, uint32_t n_seg_bound);
+cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, cudaStream_t s);
 int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
@@ -121,3 +133,9 @@ void count_launch(uint64_t n);
 void set_last_error(const char* msg);  // message returned by snn_last_error()
 
 }  // namespace snn
+
+// Host-side accessors of a network for the library's own runtime parts.
+struct snn_net;
+struct snn_config;
+const snn_config* snn_config_of(const snn_net* net);
+cudaError_t snn_set_raster_count(snn_net* net, uint64_t count, cudaStream_t s);

@@ -53,6 +53,20 @@ class SnnStats(ctypes.Structure):
                  "neuron_phase_ns", "deliver_phase_ns")]
 
 
+class RequestResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("n_spikes", ctypes.c_uint64),
+                ("rec_events", ctypes.c_uint64), ("ext_events", ctypes.c_uint64),
+                ("raster_hash", ctypes.c_uint64), ("state_hash", ctypes.c_uint64),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("raster_overflow", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("ticks", "launches", "rec_events", "ext_events", "steps", "busy_ns", "used_bytes")] + \
+               [("active", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -87,6 +101,8 @@ def load():
         "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
+                              P(ctypes.c_double), vp]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
         "snn_kernel_time": (st, [vp, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_uint64)]),
         "snn_set_wait_limit": (st, [vp, ctypes.c_uint64]),
@@ -96,11 +112,18 @@ def load():
         "snn_launch_count": (ctypes.c_uint64, []),
         "snn_batch_create": (st, [P(vp), ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, P(vp)]),
         "snn_batch_step": (st, [vp, P(ctypes.c_uint32), vp]),
-        "snn_batch_set_groups": (st, [vp, P(ctypes.c_uint32)]),
-        "snn_batch_get_groups": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32)]),
         "snn_batch_set_graph": (st, [vp, ctypes.c_int32]),
         "snn_batch_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64)]),
         "snn_batch_destroy": (None, [vp]),
+        "snn_estimate_bytes": (ctypes.c_uint64, [P(SnnConfig)]),
+        "snn_now_ns": (ctypes.c_uint64, []),
+        "snn_server_create": (st, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, vp,
+                                   P(vp)]),
+        "snn_server_submit": (st, [vp, P(SnnConfig), ctypes.c_uint32, ctypes.c_uint64, P(ctypes.c_uint64)]),
+        "snn_server_tick": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32)]),
+        "snn_server_poll": (st, [vp, vp, ctypes.c_uint32, P(ctypes.c_uint32)]),
+        "snn_server_stats": (st, [vp, vp]),
+        "snn_server_destroy": (None, [vp]),
         "snn_destroy": (None, [vp]),
         "snn_last_error": (ctypes.c_char_p, []),
     }
@@ -302,6 +325,13 @@ class Network:
     def set_schedule(self, schedule: int, block: int = 0):
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
 
+    def autotune(self, trial_steps: int = 20, cache_path=None):
+        """Pick the fastest schedule (state unchanged); returns (schedule, block, ms per step)."""
+        sc, bl, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        check(load().snn_autotune(self._h, int(trial_steps), None if cache_path is None else cache_path.encode(),
+                                  ctypes.byref(sc), ctypes.byref(bl), ctypes.byref(ms), self._s))
+        return sc.value, bl.value, ms.value
+
     def set_timing(self, every: int):
         """Bracket the kernels of every n-th step with CUDA events (0 = off)."""
         check(load().snn_set_timing(self._h, int(every)))
@@ -351,17 +381,6 @@ class Batch:
         arr = (ctypes.c_uint32 * n)(*[int(x) for x in steps])
         check(load().snn_batch_step(self._h, arr, self._s))
 
-    def groups(self):
-        n = len(self.nets)
-        arr = (ctypes.c_uint32 * n)()
-        cap = ctypes.c_uint32()
-        check(load().snn_batch_get_groups(self._h, arr, ctypes.byref(cap)))
-        return list(arr), cap.value
-
-    def set_groups(self, ctas):
-        arr = (ctypes.c_uint32 * len(self.nets))(*[int(x) for x in ctas])
-        check(load().snn_batch_set_groups(self._h, arr))
-
     def set_graph(self, enable: bool):
         check(load().snn_batch_set_graph(self._h, 1 if enable else 0))
 
@@ -373,6 +392,75 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             load().snn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def now_ns() -> int:
+    """The library's host monotonic clock (time base of request arrivals)."""
+    return int(load().snn_now_ns())
+
+
+def estimate_bytes(cfg: dict, raster_capacity: int = 0) -> int:
+    c = config(cfg, raster_capacity)
+    return int(load().snn_estimate_bytes(ctypes.byref(c)))
+
+
+class Server:
+    """Continuous-batching simulation server (snn_server_* of the C ABI)."""
+
+    def __init__(self, budget_bytes: int, chunk_steps: int = 250, max_slots: int = 128, stream=None):
+        import torch
+        dev = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._s = ctypes.c_void_p(self.stream.cuda_stream)
+        self._alloc = _TorchAllocator(dev, self.stream)
+        h = ctypes.c_void_p()
+        check(load().snn_server_create(int(budget_bytes), int(chunk_steps), int(max_slots), self._alloc.alloc,
+                                       self._alloc.free, None, self._s, ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, cfg: dict, steps: int, arrival_ns: int = 0, raster_capacity: int = 1 << 16) -> int:
+        c = config(cfg, raster_capacity)
+        rid = ctypes.c_uint64()
+        check(load().snn_server_submit(self._h, ctypes.byref(c), int(steps), int(arrival_ns), ctypes.byref(rid)))
+        return rid.value
+
+    def tick(self):
+        a, q = ctypes.c_uint32(), ctypes.c_uint32()
+        check(load().snn_server_tick(self._h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self):
+        out = []
+        buf = (RequestResult * 256)()
+        while True:
+            n = ctypes.c_uint32()
+            check(load().snn_server_poll(self._h, buf, 256, ctypes.byref(n)))
+            out += [{f[0]: getattr(buf[i], f[0]) for f in RequestResult._fields_}
+                    for i in range(n.value)]
+            if n.value < 256:
+                return out
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(load().snn_server_stats(self._h, ctypes.byref(st)))
+        return {f[0]: getattr(st, f[0]) for f in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().snn_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -69,3 +69,52 @@ def small(grid=2, M=40, K=30, lateral="gauss", seed=3, **kw):
 # kernel, 32-38 Hz with the exponential one.  Used as imposed rates.
 PAPER_RATE_GAUSS_HZ = 7.5
 PAPER_RATE_EXP_HZ = 35.0
+
+
+def paper_rate(lateral):
+    return PAPER_RATE_GAUSS_HZ if lateral == "gauss" else PAPER_RATE_EXP_HZ
+
+
+def batched_instances(n=64, K=1125, steps=2000, seed0=0):
+    """Independent instances for one batched launch: instance s (seeds 0..n-1)
+    has a grid side uniform in 4..16 modules of 1,250 neurons, K = 1,125, the
+    Gaussian kernel for even s and the exponential one for odd s, bf16 weights
+    when bit 1 of s is set, and spikes at the paper's rate for its kernel.
+    Returns [(config, steps)]."""
+    import numpy as np
+    out = []
+    for s in range(seed0, seed0 + n):
+        rng = np.random.default_rng(1000 + s)
+        side = int(rng.integers(4, 17))
+        lateral = "gauss" if s % 2 == 0 else "exp"
+        cfg = _make(side, 1250, K, _GAUSS if lateral == "gauss" else _EXP, seed=s,
+                    weight_dtype="bf16" if (s >> 1) & 1 else "f32", imposed_rate_hz=paper_rate(lateral))
+        out.append((cfg, steps))
+    return out
+
+
+SERVED_RATE_HZ = 2.0
+
+
+def served_stream(seconds=60.0, rate_hz=20.0, seed=7, spike_rate_hz=SERVED_RATE_HZ):
+    """Poisson arrivals of simulation requests: grid side uniform 4..32 modules
+    of 1,250 neurons, K uniform 500..2,250, Gaussian or exponential kernel,
+    duration uniform 500..5,000 steps, bf16 weights, every network spiking at
+    `spike_rate_hz` (imposed).  At the paper's rates (7.5 / 35 Hz) this stream
+    asks for several times what one GPU delivers, so the default is a 2 Hz
+    background rate.  Returns [(arrival_s, config, steps)]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    t, out, k = 0.0, [], 0
+    while True:
+        t += float(rng.exponential(1.0 / rate_hz))
+        if t >= seconds:
+            return out
+        side = int(rng.integers(4, 33))
+        K = int(rng.integers(500, 2251))
+        lateral = "gauss" if rng.random() < 0.5 else "exp"
+        steps = int(rng.integers(500, 5001))
+        cfg = _make(side, 1250, K, _GAUSS if lateral == "gauss" else _EXP, seed=10000 + k, weight_dtype="bf16",
+                    imposed_rate_hz=spike_rate_hz)
+        out.append((t, cfg, steps))
+        k += 1

@@ -112,3 +112,13 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(snn, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="libsnn.so not found"):
         snn.load()
+
+
+def test_memory_estimate_tracks_the_table(lib):
+    small = snn.estimate_bytes(W.gauss_4x4_k1000())
+    big = snn.estimate_bytes(W.gauss_24x24_k1125())
+    bf = snn.estimate_bytes(W.exp_24x24_k2250(weight_dtype="bf16"))
+    f32 = snn.estimate_bytes(W.exp_24x24_k2250(weight_dtype="f32"))
+    assert 144e6 < small < 400e6            # 16 M synapses x 9 B + state
+    assert 7.3e9 < big < 7.8e9              # 810 M synapses x 9 B + ring
+    assert bf < f32 and abs((f32 - bf) - 720000 * 2256 * 2) < 1e6

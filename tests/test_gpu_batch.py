@@ -51,8 +51,6 @@ def test_batch_equals_each_network_alone(snn, graph):
     refs = [oracle.OracleNet(c) for c in cfgs]
     with snn.Batch(nets) as batch:
         batch.set_graph(graph)
-        groups, cap = batch.groups()
-        assert all(g >= 1 for g in groups) and sum(groups) <= cap
         plans = [[60, 45, 60, 0, 30, 50], [10, 10, 0, 25, 10, 10], [10, 10, 0, 25, 10, 10]]
         for steps in plans:
             batch.step(steps)
@@ -66,21 +64,29 @@ def test_batch_equals_each_network_alone(snn, graph):
         n.close()
 
 
-def test_batch_groups_can_be_set_and_are_validated(snn):
-    cfgs = _cases()[:3]
+def test_batch_of_one_equals_the_persistent_schedule(snn):
+    cfg = W.small(grid=3, M=100, K=60, seed=8, imposed_rate_hz=30.0)
+    with snn.Network(cfg) as a, snn.Network(cfg) as b:
+        a.set_schedule(2)
+        a.step(70)
+        with snn.Batch([b]) as batch:
+            batch.step([70])
+        sa, sb = a.state(), b.state()
+        for k in ("V", "c", "ref", "ring", "t"):
+            assert np.array_equal(sa[k], sb[k]), k
+        assert all(np.array_equal(x, y) for x, y in zip(a.read_spikes(), b.read_spikes()))
+
+
+def test_batch_barrier_wait_runs_out(snn):
+    cfgs = _cases()[:2]
     nets = [snn.Network(c) for c in cfgs]
-    refs = [oracle.OracleNet(c) for c in cfgs]
+    nets[0].set_wait_limit(2_000_000)
+    nets[1].set_barrier_extra(1)
     with snn.Batch(nets) as batch:
-        batch.set_groups([1, 2, 3])
-        assert batch.groups()[0] == [1, 2, 3]
-        with pytest.raises(snn.SnnError):
-            batch.set_groups([0, 1, 1])
-        batch.step(40)
-        for r in refs:
-            r.step(40)
-        for net, ref in zip(nets, refs):
-            _check(net, ref)
+        batch.step([5, 5])
     for n in nets:
+        with pytest.raises(snn.SnnError, match="SNN_ETIMEOUT"):
+            n.stats()
         n.close()
 
 

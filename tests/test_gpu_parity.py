@@ -363,3 +363,46 @@ def test_bounded_barrier_wait_reports_timeout(snn):
         ref = oracle.OracleNet(cfg)
         ref.step(10)
         _compare(net2, ref)
+
+
+def test_autotune_leaves_the_simulation_unchanged(snn, tmp_path):
+    cfg = dict(W.small(grid=3, M=200, K=150, seed=3, imposed_rate_hz=50.0), table_layout="grouped")
+    cache = str(tmp_path / "tune.txt")
+    with snn.Network(cfg) as net:
+        net.step(20)
+        sched, block, ms = net.autotune(trial_steps=15, cache_path=cache)
+        assert sched in (0, 1, 2, 3) and ms > 0
+        net.step(30)
+        ref = oracle.OracleNet(cfg)
+        ref.step(50)
+        _compare(net, ref)
+    with snn.Network(cfg) as net2:  # the cached choice is reused
+        s2, b2, ms2 = net2.autotune(trial_steps=15, cache_path=cache)
+        assert (s2, b2) == (sched, block) and ms2 == -1.0
+
+
+def test_allocation_failure_is_reported_and_releases_everything(snn):
+    import ctypes
+    L = snn.load()
+    live = {}
+    calls = {"n": 0}
+    import torch
+
+    def alloc(size, ctx):
+        calls["n"] += 1
+        if calls["n"] == 6:  # fail the sixth allocation
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(size))
+        live[p] = size
+        return p
+
+    def free(ptr, ctx):
+        live.pop(ptr)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = snn.ALLOC_FN(alloc), snn.FREE_FN(free)
+    c = snn.config(W.small())
+    h = ctypes.c_void_p()
+    st = L.snn_build_network(ctypes.byref(c), fa, ff, None, None, ctypes.byref(h))
+    assert st == snn.SNN_ENOMEM and h.value is None
+    assert live == {}  # every block obtained before the failure was returned

@@ -1,0 +1,87 @@
+"""Serving: requests admitted under a memory budget into a continuous-batching
+loop.  Every result must be the same alone and in the mix (bit for bit: the
+spike raster and final state hashes), and match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_08833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    from paper_1803_08833_gb300 import _build
+    from paper_1803_08833_gb300 import snn as S
+    _build.build()
+    S.load()
+    return S
+
+
+def _fnv(arrs):
+    h = 1469598103934665603
+    for a in arrs:
+        for b in np.ascontiguousarray(a).view(np.uint8).tolist():
+            h = ((h ^ b) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+REQUESTS = [
+    (W.small(grid=2, M=120, K=77, seed=5, imposed_rate_hz=30.0, ext_rate_hz=3000.0), 90),
+    (W.small(grid=3, M=100, K=200, lateral="exp", seed=6, weight_dtype="bf16", imposed_rate_hz=35.0), 140),
+    (W.small(grid=4, M=50, K=150, seed=7, ext_rate_hz=5000.0), 60),
+    (dict(W.small(grid=3, M=333, K=37, seed=9, imposed_rate_hz=40.0), grid_h=2), 250),
+    (W.small(grid=2, M=64, K=10, seed=1, ext_rate_hz=0.0), 30),
+]
+
+
+def _serve(snn, reqs, budget, chunk=40, stagger=False):
+    out = {}
+    with snn.Server(budget, chunk_steps=chunk) as srv:
+        ids = []
+        for k, (cfg, steps) in enumerate(reqs):
+            ids.append(srv.submit(cfg, steps))
+            if stagger and k % 2 == 1:
+                srv.tick()  # later requests arrive while earlier ones run
+        for _ in range(1000):
+            a, q = srv.tick()
+            for r in srv.poll():
+                out[r["request_id"]] = r
+            if a == 0 and q == 0:
+                break
+        for r in srv.poll():
+            out[r["request_id"]] = r
+    return [out[i] for i in ids]
+
+
+def test_results_alone_equal_results_in_the_mix(snn):
+    budget = 8 << 30
+    alone = [_serve(snn, [r], budget)[0] for r in REQUESTS]
+    mixed = _serve(snn, REQUESTS, budget, stagger=True)
+    for a, m in zip(alone, mixed):
+        assert a["status"] == 0 and m["status"] == 0
+        for k in ("steps", "n_spikes", "rec_events", "ext_events", "raster_hash", "state_hash"):
+            assert a[k] == m[k], k
+    # one of them against the oracle
+    cfg, steps = REQUESTS[1]
+    ref = oracle.OracleNet(cfg)
+    ref.step(steps)
+    st, ids = ref.raster()
+    assert mixed[1]["n_spikes"] == len(st) == ref.stats()["spikes"]
+    assert mixed[1]["raster_hash"] == _fnv([st, ids])
+    assert mixed[1]["state_hash"] == _fnv([ref.state()["V"]])
+
+
+def test_budget_admission_queues_and_rejects(snn):
+    need = [snn.estimate_bytes(c, 1 << 16) for c, _ in REQUESTS]
+    budget = int(sum(sorted(need)[-2:]) * 1.01)  # room for two of the largest at a time
+    res = _serve(snn, REQUESTS, budget, chunk=25)
+    assert all(r["status"] == 0 for r in res)
+    assert max(r["queue_ms"] for r in res) > 0.0
+    with snn.Server(need[0] // 2) as srv:
+        with pytest.raises(snn.SnnError, match="SNN_EBUDGET"):
+            srv.submit(REQUESTS[0][0], 10)
