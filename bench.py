@@ -442,6 +442,7 @@ def run_batched(snn, args, stream):
         ms_batched = a.elapsed_time(b)
         ev_batched = events() - e0
         launches_batched = snn.launch_count() - l0
+        waves, ring_budget = batch.waves()
     # plain: one instance per launch, back to back on the same stream
     e0 = events()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -459,10 +460,12 @@ def run_batched(snn, args, stream):
     v_p = ev_plain / (ms_plain / 1e3)
     return {"value": v_b, "unit": UNIT, "plain_value": v_p, "speedup_vs_plain": v_b / v_p,
             "instances": len(inst), "neurons": neurons, "steps_each": args.batch_steps,
-            "ms_batched": ms_batched, "ms_plain": ms_plain, "launches": launches_batched,
+            "ms_batched": ms_batched, "ms_plain": ms_plain, "launches": launches_batched, "waves": waves,
+            "ring_budget_mb": ring_budget / 2 ** 20,
             "workload": "64 instances, grid side U{4..16} x 1250 neurons, K=1125, Gaussian (even seed, 7.5 Hz) / "
                         "exponential (odd seed, 35 Hz), bf16 weights when seed bit 1 is set, one persistent "
-                        "launch replayed from a CUDA graph vs one persistent launch per instance"}
+                        "launch per L2-sized wave of instances, replayed from one CUDA graph, vs one persistent launch per "
+                        "instance"}
 
 
 def run_served(snn, args, stream):

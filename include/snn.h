@@ -281,10 +281,19 @@ SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh,
 typedef struct snn_batch snn_batch;
 SNN_API snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
                                     void* alloc_ctx, snn_batch** out);
+/* Networks are grouped, in order, into waves whose delay rings fit together
+ * in half the L2 cache (the ring takes one random reduction per synaptic
+ * event, which is several times slower once the rings spill to DRAM); each
+ * wave is one launch.  snn_batch_waves reports the wave count and the ring
+ * budget in bytes. */
+SNN_API snn_status snn_batch_waves(snn_batch* b, uint32_t* waves, uint64_t* ring_budget);
+/* Regroups the networks into waves for another ring budget (bytes > 0). */
+SNN_API snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes);
 /* Runs network i for steps[i] (host array of n; 0 = idle) time steps.  Async. */
 SNN_API snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream);
-/* enable != 0: snn_batch_step replays a CUDA graph holding the launch
- * (captured on first use, and again when the longest step count changes). */
+/* enable != 0: snn_batch_step replays a CUDA graph holding the launches of
+ * all waves (captured on first use, and again when a wave's longest step
+ * count changes). */
 SNN_API snn_status snn_batch_set_graph(snn_batch* b, int32_t enable);
 /* CUDA-event time (ms) and count of the batch launches since creation. */
 SNN_API snn_status snn_batch_time(snn_batch* b, double* ms, uint64_t* launches);

@@ -825,22 +825,28 @@ void snn_destroy(snn_net* n) {
 // ---------------------------------------------------------------------------
 // Batched execution.
 
+// A wave: networks advanced together by one cooperative launch.
+struct BatchWave {
+    BatchMeta meta{};
+    uint32_t first = 0, count = 0;
+    int grid = 0;
+};
+
 struct snn_batch {
     std::vector<snn_net*> nets;
     snn_alloc_fn alloc_fn = nullptr;
     snn_free_fn free_fn = nullptr;
     void* alloc_ctx = nullptr;
     std::vector<void*> blocks;
-    BatchMeta meta{};
-    NetView* d_views = nullptr;
-    uint32_t* d_steps = nullptr;
+    std::vector<BatchWave> waves;
+    uint32_t* d_steps = nullptr;  // steps of every network, in order
     uint32_t* h_steps = nullptr;  // pinned staging of the per-network steps
-    int grid = 0;
+    uint64_t ring_budget = 0;
     bool use_graph = false;
     bool graph_valid = false;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
-    uint32_t graph_steps = 0;
+    std::vector<uint32_t> graph_key;  // longest step count of each wave when the graph was captured
     EventRing ev;
 };
 
@@ -859,39 +865,26 @@ void* batch_alloc(snn_batch* b, size_t bytes) {
     return p;
 }
 
-}  // namespace
+uint64_t ring_bytes(const snn_net* n) { return (uint64_t)n->D * n->Npad * 4; }
 
-snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
-                            void* alloc_ctx, snn_batch** out) {
-    if (!out || !nets || n == 0) return fail(SNN_EINVAL, "nets, n and out must be set");
-    *out = nullptr;
-    if ((alloc_fn == nullptr) != (free_fn == nullptr))
-        return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+// Device tables of one wave: networks [first, first + count).
+snn_status build_wave(snn_batch* b, uint32_t first, uint32_t count, BatchWave* w) {
+    snn_net* const* nets = b->nets.data() + first;
     uint64_t Qtot = 0, tasks = 0;
-    for (uint32_t i = 0; i < n; ++i) {
-        if (!nets[i]) return fail(SNN_EINVAL, "network %u is NULL", i);
-        for (uint32_t j = 0; j < i; ++j)
-            if (nets[j] == nets[i]) return fail(SNN_EINVAL, "network %u appears twice", i);
+    for (uint32_t i = 0; i < count; ++i) {
         Qtot += nets[i]->Npad / 4;
         tasks += (uint64_t)nets[i]->N * ((nets[i]->K + 127) / 128);
     }
-    if (Qtot >= (1ull << 32) || tasks >= (1ull << 32)) return fail(SNN_EINVAL, "the batch is too large");
+    if (Qtot >= (1ull << 32) || tasks >= (1ull << 32)) return fail(SNN_EINVAL, "a batch wave is too large");
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = batch_grid(n, (uint32_t)(8 * PERSIST_WARPS * sms) + n);
-    if (grid <= 0) return fail(SNN_EINVAL, "the batch kernel does not fit on this device (n = %u)", n);
-    snn_batch* b = new (std::nothrow) snn_batch();
-    if (!b) return fail(SNN_ENOMEM, "host allocation failed");
-    b->nets.assign(nets, nets + n);
-    b->alloc_fn = alloc_fn;
-    b->free_fn = free_fn;
-    b->alloc_ctx = alloc_ctx;
-    b->grid = grid;
+    const int grid = batch_grid(count, (uint32_t)(8 * PERSIST_WARPS * sms) + count);
+    if (grid <= 0) return fail(SNN_EINVAL, "the batch kernel does not fit on this device (%u networks)", count);
     // global quad offsets; first and last warp overlapping each network
     const uint64_t TW = (uint64_t)grid * PERSIST_WARPS;
-    std::vector<uint32_t> qoff(n + 1, 0), wlo(n, 0), cbase(n + 1, 0);
-    for (uint32_t i = 0; i < n; ++i) qoff[i + 1] = qoff[i] + nets[i]->Npad / 4;
+    std::vector<uint32_t> qoff(count + 1, 0), wlo(count, 0), cbase(count + 1, 0);
+    for (uint32_t i = 0; i < count; ++i) qoff[i + 1] = qoff[i] + nets[i]->Npad / 4;
     auto owner = [&](uint64_t q) {  // the warp whose range [Qtot w / TW, Qtot (w+1) / TW) holds quad q
         uint64_t lo = 0, hi = TW;
         while (hi - lo > 1) {
@@ -903,57 +896,110 @@ snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc
         }
         return (uint32_t)lo;
     };
-    for (uint32_t i = 0; i < n; ++i) {
+    for (uint32_t i = 0; i < count; ++i) {
         wlo[i] = owner(qoff[i]);
         const uint32_t whi = owner(qoff[i + 1] - 1);
         cbase[i + 1] = cbase[i] + (whi - wlo[i] + 1);
     }
-    const uint32_t n_seg = cbase[n];
-    b->d_views = (NetView*)batch_alloc(b, n * sizeof(NetView));
-    b->d_steps = (uint32_t*)batch_alloc(b, n * 4);
-    uint32_t* d_qoff = (uint32_t*)batch_alloc(b, (n + 1) * 4);
-    uint32_t* d_cbase = (uint32_t*)batch_alloc(b, (n + 1) * 4);
-    uint32_t* d_wlo = (uint32_t*)batch_alloc(b, n * 4);
+    const uint32_t n_seg = cbase[count];
+    NetView* d_views = (NetView*)batch_alloc(b, count * sizeof(NetView));
+    uint32_t* d_qoff = (uint32_t*)batch_alloc(b, (count + 1) * 4);
+    uint32_t* d_cbase = (uint32_t*)batch_alloc(b, (count + 1) * 4);
+    uint32_t* d_wlo = (uint32_t*)batch_alloc(b, count * 4);
     uint32_t* d_wcnt = (uint32_t*)batch_alloc(b, (size_t)n_seg * 4);
     DevState* d_st = (DevState*)batch_alloc(b, sizeof(DevState));
-    if (!b->d_views || !b->d_steps || !d_qoff || !d_cbase || !d_wlo || !d_wcnt || !d_st ||
-        cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
-        cudaGetLastError();
-        snn_batch_destroy(b);
-        return fail(SNN_ENOMEM, "batch allocation failed");
-    }
-    std::vector<NetView> views(n);
+    if (!d_views || !d_qoff || !d_cbase || !d_wlo || !d_wcnt || !d_st) return fail(SNN_ENOMEM, "batch allocation failed");
+    std::vector<NetView> views(count);
     uint64_t limit = ~0ull;
     uint32_t extra = 0;
-    for (uint32_t i = 0; i < n; ++i) {
+    for (uint32_t i = 0; i < count; ++i) {
         views[i] = nets[i]->v;
         limit = std::min(limit, nets[i]->v.wait_limit_ns);
         extra = std::max(extra, nets[i]->v.barrier_extra);
     }
-    cudaError_t e = cudaMemcpy(b->d_views, views.data(), n * sizeof(NetView), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_qoff, qoff.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_cbase, cbase.data(), (n + 1) * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(d_wlo, wlo.data(), n * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpy(d_views, views.data(), count * sizeof(NetView), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_qoff, qoff.data(), (count + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_cbase, cbase.data(), (count + 1) * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_wlo, wlo.data(), count * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d_wcnt, 0, (size_t)n_seg * 4);
     if (e == cudaSuccess) e = cudaMemset(d_st, 0, sizeof(DevState));
-    if (e != cudaSuccess) {
-        snn_batch_destroy(b);
-        return fail(SNN_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
-    }
-    BatchMeta& m = b->meta;
-    m.views = b->d_views;
+    if (e != cudaSuccess) return fail(SNN_ECUDA, "batch set-up: %s", cudaGetErrorString(e));
+    BatchMeta& m = w->meta;
+    m.views = d_views;
     m.qoff = d_qoff;
     m.cbase = d_cbase;
     m.wlo = d_wlo;
     m.wcnt = d_wcnt;
-    m.steps = b->d_steps;
+    m.steps = b->d_steps + first;
     m.bst = d_st;
     m.wait_limit_ns = limit;
     m.barrier_extra = extra;
-    m.n = n;
+    m.n = count;
     m.n_seg = n_seg;
     m.Qtot = (uint32_t)Qtot;
+    w->first = first;
+    w->count = count;
+    w->grid = grid;
+    return SNN_OK;
+}
+
+}  // namespace
+
+snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
+                            void* alloc_ctx, snn_batch** out) {
+    if (!out || !nets || n == 0) return fail(SNN_EINVAL, "nets, n and out must be set");
+    *out = nullptr;
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+    for (uint32_t i = 0; i < n; ++i) {
+        if (!nets[i]) return fail(SNN_EINVAL, "network %u is NULL", i);
+        for (uint32_t j = 0; j < i; ++j)
+            if (nets[j] == nets[i]) return fail(SNN_EINVAL, "network %u appears twice", i);
+    }
+    snn_batch* b = new (std::nothrow) snn_batch();
+    if (!b) return fail(SNN_ENOMEM, "host allocation failed");
+    b->nets.assign(nets, nets + n);
+    b->alloc_fn = alloc_fn;
+    b->free_fn = free_fn;
+    b->alloc_ctx = alloc_ctx;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    b->ring_budget = l2 > 0 ? (uint64_t)l2 / 2 : (64ull << 20);
+    b->d_steps = (uint32_t*)batch_alloc(b, n * 4);
+    if (!b->d_steps || cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
+        cudaGetLastError();
+        snn_batch_destroy(b);
+        return fail(SNN_ENOMEM, "batch allocation failed");
+    }
+    snn_status st = snn_batch_set_ring_budget(b, b->ring_budget);
+    if (st != SNN_OK) {
+        snn_batch_destroy(b);
+        return st;
+    }
     *out = b;
+    return SNN_OK;
+}
+
+snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes) {
+    if (!b || bytes == 0) return fail(SNN_EINVAL, "batch is NULL or the budget is 0");
+    CUDA_TRY(cudaDeviceSynchronize());  // tables of the old waves may still be in use
+    b->ring_budget = bytes;
+    b->waves.clear();
+    b->graph_valid = false;
+    const uint32_t n = (uint32_t)b->nets.size();
+    // waves of consecutive networks whose delay rings fit together in the budget
+    for (uint32_t first = 0; first < n;) {
+        uint64_t used = ring_bytes(b->nets[first]);
+        uint32_t count = 1;
+        while (first + count < n && used + ring_bytes(b->nets[first + count]) <= b->ring_budget)
+            used += ring_bytes(b->nets[first + count++]);
+        BatchWave w;
+        snn_status st = build_wave(b, first, count, &w);
+        if (st != SNN_OK) return st;
+        b->waves.push_back(w);
+        first += count;
+    }
     return SNN_OK;
 }
 
@@ -963,47 +1009,67 @@ snn_status snn_batch_set_graph(snn_batch* b, int32_t enable) {
     return SNN_OK;
 }
 
+snn_status snn_batch_waves(snn_batch* b, uint32_t* waves, uint64_t* ring_budget) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    if (waves) *waves = (uint32_t)b->waves.size();
+    if (ring_budget) *ring_budget = b->ring_budget;
+    return SNN_OK;
+}
+
 snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     if (!b || !steps) return fail(SNN_EINVAL, "batch or steps is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)b->nets.size();
     // the pinned staging buffer may still feed the previous call's copy
     CUDA_TRY(cudaStreamSynchronize(s));
-    uint32_t max_steps = 0;
-    for (uint32_t i = 0; i < n; ++i) max_steps = std::max(max_steps, steps[i]);
-    if (max_steps == 0) return SNN_OK;
+    std::vector<uint32_t> key(b->waves.size(), 0);
+    bool any = false;
+    for (size_t k = 0; k < b->waves.size(); ++k) {
+        const BatchWave& w = b->waves[k];
+        for (uint32_t i = w.first; i < w.first + w.count; ++i) key[k] = std::max(key[k], steps[i]);
+        any = any || key[k] > 0;
+    }
+    if (!any) return SNN_OK;
     std::copy(steps, steps + n, b->h_steps);
     CUDA_TRY(cudaMemcpyAsync(b->d_steps, b->h_steps, n * 4, cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemsetAsync(&b->meta.bst->bar_count, 0, sizeof(uint32_t), s));
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        for (size_t k = 0; k < b->waves.size(); ++k) {
+            if (key[k] == 0) continue;
+            const BatchWave& w = b->waves[k];
+            cudaError_t e = cudaMemsetAsync(&w.meta.bst->bar_count, 0, sizeof(uint32_t), q);
+            if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, q);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     int slot = 0;
     snn_status st = timed_begin(b->ev, s, &slot);
     if (st != SNN_OK) return st;
     if (b->use_graph) {
-        if (!b->graph_valid || b->graph_steps != max_steps) {
+        if (!b->graph_valid || b->graph_key != key) {
             if (b->exec) {
                 cudaGraphExecDestroy(b->exec);
                 b->exec = nullptr;
             }
             if (!b->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
             CUDA_TRY(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-            cudaError_t le = launch_batch(b->meta, max_steps, b->grid, b->cap_stream);
+            cudaError_t le = enqueue(b->cap_stream);
             cudaGraph_t graph = nullptr;
             cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
             if (le != cudaSuccess || ce != cudaSuccess) {
                 if (graph) cudaGraphDestroy(graph);
-                return fail(SNN_ECUDA, "graph capture of the batch launch failed: %s",
+                return fail(SNN_ECUDA, "graph capture of the batch launches failed: %s",
                             cudaGetErrorString(le != cudaSuccess ? le : ce));
             }
             cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
             cudaGraphDestroy(graph);
             if (ie != cudaSuccess) return fail(SNN_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
             b->graph_valid = true;
-            b->graph_steps = max_steps;
+            b->graph_key = key;
         }
         CUDA_TRY(cudaGraphLaunch(b->exec, s));
-        count_launch(1);
     } else {
-        CUDA_TRY(launch_batch(b->meta, max_steps, b->grid, s));
+        CUDA_TRY(enqueue(s));
     }
     return timed_end(b->ev, s, slot);
 }

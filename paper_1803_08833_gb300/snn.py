@@ -113,6 +113,8 @@ def load():
         "snn_batch_create": (st, [P(vp), ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, P(vp)]),
         "snn_batch_step": (st, [vp, P(ctypes.c_uint32), vp]),
         "snn_batch_set_graph": (st, [vp, ctypes.c_int32]),
+        "snn_batch_waves": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint64)]),
+        "snn_batch_set_ring_budget": (st, [vp, ctypes.c_uint64]),
         "snn_batch_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64)]),
         "snn_batch_destroy": (None, [vp]),
         "snn_estimate_bytes": (ctypes.c_uint64, [P(SnnConfig)]),
@@ -383,6 +385,15 @@ class Batch:
 
     def set_graph(self, enable: bool):
         check(load().snn_batch_set_graph(self._h, 1 if enable else 0))
+
+    def set_ring_budget(self, nbytes: int):
+        check(load().snn_batch_set_ring_budget(self._h, int(nbytes)))
+
+    def waves(self):
+        """(number of launches per step call, ring budget in bytes)."""
+        w, r = ctypes.c_uint32(), ctypes.c_uint64()
+        check(load().snn_batch_waves(self._h, ctypes.byref(w), ctypes.byref(r)))
+        return w.value, r.value
 
     def time(self):
         ms, n = ctypes.c_double(), ctypes.c_uint64()

@@ -44,13 +44,16 @@ def _check(net, ref):
     assert s["n_spikes"] == ref.stats()["spikes"] and s["ext_events"] == ref.stats()["ext_events"]
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_equals_each_network_alone(snn, graph):
+@pytest.mark.parametrize("graph,waves", [(False, 1), (True, 1), (True, 3)])
+def test_batch_equals_each_network_alone(snn, graph, waves):
     cfgs = _cases()
     nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
     refs = [oracle.OracleNet(c) for c in cfgs]
     with snn.Batch(nets) as batch:
         batch.set_graph(graph)
+        if waves > 1:  # a ring budget that gives every network its own launch
+            batch.set_ring_budget(1)
+            assert batch.waves()[0] == len(nets)
         plans = [[60, 45, 60, 0, 30, 50], [10, 10, 0, 25, 10, 10], [10, 10, 0, 25, 10, 10]]
         for steps in plans:
             batch.step(steps)
