@@ -323,6 +323,7 @@ def run_gpu(args):
     net.close()
 
     batched = None if args.no_batched else run_batched(snn, args, stream)
+    precision = None if args.no_precision else run_precision(snn, args, stream)
     served = None if args.no_served else run_served(snn, args, stream)
 
     cpu = None
@@ -367,6 +368,7 @@ def run_gpu(args):
         "e2e": e2e,
         "batched": batched,
         "served": served,
+        "precision": precision,
         "gpu_launches": launches,
         "clocks": ck,
     }
@@ -468,6 +470,49 @@ def run_batched(snn, args, stream):
                         "instance"}
 
 
+def run_precision(snn, args, stream):
+    """The exponential long-range network at full size (24x24 x 1250, K = 2250,
+    lambda = 290 um, cut-off 1.2 mm) with bf16 and with f32 weights, 10,000 steps
+    each after 500 warm-up steps, under a 5.2 kHz drive (the low-rate state:
+    the specified drive leaves it silent, above ~5.8 kHz it saturates near
+    280 Hz).  The FP64 comparison, which the oracle can only afford on a patch,
+    is tests/test_gpu_precision.py."""
+    import numpy as np
+    import torch
+    from paper_1803_08833_gb300 import workloads as W
+    out = {}
+    rates = {}
+    for dt in ("bf16", "f32"):
+        cfg = W.exp_24x24_k2250(seed=1, weight_dtype=dt, ext_rate_hz=5200.0)
+        with snn.Network(cfg, raster_capacity=64 << 20, stream=stream) as net:
+            net.set_schedule(2)
+            net.step(500)
+            net.clear_raster()
+            s0 = net.stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(args.precision_steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            s1 = net.stats()
+            _, ids = net.read_spikes(allow_overflow=True)
+            rates[dt] = np.bincount(ids, minlength=net.N) / (args.precision_steps / 1000.0)
+            ev = s1["rec_events"] - s0["rec_events"]
+            out[dt] = {"events_per_s": ev / (ms / 1e3), "ms_per_step": ms / args.precision_steps,
+                       "rate_hz": float(rates[dt].mean()), "bytes_per_synapse": 7 if dt == "bf16" else 9,
+                       "table_gb": net.device_bytes / 1e9}
+    M = 1250
+    mod = lambda r: r.reshape(-1, M).mean(axis=1)
+    out["bf16_vs_f32"] = {
+        "mean_rate_rel_err": float(rates["bf16"].mean() / rates["f32"].mean() - 1.0),
+        "neuron_rate_corr": float(np.corrcoef(rates["bf16"], rates["f32"])[0, 1]),
+        "module_rate_corr": float(np.corrcoef(mod(rates["bf16"]), mod(rates["f32"]))[0, 1])}
+    out["workload"] = ("exp_24x24_k2250: 24x24 x 1250 neurons, K=2250 (1.62 G synapses), lambda=290 um cut at 1.2 mm, "
+                       "5.2 kHz x 0.2 mV drive (low-rate state), %d steps" % args.precision_steps)
+    return out
+
+
 def run_served(snn, args, stream):
     """Poisson stream of requests into the continuous-batching server."""
     import time as _t
@@ -544,6 +589,8 @@ def main(argv=None):
     ap.add_argument("--calibrate", action="store_true", help="measure L2 reduction and stream rates, then exit")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--precision-steps", type=int, default=10000)
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--served-seconds", type=float, default=60.0)

@@ -75,8 +75,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
             s_steps[k] = bm.steps[k];
         }
     }
-    uint32_t gen = 0;
-    if (threadIdx.x == 0) gen = bm.bst->bar_gen;
+    uint32_t gen = 0;  // barriers passed in this launch
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wg = blockIdx.x * PERSIST_WARPS + warp;

@@ -17,35 +17,34 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// Barrier over `expected` CTAs on the counters of `st` (all CTAs are
-// co-resident: cooperative launch).  Returns false if this CTA's wait ran out
-// (after limit_ns of the global timer; it then sets ERR_BARRIER_TIMEOUT) or
-// another CTA reported an error.
+// Barrier over `expected` CTAs on the arrival counter of `st` (all CTAs are
+// co-resident: cooperative launch).  The counter starts at 0 for every launch
+// (the host clears it) and only grows: the k-th barrier of the launch is
+// passed once it reaches expected * k, so arriving is a single release
+// reduction with no round trip and no reset.  `gen` counts this CTA's
+// barriers (start it at 0).  Returns false if this CTA's wait ran out (after
+// limit_ns of the global timer; it then sets ERR_BARRIER_TIMEOUT) or another
+// CTA reported an error.
 __device__ inline bool grid_barrier_on(DevState* st, uint32_t expected, uint64_t limit_ns, uint32_t& gen) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
+        gen += 1;
+        const uint32_t target = expected * gen;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->bar_count) : "memory");
         int ok = 1;
-        __threadfence();  // publish this CTA's writes before arriving
-        const uint32_t arrived = atomicAdd(&st->bar_count, 1u);
-        if (arrived == expected - 1) {
-            atomicExch(&st->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&st->bar_gen, 1u);
-        } else {
+        if ((int32_t)(ld_acquire(&st->bar_count) - target) < 0) {
             const uint64_t start = global_ns();
-            while (ld_acquire(&st->bar_gen) == gen) {
+            while ((int32_t)(ld_acquire(&st->bar_count) - target) < 0) {
                 if (global_ns() - start > limit_ns) {
                     atomicOr(&st->err, ERR_BARRIER_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
-        __threadfence();
-        gen += 1;
-        if (ld_acquire(&st->err) != 0) ok = 0;
+        if (ok && ld_acquire(&st->err) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -57,35 +56,14 @@ __device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen)
     return grid_barrier_on(v.st, G + v.barrier_extra, v.wait_limit_ns, gen);
 }
 
-// Exclusive prefix of cnt[0..n) into out[0..n], out[n] = total (one block of
-// at most 1024 threads).
+// Exclusive prefix of cnt[0..n) (global, written by other CTAs) into
+// out[0..n] (shared), out[n] = total: one coalesced pass of loads, then the
+// scan in shared memory.
+__device__ inline void block_scan_inplace(uint32_t* s, uint32_t n);
 __device__ inline void block_exclusive_scan(const uint32_t* cnt, uint32_t n, uint32_t* out) {
-    __shared__ uint32_t s_w[32];
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t a = min(threadIdx.x * per, n), b = min(a + per, n);
-    uint32_t local = 0;
-    for (uint32_t i = a; i < b; ++i) local += __ldcg(cnt + i);
-    uint32_t incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= (uint32_t)o) incl += y;
-    }
-    if (lane == 31) s_w[warp] = incl;
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) out[i] = __ldcg(cnt + i);
     __syncthreads();
-    uint32_t base = 0, total = 0;
-    for (uint32_t w = 0; w < blockDim.x / 32; ++w) {
-        if (w < warp) base += s_w[w];
-        total += s_w[w];
-    }
-    uint32_t run = base + incl - local;
-    for (uint32_t i = a; i < b; ++i) {
-        out[i] = run;
-        run += __ldcg(cnt + i);
-    }
-    if (threadIdx.x == 0) out[n] = total;
-    __syncthreads();
+    block_scan_inplace(out, n);
 }
 
 // Neuron id of staged spike j: CTA by binary search over the CTA offsets,

@@ -21,16 +21,31 @@ namespace snn {
 #define SNN_PERSIST_MIN_BLOCKS 2
 #endif
 
+// Neuron id of staged spike j: the warp by binary search over the per-warp
+// spike prefix, then that warp's staging segment.
+__device__ __forceinline__ uint32_t warp_spike_id(const NetView& v, const uint32_t* s_wpre, uint32_t TW, uint32_t Q,
+                                                  uint32_t j) {
+    uint32_t lo = 0, hi = TW;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_wpre[mid] <= j)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const uint32_t qa = (uint32_t)((uint64_t)Q * lo / TW);
+    return __ldcg(v.seg + ((size_t)qa << 2) + (j - s_wpre[lo]));
+}
+
 // n_steps time steps of network v on a group of G CTAs; `bid` is this CTA's
-// index in the group.  smem: G + 1 + G * PERSIST_WARPS + PERSIST_THREADS words.
+// index in the group.  smem: G * PERSIST_WARPS + 1 + PERSIST_THREADS words.
 template <bool BF16>
 __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, uint32_t G, uint32_t bid,
                                           uint32_t* smem) {
     const uint32_t TW = G * PERSIST_WARPS;
-    uint32_t* s_cta = smem;             // G + 1 CTA offsets
-    uint32_t* s_woff = smem + G + 1;    // TW warp offsets (CTA-local)
-    uint32_t* s_id = s_woff + TW;       // staged spike ids
-    __shared__ uint32_t s_t0, s_wcnt[PERSIST_WARPS];
+    uint32_t* s_wpre = smem;          // TW + 1 per-warp spike offsets
+    uint32_t* s_id = s_wpre + TW + 1;  // staged spike ids
+    __shared__ uint32_t s_t0;
     __shared__ unsigned long long s_rc0;
     __shared__ uint32_t s_ext[PERSIST_WARPS];
     __shared__ uint32_t s_pois[MAX_POIS];
@@ -39,7 +54,6 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     if (threadIdx.x == 0) {
         s_t0 = v.st->t;
         s_rc0 = v.st->raster_count;
-        gen = v.st->bar_gen;
     }
     __syncthreads();
     const uint32_t t0 = s_t0;
@@ -54,7 +68,6 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint64_t spikes = 0;
     uint32_t ext = 0;
     uint32_t done = 0;
-
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
     if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
     for (uint32_t step = 0; step < n_steps; ++step) {
@@ -83,16 +96,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                 if (spk & (1u << b)) v.seg[pos++] = (q << 2) + b;
             run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
-        if (lane == 0) s_wcnt[warp] = run;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int w = 0; w < PERSIST_WARPS; ++w) {
-                v.woff[bid * PERSIST_WARPS + w] = acc;
-                acc += s_wcnt[w];
-            }
-            v.cta_cnt[bid] = acc;
-        }
+        if (lane == 0) v.woff[wg] = run;  // spike count of this warp
         if (!grid_barrier(v, G, gen)) break;
         if (bid == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
@@ -100,27 +104,29 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             stamp = now;
         }
 
-        // ---- phase D: global offsets, raster, delivery
-        block_exclusive_scan(v.cta_cnt, G, s_cta);
-        for (uint32_t i = threadIdx.x; i < TW; i += blockDim.x) s_woff[i] = __ldcg(v.woff + i);
-        __syncthreads();
-        const uint32_t total = s_cta[G];
-        for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
-            const uint64_t r = rc + j;
-            if (r >= v.raster_cap) break;
-            v.raster_t[r] = t;
-            v.raster_id[r] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW, G);
-        }
+        // ---- phase D: per-warp offsets (one coalesced pass), delivery, raster
+        block_exclusive_scan(v.woff, TW, s_wpre);
+        const uint32_t total = s_wpre[TW];
+        const uint32_t slot0 = t % v.D;
         if (chunks > 0 && total > 0) {
             const uint64_t n_tasks = (uint64_t)total * chunks;
             const uint64_t ta = n_tasks * bid / G;
             const uint64_t tb = n_tasks * (bid + 1) / G;
             if (ta < tb) {
-                const uint32_t slot0 = t % v.D;
                 const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
                 for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
                     const uint32_t j = jb + threadIdx.x;
-                    if (j <= j_last) s_id[threadIdx.x] = spike_id<PERSIST_WARPS>(v, s_cta, s_woff, j, Q, TW, G);
+                    if (j <= j_last) {
+                        const uint32_t id = warp_spike_id(v, s_wpre, TW, Q, j);
+                        s_id[threadIdx.x] = id;
+                        // raster entry of every staged spike (a spike staged by two
+                        // CTAs is written twice with the same value)
+                        const uint64_t r = rc + j;
+                        if (r < v.raster_cap) {
+                            v.raster_t[r] = t;
+                            v.raster_id[r] = id;
+                        }
+                    }
                     __syncthreads();
                     const uint64_t lo = max(ta, (uint64_t)jb * chunks);
                     const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
@@ -128,6 +134,13 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                         deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol);
                     __syncthreads();
                 }
+            }
+        } else {  // no synapses: the raster alone
+            for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
+                const uint64_t r = rc + j;
+                if (r >= v.raster_cap) break;
+                v.raster_t[r] = t;
+                v.raster_id[r] = warp_spike_id(v, s_wpre, TW, Q, j);
             }
         }
         rc += total;
@@ -175,7 +188,7 @@ static const void* persistent_fn(bool bf16) {
 }
 
 static size_t persistent_smem(int grid) {
-    return (size_t)(grid + 1 + grid * PERSIST_WARPS + PERSIST_THREADS) * sizeof(uint32_t);
+    return (size_t)(grid * PERSIST_WARPS + 1 + PERSIST_THREADS) * sizeof(uint32_t);
 }
 
 // Co-resident grid: occupancy per SM x SMs, with the grid-dependent shared

@@ -64,7 +64,6 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
     if (threadIdx.x == 0) {
         s_t0 = v.st->t;
         s_rc0 = v.st->raster_count;
-        gen = v.st->bar_gen;
     }
     __syncthreads();
     const uint32_t t0 = s_t0;

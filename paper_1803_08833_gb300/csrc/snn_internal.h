@@ -31,8 +31,8 @@ struct DevState {
     uint64_t raster_base;   // raster index of the first staged spike
     uint64_t n_spikes, rec_events, ext_events;
     uint32_t err;        // sticky error bits (ERR_*)
-    uint32_t bar_count;  // grid-barrier arrivals (persistent kernel)
-    uint32_t bar_gen;    // grid-barrier generation
+    uint32_t bar_count;  // grid-barrier arrivals of the current persistent launch
+    uint32_t pad0;
     uint32_t pad;
     uint64_t phase_ns[2];  // persistent kernel, CTA 0: neuron phase + barrier, delivery phase + barrier
 };
