@@ -30,10 +30,19 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsnn.so")
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
+def _user_flags():
+    """Extra nvcc flags from SNN_NVCC_FLAGS (tuning macros such as
+    -DSNN_DELIVER_UNROLL=8); a change of them forces a rebuild."""
+    return os.environ.get("SNN_NVCC_FLAGS", "").split()
+
+
 def _flags(extra=()):
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false",
                    "-Xcompiler", "-fPIC,-ffp-contract=off,-O2,-fvisibility=hidden",
-                   "-I", INCLUDE, "-I", CSRC, *extra]
+                   "-I", INCLUDE, "-I", CSRC, *_user_flags(), *extra]
 
 
 def _deps():
@@ -44,6 +53,12 @@ def _deps():
 
 def stale() -> bool:
     if not os.path.exists(LIB):
+        return True
+    try:
+        with open(STAMP) as f:
+            if f.read() != " ".join(_user_flags()):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(f) > t for f in _deps())
@@ -74,6 +89,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(_user_flags()))
     return LIB
 
 

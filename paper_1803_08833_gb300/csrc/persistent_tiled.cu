@@ -6,20 +6,32 @@
 // Here each CTA owns target modules instead.  For target module m it gathers,
 // from every source module s whose stencil contains m, the spikes of the step
 // and the segment of each spiking neuron's row that targets m (rows are
-// grouped by target module, with a per-row segment index), accumulates the
-// events in a shared-memory tile of (D - 1) future slots x M neurons, and then
-// adds the tile into ring columns [m M, (m + 1) M) with ordinary coalesced
-// read-modify-writes: no other CTA touches those columns in this phase.  The
-// integer sums, and so the results, are the same as with the push delivery.
+// grouped by target module, with a per-row segment index), and accumulates
+// the events with shared-memory atomics in a tile of (D - 1) future slots x M
+// neurons.  The tile then goes to ring columns [m M, (m + 1) M) of the D - 1
+// future slots by bulk reductions (cp.reduce.async.bulk .add.s32, one per
+// slot row, issued by one thread and performed by the TMA unit at L2): the
+// 16-byte aligned interior of each row; the at most 3 + 3 cells at its ends
+// go by ordinary reductions.  No other CTA touches those columns in this
+// phase.  The integer sums, and so the results, are the same as with the
+// push delivery.
+//
+// Two CTAs share an SM (a tile of 20 x 1,256 cells is 100 KB), so the latency
+// chain of one CTA's tile (spike counts, segment starts, table loads, flush)
+// overlaps the other's.
 #include "grid_common.cuh"
 
 namespace snn {
 
-constexpr int TILE_THREADS = 512;
+constexpr int TILE_THREADS = 256;
 constexpr int TILE_WARPS = TILE_THREADS / 32;
-constexpr uint32_t PAIR_CAP = 1024;  // (spike, segment) pairs staged per batch
-constexpr int EV_UNROLL = 8;         // events in flight per lane
-constexpr int FLUSH_UNROLL = 8;      // ring read-modify-writes in flight per thread
+constexpr int TILE_MIN_BLOCKS = 2;
+constexpr uint32_t PAIR_CAP = 512;  // (spike, segment) pairs staged per batch
+constexpr int EV_UNROLL = 16;       // events in flight per lane
+
+#ifndef SNN_TILE_FLUSH
+#define SNN_TILE_FLUSH 0  // 0: bulk reductions by the TMA unit; 1: 16-byte read-modify-writes
+#endif
 
 __device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p, uint64_t pol) {
     uint32_t r;
@@ -37,24 +49,52 @@ __device__ __forceinline__ uint32_t ld_nc_u8(const uint8_t* p, uint64_t pol) {
     return r;
 }
 
+// Bulk reduction global[0 .. bytes) += shared[0 .. bytes) (s32), TMA engine;
+// both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_add_s32(int32_t* g, const int32_t* s, uint32_t bytes) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(s);
+    asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.s32 [%0], [%1], %2;" ::"l"(g), "r"(sa),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Source shared memory of every committed bulk operation has been read.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Every committed bulk operation has completed (its global writes performed).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk) accesses.
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// The same for global memory.
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Tile row stride (cells): covers [floor4(g), floor4(g) + RS) for any module
+// base g, so that a 16-byte aligned global cell sits on a 16-byte aligned
+// shared cell.
+__host__ __device__ __forceinline__ uint32_t tile_row_stride(uint32_t M) { return (M + 3u + 3u) & ~3u; }
+
 static size_t tiled_smem(const NetView& v, int grid) {
-    return (size_t)(v.D - 1) * v.M * sizeof(int32_t)                       // tile
-           + (size_t)(3 * PAIR_CAP + 1) * sizeof(uint32_t)                 // pair id, start, prefix
-           + (size_t)(v.max_off + 1) * sizeof(uint32_t)                    // source prefix
-           + (size_t)(grid + 1 + grid * TILE_WARPS) * sizeof(uint32_t);    // CTA / warp spike offsets
+    const size_t tile = (size_t)(v.D - 1) * tile_row_stride(v.M) * sizeof(int32_t);
+    const size_t ids = (size_t)(grid + 1 + grid * TILE_WARPS) * sizeof(uint32_t);  // aliased with the tile
+    return (tile > ids ? tile : ids)                                                //
+           + (size_t)(3 * PAIR_CAP + 1) * sizeof(uint32_t)                          // pair id, start, prefix
+           + (size_t)(v.max_off + 1) * sizeof(uint32_t);                           // source prefix
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, uint32_t n_steps) {
+__global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_tiled(NetView v, uint32_t n_steps) {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t G = gridDim.x, TW = G * TILE_WARPS;
     const uint32_t M = v.M, Dm1 = v.D - 1, nm = v.n_modules;
+    const uint32_t RS = tile_row_stride(M);
     int32_t* tile = reinterpret_cast<int32_t*>(smem);
-    uint32_t* s_pid = smem + (size_t)Dm1 * M;
+    const size_t tile_words = (size_t)Dm1 * RS;
+    const size_t ids_words = (size_t)G + 1 + (size_t)G * TILE_WARPS;
+    uint32_t* s_pid = smem + (tile_words > ids_words ? tile_words : ids_words);
     uint32_t* s_pa = s_pid + PAIR_CAP;
     uint32_t* s_pref = s_pa + PAIR_CAP;
     uint32_t* s_src = s_pref + PAIR_CAP + 1;
-    uint32_t* s_cta = s_src + v.max_off + 1;
+    uint32_t* s_cta = smem;  // raster phase only: shares the tile's space
     uint32_t* s_woff = s_cta + G + 1;
     __shared__ uint32_t s_t0, s_wcnt[TILE_WARPS], s_ext[TILE_WARPS];
     __shared__ unsigned long long s_rc0;
@@ -87,10 +127,14 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
         uint32_t* mcnt = v.mod_cnt + (size_t)par * nm;
         // ---- phase N: update, id-ordered warp segments (raster), per-module lists (delivery)
         uint32_t run = 0;
+        QuadIn nxt;  // the next chunk's loads are issued before this chunk is integrated
+        if (qa + lane < qb) nxt = load_quad(v, (qa + lane) << 2, slot);
         for (uint32_t qc = qa; qc < qb; qc += 32) {
             const uint32_t q = qc + lane;
+            const QuadIn cur = nxt;
+            if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = update_quad(v, s_pois, q << 2, t, slot, ext);
+            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -150,10 +194,12 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
         // the other parity's counters were last used by the previous step
         for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += G * blockDim.x)
             v.mod_cnt[(size_t)(par ^ 1u) * nm + m] = 0;
+        __syncthreads();  // s_cta / s_woff are dead: the tile may now be written
 
         // ---- phase D: target tiles
         for (uint32_t m = blockIdx.x; m < nm && v.K > 0; m += G) {
-            for (uint32_t x = threadIdx.x; x < Dm1 * M; x += blockDim.x) tile[x] = 0;
+            const uint32_t g = m * M;           // first ring column of the module
+            const uint32_t g4 = g & ~3u;        // tile cell 0 of every row
             const uint32_t nin = v.in_cnt[m];
             const uint32_t* isrc = v.in_src + (size_t)m * v.max_off;
             const uint32_t* ij = v.in_j + (size_t)m * v.max_off;
@@ -178,6 +224,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
             }
             __syncthreads();
             const uint32_t P = s_src[nin];
+            if (P == 0) {  // no spike reaches this module: nothing to add
+                __syncthreads();  // s_src is rewritten by the next module
+                continue;
+            }
             for (uint32_t pb = 0; pb < P; pb += PAIR_CAP) {
                 const uint32_t np = min(PAIR_CAP, P - pb);
                 for (uint32_t p = threadIdx.x; p < np; p += blockDim.x) {
@@ -196,6 +246,13 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
                     s_pid[p] = id;
                     s_pa[p] = a;
                     s_pref[p] = b - a;
+                }
+                if (pb == 0) {
+                    // the previous module's flush has finished reading the tile
+                    if (threadIdx.x == 0) bulk_wait_read();
+                    __syncthreads();
+                    int4* t4 = reinterpret_cast<int4*>(tile);
+                    for (uint32_t x = threadIdx.x; x < (Dm1 * RS) >> 2; x += blockDim.x) t4[x] = make_int4(0, 0, 0, 0);
                 }
                 __syncthreads();
                 block_scan_inplace(s_pref, np);  // exclusive, s_pref[np] = events of the batch
@@ -216,15 +273,16 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
                     }
                     pp = lo;
                 }
-                const uint32_t mbase = m * M;
+                const uint32_t ph = g - g4;  // tile column of ring column g
                 for (uint32_t base = e0; base < e1; base += 32 * EV_UNROLL) {
                     uint32_t tg[EV_UNROLL], wb[EV_UNROLL], dd[EV_UNROLL];
-                    bool ok[EV_UNROLL];
 #pragma unroll
                     for (int u = 0; u < EV_UNROLL; ++u) {
                         const uint32_t e = base + u * 32 + lane;
-                        ok[u] = e < e1;
-                        if (ok[u]) {
+                        tg[u] = 0xFFFFFFFFu;
+                        wb[u] = 0;
+                        dd[u] = 0;
+                        if (e < e1) {
                             while (pp + 1 < np && s_pref[pp + 1] <= e) ++pp;
                             const size_t idx = (size_t)s_pid[pp] * v.Kpad + s_pa[pp] + (e - s_pref[pp]);
                             tg[u] = ld_nc_u32(v.tgt + idx, pol);
@@ -235,44 +293,87 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
                     }
 #pragma unroll
                     for (int u = 0; u < EV_UNROLL; ++u) {
-                        if (!ok[u]) continue;
-                        const float w = BF16 ? __uint_as_float(wb[u] << 16) : __uint_as_float(wb[u]);
-                        const uint32_t col = tg[u] - mbase, row = dd[u] - 1u;
-                        if (col < M && row < Dm1) atomicAdd(tile + (size_t)row * M + col, fx_weight(v, w));
+                        const uint32_t col = tg[u] - g, row = dd[u] - 1u;
+                        if (col < M && row < Dm1) {
+                            const float w = BF16 ? __uint_as_float(wb[u] << 16) : __uint_as_float(wb[u]);
+                            atomicAdd(tile + (size_t)row * RS + ph + col, fx_weight(v, w));
+                        }
                     }
                 }
                 __syncthreads();
             }
-            // flush: ring[(t + d) mod D][m M + n] += tile[d - 1][n]; eight independent
-            // read-modify-writes in flight per thread
-            const uint32_t cells = Dm1 * M;
-            for (uint32_t x0 = threadIdx.x; x0 < cells; x0 += FLUSH_UNROLL * blockDim.x) {
-                int32_t add[FLUSH_UNROLL], old[FLUSH_UNROLL];
-                int32_t* dst[FLUSH_UNROLL];
+            // flush: ring[(t + 1 + r) mod D][g .. g + M) += tile row r
+            fence_async_shared();
+            __syncthreads();
+            const uint32_t a4 = (g + 3u) & ~3u, b4 = (g + M) & ~3u;  // aligned interior [a4, b4)
+            const bool bulk = b4 > a4;
+#if SNN_TILE_FLUSH == 1
+            // interior by 16-byte read-modify-writes, four slot rows in flight
+            if (bulk) {
+                const uint32_t nv = (b4 - a4) >> 2;
+                for (uint32_t r0 = 0; r0 < Dm1; r0 += 4) {
+                    for (uint32_t x = threadIdx.x; x < nv; x += blockDim.x) {
+                        int4 add[4], old[4];
+                        int4* dst[4];
 #pragma unroll
-                for (int u = 0; u < FLUSH_UNROLL; ++u) {
-                    const uint32_t x = x0 + u * blockDim.x;
-                    add[u] = 0;
-                    dst[u] = nullptr;
-                    if (x < cells) {
-                        add[u] = tile[x];
-                        const uint32_t row = x / M, col = x - row * M;
-                        uint32_t sl = slot + row + 1;
-                        if (sl >= v.D) sl -= v.D;
-                        dst[u] = v.ring + (size_t)sl * v.Npad + (size_t)m * M + col;
+                        for (int u = 0; u < 4; ++u) {
+                            dst[u] = nullptr;
+                            if (r0 + u < Dm1) {
+                                uint32_t sl = slot + r0 + u + 1;
+                                if (sl >= v.D) sl -= v.D;
+                                dst[u] = reinterpret_cast<int4*>(v.ring + (size_t)sl * v.Npad + a4) + x;
+                                add[u] = reinterpret_cast<const int4*>(tile + (size_t)(r0 + u) * RS + (a4 - g4))[x];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (dst[u]) old[u] = __ldcg(dst[u]);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (dst[u])
+                                __stcg(dst[u], make_int4(old[u].x + add[u].x, old[u].y + add[u].y, old[u].z + add[u].z,
+                                                         old[u].w + add[u].w));
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < FLUSH_UNROLL; ++u) old[u] = add[u] != 0 ? __ldcg(dst[u]) : 0;
-#pragma unroll
-                for (int u = 0; u < FLUSH_UNROLL; ++u)
-                    if (add[u] != 0) *dst[u] = old[u] + add[u];
             }
-            __syncthreads();
+#else
+            if (threadIdx.x == 0 && bulk) {
+                for (uint32_t r = 0; r < Dm1; ++r) {
+                    uint32_t sl = slot + r + 1;
+                    if (sl >= v.D) sl -= v.D;
+                    int32_t* gp = v.ring + (size_t)sl * v.Npad + a4;
+                    const int32_t* sp = tile + (size_t)r * RS + (a4 - g4);
+                    const uint32_t bytes = (b4 - a4) * 4u;
+                    if ((((uintptr_t)gp | (uintptr_t)sp | bytes) & 15u) == 0)
+                        bulk_add_s32(gp, sp, bytes);
+                    else
+                        atomicOr(&v.st->err, ERR_ALIGNMENT);  // never expected: skip rather than fault
+                }
+                bulk_commit();
+            }
+#endif
+            // the cells outside the aligned interior
+            const uint32_t ne = bulk ? (a4 - g) + (g + M - b4) : M;
+            for (uint32_t x = threadIdx.x; x < Dm1 * ne; x += blockDim.x) {
+                const uint32_t r = x / ne, k = x - r * ne;
+                const uint32_t c = !bulk ? g + k : (k < a4 - g ? g + k : b4 + (k - (a4 - g)));
+                const int32_t val = tile[(size_t)r * RS + (c - g4)];
+                if (val != 0) {
+                    uint32_t sl = slot + r + 1;
+                    if (sl >= v.D) sl -= v.D;
+                    red_add(v.ring + (size_t)sl * v.Npad + c, val);
+                }
+            }
+        }
+        // every bulk reduction of this step has landed before the barrier
+        if (threadIdx.x == 0) {
+            bulk_wait_all();
+            fence_async_global();
         }
         rc += total;
         spikes += total;
         if (!grid_barrier(v, G, gen)) break;
+        if (threadIdx.x == 0) fence_async_global();  // generic writes of other CTAs before our next bulk reads
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_d += now - stamp;
@@ -280,6 +381,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_run_steps_tiled(NetView v, 
         }
         done = step + 1;
     }
+    if (threadIdx.x == 0) bulk_wait_all();  // also on an early exit
 
     uint32_t e = ext;
 #pragma unroll
@@ -307,24 +409,29 @@ static const void* tiled_fn(bool bf16) {
     return bf16 ? (const void*)k_run_steps_tiled<true> : (const void*)k_run_steps_tiled<false>;
 }
 
+// Co-resident grid: up to TILE_MIN_BLOCKS CTAs per SM, 0 if the tile does not fit.
 int tiled_grid(const NetView& v) {
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t smem = tiled_smem(v, sms);
-    if (smem > (size_t)optin) return 0;
     const void* fn = tiled_fn(v.w_bf16 != 0);
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
+    for (int per_sm = TILE_MIN_BLOCKS; per_sm >= 1; --per_sm) {
+        const int grid = per_sm * sms;
+        const size_t smem = tiled_smem(v, grid);
+        if (smem > (size_t)optin) continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        int fit = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, TILE_THREADS, smem) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (fit >= per_sm) return grid;
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, TILE_THREADS, smem) != cudaSuccess || per_sm < 1) {
-        cudaGetLastError();
-        return 0;
-    }
-    return sms;  // one CTA per SM
+    return 0;
 }
 
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {

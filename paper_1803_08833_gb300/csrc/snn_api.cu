@@ -566,7 +566,7 @@ snn_status snn_read_spikes(snn_net* n, uint32_t* steps, uint32_t* ids, size_t ca
     if (m && ids) CUDA_TRY(cudaMemcpyAsync(ids, n->v.raster_id, m * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     *n_out = m;
-    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out (error bits 0x%x)", ds.err);
+    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out or a device check failed (error bits 0x%x)", ds.err);
     if (ds.raster_count > n->v.raster_cap)
         return fail(SNN_EOVERFLOW, "raster overflow: %llu spikes recorded, capacity %llu",
                     (unsigned long long)ds.raster_count, (unsigned long long)n->v.raster_cap);
@@ -593,7 +593,7 @@ snn_status snn_get_stats(snn_net* n, snn_stats* out, void* stream) {
     out->raster_capacity = n->v.raster_cap;
     out->neuron_phase_ns = ds.phase_ns[0];
     out->deliver_phase_ns = ds.phase_ns[1];
-    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out (error bits 0x%x)", ds.err);
+    if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out or a device check failed (error bits 0x%x)", ds.err);
     return SNN_OK;
 }
 

@@ -15,6 +15,7 @@ constexpr int NEURON_THREADS = 256;
 constexpr int PERSIST_THREADS = 256;                 // threads per CTA of the persistent kernel
 constexpr int PERSIST_WARPS = PERSIST_THREADS / 32;
 constexpr uint32_t ERR_BARRIER_TIMEOUT = 1u;         // DevState::err bits
+constexpr uint32_t ERR_ALIGNMENT = 2u;               // a bulk copy address was not 16-byte aligned (skipped)
 constexpr int NEURONS_PER_THREAD = 4;
 constexpr int NEURONS_PER_BLOCK = NEURON_THREADS * NEURONS_PER_THREAD;  // 1024
 constexpr int MAX_POIS = 64;  // Poisson table entries (padded to a power of two)

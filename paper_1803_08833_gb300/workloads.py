@@ -118,3 +118,22 @@ def served_stream(seconds=60.0, rate_hz=20.0, seed=7, spike_rate_hz=SERVED_RATE_
                     imposed_rate_hz=spike_rate_hz)
         out.append((t, cfg, steps))
         k += 1
+
+
+def gauss_48x48_k1125(seed=1, **kw):
+    """Table I's 48x48 grid: 2.88 M neurons, K=1,125 (3.24 G synapses, 29 GB), Gaussian 3-sigma."""
+    return _make(48, 1250, 1125, _GAUSS, seed, **kw)
+
+
+def gauss_96x96_k1125(seed=1, **kw):
+    """Table I's 96x96 grid: 11.5 M neurons, K=1,125 (13 G synapses, ~117 GB), Gaussian 3-sigma."""
+    return _make(96, 1250, 1125, _GAUSS, seed, **kw)
+
+
+def swa_48x48(seed=1, K=1100, **kw):
+    """The slow-wave grid of Sec. III-C: 48x48 modules spaced 400 um, exponential
+    decay lambda = 240 um (the paper's 3.2 G synapses over 2.9 M neurons is
+    ~1,100 per neuron); cut-off at 1.2 mm.  Grid and kernel only: the slow-wave
+    model itself is not published."""
+    lateral = {"kernel": "exp", "sigma_um": 100.0, "lambda_um": 240.0, "cutoff_um": 1200.0}
+    return _make(48, 1250, K, lateral, seed, spacing_um=400.0, **kw)

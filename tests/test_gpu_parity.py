@@ -406,3 +406,34 @@ def test_allocation_failure_is_reported_and_releases_everything(snn):
     st = L.snn_build_network(ctypes.byref(c), fa, ff, None, None, ctypes.byref(h))
     assert st == snn.SNN_ENOMEM and h.value is None
     assert live == {}  # every block obtained before the failure was returned
+
+
+def test_table_one_48x48_grid_runs_and_matches_sampled_rows(snn):
+    """Table I's 48x48 grid (2.88 M neurons, 3.24 G synapses): sampled rows equal
+    the oracle's, 50 persistent steps keep the invariants."""
+    cfg = W.gauss_48x48_k1125(seed=4, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ)
+    rng = np.random.default_rng(1)
+    with snn.Network(cfg, raster_capacity=1 << 22) as net:
+        assert net.N == 48 * 48 * 1250
+        for r in rng.integers(0, net.N, 200).tolist() + [net.N - 1]:
+            tgt, w, d = net.csr(r, 1)
+            ot, ow, od = oracle.gen_rows(cfg, r, 1)
+            assert np.array_equal(tgt, ot) and np.array_equal(w.view(np.uint32), ow.view(np.uint32))
+            assert np.array_equal(d, od)
+        net.set_schedule(2)
+        net.step(50)
+        st, ids = net.read_spikes()
+        s = net.stats()
+        assert s["rec_events"] == s["n_spikes"] * 1125 and len(st) == s["n_spikes"]
+        assert np.all(np.diff(st.astype(np.int64) * net.N + ids) > 0)
+        rate = s["n_spikes"] / (net.N * 50) * 1000.0
+        assert 4.0 < rate < 12.0
+
+
+def test_slow_wave_grid_tables(snn):
+    cfg = dict(W.swa_48x48(), neurons_per_module=2, K=8)
+    with snn.Network(cfg) as net:
+        T, TM, cnt = net.cdf()
+    for m in (0, 47, 48 * 24 + 24, 48 * 48 - 1):
+        oT, oTM, _ = oracle.cdf_table(cfg, m)
+        assert cnt[m] == len(oT) and np.array_equal(T[m, :len(oT)], oT) and np.array_equal(TM[m, :len(oT)], oTM)
