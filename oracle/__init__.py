@@ -54,6 +54,11 @@ class OrParams(ctypes.Structure):
         ("imposed_rate_hz", ctypes.c_float),
         ("weight_bf16", ctypes.c_int32), ("fx_shift", ctypes.c_uint32),
         ("seed", ctypes.c_uint64),
+        ("conn_rule", ctypes.c_int32), ("p_local", ctypes.c_float),
+        ("A_remote", ctypes.c_double), ("p_min", ctypes.c_double),
+        ("inh_local_only", ctypes.c_int32), ("weight_dist", ctypes.c_int32),
+        ("w_exc_sd", ctypes.c_float), ("w_inh_sd", ctypes.c_float),
+        ("delay_dist", ctypes.c_int32), ("delay_tau_ms", ctypes.c_float),
     ]
 
 
@@ -65,6 +70,7 @@ class OrConsts(ctypes.Structure):
         ("a_m", ctypes.c_float), ("a_c", ctypes.c_float), ("kc", ctypes.c_float),
         ("J_ext_fx", ctypes.c_int32), ("imposed_thresh", ctypes.c_uint64),
         ("pois_len", ctypes.c_uint32), ("pois", ctypes.c_uint64 * 64),
+        ("n_pair_offsets", ctypes.c_uint32),
     ]
 
 
@@ -86,6 +92,15 @@ def params(cfg: dict) -> OrParams:
             continue
         if k == "kernel":
             p.kernel = {"gauss": 0, "exp": 1}.get(v, v)
+            continue
+        if k == "conn_rule":
+            p.conn_rule = {"fixed_k": 0, "pairwise": 1}.get(v, v)
+            continue
+        if k == "weight_dist":
+            p.weight_dist = {"uniform": 0, "gauss": 1}.get(v, v)
+            continue
+        if k == "delay_dist":
+            p.delay_dist = {"uniform": 0, "exp": 1}.get(v, v)
             continue
         if k in _IGNORED:
             continue
@@ -136,6 +151,13 @@ def lib():
         L.or_get_stats.argtypes = [ctypes.c_void_p, u64p, u64p, u64p]
         L.or_gen_rows.argtypes = [P(OrParams), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]
+        L.or_gen_rows_v.argtypes = [P(OrParams), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_pair_stencil.argtypes = [P(OrParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_uint32, u32p]
+        L.or_weight_table.argtypes = [P(OrParams), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_delay_table.argtypes = [P(OrParams), ctypes.c_void_p, u32p]
+        L.or_get_row_ptr.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.or_initial_V.argtypes = [P(OrParams), ctypes.c_uint32]
         L.or_initial_V.restype = ctypes.c_float
         L.or_drive.argtypes = [P(OrParams), P(OrConsts), ctypes.c_uint32, ctypes.c_uint32, u32p,
@@ -215,6 +237,56 @@ def gen_rows(cfg: dict, first: int, count: int):
     return tgt, w, d
 
 
+def gen_rows_v(cfg: dict, first: int, count: int):
+    """Rows [first, first + count) of either connection rule, back to back:
+    (targets, weights, delays, row lengths)."""
+    p = params(cfg)
+    c = constants(cfg)
+    M = int(cfg["neurons_per_module"])
+    per_row = int(cfg.get("K", 0)) if int(p.conn_rule) == 0 else max(1, c["n_pair_offsets"]) * M
+    cap = max(1, per_row * count)
+    tgt = np.empty(cap, np.uint32)
+    w = np.empty(cap, np.float32)
+    d = np.empty(cap, np.uint8)
+    ln = np.empty(max(1, count), np.uint32)
+    if lib().or_gen_rows_v(ctypes.byref(p), first, count, cap, _ptr(tgt), _ptr(w), _ptr(d), _ptr(ln)):
+        raise ValueError(lib().or_error().decode())
+    n = int(ln[:count].sum())
+    return tgt[:n].copy(), w[:n].copy(), d[:n].copy(), ln[:count].copy()
+
+
+def pair_stencil(cfg: dict):
+    """(dx, dy, probability, uint64 threshold) of the per-pair law's stencil."""
+    p = params(cfg)
+    n = ctypes.c_uint32()
+    if lib().or_pair_stencil(ctypes.byref(p), None, None, None, None, 0, ctypes.byref(n)):
+        raise ValueError(lib().or_error().decode())
+    k = n.value
+    dx = np.empty(k, np.int32)
+    dy = np.empty(k, np.int32)
+    pr = np.empty(k, np.float64)
+    th = np.empty(k, np.uint64)
+    lib().or_pair_stencil(ctypes.byref(p), _ptr(dx), _ptr(dy), _ptr(pr), _ptr(th), k, ctypes.byref(n))
+    return dx, dy, pr, th
+
+
+def weight_table(cfg: dict, exc: bool):
+    """(float32, float64) 4096-entry Gaussian efficacy table."""
+    tab = np.empty(4096, np.float32)
+    tab64 = np.empty(4096, np.float64)
+    lib().or_weight_table(ctypes.byref(params(cfg)), 1 if exc else 0, _ptr(tab), _ptr(tab64))
+    return tab, tab64
+
+
+def delay_table(cfg: dict):
+    """Thresholds of the exponential delay law (uint64)."""
+    thr = np.empty(256, np.uint64)
+    n = ctypes.c_uint32()
+    if lib().or_delay_table(ctypes.byref(params(cfg)), _ptr(thr), ctypes.byref(n)):
+        raise ValueError(lib().or_error().decode())
+    return thr[:n.value].copy()
+
+
 def initial_V(cfg: dict, i: int) -> float:
     return float(lib().or_initial_V(ctypes.byref(params(cfg)), i))
 
@@ -249,7 +321,7 @@ class OracleNet:
         if not self._h:
             raise ValueError(lib().or_error().decode())
         self.N = self.consts["N"]
-        self.K = int(cfg["K"])
+        self.K = int(cfg.get("K", 0))
         self.D = self.consts["D"]
 
     def close(self):
@@ -292,6 +364,11 @@ class OracleNet:
             w = np.empty(ns, np.float32)
             lib().or_get_csr(self._h, _ptr(tgt), _ptr(w), _ptr(d))
         return tgt, w, d
+
+    def row_ptr(self):
+        rp = np.empty(self.N + 1, np.uint64)
+        lib().or_get_row_ptr(self._h, _ptr(rp))
+        return rp
 
     def raster(self):
         n = int(lib().or_raster_size(self._h))

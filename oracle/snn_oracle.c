@@ -31,6 +31,17 @@
  *     grid boundaries; draws with replacement (autapses/multapses allowed).
  *   - Flow step 5 (sorting the inputs) is replaced by an exact int32 fixed
  *     point sum: integer addition does not depend on the order.
+ *   - The per-pair law of Sec. III-B (conn_rule 1): every ordered pair of
+ *     distinct neurons in one module is connected with probability p_local,
+ *     a pair at module distance r > 0 with probability A f(r) (f the
+ *     Gaussian or exponential shape), modules with A f(r) <= p_min get none;
+ *     one independent draw per pair, so no autapses and no multapses, and the
+ *     out-degree varies from neuron to neuron; inhibitory neurons connect
+ *     inside their module only (the caption of Fig. 3); open boundaries.
+ *   - Gaussian efficacies (Sec. II-B) are drawn by inverse CDF from a
+ *     4096-quantile table; exponential delays are the continuous law of mean
+ *     delay_tau_ms floored onto whole steps from d_exc_lo and truncated at
+ *     d_exc_hi (renormalised).  The paper gives neither's parameters.
  */
 #include "snn_oracle.h"
 
@@ -42,6 +53,8 @@
 #define OR_TAG_GEN 0u
 #define OR_TAG_DRIVE 1u
 #define OR_TAG_INIT 2u
+#define OR_TAG_CONN 3u
+#define OR_WTAB 4096u
 
 static char g_err[256];
 
@@ -133,6 +146,24 @@ int or_constants(const or_params* p, or_consts* c) {
         set_err("delays must satisfy 1 <= lo <= hi <= 255");
         return -1;
     }
+    if (p->conn_rule != 0 && p->conn_rule != 1) {
+        set_err("conn_rule must be 0 or 1");
+        return -1;
+    }
+    if (p->conn_rule == 1 &&
+        (!(p->p_local >= 0.0f && p->p_local <= 1.0f) || !(p->A_remote >= 0.0 && p->A_remote <= 1.0) ||
+         !(p->p_min > 0.0 && p->p_min < 1.0))) {
+        set_err("rule 1 needs 0 <= p_local <= 1, 0 <= A_remote <= 1, 0 < p_min < 1");
+        return -1;
+    }
+    if ((p->weight_dist != 0 && p->weight_dist != 1) || !(p->w_exc_sd >= 0.0f) || !(p->w_inh_sd >= 0.0f)) {
+        set_err("weight_dist must be 0 or 1 with non-negative deviations");
+        return -1;
+    }
+    if ((p->delay_dist != 0 && p->delay_dist != 1) || (p->delay_dist == 1 && !(p->delay_tau_ms > 0.0f))) {
+        set_err("delay_dist must be 0 or 1, with delay_tau_ms > 0 for 1");
+        return -1;
+    }
     if (p->fx_shift < 8 || p->fx_shift > 24) {
         set_err("fx_shift must be in [8, 24]");
         return -1;
@@ -201,6 +232,12 @@ int or_constants(const or_params* p, or_consts* c) {
     if (pf < 0.0) pf = 0.0;
     if (pf > 1.0) pf = 1.0;
     c->imposed_thresh = (uint64_t)floor(pf * 4294967296.0);
+    c->n_pair_offsets = 0;
+    if (p->conn_rule == 1) {
+        uint32_t n = 0;
+        if (or_pair_stencil(p, NULL, NULL, NULL, NULL, 0, &n)) return -1;
+        c->n_pair_offsets = n;
+    }
     return 0;
 }
 
@@ -275,6 +312,93 @@ int or_cdf_table(const or_params* p, uint32_t module, uint32_t* thresh, uint32_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* The per-pair law (Sec. III-B).  The stencil radius grows while the pair
+ * probability on an axis still exceeds p_min (f decreases with r). */
+int or_pair_stencil(const or_params* p, int32_t* dx, int32_t* dy, double* prob, uint64_t* thresh,
+                    uint32_t cap, uint32_t* n_out) {
+    if (p->conn_rule != 1) {
+        set_err("the pair stencil belongs to conn_rule 1");
+        return -1;
+    }
+    uint32_t R = 0;
+    while (R < 4096 && p->A_remote * kernel_value(p, (R + 1) * (R + 1)) > p->p_min) ++R;
+    uint32_t n = 0;
+    for (int32_t y = -(int32_t)R; y <= (int32_t)R; ++y) {
+        for (int32_t x = -(int32_t)R; x <= (int32_t)R; ++x) {
+            double pr;
+            if (x == 0 && y == 0)
+                pr = (double)p->p_local;
+            else {
+                pr = p->A_remote * kernel_value(p, (uint32_t)(x * x + y * y));
+                if (!(pr > p->p_min)) continue;
+            }
+            if (dx) {
+                if (n >= cap) {
+                    set_err("stencil capacity too small");
+                    return -1;
+                }
+                dx[n] = x;
+                dy[n] = y;
+                if (prob) prob[n] = pr;
+                if (thresh) thresh[n] = pr >= 1.0 ? 4294967296ull : (uint64_t)floor(pr * 4294967296.0);
+            }
+            ++n;
+        }
+    }
+    *n_out = n;
+    return 0;
+}
+
+/* Standard normal CDF and its inverse by bisection to the resolution of a
+ * double (slow, but only 4096 values per table). */
+static double std_normal_cdf(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+static double std_normal_quantile(double q) {
+    double lo = -40.0, hi = 40.0;
+    for (int it = 0; it < 4000; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        if (std_normal_cdf(mid) < q)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return fabs(std_normal_cdf(lo) - q) <= fabs(std_normal_cdf(hi) - q) ? lo : hi;
+}
+
+int or_weight_table(const or_params* p, int exc, float* tab, double* tab64) {
+    double mean = exc ? 0.5 * ((double)p->w_exc_lo + (double)p->w_exc_hi) : (double)p->w_inh;
+    double sd = exc ? (double)p->w_exc_sd : (double)p->w_inh_sd;
+    for (uint32_t k = 0; k < OR_WTAB; ++k) {
+        double z = std_normal_quantile(((double)k + 0.5) / (double)OR_WTAB);
+        double w = mean + sd * z;
+        if (exc && w < 0.0) w = 0.0; /* an efficacy keeps the sign of its population */
+        if (!exc && w > 0.0) w = 0.0;
+        if (tab) tab[k] = (float)w;
+        if (tab64) tab64[k] = w;
+    }
+    return 0;
+}
+
+/* P(delay <= d_lo + k) = (1 - e^{-(k+1)/tau}) / (1 - e^{-span/tau}), tau in steps. */
+int or_delay_table(const or_params* p, uint64_t* thr, uint32_t* n_out) {
+    uint32_t span = p->d_exc_hi - p->d_exc_lo + 1u;
+    double tau = (double)p->delay_tau_ms / (double)p->dt;
+    if (!(tau > 0.0)) {
+        set_err("delay_tau_ms must be positive");
+        return -1;
+    }
+    double Z = 1.0 - exp(-(double)span / tau);
+    for (uint32_t k = 0; k + 1 < span; ++k) {
+        double F = (1.0 - exp(-(double)(k + 1) / tau)) / Z;
+        double x = floor(F * 4294967296.0);
+        thr[k] = x >= 4294967296.0 ? 4294967296ull : (uint64_t)x;
+    }
+    *n_out = span - 1u;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 int or_lif_update(const or_consts* c, const or_params* p, float* V, float* cf, uint8_t* ref,
                   int exc, int32_t I_fx, int forced) {
     int was_ref = *ref > 0;
@@ -314,8 +438,9 @@ struct or_net {
     or_params p;
     or_consts c;
     int fp64;
-    uint32_t N, K, M;
+    uint32_t N, M;
     uint64_t nsyn;
+    uint64_t* row_ptr;  /* N + 1 row offsets */
     uint32_t* tgt;
     float* w;
     double* w64;
@@ -341,90 +466,279 @@ static int is_exc(const or_net* n, uint32_t i) { return (i % n->M) < n->c.n_exc;
 
 void or_destroy(or_net* n) {
     if (!n) return;
-    free(n->tgt); free(n->w); free(n->w64); free(n->d);
+    free(n->row_ptr); free(n->tgt); free(n->w); free(n->w64); free(n->d);
     free(n->V); free(n->cf); free(n->V64); free(n->c64); free(n->ref);
     free(n->ring); free(n->ring64); free(n->spk); free(n->rst_t); free(n->rst_id);
     free(n);
 }
 
-/* Synapse generation (Sec. II-B): synapse k of neuron i draws one Philox
- * block (i, k, GEN); u0 picks the target module by inverse CDF, u1 the neuron
- * inside it, u2 the weight and u3 the delay.  Rows [first, first + count) are
- * written from offset 0 of the output arrays; w (float) or w64 (double) is
- * filled, whichever is non-NULL. */
-static int gen_rows(const or_params* p, const or_consts* c, uint32_t first, uint32_t count,
-                    uint32_t* tgt, float* w, double* w64, uint8_t* d) {
-    uint32_t cap = c->max_offsets;
-    uint32_t nm = c->n_modules;
-    uint32_t M = p->neurons_per_module;
-    uint32_t* T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
-    uint32_t* TM = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)cap * nm);
-    uint32_t* cnt = (uint32_t*)calloc(nm, sizeof(uint32_t));
-    if (!T || !TM || !cnt) {
-        free(T); free(TM); free(cnt);
-        set_err("out of memory");
-        return -1;
-    }
-    uint32_t m0 = first / M, m1 = count ? (first + count - 1) / M : m0;
-    for (uint32_t m = m0; m <= m1 && m < nm; ++m) {
-        if (or_cdf_table(p, m, T + (size_t)m * cap, TM + (size_t)m * cap, NULL, cap, &cnt[m])) {
-            free(T); free(TM); free(cnt);
+/* What synapse generation needs besides the description: the target-module
+ * tables (rule 0) or the pair stencil (rule 1), and the efficacy and delay
+ * tables of the chosen distributions. */
+typedef struct gen_ctx {
+    const or_params* p;
+    const or_consts* c;
+    uint32_t cap;                 /* rule 0: table entries per module */
+    uint32_t *T, *TM, *cnt;       /* rule 0: per-module thresholds, targets, sizes */
+    uint32_t ns;                  /* rule 1: stencil size */
+    int32_t *sdx, *sdy;           /* rule 1: stencil offsets */
+    uint64_t* sthr;               /* rule 1: pair thresholds */
+    float *wt_e, *wt_i;           /* Gaussian efficacy tables */
+    double *wt64_e, *wt64_i;
+    uint64_t dthr[256];           /* exponential delay thresholds */
+    uint32_t n_dthr;
+} gen_ctx;
+
+static void gen_free(gen_ctx* g) {
+    free(g->T); free(g->TM); free(g->cnt); free(g->sdx); free(g->sdy); free(g->sthr);
+    free(g->wt_e); free(g->wt_i); free(g->wt64_e); free(g->wt64_i);
+    memset(g, 0, sizeof *g);
+}
+
+/* Prepares generation of rows [first, first + count). */
+static int gen_init(gen_ctx* g, const or_params* p, const or_consts* c, uint32_t first, uint32_t count) {
+    memset(g, 0, sizeof *g);
+    g->p = p;
+    g->c = c;
+    uint32_t M = p->neurons_per_module, nm = c->n_modules;
+    if (p->conn_rule == 0) {
+        g->cap = c->max_offsets;
+        g->T = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)g->cap * nm);
+        g->TM = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)g->cap * nm);
+        g->cnt = (uint32_t*)calloc(nm, sizeof(uint32_t));
+        if (!g->T || !g->TM || !g->cnt) goto oom;
+        uint32_t m0 = first / M, m1 = count ? (first + count - 1) / M : m0;
+        for (uint32_t m = m0; m <= m1 && m < nm; ++m)
+            if (or_cdf_table(p, m, g->T + (size_t)m * g->cap, g->TM + (size_t)m * g->cap, NULL, g->cap,
+                             &g->cnt[m])) {
+                gen_free(g);
+                return -1;
+            }
+    } else {
+        g->ns = c->n_pair_offsets;
+        g->sdx = (int32_t*)malloc(sizeof(int32_t) * g->ns);
+        g->sdy = (int32_t*)malloc(sizeof(int32_t) * g->ns);
+        g->sthr = (uint64_t*)malloc(sizeof(uint64_t) * g->ns);
+        if (!g->sdx || !g->sdy || !g->sthr) goto oom;
+        uint32_t n = 0;
+        if (or_pair_stencil(p, g->sdx, g->sdy, NULL, g->sthr, g->ns, &n)) {
+            gen_free(g);
             return -1;
         }
     }
-    float span = p->w_exc_hi - p->w_exc_lo;
-    uint32_t dspan = p->d_exc_hi - p->d_exc_lo + 1u;
-    for (uint32_t r = 0; r < count; ++r) {
-        uint32_t i = first + r;
-        uint32_t s = i / M;
-        const uint32_t* Ts = T + (size_t)s * cap;
-        const uint32_t* TMs = TM + (size_t)s * cap;
-        uint32_t ns = cnt[s];
-        int exc = (i % M) < c->n_exc;
+    if (p->weight_dist == 1) {
+        g->wt_e = (float*)malloc(sizeof(float) * OR_WTAB);
+        g->wt_i = (float*)malloc(sizeof(float) * OR_WTAB);
+        g->wt64_e = (double*)malloc(sizeof(double) * OR_WTAB);
+        g->wt64_i = (double*)malloc(sizeof(double) * OR_WTAB);
+        if (!g->wt_e || !g->wt_i || !g->wt64_e || !g->wt64_i) goto oom;
+        or_weight_table(p, 1, g->wt_e, g->wt64_e);
+        or_weight_table(p, 0, g->wt_i, g->wt64_i);
+    }
+    if (p->delay_dist == 1 && or_delay_table(p, g->dthr, &g->n_dthr)) {
+        gen_free(g);
+        return -1;
+    }
+    return 0;
+oom:
+    gen_free(g);
+    set_err("out of memory");
+    return -1;
+}
+
+/* Efficacy and delay of one synapse from words u2 (efficacy) and u3 (delay)
+ * of its Philox block. */
+static void syn_attr(const gen_ctx* g, int exc, const uint32_t u[4], float* w, double* w64, uint8_t* d) {
+    const or_params* p = g->p;
+    if (exc) {
+        if (p->delay_dist == 0) {
+            uint32_t dspan = p->d_exc_hi - p->d_exc_lo + 1u;
+            *d = (uint8_t)(p->d_exc_lo + (uint32_t)(((uint64_t)u[3] * dspan) >> 32));
+        } else {
+            uint32_t k = 0;
+            for (uint32_t j = 0; j < g->n_dthr; ++j)
+                if (g->dthr[j] <= (uint64_t)u[3]) ++k;
+            *d = (uint8_t)(p->d_exc_lo + k);
+        }
+        if (p->weight_dist == 0) {
+            if (w64) {
+                double lo = (double)p->w_exc_lo, hi = (double)p->w_exc_hi;
+                *w64 = lo + (hi - lo) * unit24d(u[2]);
+            } else {
+                float x = (p->w_exc_hi - p->w_exc_lo) * unit24(u[2]);
+                *w = p->w_exc_lo + x;
+            }
+        } else {
+            if (w64)
+                *w64 = g->wt64_e[u[2] >> 20];
+            else
+                *w = g->wt_e[u[2] >> 20];
+        }
+    } else {
+        *d = (uint8_t)p->d_inh;
+        if (p->weight_dist == 0) {
+            if (w64)
+                *w64 = (double)p->w_inh;
+            else
+                *w = p->w_inh;
+        } else {
+            if (w64)
+                *w64 = g->wt64_i[u[2] >> 20];
+            else
+                *w = g->wt_i[u[2] >> 20];
+        }
+    }
+    if (!w64 && p->weight_bf16) *w = or_bf16_to_float(or_bf16_bits(*w));
+}
+
+/* Row of neuron i (Sec. II-B), written at out[0 ..).  Rule 0: synapse k draws
+ * one Philox block (i, k, GEN); u0 picks the target module by inverse CDF, u1
+ * the neuron inside it.  Rule 1: for every stencil offset (index o) inside
+ * the grid and every neuron j of that module, word j % 4 of the block
+ * (i, o * ceil(M/4) + j / 4, CONN) below the pair threshold makes a synapse;
+ * the k-th synapse of the row takes its efficacy and delay from words u2, u3
+ * of block (i, k, GEN) in both rules.  Returns the row length, or -1 if it
+ * would pass `cap` (a NULL tgt only counts). */
+static int64_t gen_row(const gen_ctx* g, uint32_t i, uint64_t cap, uint32_t* tgt, float* w, double* w64,
+                       uint8_t* d) {
+    const or_params* p = g->p;
+    uint32_t M = p->neurons_per_module;
+    uint32_t s = i / M;
+    int exc = (i % M) < g->c->n_exc;
+    if (p->conn_rule == 0) {
+        if ((uint64_t)p->K > cap) return -1;
+        const uint32_t* Ts = g->T + (size_t)s * g->cap;
+        const uint32_t* TMs = g->TM + (size_t)s * g->cap;
+        uint32_t ns = g->cnt[s];
         for (uint32_t k = 0; k < p->K; ++k) {
             uint32_t u[4];
             draw(p, i, k, OR_TAG_GEN, u);
+            if (!tgt) continue;
             uint32_t j = 0;
             while (j + 1 < ns && Ts[j] <= u[0]) ++j; /* first entry with u0 < T */
-            uint32_t tmod = TMs[j];
-            size_t e = (size_t)r * p->K + k;
-            tgt[e] = tmod * M + (uint32_t)(((uint64_t)u[1] * M) >> 32);
-            if (exc) {
-                d[e] = (uint8_t)(p->d_exc_lo + (uint32_t)(((uint64_t)u[3] * dspan) >> 32));
-                if (w64) {
-                    double lo = (double)p->w_exc_lo, hi = (double)p->w_exc_hi;
-                    w64[e] = lo + (hi - lo) * unit24d(u[2]);
-                } else {
-                    float x = span * unit24(u[2]);
-                    w[e] = p->w_exc_lo + x;
-                }
-            } else {
-                d[e] = (uint8_t)p->d_inh;
-                if (w64)
-                    w64[e] = (double)p->w_inh;
-                else
-                    w[e] = p->w_inh;
+            tgt[k] = TMs[j] * M + (uint32_t)(((uint64_t)u[1] * M) >> 32);
+            syn_attr(g, exc, u, w ? w + k : NULL, w64 ? w64 + k : NULL, d + k);
+        }
+        return p->K;
+    }
+    int32_t sx = (int32_t)(s % p->grid_w), sy = (int32_t)(s / p->grid_w);
+    uint32_t a = i % M, c4 = (M + 3u) / 4u;
+    uint64_t k = 0;
+    for (uint32_t o = 0; o < g->ns; ++o) {
+        int local = g->sdx[o] == 0 && g->sdy[o] == 0;
+        if (!exc && p->inh_local_only && !local) continue;
+        int32_t tx = sx + g->sdx[o], ty = sy + g->sdy[o];
+        if (tx < 0 || ty < 0 || tx >= (int32_t)p->grid_w || ty >= (int32_t)p->grid_h) continue;
+        uint32_t base = ((uint32_t)ty * p->grid_w + (uint32_t)tx) * M;
+        for (uint32_t j = 0; j < M; ++j) {
+            if (local && j == a) continue; /* no autapse */
+            uint32_t u[4];
+            draw(p, i, o * c4 + j / 4u, OR_TAG_CONN, u);
+            if ((uint64_t)u[j % 4u] >= g->sthr[o]) continue;
+            if (k >= cap) return -1;
+            if (tgt) {
+                uint32_t v[4];
+                draw(p, i, (uint32_t)k, OR_TAG_GEN, v);
+                tgt[k] = base + j;
+                syn_attr(g, exc, v, w ? w + k : NULL, w64 ? w64 + k : NULL, d + k);
             }
-            if (!w64 && p->weight_bf16) w[e] = or_bf16_to_float(or_bf16_bits(w[e]));
+            ++k;
         }
     }
-    free(T); free(TM); free(cnt);
+    return (int64_t)k;
+}
+
+static int grow(or_net* n, uint64_t need) {
+    uint64_t cap = n->nsyn ? n->nsyn : 1;
+    if (need <= cap) return 0;
+    while (cap < need) cap *= 2;
+    uint32_t* t = (uint32_t*)realloc(n->tgt, sizeof(uint32_t) * cap);
+    if (!t) return -1;
+    n->tgt = t;
+    uint8_t* d = (uint8_t*)realloc(n->d, cap);
+    if (!d) return -1;
+    n->d = d;
+    if (n->fp64) {
+        double* w = (double*)realloc(n->w64, sizeof(double) * cap);
+        if (!w) return -1;
+        n->w64 = w;
+    } else {
+        float* w = (float*)realloc(n->w, sizeof(float) * cap);
+        if (!w) return -1;
+        n->w = w;
+    }
+    n->nsyn = cap; /* capacity while generating; set to the total afterwards */
     return 0;
 }
 
+/* The whole table, rows back to back. */
 static int generate(or_net* n) {
-    return gen_rows(&n->p, &n->c, 0, n->N, n->tgt, n->w, n->w64, n->d);
+    gen_ctx g;
+    if (gen_init(&g, &n->p, &n->c, 0, n->N)) return -1;
+    uint64_t used = 0;
+    int rc = 0;
+    n->row_ptr[0] = 0;
+    for (uint32_t i = 0; i < n->N && rc == 0; ++i) {
+        for (;;) {
+            uint64_t room = n->nsyn - used;
+            int64_t len = gen_row(&g, i, room, n->tgt + used, n->w ? n->w + used : NULL,
+                                  n->w64 ? n->w64 + used : NULL, n->d + used);
+            if (len >= 0) {
+                used += (uint64_t)len;
+                break;
+            }
+            if (grow(n, n->nsyn + (uint64_t)n->M * g.ns + n->p.K + 1)) {
+                set_err("out of memory");
+                rc = -1;
+                break;
+            }
+        }
+        n->row_ptr[i + 1] = used;
+    }
+    gen_free(&g);
+    n->nsyn = used;
+    return rc;
 }
 
-int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
-                uint8_t* d) {
+int or_gen_rows_v(const or_params* p, uint32_t first, uint32_t count, uint64_t cap, uint32_t* tgt,
+                  float* w, uint8_t* d, uint32_t* len) {
     or_consts c;
     if (or_constants(p, &c)) return -1;
     if ((uint64_t)first + count > c.N) {
         set_err("rows out of range");
         return -1;
     }
-    return gen_rows(p, &c, first, count, tgt, w, NULL, d);
+    gen_ctx g;
+    if (gen_init(&g, p, &c, first, count)) return -1;
+    uint64_t used = 0;
+    for (uint32_t r = 0; r < count; ++r) {
+        int64_t n = gen_row(&g, first + r, cap - used, tgt + used, w + used, NULL, d + used);
+        if (n < 0) {
+            gen_free(&g);
+            set_err("row capacity too small");
+            return -1;
+        }
+        len[r] = (uint32_t)n;
+        used += (uint64_t)n;
+    }
+    gen_free(&g);
+    return 0;
+}
+
+int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
+                uint8_t* d) {
+    if (p->conn_rule != 0) {
+        set_err("rows of variable length: use or_gen_rows_v");
+        return -1;
+    }
+    uint32_t* len = (uint32_t*)malloc(sizeof(uint32_t) * (count ? count : 1));
+    if (!len) {
+        set_err("out of memory");
+        return -1;
+    }
+    int r = or_gen_rows_v(p, first, count, (uint64_t)count * p->K, tgt, w, d, len);
+    free(len);
+    return r;
 }
 
 float or_initial_V(const or_params* p, uint32_t i) {
@@ -453,10 +767,11 @@ or_net* or_create(const or_params* p, int fp64) {
     n->c = c;
     n->fp64 = fp64 ? 1 : 0;
     n->N = c.N;
-    n->K = p->K;
     n->M = p->neurons_per_module;
-    n->nsyn = (uint64_t)n->N * n->K;
+    n->nsyn = p->conn_rule == 0 ? (uint64_t)n->N * p->K : (uint64_t)n->N * 64u;
     size_t ns = (size_t)n->nsyn ? (size_t)n->nsyn : 1;
+    n->nsyn = ns;
+    n->row_ptr = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n->N + 1));
     n->tgt = (uint32_t*)malloc(sizeof(uint32_t) * ns);
     n->d = (uint8_t*)malloc(ns);
     if (n->fp64)
@@ -474,7 +789,7 @@ or_net* or_create(const or_params* p, int fp64) {
         n->cf = (float*)calloc(n->N, sizeof(float));
         n->ring = (int64_t*)calloc((size_t)c.D * n->N, sizeof(int64_t));
     }
-    if (!n->tgt || !n->d || (!n->w && !n->w64) || !n->ref || !n->spk ||
+    if (!n->row_ptr || !n->tgt || !n->d || (!n->w && !n->w64) || !n->ref || !n->spk ||
         (n->fp64 ? (!n->V64 || !n->c64 || !n->ring64) : (!n->V || !n->cf || !n->ring))) {
         or_destroy(n);
         set_err("out of memory");
@@ -503,6 +818,10 @@ or_net* or_create(const or_params* p, int fp64) {
 }
 
 uint64_t or_n_synapses(const or_net* n) { return n->nsyn; }
+
+void or_get_row_ptr(const or_net* n, uint64_t* row_ptr) {
+    memcpy(row_ptr, n->row_ptr, sizeof(uint64_t) * ((size_t)n->N + 1));
+}
 
 void or_get_csr(const or_net* n, uint32_t* tgt, float* w, uint8_t* d) {
     if (tgt) memcpy(tgt, n->tgt, sizeof(uint32_t) * n->nsyn);
@@ -542,7 +861,7 @@ static int raster_push(or_net* n, uint32_t t, uint32_t id) {
 }
 
 static void deliver_one(or_net* n, uint32_t t, uint32_t src, uint32_t k) {
-    size_t e = (size_t)src * n->K + k;
+    size_t e = (size_t)n->row_ptr[src] + k;
     uint32_t slot = (t + n->d[e]) % n->c.D;
     size_t r = (size_t)slot * n->N + n->tgt[e];
     if (n->fp64) {
@@ -605,30 +924,46 @@ static int step_once(or_net* n) {
         }
     }
     n->n_spikes += nspk;
-    n->rec += (uint64_t)nspk * n->K;
+    uint64_t total = 0;
+    for (uint32_t s = 0; s < nspk; ++s) total += n->row_ptr[n->spk[s] + 1] - n->row_ptr[n->spk[s]];
+    n->rec += total;
     /* flow steps 2-3: queue every spike at its targets, in the slot of the
      * step at which it arrives (t + delay) */
     if (n->shuffle_seed == 0) {
-        for (uint32_t s = 0; s < nspk; ++s)
-            for (uint32_t k = 0; k < n->K; ++k) deliver_one(n, t, n->spk[s], k);
+        for (uint32_t s = 0; s < nspk; ++s) {
+            uint32_t len = (uint32_t)(n->row_ptr[n->spk[s] + 1] - n->row_ptr[n->spk[s]]);
+            for (uint32_t k = 0; k < len; ++k) deliver_one(n, t, n->spk[s], k);
+        }
     } else {
+        /* every (spike, synapse) event in a random order */
         uint64_t st = n->shuffle_seed ^ ((uint64_t)t << 32);
-        uint64_t total = (uint64_t)nspk * n->K;
-        uint64_t* ord = (uint64_t*)malloc(sizeof(uint64_t) * (total ? total : 1));
-        if (!ord) {
+        uint32_t* src = (uint32_t*)malloc(sizeof(uint32_t) * (total ? total : 1));
+        uint32_t* syn = (uint32_t*)malloc(sizeof(uint32_t) * (total ? total : 1));
+        if (!src || !syn) {
+            free(src);
+            free(syn);
             set_err("out of memory");
             return -1;
         }
-        for (uint64_t e = 0; e < total; ++e) ord[e] = e;
-        for (uint64_t e = total; e > 1; --e) {
-            uint64_t j = mix64(&st) % e;
-            uint64_t tmp = ord[e - 1];
-            ord[e - 1] = ord[j];
-            ord[j] = tmp;
+        uint64_t e = 0;
+        for (uint32_t s = 0; s < nspk; ++s) {
+            uint32_t len = (uint32_t)(n->row_ptr[n->spk[s] + 1] - n->row_ptr[n->spk[s]]);
+            for (uint32_t k = 0; k < len; ++k, ++e) {
+                src[e] = n->spk[s];
+                syn[e] = k;
+            }
         }
-        for (uint64_t e = 0; e < total; ++e)
-            deliver_one(n, t, n->spk[ord[e] / n->K], (uint32_t)(ord[e] % n->K));
-        free(ord);
+        for (e = total; e > 1; --e) {
+            uint64_t j = mix64(&st) % e;
+            uint32_t a = src[e - 1], b = syn[e - 1];
+            src[e - 1] = src[j];
+            syn[e - 1] = syn[j];
+            src[j] = a;
+            syn[j] = b;
+        }
+        for (e = 0; e < total; ++e) deliver_one(n, t, src[e], syn[e]);
+        free(src);
+        free(syn);
     }
     n->t = t + 1;
     return 0;

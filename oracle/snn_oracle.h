@@ -16,6 +16,12 @@
  *                        stencil sizes, chi-square of drawn distances
  *   synapse generation   pinned: N*K total, weight/delay ranges and chi-square,
  *                        uniform in-degree, 2x2 all-pairs frequencies
+ *   per-pair law         pinned: pair frequencies per offset against p_local and
+ *   (rule 1)             A f(r) (binomial bounds), stencil against the p_min
+ *                        cut, no autapses or multapses, inhibitory rows local,
+ *                        Table I synapse totals of the expected out-degree
+ *   Gaussian efficacies  pinned: table against normal quantiles (scipy)
+ *   exponential delays   pinned: thresholds against the truncated geometric law
  *   or_lif_update        pinned: discrete closed-form f-I curve, continuous f-I
  *                        within O(dt), propagator vs numerical ODE solution,
  *                        adaptation steady state
@@ -51,6 +57,22 @@ typedef struct or_params {
     int32_t weight_bf16;            /* 1: weights rounded to bfloat16 */
     uint32_t fx_shift;              /* fixed-point input scale 2^-fx_shift mV */
     uint64_t seed;
+    /* connection law and the distributions of efficacies and delays (Sec. II-B,
+     * Sec. III-B); all zero = the fixed out-degree rule with uniform draws */
+    int32_t conn_rule;              /* 0: K synapses per neuron, target module drawn from the
+                                       normalised kernel; 1: the per-pair law of Sec. III-B */
+    float p_local;                  /* rule 1: synapse probability to each other neuron of the
+                                       source's own module (Sec. III-B: 80 %) */
+    double A_remote;                /* rule 1: probability A f(r) to each neuron of a module at
+                                       distance r > 0, f the Gaussian or exponential shape */
+    double p_min;                   /* rule 1: modules with A f(r) <= p_min get no synapse */
+    int32_t inh_local_only;         /* rule 1: inhibitory neurons project inside their module only */
+    int32_t weight_dist;            /* 0: exc uniform [w_exc_lo, w_exc_hi), inh w_inh;
+                                       1: Gaussian, exc mean (lo + hi) / 2, inh mean w_inh */
+    float w_exc_sd, w_inh_sd;       /* standard deviations of the Gaussian efficacies */
+    int32_t delay_dist;             /* 0: exc uniform integer in [d_exc_lo, d_exc_hi];
+                                       1: exponential of mean delay_tau_ms, truncated to it */
+    float delay_tau_ms;
 } or_params;
 
 typedef struct or_consts {
@@ -60,6 +82,7 @@ typedef struct or_consts {
     uint64_t imposed_thresh;        /* forced spike when u1 < this (2^32 = always) */
     uint32_t pois_len;
     uint64_t pois[64];              /* n_ext = #{k : pois[k] <= u0} */
+    uint32_t n_pair_offsets;        /* rule 1: stencil size, local offset included; else 0 */
 } or_consts;
 
 typedef struct or_net or_net;
@@ -93,6 +116,24 @@ float or_initial_V(const or_params* p, uint32_t i);
 void or_drive(const or_params* p, const or_consts* c, uint32_t i, uint32_t t, uint32_t* n_ext,
               int* forced);
 
+/* Rule 1 stencil (Sec. III-B): the offsets (dx, dy), in the fixed order dy
+ * outer, dx inner, whose pair probability exceeds p_min; prob[j] is the
+ * probability of a synapse to each neuron of the module at that offset
+ * (p_local at (0, 0)), thresh[j] = floor(prob[j] * 2^32) (2^32 if prob >= 1). */
+int or_pair_stencil(const or_params* p, int32_t* dx, int32_t* dy, double* prob, uint64_t* thresh,
+                    uint32_t cap, uint32_t* n_out);
+/* Gaussian efficacies: entry k of the 4096-entry table is the (k + 1/2)/4096
+ * quantile of N(mean, sd) (clipped to the sign of the population), as float
+ * and (tab64) as double; a synapse takes entry u2 >> 20. */
+int or_weight_table(const or_params* p, int exc, float* tab, double* tab64);
+/* Exponential delays: thresholds thr[k], k < *n_out = d_exc_hi - d_exc_lo,
+ * and an excitatory delay is d_exc_lo + #{k : thr[k] <= u3}. */
+int or_delay_table(const or_params* p, uint64_t* thr, uint32_t* n_out);
+/* Rows [first, first + count) of either rule stored back to back: row
+ * first + r has len[r] synapses; at most `cap` synapses in all. */
+int or_gen_rows_v(const or_params* p, uint32_t first, uint32_t count, uint64_t cap, uint32_t* tgt,
+                  float* w, uint8_t* d, uint32_t* len);
+
 /* fp64 != 0 builds the double-precision variant (double state, double
  * weights, no fixed point) used as the precision reference. */
 or_net* or_create(const or_params* p, int fp64);
@@ -100,6 +141,8 @@ void or_destroy(or_net* net);
 const char* or_error(void);
 
 uint64_t or_n_synapses(const or_net* net);
+/* Row offsets of the synapse table (N + 1 entries): row i is [row_ptr[i], row_ptr[i + 1]). */
+void or_get_row_ptr(const or_net* net, uint64_t* row_ptr);
 void or_get_csr(const or_net* net, uint32_t* tgt, float* w, uint8_t* d);
 void or_get_csr_f64(const or_net* net, double* w);
 

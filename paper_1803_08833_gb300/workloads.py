@@ -38,6 +38,28 @@ def _make(grid, M, K, lateral, seed, weight_dtype="f32", imposed_rate_hz=0.0, **
     return cfg
 
 
+# The per-pair law of Sec. III-B: 80 % local probability, a remote law A f(r)
+# (A = 0.05 Gaussian, 0.03 exponential) cut where it falls to 1/1000,
+# inhibitory neurons local only; Gaussian efficacies (Sec. II-B) with 25 %
+# relative spread and exponential delays of mean 5 ms (the paper gives no
+# parameters for either).
+_PAIRWISE = {
+    "conn_rule": "pairwise", "p_local": 0.8, "p_min": 1e-3, "inh_local_only": 1,
+    "weight_dist": "gauss", "w_exc_sd": 0.05, "w_inh_sd": 0.2,
+    "delay_dist": "exp", "delay_tau_ms": 5.0,
+}
+PAIRWISE_A = {"gauss": 0.05, "exp": 0.03}
+
+
+def pairwise(grid=24, M=1250, lateral="gauss", seed=1, **kw):
+    """A grid x grid network under the per-pair law; Table I's grids are 24, 48
+    and 96 modules per side."""
+    lat = _GAUSS if lateral == "gauss" else _EXP
+    cfg = _make(grid, M, 0, lat, seed, **dict(_PAIRWISE, A_remote=PAIRWISE_A[lateral]))
+    cfg.update(kw)
+    return cfg
+
+
 def gauss_4x4_k1000(seed=1, **kw):
     """4x4 modules x 1,000 neurons (16k), K=1,000, Gaussian 3-sigma, FP32 weights."""
     return _make(4, 1000, 1000, _GAUSS, seed, **kw)

@@ -1,0 +1,220 @@
+"""Pin the oracle's per-pair connection law (Sec. III-B) and the Gaussian
+efficacy / exponential delay distributions (Sec. II-B) against the law's
+closed forms, binomial bounds, normal quantiles and Table I."""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1803_08833_gb300 import workloads as W
+
+
+def _grid_d2(cfg, s, t):
+    gw = cfg["grid_w"]
+    return (s % gw - t % gw) ** 2 + (s // gw - t // gw) ** 2
+
+
+def test_stencil_is_the_one_in_a_thousand_cut():
+    """Gaussian, A = 0.05, sigma = one spacing: A e^{-r^2/2} > 1e-3 holds up to
+    r^2 = 5 (e^{-4} A = 9.2e-4 at r^2 = 8 does not), i.e. the 5x5 square minus
+    its corners, 21 modules.  Exponential, A = 0.03, lambda = 2.9 spacings:
+    r < 2.9 ln 30 = 9.86, i.e. r^2 <= 97, the 301 lattice points of that disc."""
+    g = W.pairwise(grid=9, M=20)
+    dx, dy, p, th = oracle.pair_stencil(g)
+    assert len(dx) == 21
+    r2 = dx * dx + dy * dy
+    assert r2.max() == 5 and set(r2.tolist()) == {0, 1, 2, 4, 5}
+    loc = (dx == 0) & (dy == 0)
+    assert p[loc][0] == np.float64(np.float32(0.8))
+    assert np.allclose(p[r2 == 1], 0.05 * math.exp(-0.5), rtol=1e-15)
+    assert np.allclose(p[r2 == 5], 0.05 * math.exp(-2.5), rtol=1e-15)
+    assert np.array_equal(th, np.floor(p * 2.0 ** 32).astype(np.uint64))
+    # fixed order: dy outer, dx inner
+    key = (dy + 100) * 1000 + (dx + 100)
+    assert np.all(np.diff(key) > 0)
+    e = W.pairwise(grid=9, M=20, lateral="exp")
+    dx, dy, p, th = oracle.pair_stencil(e)
+    assert len(dx) == 301 and (dx * dx + dy * dy).max() == 97
+    assert sum(1 for x in range(-10, 11) for y in range(-10, 11) if x * x + y * y <= 97) == 301
+
+
+def _net(cfg):
+    net = oracle.OracleNet(cfg)
+    rp = net.row_ptr().astype(np.int64)
+    tgt, w, d = net.csr()
+    return net, rp, tgt, w, d
+
+
+@pytest.mark.parametrize("lateral", ["gauss", "exp"])
+def test_pair_frequencies_follow_the_law(lateral):
+    """Synapses per (source, target module) pair class against M p binomial
+    bounds, summed over the interior excitatory sources."""
+    grid, M = (7, 160) if lateral == "gauss" else (21, 24)
+    cfg = W.pairwise(grid=grid, M=M, lateral=lateral, seed=3)
+    net, rp, tgt, w, d = _net(cfg)
+    dx, dy, p, _ = oracle.pair_stencil(cfg)
+    R = int(np.abs(dx).max())
+    n_exc = int(math.floor(0.8 * M + 0.5))
+    src = np.repeat(np.arange(net.N), np.diff(rp))
+    sm, tm = src // M, tgt // M
+    sx, sy = sm % grid, sm // grid
+    interior = (sx >= R) & (sx < grid - R) & (sy >= R) & (sy < grid - R) & ((src % M) < n_exc)
+    n_src = sum(1 for i in range(net.N) if (i % M) < n_exc and R <= (i // M) % grid < grid - R
+                and R <= (i // M) // grid < grid - R)
+    ox = (tm % grid - sx)[interior]
+    oy = (tm // grid - sy)[interior]
+    for k in range(len(dx)):
+        obs = int(np.sum((ox == dx[k]) & (oy == dy[k])))
+        trials = n_src * (M - 1 if dx[k] == 0 and dy[k] == 0 else M)
+        mean, sd = trials * p[k], math.sqrt(trials * p[k] * (1 - p[k]))
+        assert abs(obs - mean) < 5 * sd + 1, (k, dx[k], dy[k], obs, mean)
+    # nothing outside the stencil
+    assert (ox * ox + oy * oy).max() == (dx * dx + dy * dy).max()
+
+
+def test_rows_are_distinct_local_for_inhibitory_and_in_stencil_order():
+    cfg = W.pairwise(grid=5, M=100, seed=9)
+    net, rp, tgt, w, d = _net(cfg)
+    dx, dy, _, _ = oracle.pair_stencil(cfg)
+    order = {(int(a), int(b)): k for k, (a, b) in enumerate(zip(dx, dy))}
+    M, g = 100, 5
+    for i in range(net.N):
+        row = tgt[rp[i]:rp[i + 1]].astype(np.int64)
+        assert i not in row  # no autapse
+        assert len(np.unique(row)) == len(row)  # no multapse
+        s = i // M
+        o = [order[(int(t // M % g - s % g), int(t // M // g - s // g))] for t in row]
+        assert o == sorted(o)  # grouped by stencil offset, in stencil order
+        if (i % M) >= 80:  # inhibitory: own module only, efficacy <= 0, delay d_inh
+            assert np.all(row // M == s)
+            assert np.all(w[rp[i]:rp[i + 1]] <= 0) and np.all(d[rp[i]:rp[i + 1]] == 1)
+
+
+def test_total_equals_the_expected_out_degree():
+    """The whole table against the law's expectation (sum of M p over each
+    source's in-grid stencil), binomial bounds."""
+    cfg = W.pairwise(grid=6, M=120, seed=4)
+    net, rp, tgt, w, d = _net(cfg)
+    dx, dy, p, _ = oracle.pair_stencil(cfg)
+    M, g, n_exc = 120, 6, 96
+    mean = var = 0.0
+    for s in range(g * g):
+        for k in range(len(dx)):
+            tx, ty = s % g + dx[k], s // g + dy[k]
+            if not (0 <= tx < g and 0 <= ty < g):
+                continue
+            local = dx[k] == 0 and dy[k] == 0
+            n_src = M if local else n_exc
+            trials = n_src * (M - 1 if local else M)
+            mean += trials * p[k]
+            var += trials * p[k] * (1 - p[k])
+    assert abs(int(rp[-1]) - mean) < 5 * math.sqrt(var)
+    assert net.stats()["rec_events"] == 0
+
+
+def _expected_total(grid, M, lateral):
+    """Expected recurrent synapses of a grid under the per-pair law."""
+    cfg = W.pairwise(grid=grid, M=M, lateral=lateral)
+    dx, dy, p, _ = oracle.pair_stencil(cfg)
+    n_exc = math.floor(0.8 * M + 0.5)
+    total = 0.0
+    for k in range(len(dx)):
+        nx, ny = grid - abs(int(dx[k])), grid - abs(int(dy[k]))  # sources whose target is in-grid
+        if dx[k] == 0 and dy[k] == 0:
+            total += grid * grid * M * (M - 1) * p[k]
+        else:
+            total += nx * ny * n_exc * M * p[k]
+    return total
+
+
+@pytest.mark.parametrize("lateral,grid,table_g,tol", [
+    ("gauss", 24, 0.9e9, 0.03), ("gauss", 48, 3.5e9, 0.03), ("gauss", 96, 14.2e9, 0.03),
+    ("exp", 24, 1.5e9, 0.04), ("exp", 48, 5.9e9, 0.07), ("exp", 96, 23.4e9, 0.11)])
+def test_table_one_recurrent_synapses(lateral, grid, table_g, tol):
+    """Table I's recurrent-synapse counts (two significant digits) against the
+    law's expectation at M = 1,250: within 3 % for the Gaussian grids; the
+    exponential grids come out 3-10 % above the table (reading in the design
+    notes)."""
+    assert abs(_expected_total(grid, 1250, lateral) / table_g - 1.0) < tol
+
+
+def test_gaussian_efficacy_table_is_normal_quantiles():
+    cfg = W.pairwise(grid=2, M=10)
+    q = (np.arange(4096) + 0.5) / 4096
+    f = lambda x: float(np.float32(x))  # the description holds float32 parameters
+    for exc, mean, sd in ((True, (f(0.1) + f(0.3)) / 2, f(0.05)), (False, f(-0.8), f(0.2))):
+        tab, tab64 = oracle.weight_table(cfg, exc)
+        ref = mean + sd * stats.norm.ppf(q)
+        assert np.allclose(tab64, ref, rtol=0, atol=1e-12)
+        assert np.array_equal(tab, tab64.astype(np.float32))
+        assert np.all(np.diff(tab64) > 0)
+    # clipping keeps the sign of the population
+    tab, _ = oracle.weight_table(dict(cfg, w_exc_sd=0.2), True)
+    assert tab.min() == 0.0 and np.sum(tab == 0) == np.sum(0.2 + 0.2 * stats.norm.ppf(q) <= 0)
+
+
+def test_drawn_efficacies_and_delays():
+    """Excitatory efficacies N(0.2, 0.05) and delays of the truncated
+    exponential law P(d) ~ e^{-(d-1)/5} - e^{-d/5} on 1..20 (chi-square)."""
+    cfg = W.pairwise(grid=4, M=200, seed=6)
+    net, rp, tgt, w, d = _net(cfg)
+    src = np.repeat(np.arange(net.N), np.diff(rp))
+    exc = (src % 200) < 160
+    we = w[exc].astype(np.float64)
+    n = we.size
+    assert abs(we.mean() - 0.2) < 5 * 0.05 / math.sqrt(n)
+    assert abs(we.std() - 0.05) < 0.002
+    assert stats.kstest(we, stats.norm(0.2, 0.05).cdf).pvalue > 1e-4
+    de = d[exc].astype(np.int64)
+    assert de.min() >= 1 and de.max() <= 20
+    k = np.arange(1, 21)
+    pk = np.exp(-(k - 1) / 5.0) - np.exp(-k / 5.0)
+    pk /= pk.sum()
+    chi = stats.chisquare(np.bincount(de, minlength=21)[1:], pk * de.size)
+    assert chi.pvalue > 1e-3
+    thr = oracle.delay_table(cfg).astype(np.float64) / 2.0 ** 32
+    assert np.allclose(thr, np.cumsum(pk)[:-1], rtol=0, atol=2 ** -31)
+
+
+def test_variable_rows_deliver_in_any_order():
+    """Delivery over rows of different lengths: the ring after a shuffled
+    delivery equals the id-ordered one; recurrent events count row lengths."""
+    cfg = W.pairwise(grid=3, M=60, seed=2, imposed_rate_hz=40.0, ext_rate_hz=3000.0)
+    a = oracle.OracleNet(cfg)
+    b = oracle.OracleNet(cfg)
+    b.set_delivery_shuffle(12345)
+    a.step(60)
+    b.step(60)
+    sa, sb = a.state(), b.state()
+    assert np.array_equal(sa["ring"], sb["ring"]) and np.array_equal(sa["V"], sb["V"])
+    st, ids = a.raster()
+    assert len(ids) > 0
+    rp = a.row_ptr().astype(np.int64)
+    assert a.stats()["rec_events"] == int(np.sum(rp[ids + 1] - rp[ids]))
+
+
+def test_gen_rows_v_equals_the_built_table():
+    cfg = W.pairwise(grid=4, M=50, lateral="exp", seed=8)
+    net, rp, tgt, w, d = _net(cfg)
+    for first, count in ((0, 3), (77, 20), (net.N - 5, 5)):
+        t2, w2, d2, ln = oracle.gen_rows_v(cfg, first, count)
+        assert np.array_equal(ln, np.diff(rp[first:first + count + 1]))
+        sl = slice(rp[first], rp[first + count])
+        assert np.array_equal(t2, tgt[sl]) and np.array_equal(d2, d[sl])
+        assert np.array_equal(w2.view(np.uint32), w[sl].view(np.uint32))
+
+
+def test_fixed_k_rule_takes_the_new_distributions_too():
+    """Gaussian efficacies and exponential delays are independent of the rule:
+    with the fixed out-degree rule every row still has K synapses."""
+    cfg = W.small(grid=3, M=50, K=40, seed=4)
+    cfg.update(weight_dist="gauss", w_exc_sd=0.05, w_inh_sd=0.2, delay_dist="exp", delay_tau_ms=5.0)
+    net, rp, tgt, w, d = _net(cfg)
+    assert np.array_equal(np.diff(rp), np.full(net.N, 40))
+    base = oracle.OracleNet(W.small(grid=3, M=50, K=40, seed=4)).csr()[0]
+    assert np.array_equal(tgt, base)  # targets do not depend on the efficacy/delay laws
+    tab, _ = oracle.weight_table(cfg, True)
+    src = np.repeat(np.arange(net.N), 40)
+    assert np.all(np.isin(w[(src % 50) < 40], tab))
