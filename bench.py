@@ -324,6 +324,7 @@ def run_gpu(args):
 
     batched = None if args.no_batched else run_batched(snn, args, stream)
     precision = None if args.no_precision else run_precision(snn, args, stream)
+    table_one = None if args.no_table_one else run_table_one(snn, args, stream)
     served = None if args.no_served else run_served(snn, args, stream)
 
     cpu = None
@@ -369,6 +370,7 @@ def run_gpu(args):
         "batched": batched,
         "served": served,
         "precision": precision,
+        "table_one": table_one,
         "gpu_launches": launches,
         "clocks": ck,
     }
@@ -513,6 +515,53 @@ def run_precision(snn, args, stream):
     return out
 
 
+def run_table_one(snn, args, stream):
+    """Table I's grids: the 24x24 network under the paper's per-pair law
+    (Gaussian at 7.5 Hz, exponential at 35 Hz, bf16) and the 48x48 / 96x96
+    Gaussian grids with the fixed out-degree rule (and 48x48 per-pair): build
+    time, synapses, device memory and persistent-schedule throughput."""
+    import time as _t
+
+    import torch
+    from paper_1803_08833_gb300 import workloads as W
+    cases = [
+        ("pairwise_24x24_gauss", W.pairwise(grid=24, seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 1000),
+        ("pairwise_24x24_exp_bf16", W.pairwise(grid=24, lateral="exp", seed=1, weight_dtype="bf16",
+                                               imposed_rate_hz=W.PAPER_RATE_EXP_HZ), 300),
+        ("pairwise_48x48_gauss", W.pairwise(grid=48, seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 300),
+        ("fixed_48x48_gauss_k1125", W.gauss_48x48_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 300),
+        ("fixed_96x96_gauss_k1125", W.gauss_96x96_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 100),
+    ]
+    out = {}
+    for name, cfg, steps in cases:
+        steps = max(1, int(steps * args.table_one_scale))
+        torch.cuda.synchronize()
+        t0 = _t.perf_counter()
+        with snn.Network(cfg, raster_capacity=1 << 24, stream=stream) as net:
+            torch.cuda.synchronize()
+            build_ms = (_t.perf_counter() - t0) * 1e3
+            syn = int(net.row_lengths().astype("int64").sum())
+            net.set_schedule(2)
+            net.step(20)
+            s0 = net.stats()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            net.step(steps)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            s1 = net.stats()
+            ev = s1["rec_events"] - s0["rec_events"]
+            out[name] = {"neurons": net.N, "synapses": syn, "device_gb": round(net.device_bytes / 1e9, 2),
+                         "build_ms": round(build_ms, 1), "steps": steps, "us_per_step": ms * 1e3 / steps,
+                         "events_per_s": ev / (ms / 1e3),
+                         "rate_hz": (s1["n_spikes"] - s0["n_spikes"]) / (net.N * steps) * 1000.0}
+    out["workload"] = ("Table I grids (100 um spacing, 1250 neurons per module); per-pair law: 80 % local, "
+                       "A exp(-r^2/2 sigma^2) A=0.05 / A exp(-r/lambda) A=0.03 cut at 1/1000, inhibitory local only, "
+                       "Gaussian efficacies, exponential delays (mean 5 ms); imposed paper rates; persistent schedule")
+    return out
+
+
 def run_served(snn, args, stream):
     """Poisson stream of requests into the continuous-batching server."""
     import time as _t
@@ -590,6 +639,8 @@ def main(argv=None):
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-table-one", action="store_true")
+    ap.add_argument("--table-one-scale", type=float, default=1.0, help="scale of the Table I legs' step counts")
     ap.add_argument("--precision-steps", type=int, default=10000)
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2000)

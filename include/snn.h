@@ -58,6 +58,9 @@ typedef enum snn_status {
 enum { SNN_KERNEL_GAUSS = 0, SNN_KERNEL_EXP = 1 };
 enum { SNN_WEIGHT_F32 = 0, SNN_WEIGHT_BF16 = 1 };
 enum { SNN_LAYOUT_DRAW = 0, SNN_LAYOUT_GROUPED = 1 };
+enum { SNN_RULE_FIXED_K = 0, SNN_RULE_PAIRWISE = 1 };
+enum { SNN_WDIST_UNIFORM = 0, SNN_WDIST_GAUSS = 1 };
+enum { SNN_DDIST_UNIFORM = 0, SNN_DDIST_EXP = 1 };
 
 /* Network description; plain data, copied by snn_build_network. */
 typedef struct snn_config {
@@ -89,12 +92,40 @@ typedef struct snn_config {
                                     SNN_LAYOUT_GROUPED: the same synapses stably grouped by target
                                     module (stencil order), plus a per-row segment index; needed
                                     by schedule 3 */
+    /* Connection law (Sec. III-B).  SNN_RULE_FIXED_K: every neuron projects K
+     * synapses whose target module is drawn from the normalised kernel
+     * (fields above).  SNN_RULE_PAIRWISE: every ordered pair of distinct
+     * neurons in one module is connected with probability p_local, a pair at
+     * module distance r > 0 with probability A_remote f(r) (f the Gaussian or
+     * exponential shape of `kernel`, unnormalised), modules where that falls
+     * to p_min or below get none; one draw per pair (no autapses, no
+     * multapses); K is ignored and the out-degree varies per neuron; rows are
+     * ordered by target module (stencil order) and by neuron.  Needs
+     * table_layout = SNN_LAYOUT_DRAW and neurons_per_module <= 65535. */
+    int32_t conn_rule;
+    float p_local;               /* pairwise: local connection probability (the paper: 0.8) */
+    double A_remote;             /* pairwise: remote amplitude A (the paper: 0.05 Gaussian, 0.03 exponential) */
+    double p_min;                /* pairwise: stencil cut (the paper: 1/1000) */
+    int32_t inh_local_only;      /* pairwise: inhibitory neurons project inside their module only */
+    /* Efficacies (Sec. II-B), either rule.  SNN_WDIST_UNIFORM: excitatory
+     * w_exc_lo + (w_exc_hi - w_exc_lo) U[0,1), inhibitory w_inh.
+     * SNN_WDIST_GAUSS: excitatory N((w_exc_lo + w_exc_hi) / 2, w_exc_sd^2),
+     * inhibitory N(w_inh, w_inh_sd^2), each the (k + 1/2)/4096 quantile for a
+     * uniform k in [0, 4096), clipped to the sign of the population. */
+    int32_t weight_dist;
+    float w_exc_sd, w_inh_sd;
+    /* Excitatory delays, either rule.  SNN_DDIST_UNIFORM: uniform integer in
+     * [d_exc_lo, d_exc_hi].  SNN_DDIST_EXP: an exponential of mean
+     * delay_tau_ms floored onto whole steps from d_exc_lo and truncated at
+     * d_exc_hi (renormalised).  Inhibitory delays stay d_inh. */
+    int32_t delay_dist;
+    float delay_tau_ms;
 } snn_config;
 
 typedef struct snn_stats {
     uint64_t steps;          /* time steps simulated so far */
     uint64_t n_spikes;       /* spikes emitted (including any beyond raster capacity) */
-    uint64_t rec_events;     /* recurrent synaptic events delivered: sum over spikes of K */
+    uint64_t rec_events;     /* recurrent synaptic events delivered: sum over spikes of the out-degree */
     uint64_t ext_events;     /* external Poisson events received */
     uint64_t raster_count;   /* spikes recorded since the last snn_clear_raster */
     uint64_t raster_capacity;
@@ -152,8 +183,10 @@ SNN_API snn_status snn_restore(snn_net* net, const void* host_buf, size_t n, voi
 
 /* Copies of device data for inspection (all synchronise `stream`; any
  * pointer may be NULL to skip that array):
- *   snn_get_table:  synapse table, row i of neuron i holds entries
- *                   [i*K, (i+1)*K) (padding removed); weights as float.
+ *   snn_get_table:  synapse table, rows of neurons 0..N-1 back to back
+ *                   (padding removed; row i has K entries under the fixed
+ *                   out-degree rule, snn_get_row_lengths entries under the
+ *                   pairwise rule); weights as float.
  *   snn_get_cdf:    per source module m, entries [m*max_offsets, ...):
  *                   thresholds (uint32; target j = #{thresholds <= u}) and
  *                   target modules, plus counts[m]; *max_offsets set.
@@ -168,8 +201,8 @@ SNN_API snn_status snn_get_table(snn_net* net, uint32_t* tgt, float* w, uint8_t*
  * module's stencil count on equal K.  With seg == NULL only *stride is set. */
 SNN_API snn_status snn_get_segments(snn_net* net, uint32_t first, uint32_t count, uint16_t* seg, uint32_t* stride,
                                     void* stream);
-/* Rows [first, first + count) of the synapse table, laid out as snn_get_table
- * lays out the whole table.  Errors: SNN_EINVAL if the rows are out of range. */
+/* Rows [first, first + count) of the synapse table, back to back as in
+ * snn_get_table.  Errors: SNN_EINVAL if the rows are out of range. */
 SNN_API snn_status snn_get_rows(snn_net* net, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
                                 uint8_t* d, void* stream);
 SNN_API snn_status snn_get_cdf(snn_net* net, uint32_t* thresh, uint32_t* tgt_module, uint32_t* counts,
@@ -179,7 +212,23 @@ SNN_API snn_status snn_get_state(snn_net* net, float* V, float* c, uint8_t* ref,
 SNN_API snn_status snn_set_state(snn_net* net, const float* V, const float* c, const uint8_t* ref,
                          void* stream);
 
-/* Sizes of the network: N neurons, K, D ring rows, bytes of device memory. */
+/* Out-degree of rows [first, first + count) (K each under the fixed rule).
+ * Errors: SNN_EINVAL if the rows are out of range. */
+SNN_API snn_status snn_get_row_lengths(snn_net* net, uint32_t first, uint32_t count, uint32_t* len, void* stream);
+
+/* The construction tables the library derives on the host in FP64 from a
+ * description, without building anything (any pointer may be NULL):
+ * Gaussian efficacy quantiles (2 x 4096 floats, excitatory then inhibitory;
+ * weight_dist = SNN_WDIST_GAUSS), exponential delay thresholds (*n_dthr
+ * entries, an excitatory delay is d_exc_lo + #{k : dthr[k] <= u}), and the
+ * pairwise stencil (*n_pair entries of dx, dy and floor(p 2^32), at most cap
+ * written).  No GPU work.  Errors: SNN_EINVAL (invalid description or cap). */
+SNN_API snn_status snn_construction_tables(const snn_config* cfg, float* wtab, uint64_t* dthr, uint32_t* n_dthr,
+                                           int32_t* pair_dx, int32_t* pair_dy, uint64_t* pair_thr, uint32_t cap,
+                                           uint32_t* n_pair);
+
+/* Sizes of the network: N neurons, K (the largest out-degree), D ring rows,
+ * bytes of device memory. */
 SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t* D, uint64_t* device_bytes);
 
 /* Execution schedule of snn_step.

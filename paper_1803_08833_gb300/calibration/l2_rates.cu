@@ -4,7 +4,10 @@
 // buffers of several sizes (the delay ring takes one such reduction per
 // synaptic event), (2) the same with the 32 lanes of a warp on consecutive
 // words, (3) a streaming 16-byte read of a 4 GB table (the synapse table
-// stream), (4) the stream with one random reduction per loaded word.
+// stream), (4) the stream with one random reduction per loaded word, (5)
+// reads of short contiguous segments at random places of a region of the
+// table (segment length x region size: the access pattern of a delivery
+// that reads a few dozen synapses per row).
 // Prints one JSON object.  Every address is inside its buffer.
 #include <cuda_runtime.h>
 
@@ -55,6 +58,29 @@ __global__ void k_stream_red(const uint4* tab, size_t n16, int* buf, uint32_t n)
         for (int q = 0; q < 4; ++q)
             asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(buf + t[q]), "r"(1) : "memory");
     }
+}
+
+// Each warp reads `segs` segments of L bytes (a multiple of 128) at random
+// 128-byte aligned offsets of the first `region` bytes, 8 segments in flight.
+__global__ void k_seg_read(const uint32_t* tab, size_t region, uint32_t L, uint32_t segs, uint32_t salt,
+                           uint32_t* sink) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t slots = (region - L) / 128;
+    uint32_t acc = 0;
+    for (uint32_t s0 = 0; s0 < segs; s0 += 8) {
+        uint32_t v[8][4];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const size_t base =
+                ((size_t)mix32(w * 7919u + (s0 + u) * 104729u + salt) * 2654435761ull % slots) * 32;  // words
+            for (uint32_t k = 0; k < 4; ++k) v[u][k] = 0;
+            for (uint32_t k = 0; k < L / 128 && k < 4; ++k) v[u][k] = __ldcs(tab + base + k * 32 + lane);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u][0] ^ v[u][1] ^ v[u][2] ^ v[u][3];
+    }
+    if (acc == 0x12345678u) sink[0] = acc;
 }
 
 __global__ void k_fill(uint4* tab, size_t n16) {
@@ -123,6 +149,26 @@ int main() {
     cudaEventElapsedTime(&ms, a, b);
     printf(", \"stream_plus_random_red\": {\"red_per_s\": %.4g, \"table_gb_per_s\": %.1f}", part * 4.0 / (ms * 1e-3),
            part * 16.0 / (ms * 1e-3) / 1e9);
+    // short segments at random places: 128 B and 512 B over 512 MB, 1 GB and 4 GB
+    printf(", \"segment_read_gb_per_s\": {");
+    const size_t regions[] = {(size_t)512 << 20, (size_t)1 << 30, tab_bytes};
+    const uint32_t lens[] = {128, 512};
+    const uint32_t segs = 64;
+    int first = 1;
+    for (uint32_t L : lens)
+        for (size_t R : regions) {
+            const int sgrid = sms * 8;
+            const double bytes = (double)sgrid * 8 * segs * L;  // 8 warps per block
+            k_seg_read<<<sgrid, 256>>>((const uint32_t*)tab, R, L, segs, 3, sink);
+            cudaEventRecord(a);
+            for (int it = 0; it < 3; ++it) k_seg_read<<<sgrid, 256>>>((const uint32_t*)tab, R, L, segs, 11 + it, sink);
+            cudaEventRecord(b);
+            cudaEventSynchronize(b);
+            cudaEventElapsedTime(&ms, a, b);
+            printf("%s\"%u B in %zu MB\": %.1f", first ? "" : ", ", L, R >> 20, 3.0 * bytes / (ms * 1e-3) / 1e9);
+            first = 0;
+        }
+    printf("}");
     const cudaError_t e = cudaGetLastError();
     printf(", \"status\": \"%s\"}\n", cudaGetErrorString(e));
     return e == cudaSuccess ? 0 : 1;

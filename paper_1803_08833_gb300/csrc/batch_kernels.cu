@@ -99,10 +99,11 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
                     const uint32_t slot = t % v.D;
                     const uint32_t qa = q0 - s_qoff[k], qb = qe - s_qoff[k];
                     uint32_t ext = 0;
+                    uint64_t rec = 0;
                     for (uint32_t qc = qa; qc < qb; qc += 32) {
                         const uint32_t q = qc + lane;
                         uint32_t spk = 0;
-                        if (q < qb) spk = update_quad(v, v.pois32, q << 2, t, slot, ext);
+                        if (q < qb) spk = update_quad(v, v.pois32, q << 2, t, slot, ext, rec);
                         const uint32_t cnt = __popc(spk);
                         uint32_t incl = cnt;
 #pragma unroll
@@ -120,6 +121,12 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
                     for (int o = 16; o > 0; o >>= 1) ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
                     if (lane == 0 && ext) atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->ext_events),
                                                     (unsigned long long)ext);
+                    if (v.row_len) {  // pairwise rule: recurrent events are the spiking rows' lengths
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) rec += __shfl_xor_sync(0xFFFFFFFFu, rec, o);
+                        if (lane == 0 && rec) atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->rec_events),
+                                                        (unsigned long long)rec);
+                    }
                 }
                 if (lane == 0) bm.wcnt[s_cbase[k] + (wg - bm.wlo[k])] = run;
                 q0 = qe;
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
             st->t = s_t0[k] + min(s_steps[k], done);
             st->raster_count = s_rc[k];
             st->n_spikes += s_spk[k];
-            st->rec_events += s_spk[k] * bm.views[k].K;
+            if (!bm.views[k].row_len) st->rec_events += s_spk[k] * bm.views[k].K;
             st->n_spk = 0;
         }
     }

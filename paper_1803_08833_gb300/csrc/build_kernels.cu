@@ -6,6 +6,10 @@
 //                  converted to uint32 thresholds.
 //   k_gen_synapses per (neuron, 4 synapses): Philox draws -> target module by
 //                  inverse CDF, target neuron, weight, delay; 16 B vector stores.
+//   k_pair_count / k_pair_rows / k_pair_fill
+//                  the pairwise law of Sec. III-B: per (neuron, stencil entry)
+//                  the connection draws of every candidate target, counted,
+//                  turned into row offsets, then written.
 //   k_init_state   V = V_th * U[0,1), c = 0, ref = 0.
 //
 // Floating point is written with explicit round-to-nearest intrinsics, so no
@@ -94,6 +98,25 @@ __device__ __forceinline__ uint32_t upper_index(const uint32_t* __restrict__ T, 
     return lo;
 }
 
+// Efficacy and delay of a synapse from words u2 and u3 of its Philox block
+// (Sec. II-B): uniform or Gaussian-quantile efficacy, uniform or truncated
+// exponential delay; inhibitory delays are constant.
+__device__ __forceinline__ void syn_attr(const BuildView& b, bool exc, uint32_t u2, uint32_t u3, float& w, uint32_t& d) {
+    if (exc) {
+        w = b.weight_dist ? __ldg(b.wtab + (u2 >> 20)) : __fadd_rn(b.w_lo, __fmul_rn(b.w_span, unit24(u2)));
+        if (b.delay_dist) {
+            uint32_t k = 0;
+            for (uint32_t j = 0; j < b.n_dthr; ++j) k += __ldg(b.dthr + j) <= (uint64_t)u3 ? 1u : 0u;
+            d = b.d_lo + k;
+        } else {
+            d = b.d_lo + __umulhi(u3, b.d_span);
+        }
+    } else {
+        w = b.weight_dist ? __ldg(b.wtab + WTAB + (u2 >> 20)) : b.w_inh;
+        d = b.d_inh;
+    }
+}
+
 template <bool BF16>
 __global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __restrict__ tgt,
                                                       void* __restrict__ wout, uint8_t* __restrict__ dout) {
@@ -120,13 +143,7 @@ __global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __r
             const U4 u = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
             const uint32_t j = upper_index(T, n, u.x);
             tg[q] = __ldg(TM + j) * b.M + __umulhi(u.y, b.M);
-            if (exc) {
-                w[q] = __fadd_rn(b.w_lo, __fmul_rn(b.w_span, unit24(u.z)));
-                d[q] = b.d_lo + __umulhi(u.w, b.d_span);
-            } else {
-                w[q] = b.w_inh;
-                d[q] = b.d_inh;
-            }
+            syn_attr(b, exc, u.z, u.w, w[q], d[q]);
         }
     }
     const size_t e = (size_t)i * b.Kpad + k0;
@@ -157,13 +174,7 @@ __device__ __forceinline__ Draw draw_synapse(const BuildView& b, uint32_t i, uin
     Draw r;
     r.j = upper_index(T, n, u.x);
     r.tgt = __ldg(TM + r.j) * b.M + __umulhi(u.y, b.M);
-    if (exc) {
-        r.w = __fadd_rn(b.w_lo, __fmul_rn(b.w_span, unit24(u.z)));
-        r.d = b.d_lo + __umulhi(u.w, b.d_span);
-    } else {
-        r.w = b.w_inh;
-        r.d = b.d_inh;
-    }
+    syn_attr(b, exc, u.z, u.w, r.w, r.d);
     return r;
 }
 
@@ -243,6 +254,102 @@ __global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __re
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pairwise law (Sec. III-B).  Stencil entry o of neuron i covers the target
+// module at (sx + dx_o, sy + dy_o); candidate j of that module is connected
+// when word j % 4 of Philox (i, o * ceil(M/4) + j / 4, CONN) is below the
+// entry's threshold (never j = i: no autapse).  Inhibitory neurons keep only
+// the local entry when inh_local_only is set.  The row lists the connections
+// in (o, j) order; the k-th takes its efficacy and delay from Philox
+// (i, k, GEN).
+
+// Candidates of (i, o) that connect; with `out`, writes them from row offset
+// `start` on.  Returns the count.
+template <bool WRITE, bool BF16>
+__device__ __forceinline__ uint32_t pair_entry(const BuildView& b, uint32_t i, uint32_t o, uint32_t start,
+                                               uint32_t* __restrict__ tgt, void* __restrict__ wout,
+                                               uint8_t* __restrict__ dout) {
+    const uint32_t s = i / b.M, a = i - s * b.M;
+    const bool exc = a < b.n_exc;
+    const int dx = __ldg(b.pair_dx + o), dy = __ldg(b.pair_dy + o);
+    const bool local = dx == 0 && dy == 0;
+    if (!exc && b.inh_local_only && !local) return 0;
+    const int tx = (int)(s % b.grid_w) + dx, ty = (int)(s / b.grid_w) + dy;
+    if (tx < 0 || ty < 0 || tx >= (int)b.grid_w || ty >= (int)b.grid_h) return 0;
+    const uint32_t base = ((uint32_t)ty * b.grid_w + (uint32_t)tx) * b.M;
+    const uint64_t thr = __ldg(b.pair_thr + o);
+    const uint32_t c4 = (b.M + 3u) >> 2;
+    uint32_t n = 0;
+    for (uint32_t g = 0; g < c4; ++g) {
+        const U4 u = philox4x32_10(i, o * c4 + g, TAG_CONN, 0u, b.key0, b.key1);
+        const uint32_t uw[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t j = (g << 2) + q;
+            if (j >= b.M || (local && j == a) || (uint64_t)uw[q] >= thr) continue;
+            if (WRITE) {
+                const uint32_t k = start + n;
+                const U4 v = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
+                float w;
+                uint32_t d;
+                syn_attr(b, exc, v.z, v.w, w, d);
+                const size_t e = (size_t)i * b.Kpad + k;
+                tgt[e] = base + j;
+                if (BF16)
+                    reinterpret_cast<__nv_bfloat16*>(wout)[e] = __float2bfloat16_rn(w);
+                else
+                    reinterpret_cast<float*>(wout)[e] = w;
+                dout[e] = (uint8_t)d;
+            }
+            ++n;
+        }
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(256) k_pair_count(BuildView b) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)b.N * b.pair_n) return;
+    const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
+    const uint32_t n = pair_entry<false, false>(b, i, o, 0u, nullptr, nullptr, nullptr);
+    b.pair_cnt[gid] = (uint16_t)min(n, 0xFFFFu);
+}
+
+// One warp per row: exclusive prefix of the entry counts (in place: the row
+// offset of each entry), the row length and the longest row.
+__global__ void __launch_bounds__(256) k_pair_rows(BuildView b) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= b.N) return;  // warp-uniform
+    uint16_t* c = b.pair_cnt + (size_t)i * b.pair_n;
+    uint32_t run = 0;
+    for (uint32_t o0 = 0; o0 < b.pair_n; o0 += 32) {
+        const uint32_t o = o0 + lane;
+        const uint32_t x = o < b.pair_n ? c[o] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, k);
+            if (lane >= (uint32_t)k) incl += y;
+        }
+        if (o < b.pair_n) c[o] = (uint16_t)min(run + incl - x, 0xFFFFu);
+        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+    }
+    if (lane == 0) {
+        b.row_len[i] = run;
+        atomicMax(b.max_len, run);
+    }
+}
+
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __restrict__ tgt, void* __restrict__ wout,
+                                                   uint8_t* __restrict__ dout) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)b.N * b.pair_n) return;
+    const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
+    pair_entry<true, BF16>(b, i, o, b.pair_cnt[gid], tgt, wout, dout);
+}
+
 __global__ void k_init_state(BuildView b, float* __restrict__ V, float* __restrict__ c,
                              uint8_t* __restrict__ ref) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -289,6 +396,34 @@ cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8
         k_gen_grouped<true><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
     else
         k_gen_grouped<false><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+static unsigned pair_blocks(const BuildView& b) {
+    return (unsigned)(((uint64_t)b.N * b.pair_n + 255) / 256);
+}
+
+cudaError_t launch_pair_count(const BuildView& b, cudaStream_t s) {
+    if (b.N == 0 || b.pair_n == 0) return cudaSuccess;
+    k_pair_count<<<pair_blocks(b), 256, 0, s>>>(b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s) {
+    if (b.N == 0) return cudaSuccess;
+    k_pair_rows<<<(b.N + 7) / 8, 256, 0, s>>>(b);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_fill(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s) {
+    if (b.N == 0 || b.pair_n == 0) return cudaSuccess;
+    if (b.w_bf16)
+        k_pair_fill<true><<<pair_blocks(b), 256, 0, s>>>(b, tgt, w, d);
+    else
+        k_pair_fill<false><<<pair_blocks(b), 256, 0, s>>>(b, tgt, w, d);
     count_launch(1);
     return cudaGetLastError();
 }

@@ -82,11 +82,12 @@ __device__ __forceinline__ QuadIn load_quad(const NetView& v, uint32_t base, uin
 }
 
 // Integrates the loaded quad for step t, stores the new state, clears the ring
-// slot.  Returns a 4-bit spike mask; adds the external events to `ext`.  The
+// slot.  Returns a 4-bit spike mask; adds the external events to `ext` and,
+// under the pairwise rule, the spiking rows' lengths to `rec`.  The
 // four Philox draws are computed first, unconditionally (neurons past N are
 // padding and are not updated), so their dependency chains interleave.
 __device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
-                                                 uint32_t slot, const QuadIn& in, uint32_t& ext) {
+                                                 uint32_t slot, const QuadIn& in, uint32_t& ext, uint64_t& rec) {
     U4 u[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = philox4x32_10(base + q, t, TAG_DRIVE, 0u, v.key0, v.key1);
@@ -120,12 +121,17 @@ __device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_
     *reinterpret_cast<float4*>(v.V + base) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
     *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
     *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
+    if (v.row_len != nullptr && spk != 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (spk & (1u << q)) rec += __ldg(v.row_len + base + q);
+    }
     return spk;
 }
 
 __device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
-                                                uint32_t slot, uint32_t& ext) {
-    return compute_quad(v, s_pois, base, t, slot, load_quad(v, base, slot), ext);
+                                                uint32_t slot, uint32_t& ext, uint64_t& rec) {
+    return compute_quad(v, s_pois, base, t, slot, load_quad(v, base, slot), ext, rec);
 }
 
 // ---------------------------------------------------------------------------
@@ -189,9 +195,11 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
             const uint32_t jj = (uint32_t)(task / chunks);
             const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
             const uint32_t k0 = (ch << 7) + (lane << 2);
-            if (k0 < v.K) {
-                nv[u] = min(4u, v.K - k0);
-                const size_t e = (size_t)ids[jj - j0] * v.Kpad + k0;
+            const uint32_t id = ids[jj - j0];
+            const uint32_t L = v.row_len ? __ldg(v.row_len + id) : v.K;  // row length
+            if (k0 < L) {
+                nv[u] = min(4u, L - k0);
+                const size_t e = (size_t)id * v.Kpad + k0;
                 tg[u] = ld_u4(v.tgt + e, pol);
                 if (BF16) {
                     const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);

@@ -67,6 +67,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint64_t rc = s_rc0;
     uint64_t spikes = 0;
     uint32_t ext = 0;
+    uint64_t rec = 0;  // pairwise rule: row lengths of this thread's spikes
     uint32_t done = 0;
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
     if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
@@ -82,7 +83,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             const QuadIn cur = nxt;
             if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext);
+            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext, rec);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -157,19 +158,30 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     // ---- epilogue: counters of the launch
     uint32_t e = ext;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
-    if (lane == 0) s_ext[warp] = e;
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+        rec += __shfl_xor_sync(0xFFFFFFFFu, rec, o);
+    }
+    __shared__ unsigned long long s_rec[PERSIST_WARPS];
+    if (lane == 0) {
+        s_ext[warp] = e;
+        s_rec[warp] = rec;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long be = 0;
-        for (int w = 0; w < PERSIST_WARPS; ++w) be += s_ext[w];
+        unsigned long long be = 0, br = 0;
+        for (int w = 0; w < PERSIST_WARPS; ++w) {
+            be += s_ext[w];
+            br += s_rec[w];
+        }
         atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->ext_events), be);
+        if (v.row_len && br) atomicAdd(reinterpret_cast<unsigned long long*>(&v.st->rec_events), br);
         if (bid == 0 && done == n_steps) {
             DevState* st = v.st;
             st->t = t0 + n_steps;
             st->raster_count = rc;
             st->n_spikes += spikes;
-            st->rec_events += spikes * v.K;
+            if (!v.row_len) st->rec_events += spikes * v.K;
             st->n_spk = 0;
             st->phase_ns[0] += ph_n;
             st->phase_ns[1] += ph_d;

@@ -29,10 +29,6 @@ constexpr int TILE_MIN_BLOCKS = 2;
 constexpr uint32_t PAIR_CAP = 512;  // (spike, segment) pairs staged per batch
 constexpr int EV_UNROLL = 16;       // events in flight per lane
 
-#ifndef SNN_TILE_FLUSH
-#define SNN_TILE_FLUSH 0  // 0: bulk reductions by the TMA unit; 1: 16-byte read-modify-writes
-#endif
-
 __device__ __forceinline__ uint32_t ld_nc_u32(const uint32_t* p, uint64_t pol) {
     uint32_t r;
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
@@ -117,6 +113,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
     uint64_t rc = s_rc0;
     uint64_t spikes = 0;
     uint32_t ext = 0, done = 0;
+    uint64_t rec_unused = 0;  // the grouped layout exists for the fixed out-degree rule only
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0) stamp = global_ns();
 
@@ -134,7 +131,7 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
             const QuadIn cur = nxt;
             if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext);
+            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext, rec_unused);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -307,36 +304,6 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
             __syncthreads();
             const uint32_t a4 = (g + 3u) & ~3u, b4 = (g + M) & ~3u;  // aligned interior [a4, b4)
             const bool bulk = b4 > a4;
-#if SNN_TILE_FLUSH == 1
-            // interior by 16-byte read-modify-writes, four slot rows in flight
-            if (bulk) {
-                const uint32_t nv = (b4 - a4) >> 2;
-                for (uint32_t r0 = 0; r0 < Dm1; r0 += 4) {
-                    for (uint32_t x = threadIdx.x; x < nv; x += blockDim.x) {
-                        int4 add[4], old[4];
-                        int4* dst[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            dst[u] = nullptr;
-                            if (r0 + u < Dm1) {
-                                uint32_t sl = slot + r0 + u + 1;
-                                if (sl >= v.D) sl -= v.D;
-                                dst[u] = reinterpret_cast<int4*>(v.ring + (size_t)sl * v.Npad + a4) + x;
-                                add[u] = reinterpret_cast<const int4*>(tile + (size_t)(r0 + u) * RS + (a4 - g4))[x];
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (dst[u]) old[u] = __ldcg(dst[u]);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u)
-                            if (dst[u])
-                                __stcg(dst[u], make_int4(old[u].x + add[u].x, old[u].y + add[u].y, old[u].z + add[u].z,
-                                                         old[u].w + add[u].w));
-                    }
-                }
-            }
-#else
             if (threadIdx.x == 0 && bulk) {
                 for (uint32_t r = 0; r < Dm1; ++r) {
                     uint32_t sl = slot + r + 1;
@@ -351,7 +318,6 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
                 }
                 bulk_commit();
             }
-#endif
             // the cells outside the aligned interior
             const uint32_t ne = bulk ? (a4 - g) + (g + M - b4) : M;
             for (uint32_t x = threadIdx.x; x < Dm1 * ne; x += blockDim.x) {

@@ -132,7 +132,24 @@ snn_status validate(const snn_config* c) {
     if (N > (uint64_t)MAX_NEURON_BLOCKS * NEURONS_PER_BLOCK)
         return fail(SNN_EINVAL, "too many neurons (%llu > %u)", (unsigned long long)N,
                     MAX_NEURON_BLOCKS * NEURONS_PER_BLOCK);
-    if (c->K > 16384) return fail(SNN_EINVAL, "K must be <= 16384");
+    if (c->conn_rule != SNN_RULE_FIXED_K && c->conn_rule != SNN_RULE_PAIRWISE)
+        return fail(SNN_EINVAL, "conn_rule must be SNN_RULE_FIXED_K or SNN_RULE_PAIRWISE");
+    if (c->conn_rule == SNN_RULE_FIXED_K && c->K > 16384) return fail(SNN_EINVAL, "K must be <= 16384");
+    if (c->conn_rule == SNN_RULE_PAIRWISE) {
+        if (!(c->p_local >= 0.0f && c->p_local <= 1.0f) || !(c->A_remote >= 0.0 && c->A_remote <= 1.0) ||
+            !(c->p_min > 0.0 && c->p_min < 1.0))
+            return fail(SNN_EINVAL, "pairwise rule: need 0 <= p_local <= 1, 0 <= A_remote <= 1, 0 < p_min < 1");
+        if (c->neurons_per_module > MAX_ROW)
+            return fail(SNN_EINVAL, "pairwise rule: neurons_per_module must be <= %u", MAX_ROW);
+        if (c->table_layout != SNN_LAYOUT_DRAW)
+            return fail(SNN_EINVAL, "pairwise rule: rows come in stencil order; table_layout must be SNN_LAYOUT_DRAW");
+    }
+    if ((c->weight_dist != SNN_WDIST_UNIFORM && c->weight_dist != SNN_WDIST_GAUSS) || !(c->w_exc_sd >= 0.0f) ||
+        !(c->w_inh_sd >= 0.0f) || !std::isfinite(c->w_exc_sd) || !std::isfinite(c->w_inh_sd))
+        return fail(SNN_EINVAL, "weight_dist must be SNN_WDIST_UNIFORM or SNN_WDIST_GAUSS with finite sd >= 0");
+    if ((c->delay_dist != SNN_DDIST_UNIFORM && c->delay_dist != SNN_DDIST_EXP) ||
+        (c->delay_dist == SNN_DDIST_EXP && !(c->delay_tau_ms > 0.0f && std::isfinite(c->delay_tau_ms))))
+        return fail(SNN_EINVAL, "delay_dist must be SNN_DDIST_UNIFORM, or SNN_DDIST_EXP with delay_tau_ms > 0");
     if (!(c->exc_fraction >= 0.0f && c->exc_fraction <= 1.0f))
         return fail(SNN_EINVAL, "exc_fraction must be in [0, 1]");
     if (!(c->spacing_um > 0.0f)) return fail(SNN_EINVAL, "spacing_um must be positive");
@@ -162,7 +179,10 @@ snn_status validate(const snn_config* c) {
         !std::isfinite(c->V_th_mV) || !std::isfinite(c->V_reset_mV) || !std::isfinite(c->E_mV) ||
         !std::isfinite(c->J_ext_mV) || !std::isfinite(c->g_c_mV) || !std::isfinite(c->alpha_c))
         return fail(SNN_EINVAL, "non-finite parameter");
-    const float wmax = std::fmax(std::fabs(c->w_exc_lo), std::fmax(std::fabs(c->w_exc_hi), std::fabs(c->w_inh)));
+    float wmax = std::fmax(std::fabs(c->w_exc_lo), std::fmax(std::fabs(c->w_exc_hi), std::fabs(c->w_inh)));
+    if (c->weight_dist == SNN_WDIST_GAUSS)  // the table's extreme quantiles lie within 4 sd of the mean
+        wmax = std::fmax(std::fabs(0.5f * (c->w_exc_lo + c->w_exc_hi)) + 4.0f * c->w_exc_sd,
+                         std::fabs(c->w_inh) + 4.0f * c->w_inh_sd);
     if (std::ldexp((double)wmax, (int)c->fx_shift) > 1.0e9 ||
         std::ldexp((double)std::fabs(c->J_ext_mV), (int)c->fx_shift) > 1.0e8)
         return fail(SNN_EINVAL, "weights too large for the fixed-point scale");
@@ -265,6 +285,119 @@ std::vector<int16_t> disc_offsets(const snn_config& c, uint32_t* R2_out) {
     return off;
 }
 
+// Unnormalised lateral shape f at squared grid distance d2 (the same
+// expression order as the device kernel of the target-module tables).
+double lateral_shape(const snn_config& c, uint32_t d2) {
+    const double sp = (double)c.spacing_um;
+    if (c.kernel == SNN_KERNEL_GAUSS) {
+        const double num = (double)d2 * sp * sp;
+        const double den = 2.0 * c.sigma_um * c.sigma_um;
+        return std::exp(-(num / den));
+    }
+    const double r = sp * std::sqrt((double)d2);
+    return std::exp(-(r / c.lambda_um));
+}
+
+// Standard normal quantile: the rational approximation of P. J. Acklam (2003)
+// refined by two Halley steps on the CDF 0.5 erfc(-x / sqrt 2).
+double normal_quantile(double p) {
+    static const double a[6] = {-3.969683028665376e+01, 2.209460984245205e+02, -2.759285104469687e+02,
+                                1.383577518672690e+02,  -3.066479806614716e+01, 2.506628277459239e+00};
+    static const double b[5] = {-5.447609879822406e+01, 1.615858368580409e+02, -1.556989798598866e+02,
+                                6.680131188771972e+01,  -1.328068155288572e+01};
+    static const double c[6] = {-7.784894002430293e-03, -3.223964580411365e-01, -2.400758277161838e+00,
+                                -2.549732539343734e+00, 4.374664141464968e+00,  2.938163982698783e+00};
+    static const double d[4] = {7.784695709041462e-03, 3.224671290700398e-01, 2.445134137142996e+00,
+                                3.754408661907416e+00};
+    const double plow = 0.02425;
+    double x;
+    if (p < plow) {
+        const double q = std::sqrt(-2.0 * std::log(p));
+        x = (((((c[0] * q + c[1]) * q + c[2]) * q + c[3]) * q + c[4]) * q + c[5]) /
+            ((((d[0] * q + d[1]) * q + d[2]) * q + d[3]) * q + 1.0);
+    } else if (p > 1.0 - plow) {
+        const double q = std::sqrt(-2.0 * std::log(1.0 - p));
+        x = -(((((c[0] * q + c[1]) * q + c[2]) * q + c[3]) * q + c[4]) * q + c[5]) /
+            ((((d[0] * q + d[1]) * q + d[2]) * q + d[3]) * q + 1.0);
+    } else {
+        const double q = p - 0.5, r = q * q;
+        x = (((((a[0] * r + a[1]) * r + a[2]) * r + a[3]) * r + a[4]) * r + a[5]) * q /
+            (((((b[0] * r + b[1]) * r + b[2]) * r + b[3]) * r + b[4]) * r + 1.0);
+    }
+    for (int it = 0; it < 2; ++it) {
+        const double e = 0.5 * std::erfc(-x / std::sqrt(2.0)) - p;
+        const double u = e * std::sqrt(2.0 * 3.14159265358979323846) * std::exp(0.5 * x * x);
+        x = x - u / (1.0 + 0.5 * x * u);
+    }
+    return x;
+}
+
+// Construction tables derived on the host in FP64.
+struct HostTables {
+    std::vector<int32_t> pdx, pdy;  // pairwise stencil, (dy, dx) order
+    std::vector<uint64_t> pthr;     // floor(p 2^32), 2^32 = always
+    std::vector<float> wtab;        // 2 x WTAB Gaussian efficacy quantiles (excitatory, inhibitory)
+    std::vector<uint64_t> dthr;     // exponential delay thresholds
+};
+
+void host_tables(const snn_config& c, HostTables* t) {
+    if (c.conn_rule == SNN_RULE_PAIRWISE) {
+        // stencil radius: grow while the pair probability on an axis exceeds p_min
+        uint32_t R = 0;
+        while (R < 4096 && c.A_remote * lateral_shape(c, (R + 1) * (R + 1)) > c.p_min) ++R;
+        for (int y = -(int)R; y <= (int)R; ++y)
+            for (int x = -(int)R; x <= (int)R; ++x) {
+                double p;
+                if (x == 0 && y == 0) {
+                    p = (double)c.p_local;
+                } else {
+                    p = c.A_remote * lateral_shape(c, (uint32_t)(x * x + y * y));
+                    if (!(p > c.p_min)) continue;
+                }
+                t->pdx.push_back(x);
+                t->pdy.push_back(y);
+                t->pthr.push_back(p >= 1.0 ? 4294967296ull : (uint64_t)std::floor(p * 4294967296.0));
+            }
+    }
+    if (c.weight_dist == SNN_WDIST_GAUSS) {
+        t->wtab.resize(2 * WTAB);
+        for (int pop = 0; pop < 2; ++pop) {
+            const double mean = pop == 0 ? 0.5 * ((double)c.w_exc_lo + (double)c.w_exc_hi) : (double)c.w_inh;
+            const double sd = pop == 0 ? (double)c.w_exc_sd : (double)c.w_inh_sd;
+            for (uint32_t k = 0; k < WTAB; ++k) {
+                double w = mean + sd * normal_quantile(((double)k + 0.5) / (double)WTAB);
+                if (pop == 0 && w < 0.0) w = 0.0;  // efficacies keep the sign of their population
+                if (pop == 1 && w > 0.0) w = 0.0;
+                t->wtab[pop * WTAB + k] = (float)w;
+            }
+        }
+    }
+    if (c.delay_dist == SNN_DDIST_EXP) {
+        // P(delay <= d_lo + k) = (1 - e^{-(k+1)/tau}) / (1 - e^{-span/tau}), tau in steps
+        const uint32_t span = c.d_exc_hi - c.d_exc_lo + 1u;
+        const double tau = (double)c.delay_tau_ms / (double)c.dt_ms;
+        const double Z = 1.0 - std::exp(-(double)span / tau);
+        for (uint32_t k = 0; k + 1 < span; ++k) {
+            const double F = (1.0 - std::exp(-(double)(k + 1) / tau)) / Z;
+            const double x = std::floor(F * 4294967296.0);
+            t->dthr.push_back(x >= 4294967296.0 ? 4294967296ull : (uint64_t)x);
+        }
+    }
+}
+
+void free_block(snn_net* n, void* p, size_t bytes) {
+    for (size_t i = 0; i < n->blocks.size(); ++i)
+        if (n->blocks[i] == p) {
+            if (n->free_fn)
+                n->free_fn(p, n->alloc_ctx);
+            else if (!n->alloc_fn)
+                cudaFree(p);
+            n->blocks.erase(n->blocks.begin() + i);
+            n->device_bytes -= (bytes + 255) & ~(size_t)255;
+            return;
+        }
+}
+
 snn_status build_impl(snn_net* n, cudaStream_t s) {
     const snn_config& c = n->cfg;
     snn_status st = derive(n);
@@ -275,6 +408,92 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
 
     NetView& v = n->v;
     n->pgrid = persistent_grid(v.w_bf16 != 0);
+    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
+    HostTables ht;
+    host_tables(c, &ht);
+
+    BuildView b{};
+    b.grid_w = c.grid_w;
+    b.grid_h = c.grid_h;
+    b.n_modules = n->n_modules;
+    b.max_off = n->max_off;
+    b.M = n->M;
+    b.N = n->N;
+    b.Npad = n->Npad;
+    b.n_exc = n->n_exc;
+    b.d_lo = c.d_exc_lo;
+    b.d_span = c.d_exc_hi - c.d_exc_lo + 1u;
+    b.d_inh = c.d_inh;
+    b.key0 = v.key0;
+    b.key1 = v.key1;
+    b.kernel = c.kernel;
+    b.spacing = (double)c.spacing_um;
+    b.sigma = c.sigma_um;
+    b.lambda = c.lambda_um;
+    b.w_lo = c.w_exc_lo;
+    b.w_span = c.w_exc_hi - c.w_exc_lo;
+    b.w_inh = c.w_inh;
+    b.V_th = c.V_th_mV;
+    b.w_bf16 = v.w_bf16;
+    b.weight_dist = c.weight_dist;
+    b.delay_dist = c.delay_dist;
+    b.inh_local_only = c.inh_local_only;
+
+    // construction-only buffers, released at the end of the build
+    std::vector<std::pair<void*, size_t>> temps;
+    auto temp = [&](size_t bytes) -> void* {
+        void* p = dev_alloc(n, bytes);
+        if (p) temps.push_back({p, bytes});
+        return p;
+    };
+    if (!ht.wtab.empty()) {
+        float* wt = (float*)temp(ht.wtab.size() * 4);
+        if (!wt) return fail(SNN_ENOMEM, "device allocation of the efficacy table failed");
+        CUDA_TRY(cudaMemcpyAsync(wt, ht.wtab.data(), ht.wtab.size() * 4, cudaMemcpyHostToDevice, s));
+        b.wtab = wt;
+    }
+    if (!ht.dthr.empty()) {
+        uint64_t* dt = (uint64_t*)temp(ht.dthr.size() * 8);
+        if (!dt) return fail(SNN_ENOMEM, "device allocation of the delay table failed");
+        CUDA_TRY(cudaMemcpyAsync(dt, ht.dthr.data(), ht.dthr.size() * 8, cudaMemcpyHostToDevice, s));
+        b.dthr = dt;
+        b.n_dthr = (uint32_t)ht.dthr.size();
+    }
+    if (pairwise) {
+        // out-degrees first: the row stride of the table is the longest row
+        b.pair_n = (uint32_t)ht.pdx.size();
+        int32_t* pdx = (int32_t*)temp(ht.pdx.size() * 4);
+        int32_t* pdy = (int32_t*)temp(ht.pdy.size() * 4);
+        uint64_t* pthr = (uint64_t*)temp(ht.pthr.size() * 8);
+        uint16_t* pcnt = (uint16_t*)temp((size_t)n->N * b.pair_n * 2);
+        uint32_t* maxl = (uint32_t*)temp(4);
+        uint32_t* rlen = (uint32_t*)dev_alloc(n, (size_t)n->N * 4);
+        if (!pdx || !pdy || !pthr || !pcnt || !maxl || !rlen)
+            return fail(SNN_ENOMEM, "device allocation of the pairwise construction buffers failed");
+        CUDA_TRY(cudaMemcpyAsync(pdx, ht.pdx.data(), ht.pdx.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pdy, ht.pdy.data(), ht.pdy.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(pthr, ht.pthr.data(), ht.pthr.size() * 8, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemsetAsync(maxl, 0, 4, s));
+        b.pair_dx = pdx;
+        b.pair_dy = pdy;
+        b.pair_thr = pthr;
+        b.pair_cnt = pcnt;
+        b.row_len = rlen;
+        b.max_len = maxl;
+        CUDA_TRY(launch_pair_count(b, s));
+        CUDA_TRY(launch_pair_rows(b, s));
+        uint32_t longest = 0;
+        CUDA_TRY(cudaMemcpyAsync(&longest, maxl, 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (longest > MAX_ROW) return fail(SNN_EINVAL, "pairwise rule: a row of %u synapses exceeds %u", longest, MAX_ROW);
+        n->K = longest;
+        n->Kpad = (longest + K_ALIGN - 1) / K_ALIGN * K_ALIGN;
+        v.K = n->K;
+        v.Kpad = n->Kpad;
+        v.row_len = rlen;
+    }
+    b.K = n->K;
+    b.Kpad = n->Kpad;
     const size_t nsyn = (size_t)n->N * n->Kpad;
     const size_t wbytes = v.w_bf16 ? 2 : 4;
     struct Req {
@@ -292,6 +511,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         {(void**)&v.blk_cnt, (size_t)n->nb * 4},
         {(void**)&v.blk_off, (size_t)(n->nb + 1) * 4},
         {(void**)&v.blk_ext, (size_t)n->nb * 8},
+        {(void**)&v.blk_rec, (size_t)n->nb * 8},
         {(void**)&v.raster_t, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.raster_id, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.st, sizeof(DevState)},
@@ -341,40 +561,14 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         v.in_j = in_j;
         v.in_cnt = in_cnt;
     }
-    // construction-only buffers (released at the end of the build)
     const size_t scratch_bytes = (size_t)n->n_modules * n->max_off * sizeof(double);
     const size_t off_bytes = off.size() * sizeof(int16_t);
-    void* scratch = dev_alloc(n, scratch_bytes);
-    void* doff = dev_alloc(n, off_bytes);
+    void* scratch = temp(scratch_bytes);
+    void* doff = temp(off_bytes);
     if (!scratch || !doff) return fail(SNN_ENOMEM, "device allocation of construction scratch failed");
 
     CUDA_TRY(cudaMemcpyAsync(doff, off.data(), off_bytes, cudaMemcpyHostToDevice, s));
 
-    BuildView b{};
-    b.grid_w = c.grid_w;
-    b.grid_h = c.grid_h;
-    b.n_modules = n->n_modules;
-    b.max_off = n->max_off;
-    b.M = n->M;
-    b.N = n->N;
-    b.Npad = n->Npad;
-    b.K = n->K;
-    b.Kpad = n->Kpad;
-    b.n_exc = n->n_exc;
-    b.d_lo = c.d_exc_lo;
-    b.d_span = c.d_exc_hi - c.d_exc_lo + 1u;
-    b.d_inh = c.d_inh;
-    b.key0 = v.key0;
-    b.key1 = v.key1;
-    b.kernel = c.kernel;
-    b.spacing = (double)c.spacing_um;
-    b.sigma = c.sigma_um;
-    b.lambda = c.lambda_um;
-    b.w_lo = c.w_exc_lo;
-    b.w_span = c.w_exc_hi - c.w_exc_lo;
-    b.w_inh = c.w_inh;
-    b.V_th = c.V_th_mV;
-    b.w_bf16 = v.w_bf16;
     b.offsets = (const int16_t*)doff;
     b.scratch = (double*)scratch;
     b.cdf_T = n->cdf_T;
@@ -383,30 +577,25 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     b.segidx = segidx;
 
     CUDA_TRY(launch_build_cdf(b, s));
-    if (grouped)
+    if (pairwise) {
+        CUDA_TRY(cudaMemsetAsync(v.tgt, 0, nsyn * 4, s));  // padding past each row's end
+        CUDA_TRY(cudaMemsetAsync(v.w, 0, nsyn * wbytes, s));
+        CUDA_TRY(cudaMemsetAsync(v.d, 0, nsyn, s));
+        CUDA_TRY(launch_pair_fill(b, v.tgt, v.w, v.d, s));
+    } else if (grouped) {
         CUDA_TRY(launch_gen_grouped(b, v.tgt, v.w, v.d, s));
-    else
+    } else {
         CUDA_TRY(launch_gen_synapses(b, v.tgt, v.w, v.d, s));
+    }
     CUDA_TRY(launch_init_state(b, v.V, v.c, v.ref, s));
     CUDA_TRY(cudaMemsetAsync(v.ring, 0, (size_t)n->D * n->Npad * 4, s));
     CUDA_TRY(cudaMemsetAsync(v.seg, 0, (size_t)n->Npad * 4, s));
     CUDA_TRY(cudaMemsetAsync(v.st, 0, sizeof(DevState), s));
     CUDA_TRY(cudaMemsetAsync(v.blk_off, 0, (size_t)(n->nb + 1) * 4, s));
     CUDA_TRY(prepare_deliver(n->nb));
-    // the scratch and offset list must outlive the kernels that read them
+    // the construction buffers must outlive the kernels that read them
     CUDA_TRY(cudaStreamSynchronize(s));
-    for (void* p : {scratch, doff}) {
-        for (size_t i = 0; i < n->blocks.size(); ++i)
-            if (n->blocks[i] == p) {
-                if (n->free_fn)
-                    n->free_fn(p, n->alloc_ctx);
-                else if (!n->alloc_fn)
-                    cudaFree(p);
-                n->blocks.erase(n->blocks.begin() + i);
-                break;
-            }
-    }
-    n->device_bytes -= ((scratch_bytes + 255) & ~(size_t)255) + ((off_bytes + 255) & ~(size_t)255);
+    for (auto& tb : temps) free_block(n, tb.first, tb.second);
     n->grid = deliver_default_grid(n->schedule, n->block, n->nb, v.w_bf16 != 0);
     n->tgrid = grouped ? tiled_grid(v) : 0;
     return SNN_OK;
@@ -613,6 +802,38 @@ snn_status snn_get_rows(snn_net* n, uint32_t first, uint32_t count, uint32_t* tg
     cudaStream_t s = (cudaStream_t)stream;
     const size_t rows = count, K = n->K, Kp = n->Kpad;
     const size_t e0 = (size_t)first * Kp;
+    if (n->v.row_len) {
+        // rows of different lengths: copy the padded rows, keep each row's first len entries
+        std::vector<uint32_t> len(rows);
+        if (rows) CUDA_TRY(cudaMemcpyAsync(len.data(), n->v.row_len + first, rows * 4, cudaMemcpyDeviceToHost, s));
+        std::vector<uint32_t> t(tgt ? rows * Kp : 0);
+        std::vector<uint8_t> dd(d ? rows * Kp : 0);
+        const bool bf = n->v.w_bf16 != 0;
+        std::vector<uint32_t> wr(w && !bf ? rows * Kp : 0);  // f32 bits
+        std::vector<uint16_t> wh(w && bf ? rows * Kp : 0);   // bf16 bits
+        if (tgt && rows) CUDA_TRY(cudaMemcpyAsync(t.data(), n->v.tgt + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
+        if (d && rows) CUDA_TRY(cudaMemcpyAsync(dd.data(), n->v.d + e0, rows * Kp, cudaMemcpyDeviceToHost, s));
+        if (w && rows) {
+            if (bf)
+                CUDA_TRY(cudaMemcpyAsync(wh.data(), (const uint16_t*)n->v.w + e0, rows * Kp * 2, cudaMemcpyDeviceToHost, s));
+            else
+                CUDA_TRY(cudaMemcpyAsync(wr.data(), (const float*)n->v.w + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
+        }
+        CUDA_TRY(cudaStreamSynchronize(s));
+        size_t o = 0;
+        for (size_t r = 0; r < rows; ++r) {
+            for (size_t k = 0; k < len[r]; ++k, ++o) {
+                const size_t e = r * Kp + k;
+                if (tgt) tgt[o] = t[e];
+                if (d) d[o] = dd[e];
+                if (w) {
+                    const uint32_t bits = bf ? (uint32_t)wh[e] << 16 : wr[e];
+                    std::memcpy(&w[o], &bits, 4);
+                }
+            }
+        }
+        return SNN_OK;
+    }
     if (tgt && K && rows)
         CUDA_TRY(cudaMemcpy2DAsync(tgt, K * 4, n->v.tgt + e0, Kp * 4, K * 4, rows, cudaMemcpyDeviceToHost, s));
     if (d && K && rows) CUDA_TRY(cudaMemcpy2DAsync(d, K, n->v.d + e0, Kp, K, rows, cudaMemcpyDeviceToHost, s));
@@ -632,6 +853,41 @@ snn_status snn_get_rows(snn_net* n, uint32_t first, uint32_t count, uint32_t* tg
         }
     }
     CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_get_row_lengths(snn_net* n, uint32_t first, uint32_t count, uint32_t* len, void* stream) {
+    if (!n || !len) return fail(SNN_EINVAL, "net or len is NULL");
+    if ((uint64_t)first + count > n->N) return fail(SNN_EINVAL, "rows [%u, %u) out of range", first, first + count);
+    if (!n->v.row_len) {
+        for (uint32_t r = 0; r < count; ++r) len[r] = n->K;
+        return SNN_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count) CUDA_TRY(cudaMemcpyAsync(len, n->v.row_len + first, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_construction_tables(const snn_config* cfg, float* wtab, uint64_t* dthr, uint32_t* n_dthr,
+                                   int32_t* pair_dx, int32_t* pair_dy, uint64_t* pair_thr, uint32_t cap,
+                                   uint32_t* n_pair) {
+    snn_status st = validate(cfg);
+    if (st != SNN_OK) return st;
+    HostTables t;
+    host_tables(*cfg, &t);
+    if (wtab && !t.wtab.empty()) std::memcpy(wtab, t.wtab.data(), t.wtab.size() * 4);
+    if (n_dthr) *n_dthr = (uint32_t)t.dthr.size();
+    if (dthr && !t.dthr.empty()) std::memcpy(dthr, t.dthr.data(), t.dthr.size() * 8);
+    if (n_pair) *n_pair = (uint32_t)t.pdx.size();
+    if (pair_dx || pair_dy || pair_thr) {
+        if (t.pdx.size() > cap) return fail(SNN_EINVAL, "stencil of %zu entries exceeds cap %u", t.pdx.size(), cap);
+        for (size_t k = 0; k < t.pdx.size(); ++k) {
+            if (pair_dx) pair_dx[k] = t.pdx[k];
+            if (pair_dy) pair_dy[k] = t.pdy[k];
+            if (pair_thr) pair_thr[k] = t.pthr[k];
+        }
+    }
     return SNN_OK;
 }
 

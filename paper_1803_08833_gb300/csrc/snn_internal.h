@@ -10,6 +10,9 @@ namespace snn {
 constexpr uint32_t TAG_GEN = 0u;    // (neuron i, synapse k): target, weight, delay
 constexpr uint32_t TAG_DRIVE = 1u;  // (neuron i, step t): external Poisson count, forced spike
 constexpr uint32_t TAG_INIT = 2u;   // (neuron i, 0): initial membrane potential
+constexpr uint32_t TAG_CONN = 3u;   // (neuron i, 4-candidate group): pairwise connection draws
+constexpr uint32_t WTAB = 4096;     // Gaussian efficacy quantiles per population
+constexpr uint32_t MAX_ROW = 65535; // longest row of the pairwise rule
 
 constexpr int NEURON_THREADS = 256;
 constexpr int PERSIST_THREADS = 256;                 // threads per CTA of the persistent kernel
@@ -53,6 +56,7 @@ struct NetView {
     uint32_t* tgt;
     void* w;
     uint8_t* d;
+    const uint32_t* row_len;  // pairwise rule: synapses of each row (K = the longest); NULL: K each
     // neuron state (Npad entries) and delay ring (D rows of Npad)
     float* V;
     float* c;
@@ -63,6 +67,7 @@ struct NetView {
     uint32_t* blk_cnt;  // spikes per neuron block
     uint32_t* blk_off;  // exclusive prefix of blk_cnt, nb + 1 entries
     uint64_t* blk_ext;  // external events per neuron block
+    uint64_t* blk_rec;  // pairwise rule: recurrent events (row lengths of the spikes) per neuron block
     uint32_t* raster_t;
     uint32_t* raster_id;
     uint64_t raster_cap;
@@ -97,6 +102,20 @@ struct BuildView {
     uint32_t* cdf_mod;
     uint32_t* cdf_n;
     uint16_t* segidx;  // grouped layout: per neuron max_off + 1 segment starts
+    // efficacy and delay laws
+    int32_t weight_dist, delay_dist;
+    const float* wtab;        // 2 x WTAB Gaussian quantiles (excitatory, then inhibitory)
+    const uint64_t* dthr;     // exponential delays: excitatory delay = d_lo + #{k : dthr[k] <= u}
+    uint32_t n_dthr;
+    // pairwise rule
+    uint32_t pair_n;          // stencil entries
+    int32_t inh_local_only;
+    const int32_t* pair_dx;   // pair_n offsets in (dy, dx) order
+    const int32_t* pair_dy;
+    const uint64_t* pair_thr; // floor(p 2^32) (2^32: always)
+    uint16_t* pair_cnt;       // N x pair_n: synapses per stencil entry, then their row offsets
+    uint32_t* row_len;        // N
+    uint32_t* max_len;        // 1: the longest row
 };
 
 // Launch wrappers (return the launch error).
@@ -104,6 +123,9 @@ cudaError_t launch_build_cdf(const BuildView& b, cudaStream_t s);
 cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d,
                                 cudaStream_t s);
 cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s);
+cudaError_t launch_pair_count(const BuildView& b, cudaStream_t s);
+cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s);
+cudaError_t launch_pair_fill(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s);
 cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* ref,
                               cudaStream_t s);
 cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);

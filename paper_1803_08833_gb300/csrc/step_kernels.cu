@@ -27,31 +27,35 @@ __device__ __forceinline__ void finish_step(const NetView& v, uint32_t t) {
     const uint32_t range = (((nb + W - 1) / W) + 31) & ~31u;
     const uint32_t b0 = warp * range, b1 = min(b0 + range, nb);
     __shared__ uint32_t s_wtot[W];
-    __shared__ unsigned long long s_wext[W];
+    __shared__ unsigned long long s_wext[W], s_wrec[W];
     uint32_t tot = 0;
-    unsigned long long ext = 0;
+    unsigned long long ext = 0, rec = 0;
 #pragma unroll 4
     for (uint32_t b = b0 + lane; b < b1; b += 32) {
         tot += __ldcg(v.blk_cnt + b);
         ext += __ldcg(reinterpret_cast<const unsigned long long*>(v.blk_ext) + b);
+        if (v.row_len) rec += __ldcg(reinterpret_cast<const unsigned long long*>(v.blk_rec) + b);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
         ext += __shfl_xor_sync(0xFFFFFFFFu, ext, o);
+        rec += __shfl_xor_sync(0xFFFFFFFFu, rec, o);
     }
     if (lane == 0) {
         s_wtot[warp] = tot;
         s_wext[warp] = ext;
+        s_wrec[warp] = rec;
     }
     __syncthreads();
     uint32_t base = 0, total = 0;
-    unsigned long long ext_total = 0;
+    unsigned long long ext_total = 0, rec_total = 0;
 #pragma unroll
     for (int w = 0; w < W; ++w) {
         if (w < (int)warp) base += s_wtot[w];
         total += s_wtot[w];
         ext_total += s_wext[w];
+        rec_total += s_wrec[w];
     }
     for (uint32_t c = b0; c < b1; c += 32) {
         const uint32_t b = c + lane;
@@ -73,7 +77,7 @@ __device__ __forceinline__ void finish_step(const NetView& v, uint32_t t) {
         st->raster_base = st->raster_count;
         st->raster_count += total;
         st->n_spikes += total;
-        st->rec_events += (uint64_t)total * v.K;
+        st->rec_events += v.row_len ? (uint64_t)rec_total : (uint64_t)total * v.K;
         st->ext_events += ext_total;
         st->t = t + 1;
         st->done = 0;
@@ -93,7 +97,8 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     const uint32_t base = blockIdx.x * NEURONS_PER_BLOCK + tid * NEURONS_PER_THREAD;
 
     uint32_t next_sum = 0;
-    const uint32_t spk = update_quad(v, s_pois, base, t, slot, next_sum);
+    uint64_t rec = 0;
+    const uint32_t spk = update_quad(v, s_pois, base, t, slot, next_sum, rec);
 
     // Block-ordered compaction: exclusive prefix of per-thread spike counts.
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -106,19 +111,28 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     }
     uint32_t ext_w = next_sum;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ext_w += __shfl_xor_sync(0xFFFFFFFFu, ext_w, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        ext_w += __shfl_xor_sync(0xFFFFFFFFu, ext_w, o);
+        rec += __shfl_xor_sync(0xFFFFFFFFu, rec, o);
+    }
     __shared__ uint32_t s_wsum[NEURON_THREADS / 32];
     __shared__ uint32_t s_wext[NEURON_THREADS / 32];
+    __shared__ unsigned long long s_wrec[NEURON_THREADS / 32];
     if (lane == 31) s_wsum[warp] = incl;
-    if (lane == 0) s_wext[warp] = ext_w;
+    if (lane == 0) {
+        s_wext[warp] = ext_w;
+        s_wrec[warp] = rec;
+    }
     __syncthreads();
     uint32_t woff = 0, btot = 0, bext = 0;
+    unsigned long long brec = 0;
 #pragma unroll
     for (int w = 0; w < NEURON_THREADS / 32; ++w) {
         const uint32_t x = s_wsum[w];
         if (w < (int)warp) woff += x;
         btot += x;
         bext += s_wext[w];
+        brec += s_wrec[w];
     }
     uint32_t pos = woff + incl - cnt;
     uint32_t* seg = v.seg + (size_t)blockIdx.x * NEURONS_PER_BLOCK;
@@ -129,6 +143,7 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     if (tid == 0) {
         v.blk_cnt[blockIdx.x] = btot;
         v.blk_ext[blockIdx.x] = bext;
+        if (v.row_len) v.blk_rec[blockIdx.x] = brec;
         __threadfence();
         const uint32_t ticket = atomicAdd(&v.st->done, 1u);
         s_last = (ticket == gridDim.x - 1);
@@ -256,6 +271,7 @@ __global__ void __launch_bounds__(256) k_deliver_thread(NetView v) {
             id = __ldcg(v.seg + (size_t)b * NEURONS_PER_BLOCK + (j - s_off[b]));
             cached_j = j;
         }
+        if (v.row_len && k >= __ldg(v.row_len + id)) continue;  // past this row's end
         const size_t e = (size_t)id * v.Kpad + k;
         const uint32_t tg = __ldg(v.tgt + e);
         const float w = BF16 ? __uint_as_float((uint32_t)__ldg(reinterpret_cast<const uint16_t*>(v.w) + e) << 16)

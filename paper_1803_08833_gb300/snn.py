@@ -44,6 +44,11 @@ class SnnConfig(ctypes.Structure):
         ("weight_dtype", ctypes.c_int32), ("fx_shift", ctypes.c_uint32),
         ("seed", ctypes.c_uint64), ("raster_capacity", ctypes.c_uint64),
         ("table_layout", ctypes.c_int32),
+        ("conn_rule", ctypes.c_int32), ("p_local", ctypes.c_float),
+        ("A_remote", ctypes.c_double), ("p_min", ctypes.c_double),
+        ("inh_local_only", ctypes.c_int32), ("weight_dist", ctypes.c_int32),
+        ("w_exc_sd", ctypes.c_float), ("w_inh_sd", ctypes.c_float),
+        ("delay_dist", ctypes.c_int32), ("delay_tau_ms", ctypes.c_float),
     ]
 
 
@@ -95,6 +100,9 @@ def load():
         "snn_get_table": (st, [vp, vp, vp, vp, vp]),
         "snn_get_rows": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp, vp, vp]),
         "snn_get_segments": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, P(ctypes.c_uint32), vp]),
+        "snn_get_row_lengths": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, vp, vp]),
+        "snn_construction_tables": (st, [P(SnnConfig), vp, vp, P(ctypes.c_uint32), vp, vp, vp, ctypes.c_uint32,
+                                         P(ctypes.c_uint32)]),
         "snn_get_cdf": (st, [vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_get_state": (st, [vp, vp, vp, vp, vp, P(ctypes.c_uint32), vp]),
         "snn_set_state": (st, [vp, vp, vp, vp, vp]),
@@ -154,12 +162,36 @@ def config(cfg: dict, raster_capacity: int = 0) -> SnnConfig:
             v = {"f32": 0, "bf16": 1}.get(v, v)
         elif k == "table_layout":
             v = {"draw": 0, "grouped": 1}.get(v, v)
+        elif k == "conn_rule":
+            v = {"fixed_k": 0, "pairwise": 1}.get(v, v)
+        elif k == "weight_dist":
+            v = {"uniform": 0, "gauss": 1}.get(v, v)
+        elif k == "delay_dist":
+            v = {"uniform": 0, "exp": 1}.get(v, v)
         if k not in names:
             raise KeyError("unknown snn_config field %r" % k)
         setattr(c, k, v)
     if raster_capacity:
         c.raster_capacity = raster_capacity
     return c
+
+
+def construction_tables(cfg: dict) -> dict:
+    """The host-derived construction tables of a description (no GPU work):
+    Gaussian efficacy quantiles, exponential delay thresholds, pairwise stencil."""
+    L = load()
+    c = config(cfg)
+    nd, npair = ctypes.c_uint32(), ctypes.c_uint32()
+    check(L.snn_construction_tables(ctypes.byref(c), None, None, ctypes.byref(nd), None, None, None, 0,
+                                    ctypes.byref(npair)))
+    wtab = np.zeros(2 * 4096, np.float32)
+    dthr = np.zeros(max(1, nd.value), np.uint64)
+    k = npair.value
+    dx, dy, thr = np.zeros(max(1, k), np.int32), np.zeros(max(1, k), np.int32), np.zeros(max(1, k), np.uint64)
+    check(L.snn_construction_tables(ctypes.byref(c), _ptr(wtab), _ptr(dthr), ctypes.byref(nd), _ptr(dx), _ptr(dy),
+                                    _ptr(thr), max(1, k), ctypes.byref(npair)))
+    return {"wtab_exc": wtab[:4096], "wtab_inh": wtab[4096:], "dthr": dthr[:nd.value],
+            "pair_dx": dx[:k], "pair_dy": dy[:k], "pair_thr": thr[:k]}
 
 
 def launch_count() -> int:
@@ -268,10 +300,18 @@ class Network:
         return {f[0]: int(getattr(s, f[0])) for f in SnnStats._fields_}
 
     # -- inspection --------------------------------------------------------
-    def csr(self, first: int = 0, count=None):
-        """Synapse rows [first, first + count) as flat (target, weight, delay) arrays."""
+    def row_lengths(self, first: int = 0, count=None):
+        """Out-degree of rows [first, first + count)."""
         count = self.N - first if count is None else count
-        ns = count * self.K
+        out = np.empty(max(1, count), np.uint32)
+        check(load().snn_get_row_lengths(self._h, first, count, _ptr(out), self._s))
+        return out[:count]
+
+    def csr(self, first: int = 0, count=None):
+        """Synapse rows [first, first + count) back to back as flat (target,
+        weight, delay) arrays (row lengths: row_lengths())."""
+        count = self.N - first if count is None else count
+        ns = int(self.row_lengths(first, count).sum()) if count else 0
         tgt = np.empty(ns, np.uint32)
         w = np.empty(ns, np.float32)
         d = np.empty(ns, np.uint8)

@@ -1,0 +1,152 @@
+"""The per-pair connection law (Sec. III-B) on the CUDA path, against the
+oracle: variable-length synapse rows bit-exact, simulations bit-exact in every
+schedule that supports the rule and in a batch, and the full 24x24 network
+checked on sampled rows, Table I's synapse total and invariants."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_08833_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("the gpu tests need a CUDA device")
+    from paper_1803_08833_gb300 import _build
+    from paper_1803_08833_gb300 import snn as S
+    _build.build()
+    S.load()
+    return S
+
+
+CSR_CASES = {
+    "gauss_f32": lambda: W.pairwise(grid=5, M=120, seed=3),
+    "exp_bf16": lambda: W.pairwise(grid=9, M=40, lateral="exp", seed=4, weight_dtype="bf16"),
+    "ragged_m": lambda: dict(W.pairwise(grid=4, M=77, seed=5), grid_h=3),
+    "all_local_inh_remote": lambda: W.pairwise(grid=4, M=50, seed=6, p_local=1.0, inh_local_only=0),
+    "uniform_laws": lambda: W.pairwise(grid=4, M=60, seed=7, weight_dist="uniform", delay_dist="uniform"),
+    "no_remote": lambda: W.pairwise(grid=3, M=30, seed=8, A_remote=0.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CSR_CASES))
+def test_rows_equal_oracle(snn, name):
+    cfg = CSR_CASES[name]()
+    ref = oracle.OracleNet(cfg)
+    rp = ref.row_ptr().astype(np.int64)
+    rt, rw, rd = ref.csr()
+    with snn.Network(cfg) as net:
+        ln = net.row_lengths()
+        assert np.array_equal(ln, np.diff(rp))
+        assert net.K == int(ln.max())
+        tgt, w, d = net.csr()
+        assert np.array_equal(tgt, rt) and np.array_equal(d, rd)
+        assert np.array_equal(w.view(np.uint32), rw.view(np.uint32))
+        # a window of rows
+        a, b = ref.N // 3, ref.N // 3 + 17
+        t2, w2, d2 = net.csr(a, b - a)
+        assert np.array_equal(t2, rt[rp[a]:rp[b]]) and np.array_equal(d2, rd[rp[a]:rp[b]])
+
+
+def _compare(net, ref):
+    st, ids = net.read_spikes()
+    rs, ri = ref.raster()
+    assert np.array_equal(st, rs) and np.array_equal(ids, ri), (len(st), len(rs))
+    s, o = net.state(), ref.state()
+    assert np.array_equal(s["V"].view(np.uint32), o["V"].view(np.uint32))
+    assert np.array_equal(s["c"].view(np.uint32), o["c"].view(np.uint32))
+    assert np.array_equal(s["ref"], o["ref"]) and np.array_equal(s["ring"], o["ring"])
+    a, b = net.stats(), ref.stats()
+    assert a["n_spikes"] == b["spikes"] and a["rec_events"] == b["rec_events"]
+    assert a["ext_events"] == b["ext_events"]
+    return len(st)
+
+
+SIM_CASES = {
+    "gauss_7.5hz": (lambda: W.pairwise(grid=5, M=200, seed=1, imposed_rate_hz=7.5), 300),
+    "exp_bf16_35hz": (lambda: W.pairwise(grid=9, M=60, lateral="exp", seed=2, weight_dtype="bf16",
+                                         imposed_rate_hz=35.0), 200),
+    "drive_5k": (lambda: W.pairwise(grid=4, M=150, seed=3, ext_rate_hz=5000.0), 250),
+    "ragged": (lambda: dict(W.pairwise(grid=3, M=333, seed=4, imposed_rate_hz=40.0), grid_h=2), 150),
+}
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("name", sorted(SIM_CASES))
+def test_simulation_bit_exact(snn, name, schedule):
+    make, steps = SIM_CASES[name]
+    cfg = make()
+    ref = oracle.OracleNet(cfg)
+    ref.step(steps)
+    with snn.Network(cfg, raster_capacity=1 << 22) as net:
+        net.set_schedule(schedule)
+        net.step(steps)
+        n = _compare(net, ref)
+    assert n > 500 or "hz" not in name
+
+
+def test_schedule_3_is_refused(snn):
+    with snn.Network(W.pairwise(grid=3, M=50)) as net:
+        with pytest.raises(snn.SnnError):
+            net.set_schedule(3)
+
+
+def test_batch_mixes_rules(snn):
+    cfgs = [W.pairwise(grid=4, M=100, seed=11, imposed_rate_hz=20.0),
+            W.small(grid=3, M=100, K=90, seed=12, imposed_rate_hz=20.0),
+            W.pairwise(grid=7, M=30, lateral="exp", seed=13, weight_dtype="bf16", imposed_rate_hz=35.0)]
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_graph(True)
+        for steps in ([40, 40, 40], [25, 0, 60]):
+            batch.step(steps)
+            for r, n in zip(refs, steps):
+                r.step(n)
+    for net, ref in zip(nets, refs):
+        _compare(net, ref)
+        net.close()
+
+
+def test_snapshot_restore(snn):
+    cfg = W.pairwise(grid=4, M=80, seed=15, imposed_rate_hz=25.0)
+    with snn.Network(cfg) as a, snn.Network(cfg) as b:
+        a.set_schedule(2)
+        a.step(100)
+        b.step(40)
+        blob = b.snapshot()
+        with snn.Network(cfg) as c:
+            c.restore(blob)
+            c.step(60)
+            sa, sc = a.state(), c.state()
+            for k in ("V", "c", "ref", "ring"):
+                assert np.array_equal(sa[k], sc[k])
+
+
+def test_full_size_24x24_gaussian(snn):
+    """Table I's 24x24 Gaussian network under the per-pair law: sampled rows
+    equal the oracle's, the synapse total is within 3 % of Table I's 0.9 G,
+    and a persistent run keeps the event count and the raster invariants."""
+    cfg = W.pairwise(grid=24, seed=21, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ)
+    rng = np.random.default_rng(2)
+    with snn.Network(cfg, raster_capacity=1 << 24) as net:
+        ln = net.row_lengths().astype(np.int64)
+        total = int(ln.sum())
+        assert abs(total / 0.9e9 - 1.0) < 0.03
+        rows = np.unique(np.concatenate([rng.integers(0, net.N, 300), [0, 999, 1000, net.N - 1]]))
+        for r in rows.tolist():
+            tgt, w, d = net.csr(r, 1)
+            ot, ow, od, ol = oracle.gen_rows_v(cfg, r, 1)
+            assert ol[0] == ln[r] and np.array_equal(tgt, ot) and np.array_equal(d, od), r
+            assert np.array_equal(w.view(np.uint32), ow.view(np.uint32)), r
+        net.set_schedule(2)
+        net.step(100)
+        st, ids = net.read_spikes()
+        s = net.stats()
+        assert s["n_spikes"] == len(ids) > 0
+        assert s["rec_events"] == int(ln[ids].sum())
+        assert np.all(np.diff(st.astype(np.int64) * net.N + ids) > 0)
