@@ -13,9 +13,10 @@ value       recurrent synaptic events / s (events = spikes x out-degree, from th
 e2e         the same metric for whole jobs through the public API: build the
             network from the host description, simulate 10,000 steps reading
             the raster into pinned host memory every 1,000 steps, destroy.
-roofline    the delivery kernel: algorithmic bytes (9 B per recurrent event:
-            uint32 target + f32 weight + uint8 delay) / its summed CUDA-event
-            time, against the measured HBM copy bandwidth.
+roofline    the persistent kernel: algorithmic bytes (8 B per recurrent event:
+            one 32-bit target | delay word + f32 weight; 26 B per neuron and
+            step) / its CUDA-event time, against the measured HBM copy
+            bandwidth.
 cpu_baseline  the oracle (single-threaded C) on a bounded sample of the same
             model, simulation phase only, like `value`.
 
@@ -38,7 +39,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "synaptic events/s on 1 GB300, % of HBM roofline; served p50/p99 latency"
 UNIT = "synaptic events/s"
-BYTES_PER_EVENT = {"f32": 9, "bf16": 7}
+BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
 # neuron update: V, c (f32) and ref (u8) read and written, ring slot read and cleared
 NEURON_BYTES = 2 * (4 + 4 + 1) + 2 * 4
 TIMESTEPS_PER_STEP = 1000
@@ -305,13 +306,13 @@ def run_gpu(args):
         launches_timed = pl
         alg_per_launch = (BYTES_PER_EVENT["f32"] * rec + NEURON_BYTES * net.N * steps_timed) / max(args.steps, 1)
         achieved = alg_per_launch / (pms / pl / 1000.0) / 1e9 if pms > 0 else None
-        bytes_note = "9 B per recurrent event + %d B per neuron per step" % NEURON_BYTES
+        bytes_note = "8 B per recurrent event + %d B per neuron per step" % NEURON_BYTES
     else:
         kernel = "k_deliver_warp<f32>"
         launches_timed = dl
         alg_per_launch = BYTES_PER_EVENT["f32"] * rec / steps_timed
         achieved = alg_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
-        bytes_note = "9 B per recurrent event"
+        bytes_note = "8 B per recurrent event"
         if NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() and NCU_TRAFFIC["bytes_per_event"]:
             traffic = NCU_TRAFFIC["bytes_per_event"] * rec / steps_timed
     net.set_timing(0)
@@ -502,7 +503,7 @@ def run_precision(snn, args, stream):
             rates[dt] = np.bincount(ids, minlength=net.N) / (args.precision_steps / 1000.0)
             ev = s1["rec_events"] - s0["rec_events"]
             out[dt] = {"events_per_s": ev / (ms / 1e3), "ms_per_step": ms / args.precision_steps,
-                       "rate_hz": float(rates[dt].mean()), "bytes_per_synapse": 7 if dt == "bf16" else 9,
+                       "rate_hz": float(rates[dt].mean()), "bytes_per_synapse": BYTES_PER_EVENT[dt],
                        "table_gb": net.device_bytes / 1e9}
     M = 1250
     mod = lambda r: r.reshape(-1, M).mean(axis=1)

@@ -5,7 +5,8 @@
 //                  constants of Sec. I and Sec. III-B) and cumulative distribution,
 //                  converted to uint32 thresholds.
 //   k_gen_synapses per (neuron, 4 synapses): Philox draws -> target module by
-//                  inverse CDF, target neuron, weight, delay; 16 B vector stores.
+//                  inverse CDF, target neuron, weight, delay; 16 B vector stores
+//                  of target | delay << 24 and of the weights.
 //   k_pair_count / k_pair_rows / k_pair_fill
 //                  the pairwise law of Sec. III-B: per (neuron, stencil entry)
 //                  the connection draws of every candidate target, counted,
@@ -118,8 +119,8 @@ __device__ __forceinline__ void syn_attr(const BuildView& b, bool exc, uint32_t 
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __restrict__ tgt,
-                                                      void* __restrict__ wout, uint8_t* __restrict__ dout) {
+__global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __restrict__ td,
+                                                      void* __restrict__ wout) {
     const uint32_t groups = b.Kpad >> 2;
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * groups) return;
@@ -147,7 +148,8 @@ __global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __r
         }
     }
     const size_t e = (size_t)i * b.Kpad + k0;
-    *reinterpret_cast<uint4*>(tgt + e) = make_uint4(tg[0], tg[1], tg[2], tg[3]);
+    *reinterpret_cast<uint4*>(td + e) =
+        make_uint4(tg[0] | (d[0] << 24), tg[1] | (d[1] << 24), tg[2] | (d[2] << 24), tg[3] | (d[3] << 24));
     if (BF16) {
         __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(wout) + e;
         __nv_bfloat162 a = __halves2bfloat162(__float2bfloat16_rn(w[0]), __float2bfloat16_rn(w[1]));
@@ -159,7 +161,6 @@ __global__ void __launch_bounds__(256) k_gen_synapses(BuildView b, uint32_t* __r
     } else {
         *reinterpret_cast<float4*>(reinterpret_cast<float*>(wout) + e) = make_float4(w[0], w[1], w[2], w[3]);
     }
-    *reinterpret_cast<uint32_t*>(dout + e) = d[0] | (d[1] << 8) | (d[2] << 16) | (d[3] << 24);
 }
 
 // Synapse (i, k): target, weight, delay and stencil index j of its target module.
@@ -185,8 +186,8 @@ __device__ __forceinline__ Draw draw_synapse(const BuildView& b, uint32_t i, uin
 // the same j), so every segment keeps the draw order: the row is the stable
 // sort of the draw-order row by stencil index (= by target module).
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __restrict__ tgt,
-                                                     void* __restrict__ wout, uint8_t* __restrict__ dout) {
+__global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __restrict__ td,
+                                                     void* __restrict__ wout) {
     extern __shared__ uint32_t s_cur[];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* cur = s_cur + warp * (b.max_off + 1);
@@ -233,24 +234,22 @@ __global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __re
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, r.j);
         if (active) {
             const uint32_t pos = cur[r.j] + __popc(peers & ((1u << lane) - 1u));
-            tgt[row + pos] = r.tgt;
+            td[row + pos] = r.tgt | (r.d << 24);
             if (BF16)
                 reinterpret_cast<__nv_bfloat16*>(wout)[row + pos] = __float2bfloat16_rn(r.w);
             else
                 reinterpret_cast<float*>(wout)[row + pos] = r.w;
-            dout[row + pos] = (uint8_t)r.d;
         }
         __syncwarp();
         if (active && lane == (uint32_t)(__ffs(peers) - 1)) cur[r.j] += __popc(peers);
         __syncwarp();
     }
     for (uint32_t k = b.K + lane; k < b.Kpad; k += 32) {  // padding entries
-        tgt[row + k] = 0u;
+        td[row + k] = 0u;
         if (BF16)
             reinterpret_cast<__nv_bfloat16*>(wout)[row + k] = __float2bfloat16_rn(0.0f);
         else
             reinterpret_cast<float*>(wout)[row + k] = 0.0f;
-        dout[row + k] = 0u;
     }
 }
 
@@ -267,8 +266,7 @@ __global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __re
 // `start` on.  Returns the count.
 template <bool WRITE, bool BF16>
 __device__ __forceinline__ uint32_t pair_entry(const BuildView& b, uint32_t i, uint32_t o, uint32_t start,
-                                               uint32_t* __restrict__ tgt, void* __restrict__ wout,
-                                               uint8_t* __restrict__ dout) {
+                                               uint32_t* __restrict__ td, void* __restrict__ wout) {
     const uint32_t s = i / b.M, a = i - s * b.M;
     const bool exc = a < b.n_exc;
     const int dx = __ldg(b.pair_dx + o), dy = __ldg(b.pair_dy + o);
@@ -294,12 +292,11 @@ __device__ __forceinline__ uint32_t pair_entry(const BuildView& b, uint32_t i, u
                 uint32_t d;
                 syn_attr(b, exc, v.z, v.w, w, d);
                 const size_t e = (size_t)i * b.Kpad + k;
-                tgt[e] = base + j;
+                td[e] = (base + j) | (d << 24);
                 if (BF16)
                     reinterpret_cast<__nv_bfloat16*>(wout)[e] = __float2bfloat16_rn(w);
                 else
                     reinterpret_cast<float*>(wout)[e] = w;
-                dout[e] = (uint8_t)d;
             }
             ++n;
         }
@@ -311,7 +308,7 @@ __global__ void __launch_bounds__(256) k_pair_count(BuildView b) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
-    const uint32_t n = pair_entry<false, false>(b, i, o, 0u, nullptr, nullptr, nullptr);
+    const uint32_t n = pair_entry<false, false>(b, i, o, 0u, nullptr, nullptr);
     b.pair_cnt[gid] = (uint16_t)min(n, 0xFFFFu);
 }
 
@@ -342,12 +339,11 @@ __global__ void __launch_bounds__(256) k_pair_rows(BuildView b) {
 }
 
 template <bool BF16>
-__global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __restrict__ tgt, void* __restrict__ wout,
-                                                   uint8_t* __restrict__ dout) {
+__global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __restrict__ td, void* __restrict__ wout) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
-    pair_entry<true, BF16>(b, i, o, b.pair_cnt[gid], tgt, wout, dout);
+    pair_entry<true, BF16>(b, i, o, b.pair_cnt[gid], td, wout);
 }
 
 __global__ void k_init_state(BuildView b, float* __restrict__ V, float* __restrict__ c,
@@ -370,19 +366,19 @@ cudaError_t launch_build_cdf(const BuildView& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s) {
+cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* td, void* w, cudaStream_t s) {
     const uint64_t threads = (uint64_t)b.N * (b.Kpad >> 2);
     if (threads == 0) return cudaSuccess;
     const uint64_t blocks = (threads + 255) / 256;
     if (b.w_bf16)
-        k_gen_synapses<true><<<(unsigned)blocks, 256, 0, s>>>(b, tgt, w, d);
+        k_gen_synapses<true><<<(unsigned)blocks, 256, 0, s>>>(b, td, w);
     else
-        k_gen_synapses<false><<<(unsigned)blocks, 256, 0, s>>>(b, tgt, w, d);
+        k_gen_synapses<false><<<(unsigned)blocks, 256, 0, s>>>(b, td, w);
     count_launch(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s) {
+cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* td, void* w, cudaStream_t s) {
     if (b.N == 0 || b.Kpad == 0) return cudaSuccess;
     const int warps = 8;
     const size_t smem = (size_t)warps * (b.max_off + 1) * sizeof(uint32_t);
@@ -393,9 +389,9 @@ cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8
     }
     const unsigned blocks = (b.N + warps - 1) / warps;
     if (b.w_bf16)
-        k_gen_grouped<true><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
+        k_gen_grouped<true><<<blocks, warps * 32, smem, s>>>(b, td, w);
     else
-        k_gen_grouped<false><<<blocks, warps * 32, smem, s>>>(b, tgt, w, d);
+        k_gen_grouped<false><<<blocks, warps * 32, smem, s>>>(b, td, w);
     count_launch(1);
     return cudaGetLastError();
 }
@@ -418,12 +414,12 @@ cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_fill(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s) {
+cudaError_t launch_pair_fill(const BuildView& b, uint32_t* td, void* w, cudaStream_t s) {
     if (b.N == 0 || b.pair_n == 0) return cudaSuccess;
     if (b.w_bf16)
-        k_pair_fill<true><<<pair_blocks(b), 256, 0, s>>>(b, tgt, w, d);
+        k_pair_fill<true><<<pair_blocks(b), 256, 0, s>>>(b, td, w);
     else
-        k_pair_fill<false><<<pair_blocks(b), 256, 0, s>>>(b, tgt, w, d);
+        k_pair_fill<false><<<pair_blocks(b), 256, 0, s>>>(b, td, w);
     count_launch(1);
     return cudaGetLastError();
 }

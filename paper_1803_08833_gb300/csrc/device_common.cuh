@@ -178,15 +178,15 @@ constexpr int DELIVER_UNROLL = SNN_DELIVER_UNROLL;
 // One warp delivers up to DELIVER_UNROLL tasks (spike, 128-synapse chunk):
 // task tk + u * tstride for u < DELIVER_UNROLL, each below `hi`.  ids[j - j0]
 // gives the neuron of staged spike j.  Each lane loads 4 consecutive synapses
-// of every task first (16 B targets, 16 B f32 or 8 B bf16 weights, 4 B
-// delays), then issues the reductions.
+// of every task first (16 B of target | delay << 24 words, 16 B f32 or 8 B
+// bf16 weights), then issues the reductions.
 template <bool BF16>
 __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
                                               uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
                                               uint32_t lane, uint64_t pol) {
     uint4 tg[DELIVER_UNROLL];
     float w[DELIVER_UNROLL][4];
-    uint32_t dd[DELIVER_UNROLL], nv[DELIVER_UNROLL];
+    uint32_t nv[DELIVER_UNROLL];
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
         const uint64_t task = tk + (uint64_t)u * tstride;
@@ -200,7 +200,7 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
             if (k0 < L) {
                 nv[u] = min(4u, L - k0);
                 const size_t e = (size_t)id * v.Kpad + k0;
-                tg[u] = ld_u4(v.tgt + e, pol);
+                tg[u] = ld_u4(v.td + e, pol);
                 if (BF16) {
                     const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
                     w[u][0] = bf16_lo(wb.x);
@@ -214,7 +214,6 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
                     w[u][2] = __uint_as_float(wf.z);
                     w[u][3] = __uint_as_float(wf.w);
                 }
-                dd[u] = ld_u1(v.d + e, pol);
             }
         }
     }
@@ -224,9 +223,9 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if ((uint32_t)q < nv[u]) {
-                uint32_t s = slot0 + ((dd[u] >> (8 * q)) & 0xFFu);
+                uint32_t s = slot0 + (tq[q] >> 24);
                 if (s >= v.D) s -= v.D;
-                red_add(v.ring + (size_t)s * v.Npad + tq[q], fx_weight(v, w[u][q]));
+                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, w[u][q]));
             }
         }
     }

@@ -39,11 +39,6 @@ __device__ __forceinline__ uint32_t ld_nc_u16(const uint16_t* p, uint64_t pol) {
     asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
     return r;
 }
-__device__ __forceinline__ uint32_t ld_nc_u8(const uint8_t* p, uint64_t pol) {
-    uint16_t r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u8 %0, [%1], %2;" : "=h"(r) : "l"(p), "l"(pol));
-    return r;
-}
 
 // Bulk reduction global[0 .. bytes) += shared[0 .. bytes) (s32), TMA engine;
 // both addresses 16-byte aligned, bytes a multiple of 16.
@@ -282,10 +277,11 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
                         if (e < e1) {
                             while (pp + 1 < np && s_pref[pp + 1] <= e) ++pp;
                             const size_t idx = (size_t)s_pid[pp] * v.Kpad + s_pa[pp] + (e - s_pref[pp]);
-                            tg[u] = ld_nc_u32(v.tgt + idx, pol);
+                            const uint32_t x = ld_nc_u32(v.td + idx, pol);
+                            tg[u] = x & 0xFFFFFFu;
+                            dd[u] = x >> 24;
                             wb[u] = BF16 ? ld_nc_u16(reinterpret_cast<const uint16_t*>(v.w) + idx, pol)
                                          : ld_nc_u32(reinterpret_cast<const uint32_t*>(v.w) + idx, pol);
-                            dd[u] = ld_nc_u8(v.d + idx, pol);
                         }
                     }
 #pragma unroll

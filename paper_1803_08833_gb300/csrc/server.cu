@@ -83,13 +83,20 @@ uint64_t snn_estimate_bytes(const snn_config* c) {
     if (!c) return 0;
     const uint64_t N = (uint64_t)c->grid_w * c->grid_h * c->neurons_per_module;
     const uint64_t Npad = (N + 1023) / 1024 * 1024;
-    const uint64_t Kpad = (c->K + 7) / 8 * 8;
+    uint64_t K = c->K, temp = 0;
+    if (c->conn_rule == SNN_RULE_PAIRWISE) {
+        uint32_t mr = 0, st = 0;
+        snn::pairwise_bounds(*c, &mr, &st);
+        K = mr;
+        temp = N * st * 2;  // per-entry counts, held during construction
+    }
+    const uint64_t Kpad = (K + 7) / 8 * 8;
     const uint64_t wb = c->weight_dtype == SNN_WEIGHT_BF16 ? 2 : 4;
     const uint64_t D = (uint64_t)std::max(c->d_exc_hi, c->d_inh) + 1;
     const double q = c->cutoff_um / (double)c->spacing_um;
     const uint64_t off = (uint64_t)(3.2 * q * q + 8 * q + 8);  // bound on the stencil size
     const uint64_t modules = (uint64_t)c->grid_w * c->grid_h;
-    uint64_t b = N * Kpad * (4 + wb + 1);             // synapse table
+    uint64_t b = N * Kpad * (4 + wb) + temp;          // synapse table (target | delay word, weight)
     b += Npad * (4 + 4 + 1 + 4 + 4) + D * Npad * 4;    // state, staging, ring
     b += c->raster_capacity * 8 + modules * off * 16;  // raster, tables
     if (c->table_layout == SNN_LAYOUT_GROUPED) b += N * (off + 1) * 2;

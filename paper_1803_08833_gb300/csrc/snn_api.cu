@@ -385,6 +385,24 @@ void host_tables(const snn_config& c, HostTables* t) {
     }
 }
 
+}  // namespace
+
+namespace snn {
+// Bounds used by memory estimates: the longest row of the pairwise rule (mean
+// of an interior excitatory neuron plus eight standard deviations) and its
+// stencil size.
+void pairwise_bounds(const snn_config& c, uint32_t* max_row, uint32_t* stencil) {
+    HostTables t;
+    host_tables(c, &t);
+    double mean = 0.0;
+    for (size_t k = 0; k < t.pthr.size(); ++k) mean += (double)t.pthr[k] / 4294967296.0 * c.neurons_per_module;
+    *max_row = (uint32_t)std::ceil(mean + 8.0 * std::sqrt(mean) + 16.0);
+    *stencil = (uint32_t)t.pthr.size();
+}
+}  // namespace snn
+
+namespace {
+
 void free_block(snn_net* n, void* p, size_t bytes) {
     for (size_t i = 0; i < n->blocks.size(); ++i)
         if (n->blocks[i] == p) {
@@ -500,9 +518,8 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         void** p;
         size_t bytes;
     } reqs[] = {
-        {(void**)&v.tgt, nsyn * 4},
+        {(void**)&v.td, nsyn * 4},
         {(void**)&v.w, nsyn * wbytes},
-        {(void**)&v.d, nsyn},
         {(void**)&v.V, (size_t)n->Npad * 4},
         {(void**)&v.c, (size_t)n->Npad * 4},
         {(void**)&v.ref, (size_t)n->Npad},
@@ -578,14 +595,13 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
 
     CUDA_TRY(launch_build_cdf(b, s));
     if (pairwise) {
-        CUDA_TRY(cudaMemsetAsync(v.tgt, 0, nsyn * 4, s));  // padding past each row's end
+        CUDA_TRY(cudaMemsetAsync(v.td, 0, nsyn * 4, s));  // padding past each row's end
         CUDA_TRY(cudaMemsetAsync(v.w, 0, nsyn * wbytes, s));
-        CUDA_TRY(cudaMemsetAsync(v.d, 0, nsyn, s));
-        CUDA_TRY(launch_pair_fill(b, v.tgt, v.w, v.d, s));
+        CUDA_TRY(launch_pair_fill(b, v.td, v.w, s));
     } else if (grouped) {
-        CUDA_TRY(launch_gen_grouped(b, v.tgt, v.w, v.d, s));
+        CUDA_TRY(launch_gen_grouped(b, v.td, v.w, s));
     } else {
-        CUDA_TRY(launch_gen_synapses(b, v.tgt, v.w, v.d, s));
+        CUDA_TRY(launch_gen_synapses(b, v.td, v.w, s));
     }
     CUDA_TRY(launch_init_state(b, v.V, v.c, v.ref, s));
     CUDA_TRY(cudaMemsetAsync(v.ring, 0, (size_t)n->D * n->Npad * 4, s));
@@ -800,59 +816,37 @@ snn_status snn_get_rows(snn_net* n, uint32_t first, uint32_t count, uint32_t* tg
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     if ((uint64_t)first + count > n->N) return fail(SNN_EINVAL, "rows [%u, %u) out of range", first, first + count);
     cudaStream_t s = (cudaStream_t)stream;
-    const size_t rows = count, K = n->K, Kp = n->Kpad;
+    const size_t rows = count, Kp = n->Kpad;
     const size_t e0 = (size_t)first * Kp;
-    if (n->v.row_len) {
-        // rows of different lengths: copy the padded rows, keep each row's first len entries
-        std::vector<uint32_t> len(rows);
-        if (rows) CUDA_TRY(cudaMemcpyAsync(len.data(), n->v.row_len + first, rows * 4, cudaMemcpyDeviceToHost, s));
-        std::vector<uint32_t> t(tgt ? rows * Kp : 0);
-        std::vector<uint8_t> dd(d ? rows * Kp : 0);
-        const bool bf = n->v.w_bf16 != 0;
-        std::vector<uint32_t> wr(w && !bf ? rows * Kp : 0);  // f32 bits
-        std::vector<uint16_t> wh(w && bf ? rows * Kp : 0);   // bf16 bits
-        if (tgt && rows) CUDA_TRY(cudaMemcpyAsync(t.data(), n->v.tgt + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
-        if (d && rows) CUDA_TRY(cudaMemcpyAsync(dd.data(), n->v.d + e0, rows * Kp, cudaMemcpyDeviceToHost, s));
-        if (w && rows) {
-            if (bf)
-                CUDA_TRY(cudaMemcpyAsync(wh.data(), (const uint16_t*)n->v.w + e0, rows * Kp * 2, cudaMemcpyDeviceToHost, s));
-            else
-                CUDA_TRY(cudaMemcpyAsync(wr.data(), (const float*)n->v.w + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
-        }
-        CUDA_TRY(cudaStreamSynchronize(s));
-        size_t o = 0;
-        for (size_t r = 0; r < rows; ++r) {
-            for (size_t k = 0; k < len[r]; ++k, ++o) {
-                const size_t e = r * Kp + k;
-                if (tgt) tgt[o] = t[e];
-                if (d) d[o] = dd[e];
-                if (w) {
-                    const uint32_t bits = bf ? (uint32_t)wh[e] << 16 : wr[e];
-                    std::memcpy(&w[o], &bits, 4);
-                }
-            }
-        }
-        return SNN_OK;
-    }
-    if (tgt && K && rows)
-        CUDA_TRY(cudaMemcpy2DAsync(tgt, K * 4, n->v.tgt + e0, Kp * 4, K * 4, rows, cudaMemcpyDeviceToHost, s));
-    if (d && K && rows) CUDA_TRY(cudaMemcpy2DAsync(d, K, n->v.d + e0, Kp, K, rows, cudaMemcpyDeviceToHost, s));
-    if (w && K && rows) {
-        if (n->v.w_bf16) {
-            std::vector<uint16_t> tmp(rows * K);
-            CUDA_TRY(cudaMemcpy2DAsync(tmp.data(), K * 2, (const uint16_t*)n->v.w + e0, Kp * 2, K * 2, rows,
-                                       cudaMemcpyDeviceToHost, s));
-            CUDA_TRY(cudaStreamSynchronize(s));
-            for (size_t e = 0; e < tmp.size(); ++e) {
-                uint32_t bits = (uint32_t)tmp[e] << 16;
-                std::memcpy(&w[e], &bits, 4);
-            }
-        } else {
-            CUDA_TRY(cudaMemcpy2DAsync(w, K * 4, (const float*)n->v.w + e0, Kp * 4, K * 4, rows,
-                                       cudaMemcpyDeviceToHost, s));
-        }
+    // copy the padded rows, keep each row's first len entries; split target | delay << 24
+    std::vector<uint32_t> len(rows, n->K);
+    if (n->v.row_len && rows)
+        CUDA_TRY(cudaMemcpyAsync(len.data(), n->v.row_len + first, rows * 4, cudaMemcpyDeviceToHost, s));
+    const bool bf = n->v.w_bf16 != 0;
+    std::vector<uint32_t> td((tgt || d) ? rows * Kp : 0);
+    std::vector<uint32_t> wr(w && !bf ? rows * Kp : 0);  // f32 bits
+    std::vector<uint16_t> wh(w && bf ? rows * Kp : 0);   // bf16 bits
+    if ((tgt || d) && rows && Kp)
+        CUDA_TRY(cudaMemcpyAsync(td.data(), n->v.td + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
+    if (w && rows && Kp) {
+        if (bf)
+            CUDA_TRY(cudaMemcpyAsync(wh.data(), (const uint16_t*)n->v.w + e0, rows * Kp * 2, cudaMemcpyDeviceToHost, s));
+        else
+            CUDA_TRY(cudaMemcpyAsync(wr.data(), (const float*)n->v.w + e0, rows * Kp * 4, cudaMemcpyDeviceToHost, s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
+    size_t o = 0;
+    for (size_t r = 0; r < rows; ++r) {
+        for (size_t k = 0; k < len[r]; ++k, ++o) {
+            const size_t e = r * Kp + k;
+            if (tgt) tgt[o] = td[e] & 0xFFFFFFu;
+            if (d) d[o] = (uint8_t)(td[e] >> 24);
+            if (w) {
+                const uint32_t bits = bf ? (uint32_t)wh[e] << 16 : wr[e];
+                std::memcpy(&w[o], &bits, 4);
+            }
+        }
+    }
     return SNN_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct snn_config;
+
 namespace snn {
 
 // Philox counter layout (c0, c1, c2, c3) = (a, b, tag, 0).
@@ -52,10 +54,10 @@ struct NetView {
     uint64_t imposed_thresh;
     uint32_t pois32[MAX_POIS];  // thresholds, then 0xFFFFFFFF padding
     int32_t w_bf16;
-    // synapse table, rows of Kpad entries per neuron
-    uint32_t* tgt;
+    // synapse table, rows of Kpad entries per neuron: target | delay << 24 in one
+    // word (N <= 2^24, delays <= 255) and the weight
+    uint32_t* td;
     void* w;
-    uint8_t* d;
     const uint32_t* row_len;  // pairwise rule: synapses of each row (K = the longest); NULL: K each
     // neuron state (Npad entries) and delay ring (D rows of Npad)
     float* V;
@@ -120,12 +122,11 @@ struct BuildView {
 
 // Launch wrappers (return the launch error).
 cudaError_t launch_build_cdf(const BuildView& b, cudaStream_t s);
-cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d,
-                                cudaStream_t s);
-cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s);
+cudaError_t launch_gen_synapses(const BuildView& b, uint32_t* td, void* w, cudaStream_t s);
+cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* td, void* w, cudaStream_t s);
 cudaError_t launch_pair_count(const BuildView& b, cudaStream_t s);
 cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s);
-cudaError_t launch_pair_fill(const BuildView& b, uint32_t* tgt, void* w, uint8_t* d, cudaStream_t s);
+cudaError_t launch_pair_fill(const BuildView& b, uint32_t* td, void* w, cudaStream_t s);
 cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* ref,
                               cudaStream_t s);
 cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);
@@ -153,6 +154,7 @@ cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cuda
 cudaError_t prepare_deliver(uint32_t nb);
 
 void count_launch(uint64_t n);
+void pairwise_bounds(const snn_config& c, uint32_t* max_row, uint32_t* stencil);
 void set_last_error(const char* msg);  // message returned by snn_last_error()
 
 }  // namespace snn

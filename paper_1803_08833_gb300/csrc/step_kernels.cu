@@ -273,12 +273,12 @@ __global__ void __launch_bounds__(256) k_deliver_thread(NetView v) {
         }
         if (v.row_len && k >= __ldg(v.row_len + id)) continue;  // past this row's end
         const size_t e = (size_t)id * v.Kpad + k;
-        const uint32_t tg = __ldg(v.tgt + e);
+        const uint32_t x = __ldg(v.td + e);
         const float w = BF16 ? __uint_as_float((uint32_t)__ldg(reinterpret_cast<const uint16_t*>(v.w) + e) << 16)
                              : __ldg(reinterpret_cast<const float*>(v.w) + e);
-        uint32_t s = slot0 + __ldg(v.d + e);
+        uint32_t s = slot0 + (x >> 24);
         if (s >= v.D) s -= v.D;
-        red_add(v.ring + (size_t)s * v.Npad + tg, fx_weight(v, w));
+        red_add(v.ring + (size_t)s * v.Npad + (x & 0xFFFFFFu), fx_weight(v, w));
     }
 }
 

@@ -49,13 +49,21 @@ _PAIRWISE = {
     "delay_dist": "exp", "delay_tau_ms": 5.0,
 }
 PAIRWISE_A = {"gauss": 0.05, "exp": 0.03}
+# Inhibitory efficacy that balances the mean recurrent input of an interior
+# neuron: under the per-pair law an excitatory-to-any in-degree of
+# 0.8 (0.8 M) + n_exc sum_r A f(r) (0.64 M + 0.204 M Gaussian, 0.64 M + 1.06 M
+# exponential) against 0.8 (0.2 M) inhibitory inputs; times the 0.2 mV mean
+# excitatory efficacy.  Without it the 1,250-neuron modules run away to the
+# refractory limit (~300 Hz) even at an imposed 7.5 Hz.
+PAIRWISE_W_INH = {"gauss": -1.05, "exp": -2.1}
 
 
 def pairwise(grid=24, M=1250, lateral="gauss", seed=1, **kw):
     """A grid x grid network under the per-pair law; Table I's grids are 24, 48
     and 96 modules per side."""
     lat = _GAUSS if lateral == "gauss" else _EXP
-    cfg = _make(grid, M, 0, lat, seed, **dict(_PAIRWISE, A_remote=PAIRWISE_A[lateral]))
+    cfg = _make(grid, M, 0, lat, seed, **dict(_PAIRWISE, A_remote=PAIRWISE_A[lateral],
+                                              w_inh=PAIRWISE_W_INH[lateral]))
     cfg.update(kw)
     return cfg
 

@@ -119,6 +119,9 @@ def test_memory_estimate_tracks_the_table(lib):
     big = snn.estimate_bytes(W.gauss_24x24_k1125())
     bf = snn.estimate_bytes(W.exp_24x24_k2250(weight_dtype="bf16"))
     f32 = snn.estimate_bytes(W.exp_24x24_k2250(weight_dtype="f32"))
-    assert 144e6 < small < 400e6            # 16 M synapses x 9 B + state
-    assert 7.3e9 < big < 7.8e9              # 810 M synapses x 9 B + ring
+    assert 128e6 < small < 400e6            # 16 M synapses x 8 B + state
+    assert 6.5e9 < big < 7.0e9              # 810 M synapses x 8 B + ring
     assert bf < f32 and abs((f32 - bf) - 720000 * 2256 * 2) < 1e6
+    # the pairwise rule: the longest-row bound sets the stride (Table I: ~1.25 k per neuron, 0.9 G in all)
+    pw = snn.estimate_bytes(W.pairwise(grid=24))
+    assert 0.9e9 * 8 < pw < 720000 * 1700 * 8

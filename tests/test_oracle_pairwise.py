@@ -144,7 +144,7 @@ def test_gaussian_efficacy_table_is_normal_quantiles():
     cfg = W.pairwise(grid=2, M=10)
     q = (np.arange(4096) + 0.5) / 4096
     f = lambda x: float(np.float32(x))  # the description holds float32 parameters
-    for exc, mean, sd in ((True, (f(0.1) + f(0.3)) / 2, f(0.05)), (False, f(-0.8), f(0.2))):
+    for exc, mean, sd in ((True, (f(0.1) + f(0.3)) / 2, f(0.05)), (False, f(cfg["w_inh"]), f(0.2))):
         tab, tab64 = oracle.weight_table(cfg, exc)
         ref = mean + sd * stats.norm.ppf(q)
         assert np.allclose(tab64, ref, rtol=0, atol=1e-12)
