@@ -48,7 +48,10 @@ JOB_TIMESTEPS = 10000
 # DRAM traffic of one delivery launch from an ncu capture of the same kernel
 # source (dram__bytes_read.sum + dram__bytes_write.sum, per recurrent event).
 # Reported only while the kernel source is unchanged since the capture.
-NCU_TRAFFIC = {"source_sha256": None, "bytes_per_event": None, "capture": None}
+# DRAM bytes (read + write) of the persistent kernel per recurrent event, from
+# one ncu capture of a smaller case of the same model (profiles/), valid only
+# for the kernel sources it was taken on.
+NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": None, "bytes_per_event": None, "capture": None}
 
 
 def _log(*a):
@@ -56,8 +59,11 @@ def _log(*a):
 
 
 def _kernel_source_sha():
-    p = os.path.join(ROOT, "paper_1803_08833_gb300", "csrc", "step_kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()
+    """Hash of every source the persistent kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("persistent_kernels.cu", "device_common.cuh", "grid_common.cuh", "philox.cuh", "snn_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1803_08833_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def _peaks():
@@ -307,14 +313,15 @@ def run_gpu(args):
         alg_per_launch = (BYTES_PER_EVENT["f32"] * rec + NEURON_BYTES * net.N * steps_timed) / max(args.steps, 1)
         achieved = alg_per_launch / (pms / pl / 1000.0) / 1e9 if pms > 0 else None
         bytes_note = "8 B per recurrent event + %d B per neuron per step" % NEURON_BYTES
+        if (schedule == 2 and NCU_TRAFFIC["source_sha256"] == _kernel_source_sha()
+                and NCU_TRAFFIC["bytes_per_event"]):
+            traffic = NCU_TRAFFIC["bytes_per_event"] * rec / max(args.steps, 1)
     else:
         kernel = "k_deliver_warp<f32>"
         launches_timed = dl
         alg_per_launch = BYTES_PER_EVENT["f32"] * rec / steps_timed
         achieved = alg_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
         bytes_note = "8 B per recurrent event"
-        if NCU_TRAFFIC["source_sha256"] == _kernel_source_sha() and NCU_TRAFFIC["bytes_per_event"]:
-            traffic = NCU_TRAFFIC["bytes_per_event"] * rec / steps_timed
     net.set_timing(0)
 
     # end-to-end jobs through the public API with host buffers
@@ -358,8 +365,10 @@ def run_gpu(args):
                                      if pl else None,
                                      "deliver_phase_us": (s1["deliver_phase_ns"] - s0["deliver_phase_ns"]) / 1e3 / steps_timed
                                      if pl else None,
-                                     "kernel_timing": "CUDA events around the kernels of every %d-th "
-                                                      "simulated step of the timed region" % args.timing_every}),
+                                     "kernel_timing": ("CUDA events around every persistent launch of the timed "
+                                                       "region; phases from the GPU timer of CTA 0" if pl else
+                                                       "CUDA events around the kernels of every %d-th simulated "
+                                                       "step of the timed region" % args.timing_every)}),
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": bytes_note, "bytes_per_launch": alg_per_launch,
@@ -591,12 +600,29 @@ def run_served(snn, args, stream):
                 _t.sleep(max(0.0, stream_reqs[i][0] - (snn.now_ns() - start) / 1e9))
         wall = (snn.now_ns() - start) / 1e9
         st = srv.stats()
+    # the same kind of requests one instance per launch (every 10th request of
+    # the stream, in turn: build, persistent run, counters, destroy)
+    import torch
+    plain_ev, plain_s, plain_n = 0, 0.0, 0
+    for t, cfg, steps in stream_reqs[::10]:
+        torch.cuda.synchronize()
+        t0 = snn.now_ns()
+        with snn.Network(cfg, raster_capacity=1 << 10, stream=stream) as net:
+            net.set_schedule(2)
+            net.step(steps)
+            plain_ev += net.stats()["rec_events"]
+        torch.cuda.synchronize()
+        plain_s += (snn.now_ns() - t0) / 1e9
+        plain_n += 1
     lat = np.array([r["latency_ms"] for r in results])
     qms = np.array([r["queue_ms"] for r in results])
     ok = sum(1 for r in results if r["status"] == 0)
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_queue_ms": float(qms.mean()), "requests": len(results), "ok": ok,
             "value": st["rec_events"] / wall, "unit": UNIT, "wall_s": wall, "arrival_window_s": args.served_seconds,
+            "busy_value": st["rec_events"] / (st["busy_ns"] / 1e9),
+            "plain_value": plain_ev / plain_s, "plain_requests": plain_n,
+            "plain": "every 10th request run alone in turn (build, persistent run, destroy): events / total time",
             "gpu_busy_frac": st["busy_ns"] / 1e9 / wall, "peak_active": peak, "launches": st["launches"],
             "budget_gb": 150, "chunk_steps": args.served_chunk,
             "workload": "Poisson arrivals at 20 req/s (seed 7), grid side U{4..32} x 1250 neurons, K U{500..2250}, "

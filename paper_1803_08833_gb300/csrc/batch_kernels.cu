@@ -14,9 +14,10 @@
 
 namespace snn {
 
-#ifndef SNN_PERSIST_MIN_BLOCKS
-#define SNN_PERSIST_MIN_BLOCKS 2
+#ifndef SNN_BATCH_MIN_BLOCKS
+#define SNN_BATCH_MIN_BLOCKS 2  // two CTAs per SM: many small networks need more warps than deep unrolling
 #endif
+constexpr int BATCH_UNROLL = 4;  // delivery tasks in flight per warp
 
 // Neuron id of spike jl of network k: the (network, warp) segment by binary
 // search over the network's part of the segment prefix, then the warp's
@@ -51,7 +52,7 @@ __device__ __forceinline__ uint32_t upper_slot(const uint32_t* pre, uint32_t n, 
     return lo;
 }
 
-__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_batch(BatchMeta bm, uint32_t n_steps) {
+__global__ void __launch_bounds__(PERSIST_THREADS, SNN_BATCH_MIN_BLOCKS) k_run_batch(BatchMeta bm, uint32_t n_steps) {
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t n = bm.n, NW = bm.n_seg;
     const uint32_t G = gridDim.x, TW = G * PERSIST_WARPS;
@@ -179,11 +180,13 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
                     __syncthreads();
                     const uint64_t lo = max(la, (uint64_t)jb * chunks);
                     const uint64_t hi = min(lb, (uint64_t)(jb + blockDim.x) * chunks);
-                    for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL) {
+                    for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * BATCH_UNROLL) {
                         if (bf16)
-                            deliver_tasks<true>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol);
+                            deliver_tasks<true, BATCH_UNROLL>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane,
+                                                              pol);
                         else
-                            deliver_tasks<false>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol);
+                            deliver_tasks<false, BATCH_UNROLL>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane,
+                                                               pol);
                     }
                     __syncthreads();
                 }

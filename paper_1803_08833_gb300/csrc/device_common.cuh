@@ -171,7 +171,7 @@ __device__ __forceinline__ uint32_t ld_u1(const void* p, uint64_t pol) {
 }
 
 #ifndef SNN_DELIVER_UNROLL
-#define SNN_DELIVER_UNROLL 4
+#define SNN_DELIVER_UNROLL 6
 #endif
 constexpr int DELIVER_UNROLL = SNN_DELIVER_UNROLL;
 
@@ -180,7 +180,7 @@ constexpr int DELIVER_UNROLL = SNN_DELIVER_UNROLL;
 // gives the neuron of staged spike j.  Each lane loads 4 consecutive synapses
 // of every task first (16 B of target | delay << 24 words, 16 B f32 or 8 B
 // bf16 weights), then issues the reductions.
-template <bool BF16>
+template <bool BF16, int DELIVER_UNROLL = snn::DELIVER_UNROLL>
 __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
                                               uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
                                               uint32_t lane, uint64_t pol) {

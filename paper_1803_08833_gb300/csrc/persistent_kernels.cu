@@ -18,7 +18,7 @@
 namespace snn {
 
 #ifndef SNN_PERSIST_MIN_BLOCKS
-#define SNN_PERSIST_MIN_BLOCKS 2
+#define SNN_PERSIST_MIN_BLOCKS 1  // one CTA per SM: registers for deep delivery unrolling
 #endif
 
 // Neuron id of staged spike j: the warp by binary search over the per-warp
@@ -76,12 +76,15 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         const uint32_t slot = t % v.D;
         // ---- phase N: this warp's neurons, 4 per lane, spikes compacted in id order
         uint32_t run = 0;
-        QuadIn nxt;  // the next chunk's loads are issued before this chunk is integrated
-        if (qa + lane < qb) nxt = load_quad(v, (qa + lane) << 2, slot);
+        // the loads of the next two chunks are in flight while a chunk is integrated
+        QuadIn n1, n2;
+        if (qa + lane < qb) n1 = load_quad(v, (qa + lane) << 2, slot);
+        if (qa + 32 + lane < qb) n2 = load_quad(v, (qa + 32 + lane) << 2, slot);
         for (uint32_t qc = qa; qc < qb; qc += 32) {
             const uint32_t q = qc + lane;
-            const QuadIn cur = nxt;
-            if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
+            const QuadIn cur = n1;
+            n1 = n2;
+            if (q + 64 < qb) n2 = load_quad(v, (q + 64) << 2, slot);
             uint32_t spk = 0;
             if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext, rec);
             const uint32_t cnt = __popc(spk);

@@ -513,6 +513,11 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     b.K = n->K;
     b.Kpad = n->Kpad;
     const size_t nsyn = (size_t)n->N * n->Kpad;
+    // the persistent kernels' per-CTA arrays hold any of their grids: at most 8 CTAs per SM
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, n->device);
+    const size_t persist_bound = (size_t)8 * (sms > 0 ? sms : 1) > (size_t)n->pgrid ? (size_t)8 * (sms > 0 ? sms : 1)
+                                                                                    : (size_t)n->pgrid;
     const size_t wbytes = v.w_bf16 ? 2 : 4;
     struct Req {
         void** p;
@@ -532,8 +537,8 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         {(void**)&v.raster_t, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.raster_id, (size_t)(c.raster_capacity ? c.raster_capacity : 1) * 4},
         {(void**)&v.st, sizeof(DevState)},
-        {(void**)&v.woff, (size_t)n->pgrid * PERSIST_WARPS * 4},
-        {(void**)&v.cta_cnt, (size_t)n->pgrid * 4},
+        {(void**)&v.woff, persist_bound * 32 * 4},  // per-warp counts: any persistent grid, <= 32 warps per CTA
+        {(void**)&v.cta_cnt, persist_bound * 4},
         {(void**)&n->cdf_T, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_mod, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_n, (size_t)n->n_modules * 4},
@@ -1286,8 +1291,16 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
         for (size_t k = 0; k < b->waves.size(); ++k) {
             if (key[k] == 0) continue;
             const BatchWave& w = b->waves[k];
-            cudaError_t e = cudaMemsetAsync(&w.meta.bst->bar_count, 0, sizeof(uint32_t), q);
-            if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, q);
+            cudaError_t e;
+            if (w.count == 1) {
+                // a network alone in its wave runs the single-network persistent kernel
+                snn_net* net = b->nets[w.first];
+                e = cudaMemsetAsync(&net->v.st->bar_count, 0, sizeof(uint32_t), q);
+                if (e == cudaSuccess) e = launch_persistent(net->v, key[k], net->pgrid, q);
+            } else {
+                e = cudaMemsetAsync(&w.meta.bst->bar_count, 0, sizeof(uint32_t), q);
+                if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, q);
+            }
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;

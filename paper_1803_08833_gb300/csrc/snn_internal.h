@@ -17,7 +17,10 @@ constexpr uint32_t WTAB = 4096;     // Gaussian efficacy quantiles per populatio
 constexpr uint32_t MAX_ROW = 65535; // longest row of the pairwise rule
 
 constexpr int NEURON_THREADS = 256;
-constexpr int PERSIST_THREADS = 256;                 // threads per CTA of the persistent kernel
+#ifndef SNN_PERSIST_THREADS
+#define SNN_PERSIST_THREADS 256
+#endif
+constexpr int PERSIST_THREADS = SNN_PERSIST_THREADS;  // threads per CTA of the persistent kernel
 constexpr int PERSIST_WARPS = PERSIST_THREADS / 32;
 constexpr uint32_t ERR_BARRIER_TIMEOUT = 1u;         // DevState::err bits
 constexpr uint32_t ERR_ALIGNMENT = 2u;               // a bulk copy address was not 16-byte aligned (skipped)
