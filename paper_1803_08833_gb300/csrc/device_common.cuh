@@ -63,34 +63,61 @@ __device__ __forceinline__ void load_poisson_table(const NetView& v, uint32_t* s
     for (uint32_t k = threadIdx.x; k < (uint32_t)MAX_POIS; k += blockDim.x) s_pois[k] = v.pois32[k];
 }
 
-// State of four consecutive neurons as loaded from memory.
+// State of four consecutive neurons as loaded from memory, with their ring
+// slot and their external drive of the step.
 struct QuadIn {
     int4 I;
     float4 V, C;
     uint32_t R;
+    uint32_t drive;  // byte q: n_ext of neuron q | forced << 7
 };
 
-// Loads neurons base .. base+3 (base a multiple of 4, < Npad) and their ring
-// slot.  The slot was last written by other SMs' L2 reductions: read at L2 (.cg).
-__device__ __forceinline__ QuadIn load_quad(const NetView& v, uint32_t base, uint32_t slot) {
-    QuadIn in;
-    in.I = __ldcg(reinterpret_cast<const int4*>(v.ring + (size_t)slot * v.Npad + base));
-    in.V = *reinterpret_cast<const float4*>(v.V + base);
-    in.C = *reinterpret_cast<const float4*>(v.c + base);
-    in.R = *reinterpret_cast<const uint32_t*>(v.ref + base);
-    return in;
-}
-
-// Integrates the loaded quad for step t, stores the new state, clears the ring
-// slot.  Returns a 4-bit spike mask; adds the external events to `ext` and,
-// under the pairwise rule, the spiking rows' lengths to `rec`.  The
-// four Philox draws are computed first, unconditionally (neurons past N are
-// padding and are not updated), so their dependency chains interleave.
-__device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
-                                                 uint32_t slot, const QuadIn& in, uint32_t& ext, uint64_t& rec) {
+// External drive of neurons base .. base+3 at step t (Philox (i, t, DRIVE)):
+// the Poisson count of word u0 and the imposed spike of word u1, one byte per
+// neuron.  The four draws are computed first, unconditionally (neurons past N
+// are padding and are not updated later), so their dependency chains interleave.
+__device__ __forceinline__ uint32_t quad_drive(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t) {
     U4 u[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[q] = philox4x32_10(base + q, t, TAG_DRIVE, 0u, v.key0, v.key1);
+    uint32_t pk = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t n_ext = poisson_count(s_pois, v.pois_pad, u[q].x);  // < MAX_POIS
+        const uint32_t forced = (uint64_t)u[q].y < v.imposed_thresh ? 0x80u : 0u;
+        pk |= (n_ext | forced) << (8 * q);
+    }
+    return pk;
+}
+
+// V, c, ref of neurons base .. base+3 (base a multiple of 4, < Npad): the
+// part of a quad that does not depend on the step's deliveries.
+__device__ __forceinline__ void load_state(const NetView& v, uint32_t base, QuadIn& in) {
+    in.V = *reinterpret_cast<const float4*>(v.V + base);
+    in.C = *reinterpret_cast<const float4*>(v.c + base);
+    in.R = *reinterpret_cast<const uint32_t*>(v.ref + base);
+}
+
+// The ring slot was last written by other SMs' L2 reductions: read at L2 (.cg).
+__device__ __forceinline__ int4 load_slot(const NetView& v, uint32_t base, uint32_t slot) {
+    return __ldcg(reinterpret_cast<const int4*>(v.ring + (size_t)slot * v.Npad + base));
+}
+
+// Everything a quad needs for step t.
+__device__ __forceinline__ QuadIn load_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
+                                            uint32_t slot) {
+    QuadIn in;
+    in.I = load_slot(v, base, slot);
+    load_state(v, base, in);
+    in.drive = quad_drive(v, s_pois, base, t);
+    return in;
+}
+
+// Integrates the loaded quad, stores the new state, clears the ring slot.
+// Returns a 4-bit spike mask; adds the external events to `ext` and, under
+// the pairwise rule, the spiking rows' lengths to `rec`.
+__device__ __forceinline__ uint32_t compute_quad(const NetView& v, uint32_t base, uint32_t slot, const QuadIn& in,
+                                                 uint32_t& ext, uint64_t& rec) {
     *reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base) = make_int4(0, 0, 0, 0);
     float Vq[4] = {in.V.x, in.V.y, in.V.z, in.V.w};
     float Cq[4] = {in.C.x, in.C.y, in.C.z, in.C.w};
@@ -101,8 +128,9 @@ __device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_
     for (int q = 0; q < 4; ++q) {
         const uint32_t i = base + q;
         uint32_t r = (in.R >> (8 * q)) & 0xFFu;
-        const uint32_t n_ext = poisson_count(s_pois, v.pois_pad, u[q].x);
-        const bool forced = (uint64_t)u[q].y < v.imposed_thresh;
+        const uint32_t dq = in.drive >> (8 * q);
+        const uint32_t n_ext = dq & 0x7Fu;
+        const bool forced = (dq & 0x80u) != 0;
         const int32_t I = (int32_t)((uint32_t)Iq[q] + n_ext * (uint32_t)v.J_ext_fx);
         float Vn = Vq[q], Cn = Cq[q];
         uint32_t rn = r;
@@ -131,7 +159,7 @@ __device__ __forceinline__ uint32_t compute_quad(const NetView& v, const uint32_
 
 __device__ __forceinline__ uint32_t update_quad(const NetView& v, const uint32_t* s_pois, uint32_t base, uint32_t t,
                                                 uint32_t slot, uint32_t& ext, uint64_t& rec) {
-    return compute_quad(v, s_pois, base, t, slot, load_quad(v, base, slot), ext, rec);
+    return compute_quad(v, base, slot, load_quad(v, s_pois, base, t, slot), ext, rec);
 }
 
 // ---------------------------------------------------------------------------

@@ -17,6 +17,42 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// Split barrier: grid_arrive publishes this CTA's arrival (after all its
+// threads' earlier writes), grid_wait waits for `expected` arrivals of the
+// current barrier.  Between the two a CTA may only do work that reads nothing
+// another CTA wrote before the barrier.  `gen` counts this CTA's barriers
+// (thread 0's copy is the one used).
+__device__ inline void grid_arrive(DevState* st, uint32_t& gen) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gen += 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&st->bar_count) : "memory");
+    }
+}
+
+__device__ inline bool grid_wait(DevState* st, uint32_t expected, uint64_t limit_ns, uint32_t gen) {
+    __shared__ int s_okw;
+    if (threadIdx.x == 0) {
+        const uint32_t target = expected * gen;
+        int ok = 1;
+        if ((int32_t)(ld_acquire(&st->bar_count) - target) < 0) {
+            const uint64_t start = global_ns();
+            while ((int32_t)(ld_acquire(&st->bar_count) - target) < 0) {
+                if (global_ns() - start > limit_ns) {
+                    atomicOr(&st->err, ERR_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (ok && ld_acquire(&st->err) != 0) ok = 0;
+        s_okw = ok;
+    }
+    __syncthreads();
+    return s_okw != 0;
+}
+
 // Barrier over `expected` CTAs on the arrival counter of `st` (all CTAs are
 // co-resident: cooperative launch).  The counter starts at 0 for every launch
 // (the host clears it) and only grows: the k-th barrier of the launch is

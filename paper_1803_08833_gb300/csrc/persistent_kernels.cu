@@ -71,22 +71,37 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint32_t done = 0;
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
     if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
+    // The first two chunks of every warp are prepared ahead: their state and
+    // external drive do not depend on other CTAs, so for step t + 1 they are
+    // loaded and drawn while this CTA waits at the barrier that ends step t.
+    QuadIn n1, n2;
+    const uint32_t qa0 = qa + lane, qa1 = qa + 32 + lane;
+    auto prepare = [&](uint32_t tt) {
+        if (qa0 < qb) {
+            load_state(v, qa0 << 2, n1);
+            n1.drive = quad_drive(v, s_pois, qa0 << 2, tt);
+        }
+        if (qa1 < qb) {
+            load_state(v, qa1 << 2, n2);
+            n2.drive = quad_drive(v, s_pois, qa1 << 2, tt);
+        }
+    };
+    prepare(t0);
     for (uint32_t step = 0; step < n_steps; ++step) {
         const uint32_t t = t0 + step;
         const uint32_t slot = t % v.D;
         // ---- phase N: this warp's neurons, 4 per lane, spikes compacted in id order
         uint32_t run = 0;
         // the loads of the next two chunks are in flight while a chunk is integrated
-        QuadIn n1, n2;
-        if (qa + lane < qb) n1 = load_quad(v, (qa + lane) << 2, slot);
-        if (qa + 32 + lane < qb) n2 = load_quad(v, (qa + 32 + lane) << 2, slot);
+        if (qa0 < qb) n1.I = load_slot(v, qa0 << 2, slot);
+        if (qa1 < qb) n2.I = load_slot(v, qa1 << 2, slot);
         for (uint32_t qc = qa; qc < qb; qc += 32) {
             const uint32_t q = qc + lane;
             const QuadIn cur = n1;
             n1 = n2;
-            if (q + 64 < qb) n2 = load_quad(v, (q + 64) << 2, slot);
+            if (q + 64 < qb) n2 = load_quad(v, s_pois, (q + 64) << 2, t, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext, rec);
+            if (q < qb) spk = compute_quad(v, q << 2, slot, cur, ext, rec);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -149,7 +164,9 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         }
         rc += total;
         spikes += total;
-        if (!grid_barrier(v, G, gen)) break;
+        grid_arrive(v.st, gen);
+        if (step + 1 < n_steps) prepare(t + 1);
+        if (!grid_wait(v.st, G + v.barrier_extra, v.wait_limit_ns, gen)) break;
         if (bid == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
             ph_d += now - stamp;

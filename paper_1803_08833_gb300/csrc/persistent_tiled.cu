@@ -120,13 +120,13 @@ __global__ void __launch_bounds__(TILE_THREADS, TILE_MIN_BLOCKS) k_run_steps_til
         // ---- phase N: update, id-ordered warp segments (raster), per-module lists (delivery)
         uint32_t run = 0;
         QuadIn nxt;  // the next chunk's loads are issued before this chunk is integrated
-        if (qa + lane < qb) nxt = load_quad(v, (qa + lane) << 2, slot);
+        if (qa + lane < qb) nxt = load_quad(v, s_pois, (qa + lane) << 2, t, slot);
         for (uint32_t qc = qa; qc < qb; qc += 32) {
             const uint32_t q = qc + lane;
             const QuadIn cur = nxt;
-            if (q + 32 < qb) nxt = load_quad(v, (q + 32) << 2, slot);
+            if (q + 32 < qb) nxt = load_quad(v, s_pois, (q + 32) << 2, t, slot);
             uint32_t spk = 0;
-            if (q < qb) spk = compute_quad(v, s_pois, q << 2, t, slot, cur, ext, rec_unused);
+            if (q < qb) spk = compute_quad(v, q << 2, slot, cur, ext, rec_unused);
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
