@@ -7,7 +7,10 @@
 // stream), (4) the stream with one random reduction per loaded word, (5)
 // reads of short contiguous segments at random places of a region of the
 // table (segment length x region size: the access pattern of a delivery
-// that reads a few dozen synapses per row).
+// that reads a few dozen synapses per row), (6) random reductions whose
+// addresses are restricted to one value of a single address bit chosen per
+// CTA from its SM index (four ways of halving the SMs, bits 7-24): the largest
+// rate difference between the two halves, to look for a die-local placement.
 // Prints one JSON object.  Every address is inside its buffer.
 #include <cuda_runtime.h>
 
@@ -81,6 +84,35 @@ __global__ void k_seg_read(const uint32_t* tab, size_t region, uint32_t L, uint3
         for (int u = 0; u < 8; ++u) acc += v[u][0] ^ v[u][1] ^ v[u][2] ^ v[u][3];
     }
     if (acc == 0x12345678u) sink[0] = acc;
+}
+
+__device__ __forceinline__ uint32_t sm_index() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Random reductions into nwords words whose byte-address bit b equals
+// group(smid) ^ flip; the address is built inside the buffer.
+__global__ void k_red_halves(int* buf, uint32_t nwords, uint32_t b, uint32_t mode, uint32_t flip, uint32_t R,
+                             uint32_t salt) {
+    const uint32_t sm = sm_index();
+    uint32_t g;
+    if (mode == 0)
+        g = sm < 76 ? 0u : 1u;
+    else if (mode == 1)
+        g = sm & 1u;
+    else if (mode == 2)
+        g = (sm >> 1) & 1u;
+    else
+        g = (sm / 38) & 1u;
+    const uint32_t bit = g ^ flip, wb = b - 2, half = nwords >> 1;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    for (uint32_t r = 0; r < R; ++r) {
+        const uint32_t a = mix32(t * 977u + r * 131071u + salt) % half;
+        const uint32_t w = ((a >> wb) << (wb + 1)) | (bit << wb) | (a & ((1u << wb) - 1u));
+        asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(buf + w), "r"(1) : "memory");
+    }
 }
 
 __global__ void k_fill(uint4* tab, size_t n16) {
@@ -169,6 +201,32 @@ int main() {
             first = 0;
         }
     printf("}");
+    // reductions by SM half and address bit (16 M words = 64 MB of the reduction buffer)
+    {
+        const uint32_t nw = 16u << 20;
+        const int hgrid = sms * 8;
+        const double hr = (double)hgrid * 256 * 64;
+        double worst = 0.0, lo = 1e300, hi = 0.0;
+        for (uint32_t mode = 0; mode < 4; ++mode)
+            for (uint32_t bb = 7; bb <= 24; ++bb) {
+                double r2[2];
+                for (uint32_t flip = 0; flip < 2; ++flip) {
+                    k_red_halves<<<hgrid, 256>>>(buf, nw, bb, mode, flip, 64, 1);
+                    cudaEventRecord(a);
+                    for (int it = 0; it < 3; ++it) k_red_halves<<<hgrid, 256>>>(buf, nw, bb, mode, flip, 64, 3 + it);
+                    cudaEventRecord(b);
+                    cudaEventSynchronize(b);
+                    cudaEventElapsedTime(&ms, a, b);
+                    r2[flip] = 3.0 * hr / (ms * 1e-3);
+                    lo = r2[flip] < lo ? r2[flip] : lo;
+                    hi = r2[flip] > hi ? r2[flip] : hi;
+                }
+                const double d = (r2[0] > r2[1] ? r2[0] - r2[1] : r2[1] - r2[0]) / (0.5 * (r2[0] + r2[1]));
+                worst = d > worst ? d : worst;
+            }
+        printf(", \"red_by_sm_half_and_address_bit\": {\"max_rel_difference\": %.4f, \"min_per_s\": %.4g, "
+               "\"max_per_s\": %.4g}", worst, lo, hi);
+    }
     const cudaError_t e = cudaGetLastError();
     printf(", \"status\": \"%s\"}\n", cudaGetErrorString(e));
     return e == cudaSuccess ? 0 : 1;
