@@ -208,10 +208,16 @@ constexpr int DELIVER_UNROLL = SNN_DELIVER_UNROLL;
 // gives the neuron of staged spike j.  Each lane loads 4 consecutive synapses
 // of every task first (16 B of target | delay << 24 words, 16 B f32 or 8 B
 // bf16 weights), then issues the reductions.
-template <bool BF16, int DELIVER_UNROLL = snn::DELIVER_UNROLL>
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// `hook` runs between the loads and the reductions: independent arithmetic
+// placed there overlaps the table loads' latency.
+template <bool BF16, int DELIVER_UNROLL = snn::DELIVER_UNROLL, class Hook = NoHook>
 __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
                                               uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
-                                              uint32_t lane, uint64_t pol) {
+                                              uint32_t lane, uint64_t pol, Hook hook = Hook()) {
     uint4 tg[DELIVER_UNROLL];
     float w[DELIVER_UNROLL][4];
     uint32_t nv[DELIVER_UNROLL];
@@ -245,6 +251,7 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
             }
         }
     }
+    hook();
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
         const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};

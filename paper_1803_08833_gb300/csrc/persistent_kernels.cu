@@ -17,6 +17,8 @@
 
 namespace snn {
 
+constexpr int MAX_DRV = 8;  // chunks per thread whose external drive is drawn ahead
+
 #ifndef SNN_PERSIST_MIN_BLOCKS
 #define SNN_PERSIST_MIN_BLOCKS 1  // one CTA per SM: registers for deep delivery unrolling
 #endif
@@ -71,19 +73,31 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint32_t done = 0;
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
     if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
+    // External drives of step t + 1 are drawn during the delivery of step t,
+    // between each delivery round's table loads and its reductions (the ALU
+    // is idle there), for up to MAX_DRV chunks of each thread; the rest are
+    // drawn in the neuron phase.
+    __shared__ uint32_t s_drv[MAX_DRV * PERSIST_THREADS];
+    const uint32_t nchunk = qa + lane < qb ? (qb - qa - lane + 31) / 32 : 0u;
+    const uint32_t nd_max = nchunk < (uint32_t)MAX_DRV ? nchunk : (uint32_t)MAX_DRV;
+    uint32_t ndrv = 0;  // chunks whose drive for the coming step is in s_drv
+    auto drive_of = [&](uint32_t k, uint32_t tt) -> uint32_t {
+        return k < ndrv ? s_drv[k * PERSIST_THREADS + threadIdx.x]
+                        : quad_drive(v, s_pois, (qa + lane + 32 * k) << 2, tt);
+    };
     // The first two chunks of every warp are prepared ahead: their state and
     // external drive do not depend on other CTAs, so for step t + 1 they are
-    // loaded and drawn while this CTA waits at the barrier that ends step t.
+    // loaded while this CTA waits at the barrier that ends step t.
     QuadIn n1, n2;
     const uint32_t qa0 = qa + lane, qa1 = qa + 32 + lane;
     auto prepare = [&](uint32_t tt) {
         if (qa0 < qb) {
             load_state(v, qa0 << 2, n1);
-            n1.drive = quad_drive(v, s_pois, qa0 << 2, tt);
+            n1.drive = drive_of(0, tt);
         }
         if (qa1 < qb) {
             load_state(v, qa1 << 2, n2);
-            n2.drive = quad_drive(v, s_pois, qa1 << 2, tt);
+            n2.drive = drive_of(1, tt);
         }
     };
     prepare(t0);
@@ -95,11 +109,16 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         // the loads of the next two chunks are in flight while a chunk is integrated
         if (qa0 < qb) n1.I = load_slot(v, qa0 << 2, slot);
         if (qa1 < qb) n2.I = load_slot(v, qa1 << 2, slot);
-        for (uint32_t qc = qa; qc < qb; qc += 32) {
+        uint32_t k = 0;
+        for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
             const uint32_t q = qc + lane;
             const QuadIn cur = n1;
             n1 = n2;
-            if (q + 64 < qb) n2 = load_quad(v, s_pois, (q + 64) << 2, t, slot);
+            if (q + 64 < qb) {
+                n2.I = load_slot(v, (q + 64) << 2, slot);
+                load_state(v, (q + 64) << 2, n2);
+                n2.drive = drive_of(k + 2, t);
+            }
             uint32_t spk = 0;
             if (q < qb) spk = compute_quad(v, q << 2, slot, cur, ext, rec);
             const uint32_t cnt = __popc(spk);
@@ -124,6 +143,15 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         }
 
         // ---- phase D: per-warp offsets (one coalesced pass), delivery, raster
+        ndrv = 0;
+        const bool next = step + 1 < n_steps;
+        auto draw_next = [&]() {
+            if (next && ndrv < nd_max) {
+                s_drv[ndrv * PERSIST_THREADS + threadIdx.x] =
+                    quad_drive(v, s_pois, (qa + lane + 32 * ndrv) << 2, t + 1);
+                ++ndrv;
+            }
+        };
         block_exclusive_scan(v.woff, TW, s_wpre);
         const uint32_t total = s_wpre[TW];
         const uint32_t slot0 = t % v.D;
@@ -150,7 +178,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                     const uint64_t lo = max(ta, (uint64_t)jb * chunks);
                     const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
                     for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
-                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol);
+                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol, draw_next);
                     __syncthreads();
                 }
             }

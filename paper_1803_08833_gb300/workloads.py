@@ -49,13 +49,16 @@ _PAIRWISE = {
     "delay_dist": "exp", "delay_tau_ms": 5.0,
 }
 PAIRWISE_A = {"gauss": 0.05, "exp": 0.03}
-# Inhibitory efficacy that balances the mean recurrent input of an interior
-# neuron: under the per-pair law an excitatory-to-any in-degree of
-# 0.8 (0.8 M) + n_exc sum_r A f(r) (0.64 M + 0.204 M Gaussian, 0.64 M + 1.06 M
-# exponential) against 0.8 (0.2 M) inhibitory inputs; times the 0.2 mV mean
-# excitatory efficacy.  Without it the 1,250-neuron modules run away to the
-# refractory limit (~300 Hz) even at an imposed 7.5 Hz.
-PAIRWISE_W_INH = {"gauss": -1.05, "exp": -2.1}
+# Inhibitory efficacy of the per-pair workloads.  Gaussian: the value that
+# balances the mean recurrent input of an interior neuron (an excitatory
+# in-degree of 0.8 (0.8 M) + n_exc sum_r A f(r) = 0.64 M + 0.204 M against
+# 0.8 (0.2 M) inhibitory inputs, times the 0.2 mV mean excitatory efficacy);
+# with -0.8 mV the 1,250-neuron modules run away to the refractory limit
+# (~300 Hz) even at an imposed 7.5 Hz.  Exponential: balance would be -2.1 mV
+# (0.64 M + 1.06 M excitatory inputs), but that network still runs away at an
+# imposed 35 Hz (261 Hz measured on the 24x24 grid); -2.6 mV keeps it at
+# 36 Hz, inside the paper's 32-38 Hz.
+PAIRWISE_W_INH = {"gauss": -1.05, "exp": -2.6}
 
 
 def pairwise(grid=24, M=1250, lateral="gauss", seed=1, **kw):
