@@ -7,7 +7,10 @@
 // (flow steps 2-4: the spikes' synapses are added into the delay ring, raster
 // entries written), a grid barrier.  Results are identical to the per-step
 // kernels: the same update, the same (step, id) spike order, the same integer
-// sums.
+// sums.  Work that depends on no other CTA is moved off the critical path:
+// the next step's external drive is drawn between delivery loads and their
+// reductions, and the state of each warp's first neuron chunks is loaded
+// between arriving at the step's last barrier and waiting on it.
 //
 // Every barrier wait is bounded by v.wait_limit_ns of %globaltimer: a CTA that
 // waits longer sets ERR_BARRIER_TIMEOUT in the device state and returns, and

@@ -85,3 +85,26 @@ def test_budget_admission_queues_and_rejects(snn):
     with snn.Server(need[0] // 2) as srv:
         with pytest.raises(snn.SnnError, match="SNN_EBUDGET"):
             srv.submit(REQUESTS[0][0], 10)
+
+
+def test_pairwise_requests_in_the_mix(snn):
+    """Requests under the per-pair law (variable-length rows) served together
+    with fixed out-degree ones: the same alone and in the mix, and a pairwise
+    result equal to the oracle."""
+    reqs = [(W.pairwise(grid=4, M=80, seed=21, imposed_rate_hz=25.0), 70),
+            REQUESTS[0],
+            (W.pairwise(grid=6, M=40, lateral="exp", seed=22, weight_dtype="bf16", imposed_rate_hz=35.0), 110)]
+    budget = 8 << 30
+    alone = [_serve(snn, [r], budget)[0] for r in reqs]
+    mixed = _serve(snn, reqs, budget, stagger=True)
+    for a, m in zip(alone, mixed):
+        assert a["status"] == 0 and m["status"] == 0
+        for k in ("steps", "n_spikes", "rec_events", "ext_events", "raster_hash", "state_hash"):
+            assert a[k] == m[k], k
+    cfg, steps = reqs[0]
+    ref = oracle.OracleNet(cfg)
+    ref.step(steps)
+    st, ids = ref.raster()
+    assert mixed[0]["n_spikes"] == len(st) and mixed[0]["rec_events"] == ref.stats()["rec_events"]
+    assert mixed[0]["raster_hash"] == _fnv([st, ids])
+    assert mixed[0]["state_hash"] == _fnv([ref.state()["V"]])
