@@ -532,8 +532,9 @@ def run_precision(snn, args, stream):
 def run_table_one(snn, args, stream):
     """Table I's grids: the 24x24 network under the paper's per-pair law
     (Gaussian at 7.5 Hz, exponential at 35 Hz, bf16) and the 48x48 / 96x96
-    Gaussian grids with the fixed out-degree rule (and 48x48 per-pair): build
-    time, synapses, device memory and persistent-schedule throughput."""
+    Gaussian grids with the fixed out-degree rule (grouped rows) and 48x48
+    per-pair: build time, synapses, device memory, delivery bands and
+    persistent-schedule throughput."""
     import time as _t
 
     import torch
@@ -543,8 +544,10 @@ def run_table_one(snn, args, stream):
         ("pairwise_24x24_exp_bf16", W.pairwise(grid=24, lateral="exp", seed=1, weight_dtype="bf16",
                                                imposed_rate_hz=W.PAPER_RATE_EXP_HZ), 300),
         ("pairwise_48x48_gauss", W.pairwise(grid=48, seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 300),
-        ("fixed_48x48_gauss_k1125", W.gauss_48x48_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 300),
-        ("fixed_96x96_gauss_k1125", W.gauss_96x96_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 100),
+        ("fixed_48x48_gauss_k1125", W.gauss_48x48_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ,
+                                                        table_layout="grouped"), 300),
+        ("fixed_96x96_gauss_k1125", W.gauss_96x96_k1125(seed=1, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ,
+                                                        table_layout="grouped"), 100),
     ]
     out = {}
     for name, cfg, steps in cases:
@@ -555,6 +558,7 @@ def run_table_one(snn, args, stream):
             torch.cuda.synchronize()
             build_ms = (_t.perf_counter() - t0) * 1e3
             syn = int(net.row_lengths().astype("int64").sum())
+            bands = net.set_bands(0)
             net.set_schedule(2)
             net.step(20)
             s0 = net.stats()
@@ -566,7 +570,7 @@ def run_table_one(snn, args, stream):
             ms = a.elapsed_time(b)
             s1 = net.stats()
             ev = s1["rec_events"] - s0["rec_events"]
-            out[name] = {"neurons": net.N, "synapses": syn, "device_gb": round(net.device_bytes / 1e9, 2),
+            out[name] = {"neurons": net.N, "synapses": syn, "device_gb": round(net.device_bytes / 1e9, 2), "bands": bands,
                          "build_ms": round(build_ms, 1), "steps": steps, "us_per_step": ms * 1e3 / steps,
                          "events_per_s": ev / (ms / 1e3),
                          "rate_hz": (s1["n_spikes"] - s0["n_spikes"]) / (net.N * steps) * 1000.0}

@@ -194,7 +194,9 @@ SNN_API snn_status snn_restore(snn_net* net, const void* host_buf, size_t n, voi
  *                   N int32 (row r = inputs of steps t with t % D == r); *t.
  *   snn_set_state:  overwrites V, c, ref (NULL keeps the current values). */
 SNN_API snn_status snn_get_table(snn_net* net, uint32_t* tgt, float* w, uint8_t* d, void* stream);
-/* Grouped layout only: segment starts of rows [first, first + count), each
+/* Segment index (grouped layout; under the pairwise law every row is grouped,
+ * with one entry per stencil offset including those outside the grid and the
+ * row length last): segment starts of rows [first, first + count), each
  * row `*stride` uint16 entries (stride = stencil size + 1): entry j is the
  * position in the row of the first synapse to the source module's j-th
  * in-grid stencil module (stencil order as in snn_get_cdf); entries from the
@@ -250,6 +252,22 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
 SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
+
+/* Banded delivery of schedule 2 (no counterpart in the paper, whose processes
+ * each own a tile of the grid): the target module rows are split into `bands`
+ * equal bands delivered one after another in every step, behind a grid
+ * barrier each, so that one band's columns of the delay ring stay in L2 when
+ * the whole ring does not (Table I's 48x48 and 96x96 grids).  A spike takes
+ * part in the bands its stencil reaches, with the synapses of its row that
+ * target the band (rows must be grouped by target module: table_layout =
+ * SNN_LAYOUT_GROUPED, or the pairwise law).  bands = 0 picks ceil(ring bytes /
+ * (L2 / 2)) for the grouped layout and 1 for the pairwise law (whose dense,
+ * ordered rows reuse the ring in L2 without bands); every network starts with
+ * that choice.
+ * *chosen (may be NULL) receives the count in use.  Results are identical for
+ * every band count.  Synchronises `stream`.  Errors: SNN_EINVAL (bands >
+ * grid_h, or > 1 without a segment index). */
+SNN_API snn_status snn_set_bands(snn_net* net, uint32_t bands, uint32_t* chosen, void* stream);
 
 /* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
  * per delivery block, 2, and 3 if the network has the grouped layout and its

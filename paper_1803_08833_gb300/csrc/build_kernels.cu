@@ -309,16 +309,17 @@ __global__ void __launch_bounds__(256) k_pair_count(BuildView b) {
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
     const uint32_t n = pair_entry<false, false>(b, i, o, 0u, nullptr, nullptr);
-    b.pair_cnt[gid] = (uint16_t)min(n, 0xFFFFu);
+    b.pair_cnt[(size_t)i * (b.pair_n + 1) + o] = (uint16_t)min(n, 0xFFFFu);
 }
 
 // One warp per row: exclusive prefix of the entry counts (in place: the row
-// offset of each entry), the row length and the longest row.
+// offset of each entry; entry pair_n holds the row length, so the row is a
+// segment index of stride pair_n + 1), the row length and the longest row.
 __global__ void __launch_bounds__(256) k_pair_rows(BuildView b) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= b.N) return;  // warp-uniform
-    uint16_t* c = b.pair_cnt + (size_t)i * b.pair_n;
+    uint16_t* c = b.pair_cnt + (size_t)i * (b.pair_n + 1);
     uint32_t run = 0;
     for (uint32_t o0 = 0; o0 < b.pair_n; o0 += 32) {
         const uint32_t o = o0 + lane;
@@ -334,6 +335,7 @@ __global__ void __launch_bounds__(256) k_pair_rows(BuildView b) {
     }
     if (lane == 0) {
         b.row_len[i] = run;
+        c[b.pair_n] = (uint16_t)min(run, 0xFFFFu);
         atomicMax(b.max_len, run);
     }
 }
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __rest
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
-    pair_entry<true, BF16>(b, i, o, b.pair_cnt[gid], td, wout);
+    pair_entry<true, BF16>(b, i, o, b.pair_cnt[(size_t)i * (b.pair_n + 1) + o], td, wout);
 }
 
 __global__ void k_init_state(BuildView b, float* __restrict__ V, float* __restrict__ c,

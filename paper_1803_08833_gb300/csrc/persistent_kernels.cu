@@ -42,14 +42,27 @@ __device__ __forceinline__ uint32_t warp_spike_id(const NetView& v, const uint32
     return __ldcg(v.seg + ((size_t)qa << 2) + (j - s_wpre[lo]));
 }
 
+// The warp (of TW) whose quad range [Q w / TW, Q (w + 1) / TW) holds neuron id
+// (TW if the neuron is past the last quad).
+__device__ __forceinline__ uint32_t warp_of_neuron(uint32_t id, uint32_t Q, uint32_t TW) {
+    const uint32_t qd = id >> 2;
+    if (qd >= Q) return TW;
+    uint32_t w = (uint32_t)((uint64_t)qd * TW / Q);
+    while (w > 0 && (uint32_t)((uint64_t)Q * w / TW) > qd) --w;
+    while (w + 1 < TW && (uint32_t)((uint64_t)Q * (w + 1) / TW) <= qd) ++w;
+    return w;
+}
+
 // n_steps time steps of network v on a group of G CTAs; `bid` is this CTA's
-// index in the group.  smem: G * PERSIST_WARPS + 1 + PERSIST_THREADS words.
+// index in the group.  smem: G * PERSIST_WARPS + 1 + 3 * PERSIST_THREADS words.
 template <bool BF16>
 __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, uint32_t G, uint32_t bid,
                                           uint32_t* smem) {
     const uint32_t TW = G * PERSIST_WARPS;
     uint32_t* s_wpre = smem;          // TW + 1 per-warp spike offsets
     uint32_t* s_id = s_wpre + TW + 1;  // staged spike ids
+    uint32_t* s_lo = s_id + PERSIST_THREADS;  // banded delivery: synapse range of each staged spike
+    uint32_t* s_hi = s_lo + PERSIST_THREADS;
     __shared__ uint32_t s_t0;
     __shared__ unsigned long long s_rc0;
     __shared__ uint32_t s_ext[PERSIST_WARPS];
@@ -158,30 +171,67 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         block_exclusive_scan(v.woff, TW, s_wpre);
         const uint32_t total = s_wpre[TW];
         const uint32_t slot0 = t % v.D;
+        const uint32_t B = v.n_bands > 1 ? v.n_bands : 1u;
+        bool ok = true;
         if (chunks > 0 && total > 0) {
-            const uint64_t n_tasks = (uint64_t)total * chunks;
-            const uint64_t ta = n_tasks * bid / G;
-            const uint64_t tb = n_tasks * (bid + 1) / G;
-            if (ta < tb) {
-                const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
-                for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
+            if (B > 1) {  // raster entries of every spike, independent of the bands
+                for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
+                    const uint64_t r = rc + j;
+                    if (r >= v.raster_cap) break;
+                    v.raster_t[r] = t;
+                    v.raster_id[r] = warp_spike_id(v, s_wpre, TW, Q, j);
+                }
+            }
+            // Banded delivery: the targets are split into B bands of module rows
+            // delivered one after another behind grid barriers, so that one
+            // band's ring columns stay in L2; a spike takes part in the bands its
+            // stencil reaches, with the synapses [lo, hi) of its grouped row that
+            // target the band.
+            for (uint32_t band = 0; band < B; ++band) {
+                if (band > 0 && !grid_barrier(v, G, gen)) {
+                    ok = false;
+                    break;
+                }
+                uint32_t jl = 0, jh = total;  // spikes that can reach this band (warp-granular)
+                if (B > 1) {
+                    const uint2 ir = v.band_ids[band];
+                    jl = s_wpre[warp_of_neuron(ir.x, Q, TW)];
+                    jh = ir.y == 0 ? 0u : s_wpre[min(warp_of_neuron(ir.y - 1, Q, TW) + 1, TW)];
+                    if (jh <= jl) continue;
+                }
+                const uint64_t n_tasks = (uint64_t)(jh - jl) * chunks;
+                const uint64_t ta = n_tasks * bid / G;
+                const uint64_t tb = n_tasks * (bid + 1) / G;
+                if (ta >= tb) continue;
+                const uint32_t j_last = jl + (uint32_t)((tb - 1) / chunks);
+                for (uint32_t jb = jl + (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
                     const uint32_t j = jb + threadIdx.x;
                     if (j <= j_last) {
                         const uint32_t id = warp_spike_id(v, s_wpre, TW, Q, j);
                         s_id[threadIdx.x] = id;
-                        // raster entry of every staged spike (a spike staged by two
-                        // CTAs is written twice with the same value)
-                        const uint64_t r = rc + j;
-                        if (r < v.raster_cap) {
-                            v.raster_t[r] = t;
-                            v.raster_id[r] = id;
+                        if (B == 1) {
+                            // raster entry of every staged spike (a spike staged by two
+                            // CTAs is written twice with the same value)
+                            const uint64_t r = rc + j;
+                            if (r < v.raster_cap) {
+                                v.raster_t[r] = t;
+                                v.raster_id[r] = id;
+                            }
+                        } else {
+                            const uint32_t src = id / v.M;
+                            const uint32_t key = v.band_key_row ? src / v.grid_w : src;
+                            const uint32_t rng = __ldg(v.band_rng + (size_t)key * B + band);
+                            const uint16_t* sg = v.segidx + (size_t)id * v.seg_stride;
+                            s_lo[threadIdx.x] = __ldg(sg + (rng & 0xFFFFu));
+                            s_hi[threadIdx.x] = __ldg(sg + (rng >> 16));
                         }
                     }
                     __syncthreads();
-                    const uint64_t lo = max(ta, (uint64_t)jb * chunks);
-                    const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
+                    const uint64_t lo = max(ta, (uint64_t)(jb - jl) * chunks);
+                    const uint64_t hi = min(tb, (uint64_t)(jb - jl + blockDim.x) * chunks);
                     for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
-                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol, draw_next);
+                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb - jl, slot0, lane, pol,
+                                            B > 1 ? s_lo : nullptr, s_hi, draw_next);
                     __syncthreads();
                 }
             }
@@ -193,6 +243,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                 v.raster_id[r] = warp_spike_id(v, s_wpre, TW, Q, j);
             }
         }
+        if (!ok) break;
         rc += total;
         spikes += total;
         grid_arrive(v.st, gen);
@@ -251,7 +302,7 @@ static const void* persistent_fn(bool bf16) {
 }
 
 static size_t persistent_smem(int grid) {
-    return (size_t)(grid * PERSIST_WARPS + 1 + PERSIST_THREADS) * sizeof(uint32_t);
+    return (size_t)(grid * PERSIST_WARPS + 1 + 3 * PERSIST_THREADS) * sizeof(uint32_t);
 }
 
 // Co-resident grid: occupancy per SM x SMs, with the grid-dependent shared

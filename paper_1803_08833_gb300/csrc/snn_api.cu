@@ -82,6 +82,9 @@ struct snn_net {
     int grid = 0;       // delivery grid of schedules 0 and 1
     int pgrid = 0;      // persistent grid (schedule 2)
     int tgrid = 0;      // tiled persistent grid (schedule 3), 0 if unavailable
+    uint32_t pair_n = 0;              // pairwise law: stencil entries
+    uint2* band_ids_dev = nullptr;    // banded delivery tables
+    uint32_t* band_rng_dev = nullptr;
     int timing_every = 0;
     uint64_t step_calls = 0;
     EventRing ev_deliver, ev_neuron, ev_persist;
@@ -416,6 +419,92 @@ void free_block(snn_net* n, void* p, size_t bytes) {
         }
 }
 
+// Bands of target module rows for the persistent delivery.  bands = 0 picks
+// ceil(ring bytes / (L2 / 2)) (1 when the ring fits) for the grouped layout,
+// and 1 for the pairwise law: its rows hit a module's neurons densely and in
+// order, so even a ring out of L2 is reused there, and bands measured slower
+// (48x48: 8.6e10 against 9.7e10 events/s).  Needs a segment index (grouped
+// layout, or the pairwise law, whose rows are grouped by construction).
+snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
+    const snn_config& c = n->cfg;
+    NetView& v = n->v;
+    if (bands == 0) {
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        const double ring = (double)n->D * n->Npad * 4.0;
+        const double budget = l2 > 0 ? 0.5 * l2 : 32.0 * (1 << 20);
+        bands = v.segidx && c.conn_rule == SNN_RULE_FIXED_K ? (uint32_t)std::ceil(ring / budget) : 1u;
+        bands = std::min<uint32_t>(std::max<uint32_t>(bands, 1u), c.grid_h);
+    }
+    if (bands < 1 || bands > c.grid_h) return fail(SNN_EINVAL, "bands must be in [1, grid_h = %u]", c.grid_h);
+    if (bands > 1 && !v.segidx)
+        return fail(SNN_EINVAL, "banded delivery needs a segment index: table_layout = SNN_LAYOUT_GROUPED or the "
+                                "pairwise law");
+    if (chosen) *chosen = bands;
+    v.n_bands = bands;
+    if (bands == 1) return SNN_OK;
+    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
+    // stencil rows (dy) in segment-index order
+    std::vector<int> sdx, sdy;
+    if (pairwise) {
+        HostTables ht;
+        host_tables(c, &ht);
+        sdx.assign(ht.pdx.begin(), ht.pdx.end());
+        sdy.assign(ht.pdy.begin(), ht.pdy.end());
+    } else {
+        uint32_t R2 = 0;
+        std::vector<int16_t> off = disc_offsets(c, &R2);
+        for (size_t o = 0; o < off.size(); o += 2) {
+            sdx.push_back(off[o]);
+            sdy.push_back(off[o + 1]);
+        }
+    }
+    if (sdy.size() + 1 > 0xFFFFu) return fail(SNN_EINVAL, "stencil too large for banded delivery");
+    int R = 0;
+    for (int dy : sdy) R = std::max(R, std::abs(dy));
+    const uint32_t H = c.grid_h, W = c.grid_w, M = c.neurons_per_module;
+    std::vector<uint32_t> row(bands + 1);
+    for (uint32_t b = 0; b <= bands; ++b) row[b] = (uint32_t)((uint64_t)H * b / bands);
+    std::vector<uint2> ids(bands);
+    for (uint32_t b = 0; b < bands; ++b) {
+        const int lo = std::max(0, (int)row[b] - R), hi = std::min((int)H, (int)row[b + 1] + R);
+        ids[b] = make_uint2((uint32_t)lo * W * M, (uint32_t)hi * W * M);
+    }
+    const uint32_t keys = pairwise ? H : n->n_modules;
+    std::vector<uint32_t> rng((size_t)keys * bands);
+    for (uint32_t k = 0; k < keys; ++k) {
+        const int sx = pairwise ? 0 : (int)(k % W), sy = pairwise ? (int)k : (int)(k / W);
+        // target rows of the entries, in segment-index order (all entries of the
+        // pairwise stencil; the in-grid entries of the fixed law's table)
+        std::vector<int> ty;
+        for (size_t o = 0; o < sdy.size(); ++o) {
+            const int tx = sx + sdx[o], y = sy + sdy[o];
+            if (!pairwise && (tx < 0 || y < 0 || tx >= (int)W || y >= (int)H)) continue;
+            ty.push_back(y);
+        }
+        for (uint32_t b = 0; b < bands; ++b) {
+            uint32_t j0 = 0, j1 = 0;
+            for (int y : ty) {
+                j0 += y < (int)row[b] ? 1u : 0u;
+                j1 += y < (int)row[b + 1] ? 1u : 0u;
+            }
+            rng[(size_t)k * bands + b] = j0 | (j1 << 16);
+        }
+    }
+    if (!n->band_ids_dev) {  // room for the largest band count
+        n->band_ids_dev = (uint2*)dev_alloc(n, (size_t)H * sizeof(uint2));
+        n->band_rng_dev = (uint32_t*)dev_alloc(n, (size_t)keys * H * 4);
+        if (!n->band_ids_dev || !n->band_rng_dev) return fail(SNN_ENOMEM, "device allocation of the band tables failed");
+    }
+    CUDA_TRY(cudaMemcpy(n->band_ids_dev, ids.data(), ids.size() * sizeof(uint2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(n->band_rng_dev, rng.data(), rng.size() * 4, cudaMemcpyHostToDevice));
+    v.band_key_row = pairwise ? 1u : 0u;
+    v.band_ids = n->band_ids_dev;
+    v.band_rng = n->band_rng_dev;
+    return SNN_OK;
+}
+
 snn_status build_impl(snn_net* n, cudaStream_t s) {
     const snn_config& c = n->cfg;
     snn_status st = derive(n);
@@ -483,7 +572,8 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         int32_t* pdx = (int32_t*)temp(ht.pdx.size() * 4);
         int32_t* pdy = (int32_t*)temp(ht.pdy.size() * 4);
         uint64_t* pthr = (uint64_t*)temp(ht.pthr.size() * 8);
-        uint16_t* pcnt = (uint16_t*)temp((size_t)n->N * b.pair_n * 2);
+        // per (neuron, stencil entry) counts, then the rows' segment index (kept)
+        uint16_t* pcnt = (uint16_t*)dev_alloc(n, (size_t)n->N * (b.pair_n + 1) * 2);
         uint32_t* maxl = (uint32_t*)temp(4);
         uint32_t* rlen = (uint32_t*)dev_alloc(n, (size_t)n->N * 4);
         if (!pdx || !pdy || !pthr || !pcnt || !maxl || !rlen)
@@ -509,6 +599,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         v.K = n->K;
         v.Kpad = n->Kpad;
         v.row_len = rlen;
+        n->pair_n = b.pair_n;
     }
     b.K = n->K;
     b.Kpad = n->Kpad;
@@ -554,6 +645,12 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     v.n_modules = n->n_modules;
     v.max_off = n->max_off;
     v.seg_stride = n->max_off + 1;
+    v.grid_w = c.grid_w;
+    v.n_bands = 1;
+    if (pairwise) {  // the pairwise rows are grouped by construction
+        v.segidx = b.pair_cnt;
+        v.seg_stride = b.pair_n + 1;
+    }
     if (grouped) {
         // per-row segment index and, per target module, its incoming (source, stencil index) list
         segidx = (uint16_t*)dev_alloc(n, (size_t)n->N * v.seg_stride * sizeof(uint16_t));
@@ -619,6 +716,11 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     for (auto& tb : temps) free_block(n, tb.first, tb.second);
     n->grid = deliver_default_grid(n->schedule, n->block, n->nb, v.w_bf16 != 0);
     n->tgrid = grouped ? tiled_grid(v) : 0;
+    if (v.segidx) {
+        uint32_t chosen = 0;
+        st = set_bands(n, 0, &chosen);  // banded delivery when the ring outgrows the L2 budget
+        if (st != SNN_OK) return st;
+    }
     return SNN_OK;
 }
 
@@ -895,7 +997,7 @@ snn_status snn_get_segments(snn_net* n, uint32_t first, uint32_t count, uint16_t
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     if (stride) *stride = n->v.seg_stride;
     if (!seg) return SNN_OK;
-    if (!n->v.segidx) return fail(SNN_EINVAL, "the network was not built with the grouped layout");
+    if (!n->v.segidx) return fail(SNN_EINVAL, "the network has no segment index (grouped layout or pairwise law)");
     if ((uint64_t)first + count > n->N) return fail(SNN_EINVAL, "rows out of range");
     cudaStream_t s = (cudaStream_t)stream;
     CUDA_TRY(cudaMemcpyAsync(seg, n->v.segidx + (size_t)first * n->v.seg_stride,
@@ -1005,6 +1107,12 @@ snn_status snn_restore(snn_net* n, const void* host_buf, size_t nbytes, void* st
     CUDA_TRY(cudaMemcpyAsync(n->v.ring, p, D * N * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SNN_OK;
+}
+
+snn_status snn_set_bands(snn_net* n, uint32_t bands, uint32_t* chosen, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight reads the tables
+    return set_bands(n, bands, chosen);
 }
 
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {

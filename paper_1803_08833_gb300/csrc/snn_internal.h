@@ -90,6 +90,13 @@ struct NetView {
     const uint32_t* in_cnt;   // n_modules
     uint32_t* mod_cnt;        // 2 x n_modules spike counts (double-buffered by step parity)
     uint32_t* seg_mod;        // Npad: spikes of module m at [m M, m M + mod_cnt)
+    // banded delivery (schedule 2): the target module rows split into n_bands
+    // bands delivered one after another, each band's ring columns L2-resident
+    uint32_t n_bands;         // 1: no banding
+    uint32_t grid_w;
+    uint32_t band_key_row;    // band_rng is indexed by source module row (1) or source module (0)
+    const uint2* band_ids;    // n_bands: neuron ids [x, y) of the sources whose stencil reaches the band
+    const uint32_t* band_rng; // keys x n_bands: segment-index entries [j0, j1) of the band, j0 | j1 << 16
 };
 
 // Parameters of the construction kernels.
@@ -118,7 +125,7 @@ struct BuildView {
     const int32_t* pair_dx;   // pair_n offsets in (dy, dx) order
     const int32_t* pair_dy;
     const uint64_t* pair_thr; // floor(p 2^32) (2^32: always)
-    uint16_t* pair_cnt;       // N x pair_n: synapses per stencil entry, then their row offsets
+    uint16_t* pair_cnt;       // N x (pair_n + 1): synapses per stencil entry, then their row offsets
     uint32_t* row_len;        // N
     uint32_t* max_len;        // 1: the longest row
 };

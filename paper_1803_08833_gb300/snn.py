@@ -109,6 +109,7 @@ def load():
         "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_set_bands": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
         "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
                               P(ctypes.c_double), vp]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
@@ -367,6 +368,11 @@ class Network:
     def set_schedule(self, schedule: int, block: int = 0):
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
 
+    def set_bands(self, bands: int = 0) -> int:
+        """Banded delivery of schedule 2 (0 = automatic); returns the band count in use."""
+        out = ctypes.c_uint32()
+        check(load().snn_set_bands(self._h, int(bands), ctypes.byref(out), self._s))
+        return out.value
     def autotune(self, trial_steps: int = 20, cache_path=None):
         """Pick the fastest schedule (state unchanged); returns (schedule, block, ms per step)."""
         sc, bl, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()

@@ -437,3 +437,45 @@ def test_slow_wave_grid_tables(snn):
     for m in (0, 47, 48 * 24 + 24, 48 * 48 - 1):
         oT, oTM, _ = oracle.cdf_table(cfg, m)
         assert cnt[m] == len(oT) and np.array_equal(T[m, :len(oT)], oT) and np.array_equal(TM[m, :len(oT)], oTM)
+
+
+BAND_CASES = {
+    "gauss_grouped": lambda: W.small(grid=6, M=100, K=150, seed=31, imposed_rate_hz=30.0, table_layout="grouped"),
+    "exp_grouped_bf16": lambda: dict(W.small(grid=5, M=60, K=200, lateral="exp", seed=32, weight_dtype="bf16",
+                                             imposed_rate_hz=35.0, table_layout="grouped"), grid_h=7),
+    "pairwise_gauss": lambda: W.pairwise(grid=8, M=60, seed=33, imposed_rate_hz=25.0),
+    "pairwise_exp": lambda: W.pairwise(grid=9, M=30, lateral="exp", seed=34, imposed_rate_hz=35.0),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BAND_CASES))
+def test_banded_delivery_bit_exact(snn, name):
+    """Delivery in bands of target module rows (each band's ring columns
+    L2-resident on large grids) gives the oracle's results for every band
+    count."""
+    cfg = BAND_CASES[name]()
+    steps = 80
+    ref = oracle.OracleNet(cfg)
+    ref.step(steps)
+    for bands in (1, 2, 3, cfg["grid_h"]):
+        with snn.Network(cfg, raster_capacity=1 << 22) as net:
+            assert net.set_bands(bands) == bands
+            net.set_schedule(2)
+            net.step(steps // 2)
+            net.step(steps - steps // 2)
+            n = _compare(net, ref)
+    assert n > 200
+
+
+def test_band_choice_and_errors(snn):
+    with snn.Network(W.small(grid=3, M=50, K=20)) as net:  # draw layout: no segment index
+        assert net.set_bands(0) == 1
+        with pytest.raises(snn.SnnError, match="segment index"):
+            net.set_bands(2)
+    with snn.Network(W.small(grid=3, M=50, K=20, table_layout="grouped")) as net:
+        assert net.set_bands(0) == 1  # a 13 KB ring fits in L2
+        with pytest.raises(snn.SnnError, match="grid_h"):
+            net.set_bands(4)
+    # Table I's 48x48 grid: a 242 MB ring is delivered in bands by default
+    with snn.Network(W.gauss_48x48_k1125(seed=2, table_layout="grouped", imposed_rate_hz=7.5)) as net:
+        assert net.set_bands(0) >= 3
