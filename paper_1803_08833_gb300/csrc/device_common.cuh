@@ -213,14 +213,66 @@ struct NoHook {
 };
 
 // `hook` runs between the loads and the reductions: independent arithmetic
-// placed there overlaps the table loads' latency.  With `rlo` / `rhi`, only
-// synapses [rlo, rhi) of each staged spike's row are delivered (one band of
-// targets); otherwise the whole row.
+// placed there overlaps the table loads' latency.
 template <bool BF16, int DELIVER_UNROLL = snn::DELIVER_UNROLL, class Hook = NoHook>
 __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
                                               uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
-                                              uint32_t lane, uint64_t pol, const uint32_t* rlo = nullptr,
-                                              const uint32_t* rhi = nullptr, Hook hook = Hook()) {
+                                              uint32_t lane, uint64_t pol, Hook hook = Hook()) {
+    uint4 tg[DELIVER_UNROLL];
+    float w[DELIVER_UNROLL][4];
+    uint32_t nv[DELIVER_UNROLL];
+#pragma unroll
+    for (int u = 0; u < DELIVER_UNROLL; ++u) {
+        const uint64_t task = tk + (uint64_t)u * tstride;
+        nv[u] = 0;
+        if (task < hi) {
+            const uint32_t jj = (uint32_t)(task / chunks);
+            const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
+            const uint32_t k0 = (ch << 7) + (lane << 2);
+            const uint32_t id = ids[jj - j0];
+            const uint32_t L = v.row_len ? __ldg(v.row_len + id) : v.K;  // row length
+            if (k0 < L) {
+                nv[u] = min(4u, L - k0);
+                const size_t e = (size_t)id * v.Kpad + k0;
+                tg[u] = ld_u4(v.td + e, pol);
+                if (BF16) {
+                    const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
+                    w[u][0] = bf16_lo(wb.x);
+                    w[u][1] = bf16_hi(wb.x);
+                    w[u][2] = bf16_lo(wb.y);
+                    w[u][3] = bf16_hi(wb.y);
+                } else {
+                    const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
+                    w[u][0] = __uint_as_float(wf.x);
+                    w[u][1] = __uint_as_float(wf.y);
+                    w[u][2] = __uint_as_float(wf.z);
+                    w[u][3] = __uint_as_float(wf.w);
+                }
+            }
+        }
+    }
+    hook();
+#pragma unroll
+    for (int u = 0; u < DELIVER_UNROLL; ++u) {
+        const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if ((uint32_t)q < nv[u]) {
+                uint32_t s = slot0 + (tq[q] >> 24);
+                if (s >= v.D) s -= v.D;
+                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, w[u][q]));
+            }
+        }
+    }
+}
+
+// As deliver_tasks, but only synapses [rlo, rhi) of each staged spike's row
+// (the synapses that target one band of module rows).
+template <bool BF16, int DELIVER_UNROLL = snn::DELIVER_UNROLL, class Hook = NoHook>
+__device__ __forceinline__ void deliver_tasks_range(const NetView& v, uint64_t tk, uint64_t tstride, uint64_t hi,
+                                                    uint32_t chunks, const uint32_t* ids, const uint32_t* rlo,
+                                                    const uint32_t* rhi, uint32_t j0, uint32_t slot0, uint32_t lane,
+                                                    uint64_t pol, Hook hook = Hook()) {
     uint4 tg[DELIVER_UNROLL];
     float w[DELIVER_UNROLL][4];
     uint32_t msk[DELIVER_UNROLL];  // bit q: synapse k0 + q is delivered
@@ -232,17 +284,12 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
             const uint32_t jj = (uint32_t)(task / chunks);
             const uint32_t ch = (uint32_t)(task - (uint64_t)jj * chunks);
             const uint32_t k0 = (ch << 7) + (lane << 2);
-            const uint32_t id = ids[jj - j0];
-            uint32_t a = 0, L = v.row_len ? __ldg(v.row_len + id) : v.K;  // synapses [a, L) of the row
-            if (rlo) {
-                a = rlo[jj - j0];
-                L = rhi[jj - j0];
-            }
+            const uint32_t a = rlo[jj - j0], L = rhi[jj - j0];
             if (k0 < L && k0 + 4 > a) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (k0 + q >= a && k0 + q < L) msk[u] |= 1u << q;
-                const size_t e = (size_t)id * v.Kpad + k0;
+                const size_t e = (size_t)ids[jj - j0] * v.Kpad + k0;
                 tg[u] = ld_u4(v.td + e, pol);
                 if (BF16) {
                     const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);

@@ -55,7 +55,7 @@ __device__ __forceinline__ uint32_t warp_of_neuron(uint32_t id, uint32_t Q, uint
 
 // n_steps time steps of network v on a group of G CTAs; `bid` is this CTA's
 // index in the group.  smem: G * PERSIST_WARPS + 1 + 3 * PERSIST_THREADS words.
-template <bool BF16>
+template <bool BF16, bool BANDED>
 __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, uint32_t G, uint32_t bid,
                                           uint32_t* smem) {
     const uint32_t TW = G * PERSIST_WARPS;
@@ -171,45 +171,19 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         block_exclusive_scan(v.woff, TW, s_wpre);
         const uint32_t total = s_wpre[TW];
         const uint32_t slot0 = t % v.D;
-        const uint32_t B = v.n_bands > 1 ? v.n_bands : 1u;
         bool ok = true;
         if (chunks > 0 && total > 0) {
-            if (B > 1) {  // raster entries of every spike, independent of the bands
-                for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
-                    const uint64_t r = rc + j;
-                    if (r >= v.raster_cap) break;
-                    v.raster_t[r] = t;
-                    v.raster_id[r] = warp_spike_id(v, s_wpre, TW, Q, j);
-                }
-            }
-            // Banded delivery: the targets are split into B bands of module rows
-            // delivered one after another behind grid barriers, so that one
-            // band's ring columns stay in L2; a spike takes part in the bands its
-            // stencil reaches, with the synapses [lo, hi) of its grouped row that
-            // target the band.
-            for (uint32_t band = 0; band < B; ++band) {
-                if (band > 0 && !grid_barrier(v, G, gen)) {
-                    ok = false;
-                    break;
-                }
-                uint32_t jl = 0, jh = total;  // spikes that can reach this band (warp-granular)
-                if (B > 1) {
-                    const uint2 ir = v.band_ids[band];
-                    jl = s_wpre[warp_of_neuron(ir.x, Q, TW)];
-                    jh = ir.y == 0 ? 0u : s_wpre[min(warp_of_neuron(ir.y - 1, Q, TW) + 1, TW)];
-                    if (jh <= jl) continue;
-                }
-                const uint64_t n_tasks = (uint64_t)(jh - jl) * chunks;
+            if constexpr (!BANDED) {
+                const uint64_t n_tasks = (uint64_t)total * chunks;
                 const uint64_t ta = n_tasks * bid / G;
                 const uint64_t tb = n_tasks * (bid + 1) / G;
-                if (ta >= tb) continue;
-                const uint32_t j_last = jl + (uint32_t)((tb - 1) / chunks);
-                for (uint32_t jb = jl + (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
-                    const uint32_t j = jb + threadIdx.x;
-                    if (j <= j_last) {
-                        const uint32_t id = warp_spike_id(v, s_wpre, TW, Q, j);
-                        s_id[threadIdx.x] = id;
-                        if (B == 1) {
+                if (ta < tb) {
+                    const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
+                    for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
+                        const uint32_t j = jb + threadIdx.x;
+                        if (j <= j_last) {
+                            const uint32_t id = warp_spike_id(v, s_wpre, TW, Q, j);
+                            s_id[threadIdx.x] = id;
                             // raster entry of every staged spike (a spike staged by two
                             // CTAs is written twice with the same value)
                             const uint64_t r = rc + j;
@@ -217,7 +191,50 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                                 v.raster_t[r] = t;
                                 v.raster_id[r] = id;
                             }
-                        } else {
+                        }
+                        __syncthreads();
+                        const uint64_t lo = max(ta, (uint64_t)jb * chunks);
+                        const uint64_t hi = min(tb, (uint64_t)(jb + blockDim.x) * chunks);
+                        for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
+                            deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb, slot0, lane, pol,
+                                                draw_next);
+                        __syncthreads();
+                    }
+                }
+            } else {
+                // raster entries of every spike, independent of the bands
+                for (uint32_t j = bid * blockDim.x + threadIdx.x; j < total; j += G * blockDim.x) {
+                    const uint64_t r = rc + j;
+                    if (r >= v.raster_cap) break;
+                    v.raster_t[r] = t;
+                    v.raster_id[r] = warp_spike_id(v, s_wpre, TW, Q, j);
+                }
+                // Banded delivery: the targets are split into B bands of module rows
+                // delivered one after another behind grid barriers, so that one
+                // band's ring columns stay in L2; a spike takes part in the bands its
+                // stencil reaches, with the synapses [lo, hi) of its grouped row that
+                // target the band.
+                const uint32_t B = v.n_bands > 1 ? v.n_bands : 1u;
+                for (uint32_t band = 0; band < B; ++band) {
+                    if (band > 0 && !grid_barrier(v, G, gen)) {
+                        ok = false;
+                        break;
+                    }
+                    // spikes that can reach this band (warp-granular superset)
+                    const uint2 ir = v.band_ids[band];
+                    const uint32_t jl = s_wpre[warp_of_neuron(ir.x, Q, TW)];
+                    const uint32_t jh = ir.y == 0 ? 0u : s_wpre[min(warp_of_neuron(ir.y - 1, Q, TW) + 1, TW)];
+                    if (jh <= jl) continue;
+                    const uint64_t n_tasks = (uint64_t)(jh - jl) * chunks;
+                    const uint64_t ta = n_tasks * bid / G;
+                    const uint64_t tb = n_tasks * (bid + 1) / G;
+                    if (ta >= tb) continue;
+                    const uint32_t j_last = jl + (uint32_t)((tb - 1) / chunks);
+                    for (uint32_t jb = jl + (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
+                        const uint32_t j = jb + threadIdx.x;
+                        if (j <= j_last) {
+                            const uint32_t id = warp_spike_id(v, s_wpre, TW, Q, j);
+                            s_id[threadIdx.x] = id;
                             const uint32_t src = id / v.M;
                             const uint32_t key = v.band_key_row ? src / v.grid_w : src;
                             const uint32_t rng = __ldg(v.band_rng + (size_t)key * B + band);
@@ -225,14 +242,14 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                             s_lo[threadIdx.x] = __ldg(sg + (rng & 0xFFFFu));
                             s_hi[threadIdx.x] = __ldg(sg + (rng >> 16));
                         }
+                        __syncthreads();
+                        const uint64_t lo = max(ta, (uint64_t)(jb - jl) * chunks);
+                        const uint64_t hi = min(tb, (uint64_t)(jb - jl + blockDim.x) * chunks);
+                        for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
+                            deliver_tasks_range<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, s_lo, s_hi, jb - jl,
+                                                      slot0, lane, pol, draw_next);
+                        __syncthreads();
                     }
-                    __syncthreads();
-                    const uint64_t lo = max(ta, (uint64_t)(jb - jl) * chunks);
-                    const uint64_t hi = min(tb, (uint64_t)(jb - jl + blockDim.x) * chunks);
-                    for (uint64_t tk = lo + warp; tk < hi; tk += (uint64_t)PERSIST_WARPS * DELIVER_UNROLL)
-                        deliver_tasks<BF16>(v, tk, PERSIST_WARPS, hi, chunks, s_id, jb - jl, slot0, lane, pol,
-                                            B > 1 ? s_lo : nullptr, s_hi, draw_next);
-                    __syncthreads();
                 }
             }
         } else {  // no synapses: the raster alone
@@ -291,14 +308,17 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     }
 }
 
-template <bool BF16>
+// BANDED: the banded delivery of networks whose delay ring outgrows the L2
+// budget (n_bands > 1); the unbanded instance keeps the plain row walk.
+template <bool BF16, bool BANDED>
 __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_steps(NetView v, uint32_t n_steps) {
     extern __shared__ uint32_t smem[];
-    run_steps<BF16>(v, n_steps, gridDim.x, blockIdx.x, smem);
+    run_steps<BF16, BANDED>(v, n_steps, gridDim.x, blockIdx.x, smem);
 }
 
-static const void* persistent_fn(bool bf16) {
-    return bf16 ? (const void*)k_run_steps<true> : (const void*)k_run_steps<false>;
+static const void* persistent_fn(bool bf16, bool banded) {
+    if (banded) return bf16 ? (const void*)k_run_steps<true, true> : (const void*)k_run_steps<false, true>;
+    return bf16 ? (const void*)k_run_steps<true, false> : (const void*)k_run_steps<false, false>;
 }
 
 static size_t persistent_smem(int grid) {
@@ -313,20 +333,22 @@ int persistent_grid(bool bf16) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     for (int per_sm = 8; per_sm >= 1; --per_sm) {
         const int grid = per_sm * sms;
-        int fit = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persistent_fn(bf16), PERSIST_THREADS,
+        int fit = 0, fit_b = 0;  // the grid must fit both instances (bands can change later)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, persistent_fn(bf16, false), PERSIST_THREADS,
+                                                          persistent_smem(grid)) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit_b, persistent_fn(bf16, true), PERSIST_THREADS,
                                                           persistent_smem(grid)) != cudaSuccess) {
             cudaGetLastError();
             continue;
         }
-        if (fit >= per_sm) return grid;
+        if (fit >= per_sm && fit_b >= per_sm) return grid;
     }
     return sms;
 }
 
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {
     const size_t smem = persistent_smem(grid);
-    const void* fn = persistent_fn(v.w_bf16 != 0);
+    const void* fn = persistent_fn(v.w_bf16 != 0, v.n_bands > 1);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
