@@ -479,3 +479,50 @@ def test_band_choice_and_errors(snn):
     # Table I's 48x48 grid: a 242 MB ring is delivered in bands by default
     with snn.Network(W.gauss_48x48_k1125(seed=2, table_layout="grouped", imposed_rate_hz=7.5)) as net:
         assert net.set_bands(0) >= 3
+
+
+def _random_configs(n=8, seed=2026):
+    """Seeded random descriptions spanning both laws, both kernels, both weight
+    types, odd grid shapes, module sizes that are not multiples of the block,
+    uniform and Gaussian efficacies, uniform and exponential delays, rates."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        lateral = "gauss" if rng.random() < 0.5 else "exp"
+        gw, gh = int(rng.integers(1, 7)), int(rng.integers(1, 7))
+        M = int(rng.integers(7, 160))
+        extra = {"grid_h": gh, "weight_dtype": "bf16" if rng.random() < 0.4 else "f32",
+                 "imposed_rate_hz": float(rng.choice([0.0, 7.5, 35.0, 80.0])),
+                 "ext_rate_hz": float(rng.choice([0.0, 1500.0, 4000.0])),
+                 "weight_dist": "gauss" if rng.random() < 0.5 else "uniform",
+                 "delay_dist": "exp" if rng.random() < 0.5 else "uniform",
+                 "d_exc_hi": int(rng.integers(1, 25)), "seed": int(rng.integers(1, 1 << 40)),
+                 "delay_tau_ms": float(rng.uniform(1.0, 10.0)), "w_exc_sd": float(rng.uniform(0.0, 0.1)),
+                 "w_inh_sd": float(rng.uniform(0.0, 0.4))}
+        if rng.random() < 0.5:
+            cfg = W.pairwise(grid=gw, M=M, lateral=lateral, **extra)
+        else:
+            cfg = W.small(grid=gw, M=M, K=int(rng.integers(0, 300)), lateral=lateral, **extra)
+            cfg["table_layout"] = "grouped" if rng.random() < 0.5 else "draw"
+        out.append(cfg)
+    return out
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_random_descriptions_bit_exact(snn, k):
+    """Seeded random descriptions: every schedule that supports the description
+    equals the oracle after 120 steps."""
+    cfg = _random_configs()[k]
+    ref = oracle.OracleNet(cfg)
+    ref.step(120)
+    schedules = [0, 1, 2] + ([3] if cfg.get("table_layout") == "grouped" else [])
+    for schedule in schedules:
+        with snn.Network(cfg, raster_capacity=1 << 22) as net:
+            try:
+                net.set_schedule(schedule)
+            except snn.SnnError:
+                assert schedule == 3  # the tile may not fit in shared memory
+                continue
+            net.step(47)
+            net.step(73)
+            _compare(net, ref)
