@@ -9,7 +9,9 @@
 // counters, a hash of their spike raster and of their final membrane
 // potentials are recorded, their memory is released and the freed budget is
 // available to the next tick.  Requests that arrive while others run join
-// at the next tick.
+// at the next tick.  Retirement is pipelined: a network that finishes in one
+// tick is read back (on a side stream) and released while the next tick's
+// batch runs, so the host work of retiring overlaps the GPU.
 #include "snn.h"
 #include "snn_internal.h"
 
@@ -50,6 +52,7 @@ struct Active {
     uint32_t done;
     uint64_t admit_ns;
     uint64_t bytes;
+    uint64_t finish_ns;  // end of the tick that ran its last chunk
 };
 
 snn_status sfail(snn_status s, const std::string& m) {
@@ -66,9 +69,11 @@ struct snn_server {
     snn_free_fn free_fn = nullptr;
     void* alloc_ctx = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // read-back of finished networks while the next batch runs
     uint64_t next_id = 1;
     std::deque<Pending> queue;
     std::vector<Active> active;
+    std::vector<Active> finished;  // ran their last chunk, not yet retired
     std::vector<snn_request_result> done;
     uint64_t ticks = 0, launches = 0;
     uint64_t rec_events = 0, ext_events = 0, steps = 0;
@@ -120,6 +125,11 @@ snn_status snn_server_create(uint64_t budget_bytes, uint32_t chunk_steps, uint32
     s->free_fn = free_fn;
     s->alloc_ctx = alloc_ctx;
     s->stream = (cudaStream_t)stream;
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return sfail(SNN_ECUDA, "cudaStreamCreateWithFlags failed");
+    }
     *out = s;
     return SNN_OK;
 }
@@ -140,12 +150,16 @@ snn_status snn_server_submit(snn_server* s, const snn_config* cfg, uint32_t n_st
     return SNN_OK;
 }
 
-static snn_status retire(snn_server* s, Active& a, uint64_t t_ns) {
+// Reads back a finished network's counters, raster and final potentials (on
+// the side stream: its last batch has completed) and releases it.
+static snn_status retire(snn_server* s, Active& a) {
+    const uint64_t t_ns = a.finish_ns;
+    cudaStream_t rs = s->side;
     snn_request_result r{};
     r.request_id = a.req.id;
     r.status = SNN_OK;
     snn_stats st{};
-    snn_status e = snn_get_stats(a.net, &st, s->stream);
+    snn_status e = snn_get_stats(a.net, &st, rs);
     if (e != SNN_OK) r.status = e;
     r.steps = st.steps;
     r.n_spikes = st.n_spikes;
@@ -155,7 +169,7 @@ static snn_status retire(snn_server* s, Active& a, uint64_t t_ns) {
     const size_t cap = (size_t)std::min<uint64_t>(st.raster_count, a.req.cfg.raster_capacity);
     std::vector<uint32_t> steps(cap), ids(cap);
     size_t got = 0;
-    e = snn_read_spikes(a.net, steps.data(), ids.data(), cap, &got, s->stream);
+    e = snn_read_spikes(a.net, steps.data(), ids.data(), cap, &got, rs);
     if (e == SNN_EOVERFLOW)
         r.raster_overflow = 1;  // the raster kept its first `cap` spikes; the counters are complete
     else if (e != SNN_OK && r.status == SNN_OK)
@@ -167,7 +181,7 @@ static snn_status retire(snn_server* s, Active& a, uint64_t t_ns) {
     uint32_t N = 0;
     snn_get_dims(a.net, &N, nullptr, nullptr, nullptr);
     std::vector<float> V(N);
-    snn_get_state(a.net, V.data(), nullptr, nullptr, nullptr, nullptr, s->stream);
+    snn_get_state(a.net, V.data(), nullptr, nullptr, nullptr, nullptr, rs);
     r.state_hash = fnv(V.data(), (size_t)N * 4, 1469598103934665603ull);
     r.queue_ms = (double)(a.admit_ns - a.req.arrival_ns) / 1e6;
     r.latency_ms = (double)(t_ns - a.req.arrival_ns) / 1e6;
@@ -198,7 +212,7 @@ snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued
             continue;
         }
         snn_set_schedule(net, 2, 0);
-        Active a{p, net, 0, now_ns(), p.bytes};
+        Active a{p, net, 0, now_ns(), p.bytes, 0};
         s->used += p.bytes;
         s->active.push_back(a);
     }
@@ -214,6 +228,9 @@ snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued
         snn_status e = snn_batch_create(nets.data(), (uint32_t)nets.size(), s->alloc_fn, s->free_fn, s->alloc_ctx, &b);
         if (e != SNN_OK) return e;
         e = snn_batch_step(b, steps.data(), s->stream);
+        // while the batch runs: retire the networks that finished in the previous tick
+        for (auto& a : s->finished) retire(s, a);
+        s->finished.clear();
         if (e == SNN_OK && cudaStreamSynchronize(s->stream) != cudaSuccess)
             e = sfail(SNN_ECUDA, "stream synchronisation after the batch launch failed");
         snn_batch_destroy(b);
@@ -225,14 +242,19 @@ snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued
         for (size_t i = 0; i < s->active.size(); ++i) {
             Active& a = s->active[i];
             a.done += steps[i];
-            if (a.done >= a.req.steps)
-                retire(s, a, t1);
-            else
+            if (a.done >= a.req.steps) {
+                a.finish_ns = t1;
+                s->finished.push_back(a);
+            } else {
                 keep.push_back(a);
+            }
         }
         s->active.swap(keep);
+    } else {
+        for (auto& a : s->finished) retire(s, a);  // nothing runs: retire at once
+        s->finished.clear();
     }
-    if (n_active) *n_active = (uint32_t)s->active.size();
+    if (n_active) *n_active = (uint32_t)(s->active.size() + s->finished.size());
     if (n_queued) *n_queued = (uint32_t)s->queue.size();
     return SNN_OK;
 }
@@ -255,7 +277,7 @@ snn_status snn_server_stats(snn_server* s, snn_server_stats_t* out) {
     out->steps = s->steps;
     out->busy_ns = s->busy_ns;
     out->used_bytes = s->used;
-    out->active = (uint32_t)s->active.size();
+    out->active = (uint32_t)(s->active.size() + s->finished.size());
     out->queued = (uint32_t)s->queue.size();
     return SNN_OK;
 }
@@ -263,6 +285,8 @@ snn_status snn_server_stats(snn_server* s, snn_server_stats_t* out) {
 void snn_server_destroy(snn_server* s) {
     if (!s) return;
     for (auto& a : s->active) snn_destroy(a.net);
+    for (auto& a : s->finished) snn_destroy(a.net);
+    if (s->side) cudaStreamDestroy(s->side);
     delete s;
 }
 
