@@ -261,9 +261,7 @@ SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t bloc
  * part in the bands its stencil reaches, with the synapses of its row that
  * target the band (rows must be grouped by target module: table_layout =
  * SNN_LAYOUT_GROUPED, or the pairwise law).  bands = 0 picks ceil(ring bytes /
- * (L2 / 2)) for the grouped layout and 1 for the pairwise law (whose dense,
- * ordered rows reuse the ring in L2 without bands); every network starts with
- * that choice.
+ * (0.6 L2)); every network starts with that choice.
  * *chosen (may be NULL) receives the count in use.  Results are identical for
  * every band count.  Synchronises `stream`.  Errors: SNN_EINVAL (bands >
  * grid_h, or > 1 without a segment index). */

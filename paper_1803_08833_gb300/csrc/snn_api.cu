@@ -420,11 +420,11 @@ void free_block(snn_net* n, void* p, size_t bytes) {
 }
 
 // Bands of target module rows for the persistent delivery.  bands = 0 picks
-// ceil(ring bytes / (L2 / 2)) (1 when the ring fits) for the grouped layout,
-// and 1 for the pairwise law: its rows hit a module's neurons densely and in
-// order, so even a ring out of L2 is reused there, and bands measured slower
-// (48x48: 8.6e10 against 9.7e10 events/s).  Needs a segment index (grouped
-// layout, or the pairwise law, whose rows are grouped by construction).
+// ceil(ring bytes / (0.6 L2)) (1 when the ring fits): on GB300 the best band
+// counts measured were 4 for the 242 MB ring of the 48x48 grid (60 MB per
+// band) and 12 for the 968 MB ring of the 96x96 grid (81 MB per band).  Needs
+// a segment index (grouped layout, or the pairwise law, whose rows are grouped
+// by construction).
 snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
     const snn_config& c = n->cfg;
     NetView& v = n->v;
@@ -433,8 +433,8 @@ snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
         const double ring = (double)n->D * n->Npad * 4.0;
-        const double budget = l2 > 0 ? 0.5 * l2 : 32.0 * (1 << 20);
-        bands = v.segidx && c.conn_rule == SNN_RULE_FIXED_K ? (uint32_t)std::ceil(ring / budget) : 1u;
+        const double budget = l2 > 0 ? 0.6 * l2 : 32.0 * (1 << 20);
+        bands = v.segidx ? (uint32_t)std::ceil(ring / budget) : 1u;
         bands = std::min<uint32_t>(std::max<uint32_t>(bands, 1u), c.grid_h);
     }
     if (bands < 1 || bands > c.grid_h) return fail(SNN_EINVAL, "bands must be in [1, grid_h = %u]", c.grid_h);
