@@ -140,12 +140,14 @@ typedef void (*snn_free_fn)(void* ptr, void* ctx);
 
 /* Construction phase (Sec. II-A phase 1; Sec. II-B; Sec. III-B).  Validates
  * `cfg`, builds per source module the FP64 cumulative target-module table of
- * the normalised lateral kernel, draws the N*K synapses with counter-based
- * Philox into a row-per-neuron table (uint32 target, f32 or bf16 weight,
- * uint8 delay), and sets the initial state: V = V_th * U[0,1), c = 0, empty
- * delay ring.  Async on `stream` except for argument checks and allocation.
- * Errors: SNN_EINVAL (bad description), SNN_ENOMEM, SNN_ECUDA.  *out is set
- * only on success. */
+ * the normalised lateral kernel, draws the synapses with counter-based Philox
+ * (N*K under the fixed out-degree law; one draw per candidate pair under the
+ * pairwise law, which first counts every row to size the table) into a
+ * row-per-neuron table (one 32-bit word target | delay << 24, f32 or bf16
+ * weight), and sets the initial state: V = V_th * U[0,1), c = 0, empty delay
+ * ring.  Async on `stream` except for argument checks, allocation and the
+ * pairwise law's row count.  Errors: SNN_EINVAL (bad description), SNN_ENOMEM,
+ * SNN_ECUDA.  *out is set only on success. */
 SNN_API snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
                              void* alloc_ctx, void* stream, snn_net** out);
 

@@ -1,6 +1,6 @@
 """Precision of the BF16-weight path against an FP64 oracle run.
 
-Synapse weights stored in bfloat16 (7 B per synapse instead of 9 B); the input
+Synapse weights stored in bfloat16 (6 B per synapse instead of 8 B); the input
 still accumulates in exact int32 fixed point.  Reference: the oracle in FP64
 (double state, double weights, no fixed point).  Workload: the exponential
 long-range model (lambda = 290 um, cut-off 1.2 mm, K = 2,250) on a 6x6-module
