@@ -447,9 +447,8 @@ def run_batched(snn, args, stream):
     def events():
         return sum(n.stats()["rec_events"] for n in nets)
 
-    with snn.Batch(nets, stream=stream) as batch:
-        batch.set_graph(True)
-        batch.step([20] * len(nets))  # warm-up (captures the graph)
+    def timed_batch(batch):
+        batch.step([20] * len(nets))  # warm-up (captures the graph, measures the groups)
         torch.cuda.synchronize()
         e0, l0 = events(), snn.launch_count()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -457,10 +456,16 @@ def run_batched(snn, args, stream):
         batch.step(steps)
         b.record(stream)
         torch.cuda.synchronize()
-        ms_batched = a.elapsed_time(b)
-        ev_batched = events() - e0
-        launches_batched = snn.launch_count() - l0
+        return a.elapsed_time(b), events() - e0, snn.launch_count() - l0
+
+    with snn.Batch(nets, stream=stream) as batch:
+        batch.set_graph(True)
+        ms_batched, ev_batched, launches_batched = timed_batch(batch)
         waves, ring_budget = batch.waves()
+        cta = batch.groups()
+        # the same waves in one global neuron / task space each
+        batch.set_mode("global")
+        ms_global, ev_global, _ = timed_batch(batch)
     # plain: one instance per launch, back to back on the same stream
     e0 = events()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -476,14 +481,19 @@ def run_batched(snn, args, stream):
         n.close()
     v_b = ev_batched / (ms_batched / 1e3)
     v_p = ev_plain / (ms_plain / 1e3)
+    v_g = ev_global / (ms_global / 1e3)
     return {"value": v_b, "unit": UNIT, "plain_value": v_p, "speedup_vs_plain": v_b / v_p,
+            "global_value": v_g, "speedup_vs_global": v_b / v_g,
             "instances": len(inst), "neurons": neurons, "steps_each": args.batch_steps,
-            "ms_batched": ms_batched, "ms_plain": ms_plain, "launches": launches_batched, "waves": waves,
-            "ring_budget_mb": ring_budget / 2 ** 20,
+            "ms_batched": ms_batched, "ms_global": ms_global, "ms_plain": ms_plain, "launches": launches_batched,
+            "waves": waves, "ring_budget_mb": ring_budget / 2 ** 20,
+            "ctas_per_instance": {"min": min(cta), "max": max(cta)},
             "workload": "64 instances, grid side U{4..16} x 1250 neurons, K=1125, Gaussian (even seed, 7.5 Hz) / "
                         "exponential (odd seed, 35 Hz), bf16 weights when seed bit 1 is set, one persistent "
-                        "launch per L2-sized wave of instances, replayed from one CUDA graph, vs one persistent launch per "
-                        "instance"}
+                        "launch per L2-sized wave of instances (each instance on a group of CTAs of its own, "
+                        "sized by a cost model refined by the warm-up's measured group times), replayed from one "
+                        "CUDA graph, vs one persistent launch per instance (plain) and vs the same waves in one "
+                        "global neuron / task space (global)"}
 
 
 def run_precision(snn, args, stream):

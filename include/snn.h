@@ -336,15 +336,25 @@ SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh,
                                         uint32_t* counts, uint32_t* max_offsets, void* stream);
 
 /* ---- Batched execution: many independent networks in one persistent launch.
- * All networks share one global space of neurons and, every step, one global
- * space of delivery tasks, each split evenly over every warp of the grid,
- * with one pair of grid barriers per step for the whole batch; network i is
- * advanced steps[i] time steps per call.  Results are bit-identical to
- * running each network alone.  The nets stay owned by the caller and must
- * outlive the batch; the batch uses their wait limit (smallest) and barrier
- * test knob (largest).  Errors: SNN_EINVAL (NULL or repeated nets, a batch
- * too large), SNN_ENOMEM, SNN_ECUDA.  A barrier wait that runs out marks
- * every network of the batch (their snn_get_stats returns SNN_ETIMEOUT). */
+ * Network i is advanced steps[i] time steps per call.  Results are
+ * bit-identical to running each network alone.  The networks are grouped into
+ * waves (below); a wave of one network runs the persistent kernel of
+ * schedule 2, a wave of several runs one cooperative launch laid out in one
+ * of two ways (snn_batch_set_mode):
+ *  - groups: every network on a group of CTAs of its own (one CTA per SM),
+ *    sized so that the groups finish together by a cost model of a step,
+ *    (a fixed latency plus work over the group's CTAs) refined by the groups'
+ *    measured times of the previous call; each group passes its own
+ *    network's grid barriers with that network's wait limit and test knob;
+ *  - global: all networks share one global space of neurons and, every step,
+ *    one global space of delivery tasks, each split evenly over every warp of
+ *    the grid, with one pair of grid barriers per step for the whole wave,
+ *    using the smallest wait limit and the largest test knob of the wave.
+ * The nets stay owned by the caller and must outlive the batch.  Errors:
+ * SNN_EINVAL (NULL or repeated nets, a batch too large), SNN_ENOMEM,
+ * SNN_ECUDA.  A barrier wait that runs out marks its network (groups) or
+ * every network of the wave (global): their snn_get_stats returns
+ * SNN_ETIMEOUT. */
 typedef struct snn_batch snn_batch;
 SNN_API snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc_fn, snn_free_fn free_fn,
                                     void* alloc_ctx, snn_batch** out);
@@ -362,6 +372,24 @@ SNN_API snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* str
  * all waves (captured on first use, and again when a wave's longest step
  * count changes). */
 SNN_API snn_status snn_batch_set_graph(snn_batch* b, int32_t enable);
+/* Layout of the waves of two or more networks.  SNN_BATCH_GROUPS (the
+ * default): groups, except for a wave with more networks than SMs or with a
+ * banded network (snn_set_bands), which runs global.  SNN_BATCH_GLOBAL:
+ * global always.  Regroups the waves (synchronises the device).  Errors:
+ * SNN_EINVAL (NULL batch, unknown mode). */
+enum { SNN_BATCH_GROUPS = 0, SNN_BATCH_GLOBAL = 1 };
+SNN_API snn_status snn_batch_set_mode(snn_batch* b, int32_t mode);
+/* cta (host array of n): the CTAs each network's group had in the last
+ * snn_batch_step (0: idle, alone in its wave, or in a global wave). */
+SNN_API snn_status snn_batch_groups(snn_batch* b, uint32_t* cta);
+/* The CTA split of a grouped wave, host only: network i runs steps[i] steps
+ * of an estimated work[i] CTA-microseconds each (finite, >= 0), a step on G
+ * CTAs taking 8 us + work[i] / G.  Writes cta[i] (0 iff steps[i] == 0; they
+ * sum to ctas when any network runs) minimising the largest
+ * steps[i] (8 + work[i] / cta[i]).  Errors: SNN_EINVAL (NULL arrays, n = 0,
+ * n > ctas, a work that is negative or not finite). */
+SNN_API snn_status snn_plan_groups(const uint32_t* steps, const double* work, uint32_t n, uint32_t ctas,
+                                   uint32_t* cta);
 /* CUDA-event time (ms) and count of the batch launches since creation. */
 SNN_API snn_status snn_batch_time(snn_batch* b, double* ms, uint64_t* launches);
 SNN_API void snn_batch_destroy(snn_batch* b);

@@ -316,6 +316,38 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     run_steps<BF16, BANDED>(v, n_steps, gridDim.x, blockIdx.x, smem);
 }
 
+// Several independent networks in one cooperative launch, each on a group of
+// its own: CTAs [gcta[k], gcta[k+1]) run network k's steps with the loop
+// above, passing the barriers of the network's own device state, and no group
+// ever waits on another.  A small network's step is bound by its latency
+// chain (two barriers, a scan, dependent loads) rather than by traffic; side
+// by side, the groups overlap those chains instead of paying them one network
+// after another.  Banded networks are not grouped (the host keeps them out).
+__global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_groups(GroupMeta gm) {
+    extern __shared__ uint32_t smem[];
+    __shared__ NetView s_v;
+    __shared__ uint32_t s_k;
+    if (threadIdx.x == 0) {
+        uint32_t k = 0;
+        while (k < gm.n && gm.gcta[k + 1] <= blockIdx.x) ++k;
+        s_k = k;
+    }
+    __syncthreads();
+    const uint32_t k = s_k;
+    if (k >= gm.n) return;  // a CTA past the last group
+    const uint32_t g0 = gm.gcta[k], G = gm.gcta[k + 1] - g0;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(gm.views + k);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_v);
+    for (uint32_t i = threadIdx.x; i < (uint32_t)(sizeof(NetView) / 4); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const uint64_t start = global_ns();
+    if (s_v.w_bf16)
+        run_steps<true, false>(s_v, gm.steps[k], G, blockIdx.x - g0, smem);
+    else
+        run_steps<false, false>(s_v, gm.steps[k], G, blockIdx.x - g0, smem);
+    if (blockIdx.x == g0 && threadIdx.x == 0) gm.gns[k] = global_ns() - start;
+}
+
 static const void* persistent_fn(bool bf16, bool banded) {
     if (banded) return bf16 ? (const void*)k_run_steps<true, true> : (const void*)k_run_steps<false, true>;
     return bf16 ? (const void*)k_run_steps<true, false> : (const void*)k_run_steps<false, false>;
@@ -357,6 +389,34 @@ cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cuda
     uint32_t ns = n_steps;
     void* args[] = {&vv, &ns};
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
+    count_launch(1);
+    return e;
+}
+
+int groups_grid() {
+    int dev = 0, sms = 0, fit = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_groups, PERSIST_THREADS,
+                                                      persistent_smem(sms)) != cudaSuccess ||
+        fit < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return sms;
+}
+
+cudaError_t launch_groups(const GroupMeta& gm, int grid, cudaStream_t s) {
+    const size_t smem = persistent_smem(grid);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)k_run_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    GroupMeta m = gm;
+    void* args[] = {&m};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_run_groups, dim3(grid), dim3(PERSIST_THREADS), args,
+                                                smem, s);
     count_launch(1);
     return e;
 }

@@ -1188,11 +1188,15 @@ void snn_destroy(snn_net* n) {
 // ---------------------------------------------------------------------------
 // Batched execution.
 
-// A wave: networks advanced together by one cooperative launch.
+// A wave: networks advanced together by one cooperative launch, either in
+// one global neuron / task space (meta) or each on a group of CTAs (gmeta).
 struct BatchWave {
     BatchMeta meta{};
+    GroupMeta gmeta{};
     uint32_t first = 0, count = 0;
     int grid = 0;
+    bool grouped = false;
+    uint32_t stage_off = 0;  // grouped: offset of the wave's CTA prefix in the staging words
 };
 
 struct snn_batch {
@@ -1202,8 +1206,17 @@ struct snn_batch {
     void* alloc_ctx = nullptr;
     std::vector<void*> blocks;
     std::vector<BatchWave> waves;
-    uint32_t* d_steps = nullptr;  // steps of every network, in order
-    uint32_t* h_steps = nullptr;  // pinned staging of the per-network steps
+    // staging words: the steps of every network (n), then the CTA prefix of
+    // every grouped wave (count + 1 each, at most 2 n in all)
+    uint32_t* d_steps = nullptr;
+    uint32_t* h_steps = nullptr;  // pinned
+    uint32_t stage_len = 0;
+    uint64_t* d_gns = nullptr;  // per network: ns its group took in the last call
+    uint64_t* h_gns = nullptr;  // pinned copy, read back by the next call
+    std::vector<double> work;   // per network: estimated CTA-microseconds of one step
+    std::vector<uint32_t> last_cta, last_steps;  // CTAs and steps of each network's group in the last call
+    int32_t mode = SNN_BATCH_GROUPS;
+    int ggrid = 0;  // grouped kernel's grid
     uint64_t ring_budget = 0;
     bool use_graph = false;
     bool graph_valid = false;
@@ -1230,9 +1243,98 @@ void* batch_alloc(snn_batch* b, size_t bytes) {
 
 uint64_t ring_bytes(const snn_net* n) { return (uint64_t)n->D * n->Npad * 4; }
 
+// Cost model of a grouped network: one step on G CTAs takes about
+// GROUP_FIXED_US + W / G microseconds, W the step's work in CTA-microseconds.
+// The fixed part is the latency chain of a step (two grid barriers, the
+// offset scan, dependent loads), which a group pays whatever its size.
+constexpr double GROUP_FIXED_US = 8.0;
+constexpr double NEURON_US = 8e-6;  // neuron update on the whole GPU, per neuron
+constexpr double EVENT_US = 1.0 / 1.9e5;  // delivery on the whole GPU, per synaptic event
+
+// Work before any measurement: the imposed spike rate (10 Hz if none) times
+// the out-degree (the longest row under the per-pair law).
+double initial_work(const snn_net* n, int grid) {
+    const double rate = n->cfg.imposed_rate_hz > 0 ? n->cfg.imposed_rate_hz : 10.0;
+    const double events = (double)n->N * rate * n->cfg.dt_ms * 1e-3 * n->K;
+    return std::max(grid, 1) * (NEURON_US * n->N + EVENT_US * events);
+}
+
+// CTAs of a grouped wave: network i (s[i] steps, work W[i]) on G_i CTAs takes
+// about s_i (F + W_i / G_i).  The smallest makespan T whose groups fit in S
+// CTAs is found by bisection (G_i = ceil(s_i W_i / (T - s_i F)), at least 1),
+// then the CTAs left over go one at a time to the group that would finish
+// last.  Idle networks (s_i = 0) get none.  Writes the prefix gcta[0..count].
+void partition_groups(const uint32_t* s, const double* W, uint32_t count, uint32_t S, uint32_t* G, uint32_t* gcta) {
+    const double F = GROUP_FIXED_US;
+    auto need = [&](double T, bool write) {
+        uint64_t total = 0;
+        for (uint32_t i = 0; i < count; ++i) {
+            uint32_t g = 0;
+            if (s[i] > 0) {
+                const double x = s[i] * W[i] / (T - s[i] * F);
+                g = x >= S ? S : std::max(1u, (uint32_t)std::ceil(x));
+            }
+            if (write) G[i] = g;
+            total += g;
+        }
+        return total;
+    };
+    double lo = 0, hi = 0;
+    for (uint32_t i = 0; i < count; ++i) {
+        if (s[i] == 0) continue;
+        lo = std::max(lo, s[i] * (F + W[i] / S));
+        hi = std::max(hi, s[i] * (F + W[i]));
+    }
+    if (hi > 0) {
+        for (int it = 0; it < 60 && hi - lo > 1e-9 * hi; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (need(mid, false) <= S)
+                hi = mid;
+            else
+                lo = mid;
+        }
+    }
+    uint64_t used = need(hi * (1 + 1e-12), true);
+    while (used < S) {
+        uint32_t best = count;
+        double tb = -1;
+        for (uint32_t i = 0; i < count; ++i) {
+            if (G[i] == 0) continue;
+            const double t = s[i] * (F + W[i] / G[i]);
+            if (t > tb) {
+                tb = t;
+                best = i;
+            }
+        }
+        if (best == count) break;
+        ++G[best];
+        ++used;
+    }
+    gcta[0] = 0;
+    for (uint32_t i = 0; i < count; ++i) gcta[i + 1] = gcta[i] + G[i];
+}
+
 // Device tables of one wave: networks [first, first + count).
 snn_status build_wave(snn_batch* b, uint32_t first, uint32_t count, BatchWave* w) {
     snn_net* const* nets = b->nets.data() + first;
+    bool group = b->mode != SNN_BATCH_GLOBAL && count >= 2 && b->ggrid > 0 && count <= (uint32_t)b->ggrid;
+    for (uint32_t i = 0; i < count && group; ++i) group = nets[i]->v.n_bands <= 1;
+    if (group) {
+        NetView* d_views = (NetView*)batch_alloc(b, count * sizeof(NetView));
+        if (!d_views) return fail(SNN_ENOMEM, "batch allocation failed");
+        std::vector<NetView> views(count);
+        for (uint32_t i = 0; i < count; ++i) views[i] = nets[i]->v;
+        CUDA_TRY(cudaMemcpy(d_views, views.data(), count * sizeof(NetView), cudaMemcpyHostToDevice));
+        w->grouped = true;
+        w->first = first;
+        w->count = count;
+        w->grid = b->ggrid;
+        w->gmeta.views = d_views;
+        w->gmeta.steps = b->d_steps + first;
+        w->gmeta.gns = b->d_gns + first;
+        w->gmeta.n = count;
+        return SNN_OK;  // the CTA prefix is placed by the caller
+    }
     uint64_t Qtot = 0, tasks = 0;
     for (uint32_t i = 0; i < count; ++i) {
         Qtot += nets[i]->Npad / 4;
@@ -1329,12 +1431,19 @@ snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     b->ring_budget = l2 > 0 ? (uint64_t)l2 / 2 : (64ull << 20);
-    b->d_steps = (uint32_t*)batch_alloc(b, n * 4);
-    if (!b->d_steps || cudaMallocHost(&b->h_steps, n * 4) != cudaSuccess) {
+    b->d_steps = (uint32_t*)batch_alloc(b, (size_t)n * 12);
+    b->d_gns = (uint64_t*)batch_alloc(b, (size_t)n * 8);
+    if (!b->d_steps || !b->d_gns || cudaMallocHost(&b->h_steps, (size_t)n * 12) != cudaSuccess ||
+        cudaMallocHost(&b->h_gns, (size_t)n * 8) != cudaSuccess) {
         cudaGetLastError();
         snn_batch_destroy(b);
         return fail(SNN_ENOMEM, "batch allocation failed");
     }
+    b->ggrid = groups_grid();
+    b->work.resize(n);
+    b->last_cta.assign(n, 0);
+    b->last_steps.assign(n, 0);
+    for (uint32_t i = 0; i < n; ++i) b->work[i] = initial_work(b->nets[i], b->ggrid);
     snn_status st = snn_batch_set_ring_budget(b, b->ring_budget);
     if (st != SNN_OK) {
         snn_batch_destroy(b);
@@ -1351,6 +1460,7 @@ snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes) {
     b->waves.clear();
     b->graph_valid = false;
     const uint32_t n = (uint32_t)b->nets.size();
+    uint32_t stage = n;  // staging words taken: the steps, then the CTA prefixes
     // waves of consecutive networks whose delay rings fit together in the budget
     for (uint32_t first = 0; first < n;) {
         uint64_t used = ring_bytes(b->nets[first]);
@@ -1360,9 +1470,39 @@ snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes) {
         BatchWave w;
         snn_status st = build_wave(b, first, count, &w);
         if (st != SNN_OK) return st;
+        if (w.grouped) {
+            w.stage_off = stage;
+            w.gmeta.gcta = b->d_steps + stage;
+            stage += count + 1;
+        }
         b->waves.push_back(w);
         first += count;
     }
+    b->stage_len = stage;
+    return SNN_OK;
+}
+
+snn_status snn_batch_set_mode(snn_batch* b, int32_t mode) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    if (mode != SNN_BATCH_GLOBAL && mode != SNN_BATCH_GROUPS)
+        return fail(SNN_EINVAL, "unknown batch mode %d", (int)mode);
+    b->mode = mode;
+    return snn_batch_set_ring_budget(b, b->ring_budget);
+}
+
+snn_status snn_plan_groups(const uint32_t* steps, const double* work, uint32_t n, uint32_t ctas, uint32_t* cta) {
+    if (!steps || !work || !cta || n == 0) return fail(SNN_EINVAL, "steps, work and cta must be set and n > 0");
+    if (n > ctas) return fail(SNN_EINVAL, "more networks (%u) than CTAs (%u)", n, ctas);
+    for (uint32_t i = 0; i < n; ++i)
+        if (!(work[i] >= 0.0) || !std::isfinite(work[i])) return fail(SNN_EINVAL, "work[%u] is not a finite value >= 0", i);
+    std::vector<uint32_t> gcta(n + 1);
+    partition_groups(steps, work, n, ctas, cta, gcta.data());
+    return SNN_OK;
+}
+
+snn_status snn_batch_groups(snn_batch* b, uint32_t* cta) {
+    if (!b || !cta) return fail(SNN_EINVAL, "batch or cta is NULL");
+    std::copy(b->last_cta.begin(), b->last_cta.end(), cta);
     return SNN_OK;
 }
 
@@ -1385,6 +1525,12 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     const uint32_t n = (uint32_t)b->nets.size();
     // the pinned staging buffer may still feed the previous call's copy
     CUDA_TRY(cudaStreamSynchronize(s));
+    // the groups' times of the last call refine the work estimates
+    for (uint32_t i = 0; i < n; ++i) {
+        if (b->last_cta[i] == 0 || b->last_steps[i] == 0) continue;
+        const double us = (double)b->h_gns[i] * 1e-3 / b->last_steps[i];
+        b->work[i] = std::max(us - GROUP_FIXED_US, 0.05) * b->last_cta[i];
+    }
     std::vector<uint32_t> key(b->waves.size(), 0);
     bool any = false;
     for (size_t k = 0; k < b->waves.size(); ++k) {
@@ -1394,7 +1540,15 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     }
     if (!any) return SNN_OK;
     std::copy(steps, steps + n, b->h_steps);
-    CUDA_TRY(cudaMemcpyAsync(b->d_steps, b->h_steps, n * 4, cudaMemcpyHostToDevice, s));
+    std::fill(b->last_cta.begin(), b->last_cta.end(), 0u);
+    for (size_t k = 0; k < b->waves.size(); ++k) {
+        const BatchWave& w = b->waves[k];
+        if (!w.grouped) continue;
+        partition_groups(steps + w.first, b->work.data() + w.first, w.count, (uint32_t)w.grid,
+                         b->last_cta.data() + w.first, b->h_steps + w.stage_off);
+    }
+    std::copy(steps, steps + n, b->last_steps.begin());
+    CUDA_TRY(cudaMemcpyAsync(b->d_steps, b->h_steps, (size_t)b->stage_len * 4, cudaMemcpyHostToDevice, s));
     auto enqueue = [&](cudaStream_t q) -> cudaError_t {
         for (size_t k = 0; k < b->waves.size(); ++k) {
             if (key[k] == 0) continue;
@@ -1405,13 +1559,19 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
                 snn_net* net = b->nets[w.first];
                 e = cudaMemsetAsync(&net->v.st->bar_count, 0, sizeof(uint32_t), q);
                 if (e == cudaSuccess) e = launch_persistent(net->v, key[k], net->pgrid, q);
+            } else if (w.grouped) {
+                e = cudaSuccess;
+                for (uint32_t i = w.first; i < w.first + w.count && e == cudaSuccess; ++i)
+                    e = cudaMemsetAsync(&b->nets[i]->v.st->bar_count, 0, sizeof(uint32_t), q);
+                if (e == cudaSuccess) e = launch_groups(w.gmeta, w.grid, q);
             } else {
                 e = cudaMemsetAsync(&w.meta.bst->bar_count, 0, sizeof(uint32_t), q);
                 if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, q);
             }
             if (e != cudaSuccess) return e;
         }
-        return cudaSuccess;
+        // the groups' times, for the next call's partition
+        return cudaMemcpyAsync(b->h_gns, b->d_gns, b->nets.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, q);
     };
     int slot = 0;
     snn_status st = timed_begin(b->ev, s, &slot);
@@ -1460,6 +1620,7 @@ void snn_batch_destroy(snn_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->h_steps) cudaFreeHost(b->h_steps);
+    if (b->h_gns) cudaFreeHost(b->h_gns);
     destroy_events(b->ev);
     for (void* p : b->blocks) {
         if (b->free_fn)

@@ -158,6 +158,16 @@ struct BatchMeta {
 };
 int batch_grid(uint32_t n, uint32_t n_seg_bound);
 cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, cudaStream_t s);
+// Grouped batched execution: network k on its own CTAs [gcta[k], gcta[k+1]).
+struct GroupMeta {
+    const NetView* views;   // n
+    const uint32_t* gcta;   // n + 1: CTA prefix of the groups (an empty group: the network is idle)
+    const uint32_t* steps;  // n: steps of this launch per network
+    uint64_t* gns;          // n: %globaltimer ns each group took (written by its first CTA)
+    uint32_t n;
+};
+int groups_grid();  // co-resident grid of the grouped kernel (one CTA per SM)
+cudaError_t launch_groups(const GroupMeta& gm, int grid, cudaStream_t s);
 int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);

@@ -124,6 +124,9 @@ def load():
         "snn_batch_set_graph": (st, [vp, ctypes.c_int32]),
         "snn_batch_waves": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint64)]),
         "snn_batch_set_ring_budget": (st, [vp, ctypes.c_uint64]),
+        "snn_batch_set_mode": (st, [vp, ctypes.c_int32]),
+        "snn_batch_groups": (st, [vp, P(ctypes.c_uint32)]),
+        "snn_plan_groups": (st, [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp]),
         "snn_batch_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64)]),
         "snn_batch_destroy": (None, [vp]),
         "snn_estimate_bytes": (ctypes.c_uint64, [P(SnnConfig)]),
@@ -435,6 +438,19 @@ class Batch:
     def set_ring_budget(self, nbytes: int):
         check(load().snn_batch_set_ring_budget(self._h, int(nbytes)))
 
+    def set_mode(self, mode: str):
+        """'groups' (default: every network of a wave on CTAs of its own) or
+        'global' (one neuron and task space for the whole wave)."""
+        check(load().snn_batch_set_mode(self._h, {"groups": 0, "global": 1}[mode]))
+
+    def groups(self):
+        """CTAs of each network's group in the last step call (0: idle, alone
+        in its wave, or in a global wave)."""
+        n = len(self.nets)
+        arr = (ctypes.c_uint32 * n)()
+        check(load().snn_batch_groups(self._h, arr))
+        return list(arr)
+
     def waves(self):
         """(number of launches per step call, ring budget in bytes)."""
         w, r = ctypes.c_uint32(), ctypes.c_uint64()
@@ -467,6 +483,18 @@ class Batch:
 def now_ns() -> int:
     """The library's host monotonic clock (time base of request arrivals)."""
     return int(load().snn_now_ns())
+
+
+def plan_groups(steps, work, ctas: int):
+    """CTAs per network of a grouped batch wave (snn_plan_groups): steps and
+    estimated work in CTA-microseconds per step, one per network."""
+    s = np.ascontiguousarray(steps, dtype=np.uint32)
+    w = np.ascontiguousarray(work, dtype=np.float64)
+    if s.shape != w.shape:
+        raise ValueError("steps and work differ in length")
+    out = np.zeros(len(s), np.uint32)
+    check(load().snn_plan_groups(_ptr(s), _ptr(w), len(s), int(ctas), _ptr(out)))
+    return out
 
 
 def estimate_bytes(cfg: dict, raster_capacity: int = 0) -> int:

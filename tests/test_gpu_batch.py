@@ -44,12 +44,14 @@ def _check(net, ref):
     assert s["n_spikes"] == ref.stats()["spikes"] and s["ext_events"] == ref.stats()["ext_events"]
 
 
+@pytest.mark.parametrize("mode", ["groups", "global"])
 @pytest.mark.parametrize("graph,waves", [(False, 1), (True, 1), (True, 3)])
-def test_batch_equals_each_network_alone(snn, graph, waves):
+def test_batch_equals_each_network_alone(snn, graph, waves, mode):
     cfgs = _cases()
     nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
     refs = [oracle.OracleNet(c) for c in cfgs]
     with snn.Batch(nets) as batch:
+        batch.set_mode(mode)
         batch.set_graph(graph)
         if waves > 1:  # a ring budget that gives every network its own launch
             batch.set_ring_budget(1)
@@ -81,15 +83,64 @@ def test_batch_of_one_equals_the_persistent_schedule(snn):
 
 
 def test_batch_barrier_wait_runs_out(snn):
+    """Global wave: one pair of barriers for the wave, so a barrier that cannot
+    be passed (a test knob expecting one arrival too many) stops every
+    network of the wave."""
     cfgs = _cases()[:2]
     nets = [snn.Network(c) for c in cfgs]
     nets[0].set_wait_limit(2_000_000)
     nets[1].set_barrier_extra(1)
     with snn.Batch(nets) as batch:
+        batch.set_mode("global")
         batch.step([5, 5])
     for n in nets:
         with pytest.raises(snn.SnnError, match="SNN_ETIMEOUT"):
             n.stats()
+        n.close()
+
+
+def test_grouped_barrier_wait_runs_out_in_its_group_only(snn):
+    """Grouped wave: each network passes its own barriers, so only the network
+    whose barrier cannot be passed reports the timeout; the others run on and
+    still equal the oracle."""
+    cfgs = _cases()[:3]
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    for n in nets:
+        n.set_wait_limit(2_000_000)
+    nets[1].set_barrier_extra(1)
+    with snn.Batch(nets) as batch:
+        batch.step([30, 30, 30])
+        assert all(g > 0 for g in batch.groups())
+    with pytest.raises(snn.SnnError, match="SNN_ETIMEOUT"):
+        nets[1].stats()
+    for i in (0, 2):
+        refs[i].step(30)
+        _check(nets[i], refs[i])
+    for n in nets:
+        n.close()
+
+
+def test_groups_cover_the_active_networks(snn):
+    """Every network that runs gets a group, idle ones none, and the groups
+    of a wave never take more CTAs than the grid (one per SM); the split
+    follows the work (a network 16x larger gets more CTAs)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cfgs = [W.small(grid=8, M=1250, K=1125, seed=s, imposed_rate_hz=20.0) for s in range(3)]
+    cfgs.append(W.small(grid=2, M=1250, K=1125, seed=9, imposed_rate_hz=20.0))
+    nets = [snn.Network(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_graph(True)
+        for steps in ([20, 20, 0, 20], [40, 40, 40, 40], [40, 40, 40, 40]):
+            batch.step(steps)
+            g = batch.groups()
+            assert all((x > 0) == (s > 0) for x, s in zip(g, steps)) and sum(g) <= sms
+        assert g[3] < min(g[:3])
+        batch.set_mode("global")
+        batch.step([5, 5, 5, 5])
+        assert batch.groups() == [0, 0, 0, 0]
+    for n in nets:
         n.close()
 
 

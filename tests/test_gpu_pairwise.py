@@ -95,13 +95,15 @@ def test_schedule_3_is_refused(snn):
             net.set_schedule(3)
 
 
-def test_batch_mixes_rules(snn):
+@pytest.mark.parametrize("mode", ["groups", "global"])
+def test_batch_mixes_rules(snn, mode):
     cfgs = [W.pairwise(grid=4, M=100, seed=11, imposed_rate_hz=20.0),
             W.small(grid=3, M=100, K=90, seed=12, imposed_rate_hz=20.0),
             W.pairwise(grid=7, M=30, lateral="exp", seed=13, weight_dtype="bf16", imposed_rate_hz=35.0)]
     nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
     refs = [oracle.OracleNet(c) for c in cfgs]
     with snn.Batch(nets) as batch:
+        batch.set_mode(mode)
         batch.set_graph(True)
         for steps in ([40, 40, 40], [25, 0, 60]):
             batch.step(steps)
