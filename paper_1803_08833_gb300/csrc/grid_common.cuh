@@ -93,11 +93,25 @@ __device__ inline bool grid_barrier(const NetView& v, uint32_t G, uint32_t& gen)
 }
 
 // Exclusive prefix of cnt[0..n) (global, written by other CTAs) into
-// out[0..n] (shared), out[n] = total: one coalesced pass of loads, then the
-// scan in shared memory.
+// out[0..n] (shared), out[n] = total: coalesced loads, eight per thread in
+// flight before the first is stored (one L2 round trip for n <= 8 x threads;
+// a loop that stores each load before issuing the next pays one per pass),
+// then the scan in shared memory.
 __device__ inline void block_scan_inplace(uint32_t* s, uint32_t n);
 __device__ inline void block_exclusive_scan(const uint32_t* cnt, uint32_t n, uint32_t* out) {
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) out[i] = __ldcg(cnt + i);
+    for (uint32_t base = 0; base < n; base += 8 * blockDim.x) {
+        uint32_t x[8];
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            const uint32_t i = base + k * blockDim.x + threadIdx.x;
+            x[k] = i < n ? __ldcg(cnt + i) : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 8; ++k) {
+            const uint32_t i = base + k * blockDim.x + threadIdx.x;
+            if (i < n) out[i] = x[k];
+        }
+    }
     __syncthreads();
     block_scan_inplace(out, n);
 }
