@@ -14,9 +14,10 @@ e2e         the same metric for whole jobs through the public API: build the
             network from the host description, simulate 10,000 steps reading
             the raster into pinned host memory every 1,000 steps, destroy.
 roofline    the persistent kernel: algorithmic bytes (8 B per recurrent event:
-            one 32-bit target | delay word + f32 weight; 26 B per neuron and
-            step) / its CUDA-event time, against the measured HBM copy
-            bandwidth.
+            one 32-bit target | delay word + f32 weight; 8 B per neuron and
+            step: its ring slot read and cleared, the neuron state staying on
+            chip through a launch) / its CUDA-event time, against the
+            measured HBM copy bandwidth.
 cpu_baseline  the oracle (single-threaded C) on a bounded sample of the same
             model, simulation phase only, like `value`.
 
@@ -40,14 +41,12 @@ sys.path.insert(0, ROOT)
 METRIC = "synaptic events/s on 1 GB300, % of HBM roofline; served p50/p99 latency"
 UNIT = "synaptic events/s"
 BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
-# neuron update: V, c (f32) and ref (u8) read and written, ring slot read and cleared
-NEURON_BYTES = 2 * (4 + 4 + 1) + 2 * 4
+# neuron update: the ring slot read and cleared; V, c (f32) and ref (u8) stay in
+# shared memory for the whole launch (read and written back once per launch)
+NEURON_BYTES = 2 * 4
 TIMESTEPS_PER_STEP = 1000
 JOB_TIMESTEPS = 10000
 
-# DRAM traffic of one delivery launch from an ncu capture of the same kernel
-# source (dram__bytes_read.sum + dram__bytes_write.sum, per recurrent event).
-# Reported only while the kernel source is unchanged since the capture.
 # DRAM bytes (read + write) of the persistent kernel per recurrent event, from
 # one ncu capture of a smaller case of the same model (profiles/), valid only
 # for the kernel sources it was taken on.

@@ -113,11 +113,17 @@ __device__ __forceinline__ QuadIn load_quad(const NetView& v, const uint32_t* s_
     return in;
 }
 
-// Integrates the loaded quad, stores the new state, clears the ring slot.
-// Returns a 4-bit spike mask; adds the external events to `ext` and, under
-// the pairwise rule, the spiking rows' lengths to `rec`.
-__device__ __forceinline__ uint32_t compute_quad(const NetView& v, uint32_t base, uint32_t slot, const QuadIn& in,
-                                                 uint32_t& ext, uint64_t& rec) {
+// New state of a quad, before it is stored.
+struct QuadOut {
+    float4 V, C;
+    uint32_t R;
+};
+
+// Integrates the loaded quad into `out` and clears the ring slot.  Returns a
+// 4-bit spike mask; adds the external events to `ext` and, under the pairwise
+// rule, the spiking rows' lengths to `rec`.
+__device__ __forceinline__ uint32_t integrate_quad(const NetView& v, uint32_t base, uint32_t slot, const QuadIn& in,
+                                                   uint32_t& ext, uint64_t& rec, QuadOut& out) {
     *reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base) = make_int4(0, 0, 0, 0);
     float Vq[4] = {in.V.x, in.V.y, in.V.z, in.V.w};
     float Cq[4] = {in.C.x, in.C.y, in.C.z, in.C.w};
@@ -146,14 +152,29 @@ __device__ __forceinline__ uint32_t compute_quad(const NetView& v, uint32_t base
         mi += 1;
         if (mi >= v.M) mi = 0;
     }
-    *reinterpret_cast<float4*>(v.V + base) = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
-    *reinterpret_cast<float4*>(v.c + base) = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
-    *reinterpret_cast<uint32_t*>(v.ref + base) = Rout;
+    out.V = make_float4(Vq[0], Vq[1], Vq[2], Vq[3]);
+    out.C = make_float4(Cq[0], Cq[1], Cq[2], Cq[3]);
+    out.R = Rout;
     if (v.row_len != nullptr && spk != 0) {
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (spk & (1u << q)) rec += __ldg(v.row_len + base + q);
     }
+    return spk;
+}
+
+__device__ __forceinline__ void store_state(const NetView& v, uint32_t base, const QuadOut& o) {
+    *reinterpret_cast<float4*>(v.V + base) = o.V;
+    *reinterpret_cast<float4*>(v.c + base) = o.C;
+    *reinterpret_cast<uint32_t*>(v.ref + base) = o.R;
+}
+
+// Integrates the loaded quad, stores the new state, clears the ring slot.
+__device__ __forceinline__ uint32_t compute_quad(const NetView& v, uint32_t base, uint32_t slot, const QuadIn& in,
+                                                 uint32_t& ext, uint64_t& rec) {
+    QuadOut o;
+    const uint32_t spk = integrate_quad(v, base, slot, in, ext, rec, o);
+    store_state(v, base, o);
     return spk;
 }
 

@@ -18,9 +18,13 @@
 // SNN_ETIMEOUT.
 #include "grid_common.cuh"
 
+#include <algorithm>
+
 namespace snn {
 
 constexpr int MAX_DRV = 8;  // chunks per thread whose external drive is drawn ahead
+constexpr uint32_t REBALANCE_STEPS = 32;  // steps between re-weightings of the delivery split
+constexpr uint32_t MIN_SPEED_TASKS = 64;   // tasks a CTA must have delivered for its speed to count
 
 #ifndef SNN_PERSIST_MIN_BLOCKS
 #define SNN_PERSIST_MIN_BLOCKS 1  // one CTA per SM: registers for deep delivery unrolling
@@ -53,8 +57,58 @@ __device__ __forceinline__ uint32_t warp_of_neuron(uint32_t id, uint32_t Q, uint
     return w;
 }
 
+// Dynamic shared memory of run_steps on G CTAs: per-warp offsets (TW + 1),
+// staged ids and band ranges (3 x threads), split weights (G + 1), padded to
+// 16 B; then the resident state (36 B per quad) when there is one.
+__host__ __device__ constexpr uint32_t state_offset_words(uint32_t G) {
+    return (G * (PERSIST_WARPS + 1) + 2 + 3 * PERSIST_THREADS + 3) & ~3u;
+}
+
+// Delivery split weights: the CTAs' measured speeds (v.cta_speed, G words; 0
+// = not measured, replaced by the mean of the measured ones) as an inclusive
+// prefix s_wp[0..G], s_wp[0] = 0.  Every CTA computes the same prefix from the
+// same words, so the task ranges still partition the task space.
+__device__ inline void load_split_weights(const NetView& v, uint32_t G, uint32_t* s_wp) {
+    __shared__ unsigned long long s_sum;
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) {
+        s_sum = 0;
+        s_cnt = 0;
+    }
+    __syncthreads();
+    unsigned long long sum = 0;
+    uint32_t cnt = 0;
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x) {
+        const uint32_t w = __ldcg(v.cta_speed + i);
+        s_wp[i] = w;
+        sum += w;
+        cnt += w != 0;
+    }
+    if (sum) atomicAdd(&s_sum, sum);
+    if (cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    const uint32_t mean = s_cnt ? (uint32_t)(s_sum / s_cnt) : 1u;
+    for (uint32_t i = threadIdx.x; i < G; i += blockDim.x)
+        if (s_wp[i] == 0) s_wp[i] = mean > 0 ? mean : 1u;
+    __syncthreads();
+    block_scan_inplace(s_wp, G);
+}
+
 // n_steps time steps of network v on a group of G CTAs; `bid` is this CTA's
-// index in the group.  smem: G * PERSIST_WARPS + 1 + 3 * PERSIST_THREADS words.
+// index in the group.  smem: persistent_smem(G) bytes, then 36 B per quad of
+// resident neuron state for up to v.res_quads quads.
+//
+// Resident state: a CTA's neurons never change owner during a launch, so a
+// CTA whose quads fit (at most v.res_quads) copies their V, c and ref into
+// shared memory at the start, integrates them there, and writes them back at
+// the end; its neuron phase then reads only the ring slot and the drive from
+// memory.  A CTA whose quads do not fit keeps them in global memory.
+//
+// The delivery tasks of a step are split over the CTAs in proportion to each
+// CTA's measured delivery speed (tasks per ns over the last REBALANCE_STEPS
+// steps; equal shares until the first measurement): the SMs of one GB300 do
+// not deliver equally fast (a stable 15 % spread between SMs at the same
+// task count), and with an even split every step waits for the slowest.
 template <bool BF16, bool BANDED>
 __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, uint32_t G, uint32_t bid,
                                           uint32_t* smem) {
@@ -63,6 +117,11 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint32_t* s_id = s_wpre + TW + 1;  // staged spike ids
     uint32_t* s_lo = s_id + PERSIST_THREADS;  // banded delivery: synapse range of each staged spike
     uint32_t* s_hi = s_lo + PERSIST_THREADS;
+    uint32_t* s_wp = s_hi + PERSIST_THREADS;  // G + 1: prefix of the delivery split weights
+    for (uint32_t i = threadIdx.x; i <= G; i += blockDim.x) s_wp[i] = i;
+    float4* s_V = reinterpret_cast<float4*>(smem + state_offset_words(G));  // resident state
+    float4* s_C = s_V + v.res_quads;
+    uint32_t* s_R = reinterpret_cast<uint32_t*>(s_C + v.res_quads);
     __shared__ uint32_t s_t0;
     __shared__ unsigned long long s_rc0;
     __shared__ uint32_t s_ext[PERSIST_WARPS];
@@ -81,6 +140,27 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     const uint32_t qa = (uint32_t)((uint64_t)Q * wg / TW);
     const uint32_t qb = (uint32_t)((uint64_t)Q * (wg + 1) / TW);
     const uint64_t pol = evict_first_policy();
+    // this CTA's quads (the union of its warps' ranges)
+    const uint32_t cq0 = (uint32_t)((uint64_t)Q * (bid * PERSIST_WARPS) / TW);
+    const uint32_t cq1 = (uint32_t)((uint64_t)Q * (bid * PERSIST_WARPS + PERSIST_WARPS) / TW);
+    const bool res = cq1 - cq0 <= v.res_quads;  // this CTA's state fits the launch's shared memory
+    if (res) {
+        for (uint32_t q = cq0 + threadIdx.x; q < cq1; q += blockDim.x) {
+            s_V[q - cq0] = *reinterpret_cast<const float4*>(v.V + ((size_t)q << 2));
+            s_C[q - cq0] = *reinterpret_cast<const float4*>(v.c + ((size_t)q << 2));
+            s_R[q - cq0] = *reinterpret_cast<const uint32_t*>(v.ref + ((size_t)q << 2));
+        }
+        __syncthreads();
+    }
+    auto load_st = [&](uint32_t q, QuadIn& in) {
+        if (res) {
+            in.V = s_V[q - cq0];
+            in.C = s_C[q - cq0];
+            in.R = s_R[q - cq0];
+        } else {
+            load_state(v, q << 2, in);
+        }
+    };
     const uint32_t chunks = (v.K + 127) >> 7;
     uint64_t rc = s_rc0;
     uint64_t spikes = 0;
@@ -88,6 +168,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     uint64_t rec = 0;  // pairwise rule: row lengths of this thread's spikes
     uint32_t done = 0;
     uint64_t ph_n = 0, ph_d = 0, stamp = 0;
+    uint64_t d_ns = 0, d_tasks = 0, d_t0 = 0;  // thread 0: this CTA's delivery time and tasks since the last weighting
     if (bid == 0 && threadIdx.x == 0) stamp = global_ns();
     // External drives of step t + 1 are drawn during the delivery of step t,
     // between each delivery round's table loads and its reductions (the ALU
@@ -108,11 +189,11 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
     const uint32_t qa0 = qa + lane, qa1 = qa + 32 + lane;
     auto prepare = [&](uint32_t tt) {
         if (qa0 < qb) {
-            load_state(v, qa0 << 2, n1);
+            load_st(qa0, n1);
             n1.drive = drive_of(0, tt);
         }
         if (qa1 < qb) {
-            load_state(v, qa1 << 2, n2);
+            load_st(qa1, n2);
             n2.drive = drive_of(1, tt);
         }
     };
@@ -132,11 +213,21 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             n1 = n2;
             if (q + 64 < qb) {
                 n2.I = load_slot(v, (q + 64) << 2, slot);
-                load_state(v, (q + 64) << 2, n2);
+                load_st(q + 64, n2);
                 n2.drive = drive_of(k + 2, t);
             }
             uint32_t spk = 0;
-            if (q < qb) spk = compute_quad(v, q << 2, slot, cur, ext, rec);
+            if (q < qb) {
+                QuadOut o;
+                spk = integrate_quad(v, q << 2, slot, cur, ext, rec, o);
+                if (res) {
+                    s_V[q - cq0] = o.V;
+                    s_C[q - cq0] = o.C;
+                    s_R[q - cq0] = o.R;
+                } else {
+                    store_state(v, q << 2, o);
+                }
+            }
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -151,6 +242,14 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         if (lane == 0) v.woff[wg] = run;  // spike count of this warp
+        const bool reweigh = step > 0 && step % REBALANCE_STEPS == 0;
+        if (reweigh && threadIdx.x == 0) {
+            v.cta_speed[bid] = d_tasks >= MIN_SPEED_TASKS
+                                   ? (uint32_t)min((d_tasks << 20) / max(d_ns, (uint64_t)1), (uint64_t)1 << 24) | 1u
+                                   : 0u;
+            d_ns = 0;
+            d_tasks = 0;
+        }
         if (!grid_barrier(v, G, gen)) break;
         if (bid == 0 && threadIdx.x == 0) {
             const uint64_t now = global_ns();
@@ -169,14 +268,19 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             }
         };
         block_exclusive_scan(v.woff, TW, s_wpre);
+        if (reweigh) load_split_weights(v, G, s_wp);
         const uint32_t total = s_wpre[TW];
         const uint32_t slot0 = t % v.D;
+        const uint64_t wa = s_wp[bid], wb = s_wp[bid + 1], wt = s_wp[G];
+        uint64_t my_tasks = 0;
+        if (threadIdx.x == 0) d_t0 = global_ns();
         bool ok = true;
         if (chunks > 0 && total > 0) {
             if constexpr (!BANDED) {
                 const uint64_t n_tasks = (uint64_t)total * chunks;
-                const uint64_t ta = n_tasks * bid / G;
-                const uint64_t tb = n_tasks * (bid + 1) / G;
+                const uint64_t ta = n_tasks * wa / wt;
+                const uint64_t tb = n_tasks * wb / wt;
+                my_tasks = tb - ta;
                 if (ta < tb) {
                     const uint32_t j_last = (uint32_t)((tb - 1) / chunks);
                     for (uint32_t jb = (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
@@ -226,9 +330,10 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
                     const uint32_t jh = ir.y == 0 ? 0u : s_wpre[min(warp_of_neuron(ir.y - 1, Q, TW) + 1, TW)];
                     if (jh <= jl) continue;
                     const uint64_t n_tasks = (uint64_t)(jh - jl) * chunks;
-                    const uint64_t ta = n_tasks * bid / G;
-                    const uint64_t tb = n_tasks * (bid + 1) / G;
+                    const uint64_t ta = n_tasks * wa / wt;
+                    const uint64_t tb = n_tasks * wb / wt;
                     if (ta >= tb) continue;
+                    my_tasks += tb - ta;
                     const uint32_t j_last = jl + (uint32_t)((tb - 1) / chunks);
                     for (uint32_t jb = jl + (uint32_t)(ta / chunks); jb <= j_last; jb += blockDim.x) {
                         const uint32_t j = jb + threadIdx.x;
@@ -263,6 +368,11 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         if (!ok) break;
         rc += total;
         spikes += total;
+        __syncthreads();  // this CTA's delivery is done
+        if (threadIdx.x == 0) {
+            d_ns += global_ns() - d_t0;
+            d_tasks += my_tasks;
+        }
         grid_arrive(v.st, gen);
         if (step + 1 < n_steps) prepare(t + 1);
         if (!grid_wait(v.st, G + v.barrier_extra, v.wait_limit_ns, gen)) break;
@@ -274,7 +384,15 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         done = step + 1;
     }
 
-    // ---- epilogue: counters of the launch
+    // ---- epilogue: resident state back to memory, counters of the launch
+    if (res) {
+        __syncthreads();
+        for (uint32_t q = cq0 + threadIdx.x; q < cq1; q += blockDim.x) {
+            *reinterpret_cast<float4*>(v.V + ((size_t)q << 2)) = s_V[q - cq0];
+            *reinterpret_cast<float4*>(v.c + ((size_t)q << 2)) = s_C[q - cq0];
+            *reinterpret_cast<uint32_t*>(v.ref + ((size_t)q << 2)) = s_R[q - cq0];
+        }
+    }
     uint32_t e = ext;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -312,7 +430,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
 // budget (n_bands > 1); the unbanded instance keeps the plain row walk.
 template <bool BF16, bool BANDED>
 __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_steps(NetView v, uint32_t n_steps) {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     run_steps<BF16, BANDED>(v, n_steps, gridDim.x, blockIdx.x, smem);
 }
 
@@ -324,7 +442,7 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
 // by side, the groups overlap those chains instead of paying them one network
 // after another.  Banded networks are not grouped (the host keeps them out).
 __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run_groups(GroupMeta gm) {
-    extern __shared__ uint32_t smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ NetView s_v;
     __shared__ uint32_t s_k;
     if (threadIdx.x == 0) {
@@ -340,6 +458,8 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     uint32_t* dst = reinterpret_cast<uint32_t*>(&s_v);
     for (uint32_t i = threadIdx.x; i < (uint32_t)(sizeof(NetView) / 4); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
+    if (threadIdx.x == 0) s_v.res_quads = gm.res_quads;  // the launch's shared memory, whatever the group
+    __syncthreads();
     const uint64_t start = global_ns();
     if (s_v.w_bf16)
         run_steps<true, false>(s_v, gm.steps[k], G, blockIdx.x - g0, smem);
@@ -353,8 +473,47 @@ static const void* persistent_fn(bool bf16, bool banded) {
     return bf16 ? (const void*)k_run_steps<true, false> : (const void*)k_run_steps<false, false>;
 }
 
-static size_t persistent_smem(int grid) {
-    return (size_t)(grid * PERSIST_WARPS + 1 + 3 * PERSIST_THREADS) * sizeof(uint32_t);
+static size_t persistent_smem(int grid) { return (size_t)state_offset_words((uint32_t)grid) * sizeof(uint32_t); }
+
+// Raises fn's dynamic shared-memory limit to `bytes` (never lowers it: other
+// networks' launches, also from captured graphs, may need more).
+static cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess || (size_t)fa.maxDynamicSharedSizeBytes >= bytes) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Quads of resident state per CTA for network v on `grid` CTAs (the largest
+// CTA range), or 0 if they do not fit in shared memory next to everything else
+// at the occupancy the grid needs, for both the banded and the unbanded
+// instance (bands can be set later).  Raises the kernels' shared-memory limit.
+uint32_t persistent_resident_quads(const NetView& v, int grid) {
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (grid <= 0 || sms <= 0) return 0;
+    const uint64_t Q = v.Npad >> 2, TW = (uint64_t)grid * PERSIST_WARPS;
+    uint64_t most = 0;
+    for (uint64_t b = 0; b < (uint64_t)grid; ++b)
+        most = std::max(most, Q * (b * PERSIST_WARPS + PERSIST_WARPS) / TW - Q * (b * PERSIST_WARPS) / TW);
+    const size_t need = persistent_smem(grid) + most * 36;
+    if (most == 0) return 0;
+    for (int banded = 0; banded < 2; ++banded) {
+        const void* fn = persistent_fn(v.w_bf16 != 0, banded != 0);
+        cudaFuncAttributes fa{};
+        int fit = 0;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || need + fa.sharedSizeBytes > (size_t)optin ||
+            raise_smem_limit(fn, need) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, PERSIST_THREADS, need) != cudaSuccess ||
+            (int64_t)fit * sms < grid) {
+            cudaGetLastError();
+            return 0;
+        }
+    }
+    return (uint32_t)most;
 }
 
 // Co-resident grid: occupancy per SM x SMs, with the grid-dependent shared
@@ -379,13 +538,11 @@ int persistent_grid(bool bf16) {
 }
 
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s) {
-    const size_t smem = persistent_smem(grid);
     const void* fn = persistent_fn(v.w_bf16 != 0, v.n_bands > 1);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    NetView vv = v;
+    NetView vv = v;  // v.res_quads: from persistent_resident_quads for this grid, or 0
+    const size_t smem = persistent_smem(grid) + (size_t)vv.res_quads * 36;
+    cudaError_t e0 = raise_smem_limit(fn, smem);
+    if (e0 != cudaSuccess) return e0;
     uint32_t ns = n_steps;
     void* args[] = {&vv, &ns};
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
@@ -393,12 +550,29 @@ cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cuda
     return e;
 }
 
+// Quads of resident state per CTA the grouped kernel's launches offer: what
+// the opt-in shared memory leaves next to the kernel's own, at one CTA per SM.
+static uint32_t groups_resident_quads(int grid) {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, (const void*)k_run_groups) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t base = persistent_smem(grid) + fa.sharedSizeBytes + 1024;  // + margin for the runtime's own
+    return (size_t)optin > base ? (uint32_t)(((size_t)optin - base) / 36) : 0u;
+}
+
 int groups_grid() {
     int dev = 0, sms = 0, fit = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_groups, PERSIST_THREADS,
-                                                      persistent_smem(sms)) != cudaSuccess ||
+    const size_t smem = persistent_smem(sms) + (size_t)groups_resident_quads(sms) * 36;
+    if (raise_smem_limit((const void*)k_run_groups, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_groups, PERSIST_THREADS, smem) !=
+            cudaSuccess ||
         fit < 1) {
         cudaGetLastError();
         return 0;
@@ -407,13 +581,11 @@ int groups_grid() {
 }
 
 cudaError_t launch_groups(const GroupMeta& gm, int grid, cudaStream_t s) {
-    const size_t smem = persistent_smem(grid);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_run_groups, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     GroupMeta m = gm;
+    m.res_quads = groups_resident_quads(grid);
+    const size_t smem = persistent_smem(grid) + (size_t)m.res_quads * 36;
+    cudaError_t e0 = raise_smem_limit((const void*)k_run_groups, smem);
+    if (e0 != cudaSuccess) return e0;
     void* args[] = {&m};
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_run_groups, dim3(grid), dim3(PERSIST_THREADS), args,
                                                 smem, s);

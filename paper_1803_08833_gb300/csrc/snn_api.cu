@@ -630,6 +630,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         {(void**)&v.st, sizeof(DevState)},
         {(void**)&v.woff, persist_bound * 32 * 4},  // per-warp counts: any persistent grid, <= 32 warps per CTA
         {(void**)&v.cta_cnt, persist_bound * 4},
+        {(void**)&v.cta_speed, persist_bound * 4},
         {(void**)&n->cdf_T, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_mod, (size_t)n->n_modules * n->max_off * 4},
         {(void**)&n->cdf_n, (size_t)n->n_modules * 4},
@@ -716,6 +717,7 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     for (auto& tb : temps) free_block(n, tb.first, tb.second);
     n->grid = deliver_default_grid(n->schedule, n->block, n->nb, v.w_bf16 != 0);
     n->tgrid = grouped ? tiled_grid(v) : 0;
+    v.res_quads = persistent_resident_quads(v, n->pgrid);  // neuron state in shared memory during launches
     if (v.segidx) {
         uint32_t chosen = 0;
         st = set_bands(n, 0, &chosen);  // banded delivery when the ring outgrows the L2 budget
@@ -1323,7 +1325,10 @@ snn_status build_wave(snn_batch* b, uint32_t first, uint32_t count, BatchWave* w
         NetView* d_views = (NetView*)batch_alloc(b, count * sizeof(NetView));
         if (!d_views) return fail(SNN_ENOMEM, "batch allocation failed");
         std::vector<NetView> views(count);
-        for (uint32_t i = 0; i < count; ++i) views[i] = nets[i]->v;
+        for (uint32_t i = 0; i < count; ++i) {
+            views[i] = nets[i]->v;
+            views[i].res_quads = 0;  // sized for the network's own grid, not for a group
+        }
         CUDA_TRY(cudaMemcpy(d_views, views.data(), count * sizeof(NetView), cudaMemcpyHostToDevice));
         w->grouped = true;
         w->first = first;

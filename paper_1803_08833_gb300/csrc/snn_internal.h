@@ -80,6 +80,9 @@ struct NetView {
     // persistent kernel: per-warp spike offsets within the CTA, per-CTA counts
     uint32_t* woff;
     uint32_t* cta_cnt;
+    uint32_t* cta_speed;      // persistent kernel: delivery speed of each CTA (tasks per ns x 2^20, 0 = unmeasured)
+    uint32_t res_quads;       // persistent kernel: quads of V, c, ref each CTA keeps in shared memory for the
+                              // launch (0: the state stays in global memory); set per launch
     uint64_t wait_limit_ns;   // bound of every grid-barrier wait
     uint32_t barrier_extra;   // test knob: arrivals expected beyond the grid (never satisfied)
     // tiled delivery (grouped layout): per-row segment starts, incoming stencil lists
@@ -165,12 +168,14 @@ struct GroupMeta {
     const uint32_t* steps;  // n: steps of this launch per network
     uint64_t* gns;          // n: %globaltimer ns each group took (written by its first CTA)
     uint32_t n;
+    uint32_t res_quads;     // resident-state capacity of every CTA (set by launch_groups)
 };
 int groups_grid();  // co-resident grid of the grouped kernel (one CTA per SM)
 cudaError_t launch_groups(const GroupMeta& gm, int grid, cudaStream_t s);
 int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
+uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
 cudaError_t prepare_deliver(uint32_t nb);
 
 void count_launch(uint64_t n);
