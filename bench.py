@@ -50,10 +50,10 @@ JOB_TIMESTEPS = 10000
 # DRAM bytes (read + write) of the persistent kernel per recurrent event, from
 # one ncu capture of a smaller case of the same model (profiles/), valid only
 # for the kernel sources it was taken on.
-NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "3b3270ce26dd6d570361ad1fc1bdd64836bd68db1af94636f059ae702ba61cfc",
-               "bytes_per_event": 8.41,
+NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "27bf41b8671e79c6279c1ede287cf646d5f2218395b1d04e2132e5371f580f3c",
+               "bytes_per_event": 8.40,
                "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
-                          "377.6 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
+                          "377.3 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
                           "scaled to a launch by its events"}
 
 
