@@ -263,11 +263,23 @@ SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t bloc
  * part in the bands its stencil reaches, with the synapses of its row that
  * target the band (rows must be grouped by target module: table_layout =
  * SNN_LAYOUT_GROUPED, or the pairwise law).  bands = 0 picks ceil(ring bytes /
- * (0.6 L2)); every network starts with that choice.
+ * (L2 / 2)), at most grid_h / (2 R + 1) for a stencil reaching R module rows
+ * up and down; every network starts with that choice.
  * *chosen (may be NULL) receives the count in use.  Results are identical for
  * every band count.  Synchronises `stream`.  Errors: SNN_EINVAL (bands >
  * grid_h, or > 1 without a segment index). */
 SNN_API snn_status snn_set_bands(snn_net* net, uint32_t bands, uint32_t* chosen, void* stream);
+
+/* Resident neuron state of schedule 2: every CTA of the persistent launch
+ * keeps V, c and ref of its neurons in shared memory for the whole launch
+ * (read at the start, written back at the end), when they fit next to the
+ * kernel's other shared memory (36 B per 4 neurons: up to ~5,000 quads per
+ * CTA on a GB300; the 96x96 grid does not fit and keeps them in global
+ * memory).  enable = 0 keeps them in global memory, 1 (the default) restores
+ * the choice.  *resident (may be NULL) receives 1 if the launches keep the
+ * state resident.  Results are identical either way.  Synchronises `stream`.
+ * Errors: SNN_EINVAL. */
+SNN_API snn_status snn_set_resident_state(snn_net* net, int32_t enable, int32_t* resident, void* stream);
 
 /* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
  * per delivery block, 2, and 3 if the network has the grouped layout and its

@@ -420,21 +420,46 @@ void free_block(snn_net* n, void* p, size_t bytes) {
 }
 
 // Bands of target module rows for the persistent delivery.  bands = 0 picks
-// ceil(ring bytes / (0.6 L2)) (1 when the ring fits): on GB300 the best band
-// counts measured were 4 for the 242 MB ring of the 48x48 grid (60 MB per
-// band) and 12 for the 968 MB ring of the 96x96 grid (81 MB per band).  Needs
-// a segment index (grouped layout, or the pairwise law, whose rows are grouped
-// by construction).
+// ceil(ring bytes / (L2 / 2)), at most grid_h / (2 R + 1) for a stencil of
+// row radius R (1 when the ring fits).  Measured on GB300 (events/s): the
+// 242 MB ring of the 48x48 grid 3 bands 7.2e10, 4 bands 8.1e10, 6 bands
+// 7.7e10 (the per-pair 48x48: 9.4e10 / 9.5e10 / 8.9e10); the 968 MB ring of
+// the 96x96 grid 12 bands 6.4-6.6e10, 13 6.2e10, 15 6.1e10, 20 5.6e10: per-band
+// ring columns must fit in about half the L2, but bands lower than the
+// stencil split every spiking row into more short pieces.  Needs a segment
+// index (grouped layout, or the pairwise law, whose rows are grouped by
+// construction).
 snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
     const snn_config& c = n->cfg;
     NetView& v = n->v;
+    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
+    // stencil rows (dy) in segment-index order
+    std::vector<int> sdx, sdy;
+    if (v.segidx && (bands == 0 || bands > 1)) {
+        if (pairwise) {
+            HostTables ht;
+            host_tables(c, &ht);
+            sdx.assign(ht.pdx.begin(), ht.pdx.end());
+            sdy.assign(ht.pdy.begin(), ht.pdy.end());
+        } else {
+            uint32_t R2 = 0;
+            std::vector<int16_t> off = disc_offsets(c, &R2);
+            for (size_t o = 0; o < off.size(); o += 2) {
+                sdx.push_back(off[o]);
+                sdy.push_back(off[o + 1]);
+            }
+        }
+    }
+    int R = 0;
+    for (int dy : sdy) R = std::max(R, std::abs(dy));
     if (bands == 0) {
         int dev = 0, l2 = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
         const double ring = (double)n->D * n->Npad * 4.0;
-        const double budget = l2 > 0 ? 0.6 * l2 : 32.0 * (1 << 20);
+        const double budget = l2 > 0 ? 0.5 * l2 : 32.0 * (1 << 20);
         bands = v.segidx ? (uint32_t)std::ceil(ring / budget) : 1u;
+        bands = std::min<uint32_t>(bands, std::max<uint32_t>(1u, c.grid_h / (2 * (uint32_t)R + 1)));
         bands = std::min<uint32_t>(std::max<uint32_t>(bands, 1u), c.grid_h);
     }
     if (bands < 1 || bands > c.grid_h) return fail(SNN_EINVAL, "bands must be in [1, grid_h = %u]", c.grid_h);
@@ -444,25 +469,7 @@ snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
     if (chosen) *chosen = bands;
     v.n_bands = bands;
     if (bands == 1) return SNN_OK;
-    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
-    // stencil rows (dy) in segment-index order
-    std::vector<int> sdx, sdy;
-    if (pairwise) {
-        HostTables ht;
-        host_tables(c, &ht);
-        sdx.assign(ht.pdx.begin(), ht.pdx.end());
-        sdy.assign(ht.pdy.begin(), ht.pdy.end());
-    } else {
-        uint32_t R2 = 0;
-        std::vector<int16_t> off = disc_offsets(c, &R2);
-        for (size_t o = 0; o < off.size(); o += 2) {
-            sdx.push_back(off[o]);
-            sdy.push_back(off[o + 1]);
-        }
-    }
     if (sdy.size() + 1 > 0xFFFFu) return fail(SNN_EINVAL, "stencil too large for banded delivery");
-    int R = 0;
-    for (int dy : sdy) R = std::max(R, std::abs(dy));
     const uint32_t H = c.grid_h, W = c.grid_w, M = c.neurons_per_module;
     std::vector<uint32_t> row(bands + 1);
     for (uint32_t b = 0; b <= bands; ++b) row[b] = (uint32_t)((uint64_t)H * b / bands);
@@ -1115,6 +1122,15 @@ snn_status snn_set_bands(snn_net* n, uint32_t bands, uint32_t* chosen, void* str
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight reads the tables
     return set_bands(n, bands, chosen);
+}
+
+snn_status snn_set_resident_state(snn_net* n, int32_t enable, int32_t* resident, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (enable != 0 && enable != 1) return fail(SNN_EINVAL, "enable must be 0 or 1");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight uses the old view
+    n->v.res_quads = enable ? persistent_resident_quads(n->v, n->pgrid) : 0u;
+    if (resident) *resident = n->v.res_quads > 0 ? 1 : 0;
+    return SNN_OK;
 }
 
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {

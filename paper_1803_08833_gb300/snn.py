@@ -124,6 +124,7 @@ def load():
         "snn_batch_set_graph": (st, [vp, ctypes.c_int32]),
         "snn_batch_waves": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint64)]),
         "snn_batch_set_ring_budget": (st, [vp, ctypes.c_uint64]),
+        "snn_set_resident_state": (st, [vp, ctypes.c_int32, P(ctypes.c_int32), vp]),
         "snn_batch_set_mode": (st, [vp, ctypes.c_int32]),
         "snn_batch_groups": (st, [vp, P(ctypes.c_uint32)]),
         "snn_plan_groups": (st, [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp]),
@@ -376,6 +377,14 @@ class Network:
         out = ctypes.c_uint32()
         check(load().snn_set_bands(self._h, int(bands), ctypes.byref(out), self._s))
         return out.value
+
+    def set_resident_state(self, enable: bool = True) -> bool:
+        """Neuron state in shared memory through each persistent launch (when it
+        fits); returns whether the launches keep it resident."""
+        out = ctypes.c_int32()
+        check(load().snn_set_resident_state(self._h, 1 if enable else 0, ctypes.byref(out), self._s))
+        return bool(out.value)
+
     def autotune(self, trial_steps: int = 20, cache_path=None):
         """Pick the fastest schedule (state unchanged); returns (schedule, block, ms per step)."""
         sc, bl, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
