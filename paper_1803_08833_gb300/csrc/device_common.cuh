@@ -240,7 +240,7 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
                                               uint32_t chunks, const uint32_t* ids, uint32_t j0, uint32_t slot0,
                                               uint32_t lane, uint64_t pol, Hook hook = Hook()) {
     uint4 tg[DELIVER_UNROLL];
-    float w[DELIVER_UNROLL][4];
+    uint4 wr[DELIVER_UNROLL];  // raw weight bits: converted after every load of the round is issued
     uint32_t nv[DELIVER_UNROLL];
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
@@ -258,16 +258,9 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
                 tg[u] = ld_u4(v.td + e, pol);
                 if (BF16) {
                     const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
-                    w[u][0] = bf16_lo(wb.x);
-                    w[u][1] = bf16_hi(wb.x);
-                    w[u][2] = bf16_lo(wb.y);
-                    w[u][3] = bf16_hi(wb.y);
+                    wr[u] = make_uint4(wb.x, wb.y, 0u, 0u);
                 } else {
-                    const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
-                    w[u][0] = __uint_as_float(wf.x);
-                    w[u][1] = __uint_as_float(wf.y);
-                    w[u][2] = __uint_as_float(wf.z);
-                    w[u][3] = __uint_as_float(wf.w);
+                    wr[u] = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
                 }
             }
         }
@@ -276,12 +269,14 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
         const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+        const uint32_t wq[4] = {wr[u].x, wr[u].y, wr[u].z, wr[u].w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if ((uint32_t)q < nv[u]) {
                 uint32_t s = slot0 + (tq[q] >> 24);
                 if (s >= v.D) s -= v.D;
-                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, w[u][q]));
+                const float wv = BF16 ? ((q & 1) ? bf16_hi(wq[q >> 1]) : bf16_lo(wq[q >> 1])) : __uint_as_float(wq[q]);
+                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
             }
         }
     }
@@ -295,7 +290,7 @@ __device__ __forceinline__ void deliver_tasks_range(const NetView& v, uint64_t t
                                                     const uint32_t* rhi, uint32_t j0, uint32_t slot0, uint32_t lane,
                                                     uint64_t pol, Hook hook = Hook()) {
     uint4 tg[DELIVER_UNROLL];
-    float w[DELIVER_UNROLL][4];
+    uint4 wr[DELIVER_UNROLL];  // raw weight bits: converted after every load of the round is issued
     uint32_t msk[DELIVER_UNROLL];  // bit q: synapse k0 + q is delivered
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
@@ -314,16 +309,9 @@ __device__ __forceinline__ void deliver_tasks_range(const NetView& v, uint64_t t
                 tg[u] = ld_u4(v.td + e, pol);
                 if (BF16) {
                     const uint2 wb = ld_u2(reinterpret_cast<const uint16_t*>(v.w) + e, pol);
-                    w[u][0] = bf16_lo(wb.x);
-                    w[u][1] = bf16_hi(wb.x);
-                    w[u][2] = bf16_lo(wb.y);
-                    w[u][3] = bf16_hi(wb.y);
+                    wr[u] = make_uint4(wb.x, wb.y, 0u, 0u);
                 } else {
-                    const uint4 wf = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
-                    w[u][0] = __uint_as_float(wf.x);
-                    w[u][1] = __uint_as_float(wf.y);
-                    w[u][2] = __uint_as_float(wf.z);
-                    w[u][3] = __uint_as_float(wf.w);
+                    wr[u] = ld_u4(reinterpret_cast<const float*>(v.w) + e, pol);
                 }
             }
         }
@@ -332,12 +320,14 @@ __device__ __forceinline__ void deliver_tasks_range(const NetView& v, uint64_t t
 #pragma unroll
     for (int u = 0; u < DELIVER_UNROLL; ++u) {
         const uint32_t tq[4] = {tg[u].x, tg[u].y, tg[u].z, tg[u].w};
+        const uint32_t wq[4] = {wr[u].x, wr[u].y, wr[u].z, wr[u].w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             if (msk[u] & (1u << q)) {
                 uint32_t s = slot0 + (tq[q] >> 24);
                 if (s >= v.D) s -= v.D;
-                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, w[u][q]));
+                const float wv = BF16 ? ((q & 1) ? bf16_hi(wq[q >> 1]) : bf16_lo(wq[q >> 1])) : __uint_as_float(wq[q]);
+                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
             }
         }
     }
