@@ -50,7 +50,7 @@ JOB_TIMESTEPS = 10000
 # DRAM bytes (read + write) of the persistent kernel per recurrent event, from
 # one ncu capture of a smaller case of the same model (profiles/), valid only
 # for the kernel sources it was taken on.
-NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "27bf41b8671e79c6279c1ede287cf646d5f2218395b1d04e2132e5371f580f3c",
+NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "90f6e4ed6e9f11017da4979cd42add704253331f60cf792995bf8ec423ace17e",
                "bytes_per_event": 8.40,
                "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
                           "377.3 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
