@@ -63,25 +63,30 @@ __global__ void k_stream_red(const uint4* tab, size_t n16, int* buf, uint32_t n)
     }
 }
 
-// Each warp reads `segs` segments of L bytes (a multiple of 128) at random
-// 128-byte aligned offsets of the first `region` bytes, 8 segments in flight.
-__global__ void k_seg_read(const uint32_t* tab, size_t region, uint32_t L, uint32_t segs, uint32_t salt,
-                           uint32_t* sink) {
+// Each warp reads `segs` segments of CH x 128 bytes at random 128-byte aligned
+// offsets of the first `region` bytes, 8 segments in flight.  The chunk count
+// is a template constant so that every load of a round is issued before the
+// first is used (a runtime-bounded inner loop kept the loaded words in local
+// memory and serialised the reads).
+template <int CH>
+__global__ void k_seg_read(const uint32_t* tab, size_t region, uint32_t segs, uint32_t salt, uint32_t* sink) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const size_t slots = (region - L) / 128;
+    const size_t slots = (region - CH * 128) / 128;
     uint32_t acc = 0;
     for (uint32_t s0 = 0; s0 < segs; s0 += 8) {
-        uint32_t v[8][4];
+        uint32_t v[8][CH];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const size_t base =
                 ((size_t)mix32(w * 7919u + (s0 + u) * 104729u + salt) * 2654435761ull % slots) * 32;  // words
-            for (uint32_t k = 0; k < 4; ++k) v[u][k] = 0;
-            for (uint32_t k = 0; k < L / 128 && k < 4; ++k) v[u][k] = __ldcs(tab + base + k * 32 + lane);
+#pragma unroll
+            for (int k = 0; k < CH; ++k) v[u][k] = __ldcs(tab + base + k * 32 + lane);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u][0] ^ v[u][1] ^ v[u][2] ^ v[u][3];
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int k = 0; k < CH; ++k) acc ^= v[u][k];
     }
     if (acc == 0x12345678u) sink[0] = acc;
 }
@@ -181,19 +186,24 @@ int main() {
     cudaEventElapsedTime(&ms, a, b);
     printf(", \"stream_plus_random_red\": {\"red_per_s\": %.4g, \"table_gb_per_s\": %.1f}", part * 4.0 / (ms * 1e-3),
            part * 16.0 / (ms * 1e-3) / 1e9);
-    // short segments at random places: 128 B and 512 B over 512 MB, 1 GB and 4 GB
+    // short segments at random places: 128 B, 512 B and 1 KB over 512 MB, 1 GB and 4 GB
     printf(", \"segment_read_gb_per_s\": {");
     const size_t regions[] = {(size_t)512 << 20, (size_t)1 << 30, tab_bytes};
-    const uint32_t lens[] = {128, 512};
+    const uint32_t lens[] = {128, 512, 1024};
     const uint32_t segs = 64;
     int first = 1;
     for (uint32_t L : lens)
         for (size_t R : regions) {
             const int sgrid = sms * 8;
             const double bytes = (double)sgrid * 8 * segs * L;  // 8 warps per block
-            k_seg_read<<<sgrid, 256>>>((const uint32_t*)tab, R, L, segs, 3, sink);
+            auto seg = [&](uint32_t salt) {
+                if (L == 128) k_seg_read<1><<<sgrid, 256>>>((const uint32_t*)tab, R, segs, salt, sink);
+                if (L == 512) k_seg_read<4><<<sgrid, 256>>>((const uint32_t*)tab, R, segs, salt, sink);
+                if (L == 1024) k_seg_read<8><<<sgrid, 256>>>((const uint32_t*)tab, R, segs, salt, sink);
+            };
+            seg(3);
             cudaEventRecord(a);
-            for (int it = 0; it < 3; ++it) k_seg_read<<<sgrid, 256>>>((const uint32_t*)tab, R, L, segs, 11 + it, sink);
+            for (int it = 0; it < 3; ++it) seg(11 + it);
             cudaEventRecord(b);
             cudaEventSynchronize(b);
             cudaEventElapsedTime(&ms, a, b);
