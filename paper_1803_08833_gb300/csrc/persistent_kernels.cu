@@ -25,6 +25,7 @@ namespace snn {
 constexpr int MAX_DRV = 8;  // chunks per thread whose external drive is drawn ahead
 constexpr uint32_t REBALANCE_STEPS = 32;  // steps between re-weightings of the delivery split
 constexpr uint32_t MIN_SPEED_TASKS = 64;   // tasks a CTA must have delivered for its speed to count
+constexpr int PF_CHUNKS = 5;  // resident state: a warp with at most this many chunks loads all its ring slots at once
 
 #ifndef SNN_PERSIST_MIN_BLOCKS
 #define SNN_PERSIST_MIN_BLOCKS 1  // one CTA per SM: registers for deep delivery unrolling
@@ -203,31 +204,8 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         const uint32_t slot = t % v.D;
         // ---- phase N: this warp's neurons, 4 per lane, spikes compacted in id order
         uint32_t run = 0;
-        // the loads of the next two chunks are in flight while a chunk is integrated
-        if (qa0 < qb) n1.I = load_slot(v, qa0 << 2, slot);
-        if (qa1 < qb) n2.I = load_slot(v, qa1 << 2, slot);
-        uint32_t k = 0;
-        for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
-            const uint32_t q = qc + lane;
-            const QuadIn cur = n1;
-            n1 = n2;
-            if (q + 64 < qb) {
-                n2.I = load_slot(v, (q + 64) << 2, slot);
-                load_st(q + 64, n2);
-                n2.drive = drive_of(k + 2, t);
-            }
-            uint32_t spk = 0;
-            if (q < qb) {
-                QuadOut o;
-                spk = integrate_quad(v, q << 2, slot, cur, ext, rec, o);
-                if (res) {
-                    s_V[q - cq0] = o.V;
-                    s_C[q - cq0] = o.C;
-                    s_R[q - cq0] = o.R;
-                } else {
-                    store_state(v, q << 2, o);
-                }
-            }
+        // Compacts this lane's spikes of chunk quad q into the warp's staging, in id order.
+        auto stage = [&](uint32_t q, uint32_t spk) {
             const uint32_t cnt = __popc(spk);
             uint32_t incl = cnt;
 #pragma unroll
@@ -240,12 +218,79 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             for (int b = 0; b < 4; ++b)
                 if (spk & (1u << b)) v.seg[pos++] = (q << 2) + b;
             run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        };
+        if (res && qb - qa <= 32u * PF_CHUNKS) {
+            // resident state and few chunks: every ring-slot load of the warp is in
+            // flight at once (one L2 round trip), then the chunks are integrated
+            int4 Ipf[PF_CHUNKS];
+#pragma unroll
+            for (int c = 0; c < PF_CHUNKS; ++c)
+                if (qa + 32u * c + lane < qb) Ipf[c] = load_slot(v, (qa + 32u * c + lane) << 2, slot);
+            // external drives not drawn ahead are drawn while the loads are in flight
+            uint32_t drv[PF_CHUNKS];
+#pragma unroll
+            for (int c = 0; c < PF_CHUNKS; ++c) {
+                drv[c] = 0;
+                if (qa + 32u * c + lane < qb) drv[c] = c == 0 ? n1.drive : c == 1 ? n2.drive : drive_of(c, t);
+            }
+#pragma unroll
+            for (int c = 0; c < PF_CHUNKS; ++c) {
+                const uint32_t q = qa + 32u * c + lane;
+                if (qa + 32u * c >= qb) break;  // warp-uniform
+                uint32_t spk = 0;
+                if (q < qb) {
+                    QuadIn in;
+                    if (c == 0) {
+                        in = n1;  // state prepared while waiting at the last barrier
+                    } else if (c == 1) {
+                        in = n2;
+                    } else {
+                        load_st(q, in);
+                    }
+                    in.I = Ipf[c];
+                    in.drive = drv[c];
+                    QuadOut o;
+                    spk = integrate_quad(v, q << 2, slot, in, ext, rec, o);
+                    s_V[q - cq0] = o.V;
+                    s_C[q - cq0] = o.C;
+                    s_R[q - cq0] = o.R;
+                }
+                stage(q, spk);
+            }
+        } else {
+            // the loads of the next two chunks are in flight while a chunk is integrated
+            if (qa0 < qb) n1.I = load_slot(v, qa0 << 2, slot);
+            if (qa1 < qb) n2.I = load_slot(v, qa1 << 2, slot);
+            uint32_t k = 0;
+            for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
+                const uint32_t q = qc + lane;
+                const QuadIn cur = n1;
+                n1 = n2;
+                if (q + 64 < qb) {
+                    n2.I = load_slot(v, (q + 64) << 2, slot);
+                    load_st(q + 64, n2);
+                    n2.drive = drive_of(k + 2, t);
+                }
+                uint32_t spk = 0;
+                if (q < qb) {
+                    QuadOut o;
+                    spk = integrate_quad(v, q << 2, slot, cur, ext, rec, o);
+                    if (res) {
+                        s_V[q - cq0] = o.V;
+                        s_C[q - cq0] = o.C;
+                        s_R[q - cq0] = o.R;
+                    } else {
+                        store_state(v, q << 2, o);
+                    }
+                }
+                stage(q, spk);
+            }
         }
         if (lane == 0) v.woff[wg] = run;  // spike count of this warp
         const bool reweigh = step > 0 && step % REBALANCE_STEPS == 0;
         if (reweigh && threadIdx.x == 0) {
             v.cta_speed[bid] = d_tasks >= MIN_SPEED_TASKS
-                                   ? (uint32_t)min((d_tasks << 20) / max(d_ns, (uint64_t)1), (uint64_t)1 << 24) | 1u
+                                   ? (uint32_t)min((d_tasks << 20) / max(d_ns, (uint64_t)1), (uint64_t)1 << 20) | 1u
                                    : 0u;
             d_ns = 0;
             d_tasks = 0;
