@@ -378,7 +378,9 @@ SNN_API snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_
 SNN_API snn_status snn_batch_waves(snn_batch* b, uint32_t* waves, uint64_t* ring_budget);
 /* Regroups the networks into waves for another ring budget (bytes > 0). */
 SNN_API snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes);
-/* Runs network i for steps[i] (host array of n; 0 = idle) time steps.  Async. */
+/* Runs network i for steps[i] (host array of n; 0 = idle) time steps.  Async;
+ * a call first synchronises `stream`, whose previous call on this batch may
+ * still read the batch's pinned staging: keep one stream per batch. */
 SNN_API snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream);
 /* enable != 0: snn_batch_step replays a CUDA graph holding the launches of
  * all waves (captured on first use, and again when a wave's longest step
