@@ -70,3 +70,4 @@ def test_null_arguments(lib):
     assert lib.snn_plan_groups(None, None, 1, 8, None) == snn.SNN_EINVAL
     assert lib.snn_batch_set_mode(None, 0) == snn.SNN_EINVAL
     assert lib.snn_batch_groups(None, None) == snn.SNN_EINVAL
+    assert lib.snn_set_resident_state(None, 1, None, None) == snn.SNN_EINVAL
