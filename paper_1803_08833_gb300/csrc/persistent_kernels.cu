@@ -490,11 +490,10 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_PERSIST_MIN_BLOCKS) k_run
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ NetView s_v;
     __shared__ uint32_t s_k;
-    if (threadIdx.x == 0) {
-        uint32_t k = 0;
-        while (k < gm.n && gm.gcta[k + 1] <= blockIdx.x) ++k;
-        s_k = k;
-    }
+    if (threadIdx.x == 0) s_k = gm.n;  // no group: a CTA past the last one
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < gm.n; k += blockDim.x)  // the groups are disjoint: one k matches
+        if (gm.gcta[k] <= blockIdx.x && blockIdx.x < gm.gcta[k + 1]) s_k = k;
     __syncthreads();
     const uint32_t k = s_k;
     if (k >= gm.n) return;  // a CTA past the last group
