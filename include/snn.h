@@ -270,8 +270,10 @@ SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t bloc
  * grid_h, or > 1 without a segment index). */
 SNN_API snn_status snn_set_bands(snn_net* net, uint32_t bands, uint32_t* chosen, void* stream);
 
-/* Resident neuron state of schedule 2: every CTA of the persistent launch
- * keeps V, c and ref of its neurons in shared memory for the whole launch
+/* Resident neuron state of schedule 2 (no counterpart in the paper; the state
+ * is that of Eq. 1-2 and the refractory counter, Sec. III-A): every CTA of
+ * the persistent launch keeps V, c and ref of its neurons in shared memory
+ * for the whole launch
  * (read at the start, written back at the end), when they fit next to the
  * kernel's other shared memory (36 B per 4 neurons: up to ~5,000 quads per
  * CTA on a GB300; the 96x96 grid does not fit and keeps them in global
@@ -347,7 +349,9 @@ SNN_API uint64_t snn_launch_count(void);
 SNN_API snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh, uint32_t* tgt_module,
                                         uint32_t* counts, uint32_t* max_offsets, void* stream);
 
-/* ---- Batched execution: many independent networks in one persistent launch.
+/* ---- Batched execution: many independent networks in one persistent launch
+ * (no counterpart in the paper, which simulates one network per run; each
+ * network's time steps are those of snn_step, Sec. II-A flow steps 1-6).
  * Network i is advanced steps[i] time steps per call.  Results are
  * bit-identical to running each network alone.  The networks are grouped into
  * waves (below); a wave of one network runs the persistent kernel of
