@@ -50,10 +50,10 @@ JOB_TIMESTEPS = 10000
 # DRAM bytes (read + write) of the persistent kernel per recurrent event, from
 # one ncu capture of a smaller case of the same model (profiles/), valid only
 # for the kernel sources it was taken on.
-NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "21939e9edaafe6175bd67a465ade3e3b1c5d2ea308cf7e7f5e92e0d1400b91cf",
-               "bytes_per_event": 8.40,
+NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "b90c0415b662555f7b21f9ac18d86c85151df74431e875411f5be0250ca31c09",
+               "bytes_per_event": 8.39,
                "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
-                          "377.3 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
+                          "376.9 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
                           "scaled to a launch by its events"}
 
 
