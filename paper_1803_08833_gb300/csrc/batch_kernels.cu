@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(PERSIST_THREADS, SNN_BATCH_MIN_BLOCKS) k_run_b
                 ta = s_tpre[k + 1];
             }
         }
+        // every thread of the CTA is past its raster writes (which read s_rc) before
+        // the counters move on; a CTA without delivery tasks has no barrier in between
+        __syncthreads();
         for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
             const uint32_t S = s_spre[k + 1] - s_spre[k];
             s_rc[k] += S;

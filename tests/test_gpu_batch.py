@@ -149,3 +149,59 @@ def test_batch_rejects_repeated_networks(snn):
     with pytest.raises(snn.SnnError, match="twice"):
         snn.Batch([net, net])
     net.close()
+
+
+def test_waves_that_cannot_be_grouped_run_global(snn):
+    """A wave holding a banded network, and a wave with more networks than
+    SMs, run in the global layout even in groups mode: every network still
+    equals the oracle, and none of them reports a group."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    banded = W.small(grid=4, M=60, K=80, seed=51, imposed_rate_hz=30.0, table_layout="grouped")
+    cfgs = [banded, W.small(grid=2, M=50, K=40, seed=52, imposed_rate_hz=30.0)]
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    assert nets[0].set_bands(2) == 2
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.step([40, 40])
+        assert batch.groups() == [0, 0]
+    for net, ref in zip(nets, refs):
+        ref.step(40)
+        _check(net, ref)
+        net.close()
+    # more networks than SMs in one wave
+    many = [W.small(grid=1, M=12, K=6, seed=100 + i, imposed_rate_hz=60.0) for i in range(sms + 3)]
+    nets = [snn.Network(c, raster_capacity=1 << 12) for c in many]
+    with snn.Batch(nets) as batch:
+        assert batch.waves()[0] == 1
+        batch.step([25] * len(nets))
+        assert set(batch.groups()) == {0}
+    for i in (0, len(nets) // 2, len(nets) - 1):
+        ref = oracle.OracleNet(many[i])
+        ref.step(25)
+        _check(nets[i], ref)
+    for n in nets:
+        n.close()
+
+
+def test_grouped_batch_of_both_laws_and_weight_types(snn):
+    """A grouped wave mixing the per-pair law (bf16 and f32), the fixed law and
+    a network with an imposed rate of 0 (driven only by its Poisson input),
+    over several calls with changing step counts (the split is re-planned from
+    the measured group times each call): bit-exact against the oracle."""
+    cfgs = [W.pairwise(grid=5, M=80, seed=61, imposed_rate_hz=20.0, weight_dtype="bf16"),
+            W.pairwise(grid=4, M=90, lateral="exp", seed=62, imposed_rate_hz=35.0),
+            W.small(grid=5, M=100, K=150, seed=63, imposed_rate_hz=7.5, weight_dtype="bf16"),
+            W.small(grid=3, M=120, K=90, seed=64, ext_rate_hz=4000.0)]
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_graph(True)
+        for steps in ([30, 30, 30, 30], [50, 10, 0, 35], [64, 64, 64, 64]):
+            batch.step(steps)
+            assert all((g > 0) == (s > 0) for g, s in zip(batch.groups(), steps))
+            for r, k in zip(refs, steps):
+                r.step(k)
+    for net, ref in zip(nets, refs):
+        _check(net, ref)
+        net.close()
