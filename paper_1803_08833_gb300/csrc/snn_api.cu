@@ -1460,6 +1460,7 @@ snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc
         snn_batch_destroy(b);
         return fail(SNN_ENOMEM, "batch allocation failed");
     }
+    std::memset(b->h_gns, 0, (size_t)n * 8);  // no measured group time yet
     b->ggrid = groups_grid();
     b->work.resize(n);
     b->last_cta.assign(n, 0);
@@ -1548,7 +1549,7 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     CUDA_TRY(cudaStreamSynchronize(s));
     // the groups' times of the last call refine the work estimates
     for (uint32_t i = 0; i < n; ++i) {
-        if (b->last_cta[i] == 0 || b->last_steps[i] == 0) continue;
+        if (b->last_cta[i] == 0 || b->last_steps[i] == 0 || b->h_gns[i] == 0) continue;
         const double us = (double)b->h_gns[i] * 1e-3 / b->last_steps[i];
         b->work[i] = std::max(us - GROUP_FIXED_US, 0.05) * b->last_cta[i];
     }
