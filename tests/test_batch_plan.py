@@ -71,3 +71,26 @@ def test_null_arguments(lib):
     assert lib.snn_batch_set_mode(None, 0) == snn.SNN_EINVAL
     assert lib.snn_batch_groups(None, None) == snn.SNN_EINVAL
     assert lib.snn_set_resident_state(None, 1, None, None) == snn.SNN_EINVAL
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_large_split_is_locally_optimal(lib, seed):
+    """A full wave (up to one network per SM): the split uses every CTA, and no
+    single CTA moved from one group to the group that finishes last shortens
+    the makespan."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(20, 153))
+    S = 152
+    steps = rng.integers(1, 3000, n)
+    work = rng.lognormal(3.0, 1.5, n)
+    cta = snn.plan_groups(steps, work, S).astype(np.int64)
+    assert cta.sum() == S and cta.min() >= 1
+    t = steps * (F + work / cta)
+    worst = int(np.argmax(t))
+    for j in range(n):
+        if j == worst or cta[j] == 1:
+            continue
+        c2 = cta.copy()
+        c2[j] -= 1
+        c2[worst] += 1
+        assert _makespan(steps, work, c2) >= t.max() * (1 - 1e-12)
