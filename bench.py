@@ -186,6 +186,22 @@ def config_block(cfg, extra=None):
     return d
 
 
+def host_cpu():
+    """The host the CPU baseline ran on: architecture, logical CPUs and model name."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "processor") and ":" in line and not line.split(":")[1].strip().isdigit():
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"arch": platform.machine(), "logical_cpus": os.cpu_count(), "model": model or None}
+
+
 # --------------------------------------------------------------------------
 def cpu_oracle_rate(cfg, grid, min_seconds, max_steps, warm_steps=20):
     """Oracle simulation-phase throughput on a grid x grid patch of the model."""
@@ -237,7 +253,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0 / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_block(cfg, {"sample": desc}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -345,7 +362,8 @@ def run_gpu(args):
                "sample": "oracle (single-threaded C) on a %dx%d-module patch of the workload (%d neurons, "
                          "K=1125, imposed 7.5 Hz), %d simulated steps after 20 warm-up steps, %.1f s, "
                          "simulation phase only" % (args.cpu_grid, args.cpu_grid, info["neurons"], info["steps"],
-                                                    info["seconds"])}
+                                                    info["seconds"]),
+               "host": host_cpu()}
 
     if rank != 0:
         return 0
@@ -368,6 +386,12 @@ def run_gpu(args):
                                      if pl else None,
                                      "deliver_phase_us": (s1["deliver_phase_ns"] - s0["deliver_phase_ns"]) / 1e3 / steps_timed
                                      if pl else None,
+                                     # one L2 reduction per recurrent event: the reduction rate of the
+                                     # delivery phase (its barrier included), against ~2.2e11/s measured
+                                     # for random reductions alone (bench.py --calibrate)
+                                     "delivery_phase_l2_reductions_per_s":
+                                     rec / ((s1["deliver_phase_ns"] - s0["deliver_phase_ns"]) / 1e9)
+                                     if pl and s1["deliver_phase_ns"] > s0["deliver_phase_ns"] else None,
                                      "kernel_timing": ("CUDA events around every persistent launch of the timed "
                                                        "region; phases from the GPU timer of CTA 0" if pl else
                                                        "CUDA events around the kernels of every %d-th simulated "
