@@ -44,6 +44,10 @@ BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
 # neuron update: the ring slot read and cleared; V, c (f32) and ref (u8) stay in
 # shared memory for the whole launch (read and written back once per launch)
 NEURON_BYTES = 2 * 4
+# random 4-byte red.global.add.s32 into an L2-resident buffer (4-60 MB), measured on
+# GB300 by `bench.py --calibrate` (profiles/l2_rates_gb300.md): the rate that bounds
+# spike delivery, one reduction per recurrent synaptic event
+L2_RED_PER_S = 2.2e11
 TIMESTEPS_PER_STEP = 1000
 JOB_TIMESTEPS = 10000
 
@@ -402,6 +406,13 @@ def run_gpu(args):
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
                      "launches_timed": launches_timed},
+        # the bound that actually limits the path: one random L2 reduction per event
+        "l2_reduction_bound": {"achieved": rec / (pms / 1000.0) if pl and pms > 0 else None,
+                               "peak": L2_RED_PER_S, "unit": "reductions/s",
+                               "frac": rec / (pms / 1000.0) / L2_RED_PER_S if pl and pms > 0 else None,
+                               "peak_source": "calibrated (bench.py --calibrate): random red.global.add.s32 "
+                                              "into a 4-60 MB buffer",
+                               "note": "whole persistent launch (neuron phase, barriers and scan included)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "batched": batched,
