@@ -6,7 +6,8 @@ Workload: the 24x24-module Gaussian network (720,000 LIF-SFA neurons, K = 1,125,
 drive alone leaves the network nearly silent).  One benchmark step = 1,000
 simulated 1 ms time steps (one simulated second): for every time step the fused
 neuron kernel and the delivery kernel, through the C ABI.  The synapse table
-(7.3 GB) is far larger than L2, so every step streams it from HBM.
+(6.5 GB: a 32-bit target | delay word and an f32 weight per synapse) is far
+larger than L2, so every step streams it from HBM.
 
 value       recurrent synaptic events / s (events = spikes x out-degree, from the
             device counters), device-timed with CUDA events over K steps.
@@ -45,19 +46,19 @@ BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
 # shared memory for the whole launch (read and written back once per launch)
 NEURON_BYTES = 2 * 4
 # random 4-byte red.global.add.s32 into an L2-resident buffer (4-60 MB), measured on
-# GB300 by `bench.py --calibrate` (profiles/l2_rates_gb300.md): the rate that bounds
-# spike delivery, one reduction per recurrent synaptic event
+# GB300 by `bench.py --calibrate`: the rate that bounds the push delivery, one
+# reduction per recurrent synaptic event
 L2_RED_PER_S = 2.2e11
 TIMESTEPS_PER_STEP = 1000
 JOB_TIMESTEPS = 10000
 
 # DRAM bytes (read + write) of the persistent kernel per recurrent event, from
-# one ncu capture of a smaller case of the same model (profiles/), valid only
-# for the kernel sources it was taken on.
+# one ncu capture of a smaller case of the same model, valid only for the
+# kernel sources it was taken on.
 NCU_TRAFFIC = {"kernel": "k_run_steps", "source_sha256": "b90c0415b662555f7b21f9ac18d86c85151df74431e875411f5be0250ca31c09",
                "bytes_per_event": 8.39,
                "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
-                          "376.9 MB DRAM read+write for 44.9 M recurrent events (profiles/k_run_steps_gauss_12x12.md), "
+                          "376.9 MB DRAM read+write for 44.9 M recurrent events, "
                           "scaled to a launch by its events"}
 
 
@@ -181,8 +182,8 @@ def config_block(cfg, extra=None):
         "imposed_rate_hz": cfg["imposed_rate_hz"],
         "ext_drive": "%.0f Hz x %.1f mV Poisson" % (cfg["ext_rate_hz"], cfg["J_ext_mV"]),
         "timesteps_per_step": TIMESTEPS_PER_STEP,
-        "l2": "inputs larger than L2 (129 MB): the %.1f GB synapse table is streamed every step"
-              % (n * 1128 * 9 / 1e9),
+        "l2": "inputs larger than L2 (129 MB): the %.1f GB synapse table (8 B per synapse, rows padded to "
+              "1128) is streamed every step" % (n * 1128 * 8 / 1e9),
         "parallelism": "replicas",
     }
     if extra:
