@@ -340,7 +340,12 @@ SNN_API uint64_t snn_launch_count(void);
  * allocating call is made.
  * The first call on a device looks up the scratch's device address
  * (cudaGetSymbolAddress, with that device current); make it before any stream
- * capture.  Calls share the scratch, so calls that overlap on the GPU (on
+ * capture.  Every later call only enqueues two kernels on `stream` (the
+ * stencil offsets are generated on the device, no host-to-device copy), so it
+ * may be captured into a CUDA graph.  The looked-up addresses are kept per
+ * device index for the life of the process: do not call this entry point
+ * after cudaDeviceReset (or any teardown of the device's primary context).
+ * Calls share the scratch, so calls that overlap on the GPU (on
  * different streams, or from different threads) race and must be serialised
  * by the caller.  The scratch needs no clearing: every entry read is first
  * written by the same call.

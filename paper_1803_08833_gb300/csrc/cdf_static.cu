@@ -33,6 +33,19 @@ std::mutex g_setup_mutex;
 double* g_scratch_ptr[kMaxDevices] = {};
 int16_t* g_offsets_ptr[kMaxDevices] = {};
 
+// The in-disc offsets (dx, dy) with dx^2 + dy^2 <= R2 in (dy, dx) raster
+// order, at most n entries (the host's count of the same rule).
+__global__ void k_disc_offsets(int R, uint32_t R2, uint32_t n, int16_t* out) {
+    uint32_t k = 0;
+    for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx)
+            if ((uint32_t)(dx * dx + dy * dy) <= R2 && k < n) {
+                out[2 * k] = (int16_t)dx;
+                out[2 * k + 1] = (int16_t)dy;
+                ++k;
+            }
+}
+
 snn_status static_fail(snn_status s, const std::string& msg) {
     snn::set_last_error(msg.c_str());
     return s;
@@ -81,18 +94,12 @@ snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh, uint32_
     if (!(cfg->cutoff_um >= 0.0) || cfg->cutoff_um / cfg->spacing_um > 512.0)
         return static_fail(SNN_EINVAL, "cutoff_um must be in [0, 512 * spacing_um]");
 
-    // the stencil: in-disc offsets in (dy, dx) raster order
-    const double q = cfg->cutoff_um / (double)cfg->spacing_um;
-    const uint32_t R2 = (uint32_t)std::floor(q * q + 1e-9);
+    // the stencil: in-disc offsets in (dy, dx) raster order (counted on the
+    // host by the same rule snn_build_network uses; written on the device)
+    uint32_t R2 = 0;
+    const std::vector<int16_t> off = snn::disc_offsets(*cfg, &R2);
     int R = 0;
     while ((uint32_t)((R + 1) * (R + 1)) <= R2) ++R;
-    std::vector<int16_t> off;
-    for (int dy = -R; dy <= R; ++dy)
-        for (int dx = -R; dx <= R; ++dx)
-            if ((uint32_t)(dx * dx + dy * dy) <= R2) {
-                off.push_back((int16_t)dx);
-                off.push_back((int16_t)dy);
-            }
     const uint32_t n_off = (uint32_t)(off.size() / 2);
     const uint64_t n_modules = (uint64_t)cfg->grid_w * cfg->grid_h;
     if (max_offsets) *max_offsets = n_off;
@@ -116,10 +123,13 @@ snn_status snn_build_cdf_static(const snn_config* cfg, uint32_t* thresh, uint32_
     if (st != SNN_OK) return st;
 
     cudaStream_t s = (cudaStream_t)stream;
-    // The offsets are copied from pageable host memory: the call returns once
-    // the host vector has been staged, so it may go out of scope afterwards.
-    cudaError_t e = cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(int16_t), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return static_fail(SNN_ECUDA, std::string("offset upload: ") + cudaGetErrorString(e));
+    // The offsets are a pure function of the cut-off: a one-thread kernel writes
+    // them into the fixed array (no host-to-device copy, so every work item of
+    // the call is a kernel on `stream`).
+    k_disc_offsets<<<1, 1, 0, s>>>(R, R2, n_off, doff);
+    snn::count_launch(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return static_fail(SNN_ECUDA, std::string("k_disc_offsets: ") + cudaGetErrorString(e));
 
     // The scratch needs no clearing: the kernel writes every entry it reads.
     snn::BuildView b{};

@@ -271,6 +271,9 @@ snn_status derive(snn_net* n) {
     return SNN_OK;
 }
 
+}  // namespace
+
+namespace snn {
 // In-disc grid offsets (dx, dy) with dx^2 + dy^2 <= R2, in (dy, dx) raster order.
 std::vector<int16_t> disc_offsets(const snn_config& c, uint32_t* R2_out) {
     const double q = c.cutoff_um / (double)c.spacing_um;
@@ -287,6 +290,9 @@ std::vector<int16_t> disc_offsets(const snn_config& c, uint32_t* R2_out) {
     *R2_out = R2;
     return off;
 }
+}  // namespace snn
+
+namespace {
 
 // Unnormalised lateral shape f at squared grid distance d2 (the same
 // expression order as the device kernel of the target-module tables).

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct snn_config;
 
 namespace snn {
@@ -176,6 +178,10 @@ int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memor
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
+// In-disc grid offsets (dx, dy pairs) of the cut-off radius, dx^2 + dy^2 <=
+// R2 = floor((cutoff / spacing)^2), in (dy, dx) raster order (the stencil order
+// of the target-module tables); *R2_out receives R2.
+std::vector<int16_t> disc_offsets(const snn_config& c, uint32_t* R2_out);
 cudaError_t prepare_deliver(uint32_t nb);
 
 void count_launch(uint64_t n);

@@ -75,3 +75,39 @@ def test_static_rejects_tables_beyond_the_fixed_scratch(env):
     assert st == snn.SNN_EINVAL
     assert "exceeds the fixed scratch" in L.snn_last_error().decode()
     assert mo.value == 441
+
+
+def test_static_tables_under_stream_capture(env):
+    """After a first call outside capture (the address lookup), a call inside a
+    stream capture enqueues only kernels; replaying the graph writes the same
+    tables as snn_build_network."""
+    snn, torch = env
+    cfg = W.exp_24x24_k2250()
+    _static_tables(snn, torch, cfg)  # first call on this device: symbol lookup outside capture
+    L = snn.load()
+    c = snn.config(cfg)
+    mo = ctypes.c_uint32()
+    snn.check(L.snn_build_cdf_static(ctypes.byref(c), None, None, None, ctypes.byref(mo), None))
+    nm = cfg["grid_w"] * cfg["grid_h"]
+    T = torch.full((nm * mo.value,), -7, dtype=torch.int32, device="cuda")
+    TM = torch.full((nm * mo.value,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.full((nm,), -7, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        st = L.snn_build_cdf_static(ctypes.byref(c), ctypes.c_void_p(T.data_ptr()), ctypes.c_void_p(TM.data_ptr()),
+                                    ctypes.c_void_p(cnt.data_ptr()), ctypes.byref(mo), ctypes.c_void_p(s.cuda_stream))
+        g.capture_end()
+    snn.check(st)
+    assert int(cnt[0].item()) == -7  # captured, not run
+    g.replay()
+    torch.cuda.synchronize()
+    as_u32 = lambda x: x.cpu().numpy().view(np.uint32)
+    T, TM, cnt = as_u32(T).reshape(nm, mo.value), as_u32(TM).reshape(nm, mo.value), as_u32(cnt)
+    rT, rTM, rcnt = _network_tables(snn, cfg)
+    assert np.array_equal(cnt, rcnt)
+    for m in range(len(cnt)):
+        n = cnt[m]
+        assert np.array_equal(T[m, :n], rT[m, :n]), m
+        assert np.array_equal(TM[m, :n], rTM[m, :n]), m
