@@ -41,10 +41,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "synaptic events/s on 1 GB300, % of HBM roofline; served p50/p99 latency"
 UNIT = "synaptic events/s"
+# algorithmic bytes of the method: per recurrent event the synapse's uint32
+# target, weight (f32 / bf16) and uint8 delay; per neuron and step its input
+# slot read and cleared (4 + 4), V and c read and written (16), ref (2)
+ALG_BYTES_PER_EVENT = {"f32": 9, "bf16": 7}
+ALG_NEURON_BYTES = 26
+# what this build's table layout moves: one 32-bit target | delay << 24 word
+# and the weight
 BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
-# neuron update: the ring slot read and cleared; V, c (f32) and ref (u8) stay in
-# shared memory for the whole launch (read and written back once per launch)
-NEURON_BYTES = 2 * 4
+# neuron update, schedule 2: the ring slot read and cleared; V, c (f32) and ref
+# (u8) stay in shared memory for the whole launch (read and written back once
+# per launch).  Schedule 4: the state is read and written every step (18 B) and
+# the ring row entering the delay window is read and cleared (8 B).
+NEURON_BYTES = {2: 2 * 4, 3: 2 * 4 + 18, 4: 18 + 8}
 # random 4-byte red.global.add.s32 into an L2-resident buffer (4-60 MB), measured on
 # GB300 by `bench.py --calibrate`: the rate that bounds the push delivery, one
 # reduction per recurrent synaptic event
@@ -331,22 +340,37 @@ def run_gpu(args):
     # algorithmic bytes of the dominant kernel per launch / its mean CUDA-event duration
     steps_timed = args.steps * T
     traffic = None
+    packed = None
     if pl > 0:  # persistent schedule: one launch = T steps of neuron update + delivery
-        kernel = ("%s<f32> (persistent: neuron update + delivery, %d steps per launch)"
-                  % ("k_run_steps_tiled" if schedule == 3 else "k_run_steps", T))
+        kname = {3: "k_run_steps_tiled", 4: "k_run_steps_owned"}.get(schedule, "k_run_steps")
+        kernel = "%s<f32> (persistent: neuron update + delivery, %d steps per launch)" % (kname, T)
         launches_timed = pl
-        alg_per_launch = (BYTES_PER_EVENT["f32"] * rec + NEURON_BYTES * net.N * steps_timed) / max(args.steps, 1)
-        achieved = alg_per_launch / (pms / pl / 1000.0) / 1e9 if pms > 0 else None
-        bytes_note = "8 B per recurrent event + %d B per neuron per step" % NEURON_BYTES
+        launch_s = pms / pl / 1000.0
+        alg_per_launch = (ALG_BYTES_PER_EVENT["f32"] * rec + ALG_NEURON_BYTES * net.N * steps_timed) / max(args.steps, 1)
+        achieved = alg_per_launch / launch_s / 1e9 if pms > 0 else None
+        bytes_note = ("%d B per recurrent event (uint32 target + f32 weight + uint8 delay) + %d B per neuron per "
+                      "step" % (ALG_BYTES_PER_EVENT["f32"], ALG_NEURON_BYTES))
+        nb = NEURON_BYTES.get(schedule, NEURON_BYTES[2])
+        pk = (BYTES_PER_EVENT["f32"] * rec + nb * net.N * steps_timed) / max(args.steps, 1)
+        packed = {"achieved": pk / launch_s / 1e9 if pms > 0 else None,
+                  "frac": pk / launch_s / 1e9 / peak if pms > 0 else None,
+                  "bytes_per_launch": pk,
+                  "bytes": "%d B per recurrent event (target | delay word + f32 weight) + %d B per neuron per step "
+                           "(what this schedule moves)" % (BYTES_PER_EVENT["f32"], nb)}
         if (schedule == 2 and NCU_TRAFFIC["source_sha256"] == _kernel_source_sha()
                 and NCU_TRAFFIC["bytes_per_event"]):
             traffic = NCU_TRAFFIC["bytes_per_event"] * rec / max(args.steps, 1)
     else:
         kernel = "k_deliver_warp<f32>"
         launches_timed = dl
-        alg_per_launch = BYTES_PER_EVENT["f32"] * rec / steps_timed
+        alg_per_launch = ALG_BYTES_PER_EVENT["f32"] * rec / steps_timed
         achieved = alg_per_launch / (dms / max(dl, 1) / 1000.0) / 1e9 if dms > 0 else None
-        bytes_note = "8 B per recurrent event"
+        bytes_note = "%d B per recurrent event" % ALG_BYTES_PER_EVENT["f32"]
+    dphase_s = (s1["deliver_phase_ns"] - s0["deliver_phase_ns"]) / 1e9 if pl else 0.0
+    delivery_phase = ({"achieved": ALG_BYTES_PER_EVENT["f32"] * rec / dphase_s / 1e9,
+                       "frac": ALG_BYTES_PER_EVENT["f32"] * rec / dphase_s / 1e9 / peak,
+                       "bytes": "%d B per recurrent event over the delivery phases (GPU timer of CTA 0, their "
+                                "barriers included)" % ALG_BYTES_PER_EVENT["f32"]} if dphase_s > 0 else None)
     net.set_timing(0)
 
     # end-to-end jobs through the public API with host buffers
@@ -404,6 +428,7 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "algorithmic_bytes": bytes_note, "bytes_per_launch": alg_per_launch,
+                     "packed": packed, "delivery_phase": delivery_phase,
                      "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
                      "launches_timed": launches_timed},

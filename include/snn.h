@@ -250,10 +250,33 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  *      in a shared-memory tile of (D - 1) x M int32 and adds the tile into the
  *      ring with plain coalesced writes.  Needs table_layout =
  *      SNN_LAYOUT_GROUPED and a tile that fits in shared memory.
+ *   4: one cooperative launch per call, one CTA per SM, each CTA owning a
+ *      band of ceil(N / SMs) neurons: it integrates them and keeps the delay
+ *      ring rows of the next W steps of its band in shared memory (the
+ *      window, snn_set_window).  Rows are pushed as in schedule 2; an event
+ *      with delay <= W becomes a record in the owner band's queue, applied by
+ *      the owner with shared-memory atomics, one with a longer delay goes into
+ *      the ring with an L2 reduction.  Between calls the ring holds the same
+ *      values as under the other schedules.  Two grid barriers per step,
+ *      bounded like those of schedule 2.  Errors: SNN_EINVAL if no window
+ *      row fits in shared memory, SNN_ENOMEM for the queues (G x G x cap x
+ *      8 bytes, G = SMs).
  * All schedules give bit-identical results.  block: threads per block of the
  * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
 SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t block);
+
+/* Delay window of schedule 4 (no counterpart in the paper; the delay queues
+ * are those of flow step 3, Sec. II-A): window = steps of the ring each band
+ * keeps in shared memory (0 = the most that fit, at most D - 1), queue_cap =
+ * records per (owner, producer) queue and step (0 = a default from the
+ * expected events of a step).  A queue that fills up sends its further
+ * events to the ring and the owner folds them in, so any capacity gives the
+ * same results.  Outputs (may be NULL): the window and capacity in use.
+ * Synchronises `stream`.  Errors: SNN_EINVAL (window too large, capacity >
+ * 2^20), SNN_ENOMEM. */
+SNN_API snn_status snn_set_window(snn_net* net, uint32_t window, uint32_t queue_cap, uint32_t* window_out,
+                                  uint32_t* cap_out, void* stream);
 
 /* Banded delivery of schedule 2 (no counterpart in the paper, whose processes
  * each own a tile of the grid): the target module rows are split into `bands`
@@ -284,8 +307,8 @@ SNN_API snn_status snn_set_bands(snn_net* net, uint32_t bands, uint32_t* chosen,
 SNN_API snn_status snn_set_resident_state(snn_net* net, int32_t enable, int32_t* resident, void* stream);
 
 /* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
- * per delivery block, 2, and 3 if the network has the grouped layout and its
- * tile fits) for trial_steps steps from the same snapshot of the dynamic
+ * per delivery block, 2, 3 if the network has the grouped layout and its
+ * tile fits, 4 if a delay window fits) for trial_steps steps from the same snapshot of the dynamic
  * state, times each with CUDA events, restores the state (the raster and the
  * counters are as before the call) and selects the fastest.  If cache_path
  * is not NULL the choice is looked up there first and appended after

@@ -2,8 +2,9 @@
 //
 // Candidates: per-step launches with warp-per-chunk delivery at 128 and 256
 // threads per block, per-step launches with thread-per-synapse delivery at
-// 128 and 256, the persistent kernel, and the persistent target-tiled kernel
-// when the network has the grouped layout and its tile fits.  Each candidate
+// 128 and 256, the persistent kernel, the persistent target-tiled kernel
+// when the network has the grouped layout and its tile fits, and the
+// persistent owner-windowed kernel when a window fits.  Each candidate
 // runs `trial_steps` steps from the same snapshot of the dynamic state, timed
 // with CUDA events on the caller's stream; the state is restored afterwards,
 // so tuning never changes the simulation.  The choice is cached in a text
@@ -94,7 +95,7 @@ snn_status snn_autotune(snn_net* net, uint32_t trial_steps, const char* cache_pa
     std::vector<char> snap(n);
     e = snn_snapshot(net, snap.data(), n, &n, stream);
     if (e != SNN_OK) return e;
-    const int cand[][2] = {{0, 128}, {0, 256}, {1, 128}, {1, 256}, {2, 0}, {3, 0}};
+    const int cand[][2] = {{0, 128}, {0, 256}, {1, 128}, {1, 256}, {2, 0}, {3, 0}, {4, 0}};
     cudaEvent_t a, z;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess)
         return afail(SNN_ECUDA, "cudaEventCreate failed");

@@ -119,12 +119,13 @@ struct QuadOut {
     uint32_t R;
 };
 
-// Integrates the loaded quad into `out` and clears the ring slot.  Returns a
-// 4-bit spike mask; adds the external events to `ext` and, under the pairwise
-// rule, the spiking rows' lengths to `rec`.
+// Integrates the loaded quad into `out` and (CLEAR) clears the ring slot.
+// Returns a 4-bit spike mask; adds the external events to `ext` and, under the
+// pairwise rule, the spiking rows' lengths to `rec`.
+template <bool CLEAR = true>
 __device__ __forceinline__ uint32_t integrate_quad(const NetView& v, uint32_t base, uint32_t slot, const QuadIn& in,
                                                    uint32_t& ext, uint64_t& rec, QuadOut& out) {
-    *reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base) = make_int4(0, 0, 0, 0);
+    if (CLEAR) *reinterpret_cast<int4*>(v.ring + (size_t)slot * v.Npad + base) = make_int4(0, 0, 0, 0);
     float Vq[4] = {in.V.x, in.V.y, in.V.z, in.V.w};
     float Cq[4] = {in.C.x, in.C.y, in.C.z, in.C.w};
     const int32_t Iq[4] = {in.I.x, in.I.y, in.I.z, in.I.w};

@@ -82,6 +82,9 @@ struct snn_net {
     int grid = 0;       // delivery grid of schedules 0 and 1
     int pgrid = 0;      // persistent grid (schedule 2)
     int tgrid = 0;      // tiled persistent grid (schedule 3), 0 if unavailable
+    int ogrid = 0;      // owner-windowed persistent grid (schedule 4), 0 until set up
+    int2* own_rec = nullptr;  // schedule 4 record queues and their size
+    size_t own_rec_bytes = 0;
     uint32_t pair_n = 0;              // pairwise law: stencil entries
     uint2* band_ids_dev = nullptr;    // banded delivery tables
     uint32_t* band_rng_dev = nullptr;
@@ -423,6 +426,62 @@ void free_block(snn_net* n, void* p, size_t bytes) {
             n->device_bytes -= (bytes + 255) & ~(size_t)255;
             return;
         }
+}
+
+// Owner-windowed delivery (schedule 4): bands of ceil(Q / G) quads, one per
+// CTA of a grid of one CTA per SM; a window of `window` steps (0 = the largest
+// that fits in shared memory, at most D - 1); record queues of `queue_cap`
+// entries per (owner, producer) (0 = twice the expected near events of a step
+// at the larger of the imposed rate and 10 Hz, plus 64, in [64, 4096]).
+snn_status owned_setup(snn_net* n, uint32_t window, uint32_t queue_cap) {
+    NetView& v = n->v;
+    const int G = owned_grid();
+    if (G <= 0) return fail(SNN_ECUDA, "schedule 4: no multiprocessor count");
+    const uint32_t Q = n->Npad / 4;
+    const uint32_t BQ = (Q + (uint32_t)G - 1) / (uint32_t)G;
+    const uint32_t Wmax = owned_max_window(v, G, BQ);
+    if (Wmax == 0)
+        return fail(SNN_EINVAL, "schedule 4: a delay window row of %u neurons per CTA does not fit in shared memory",
+                    BQ * 4);
+    const uint32_t W = window == 0 ? Wmax : window;
+    if (W > Wmax) return fail(SNN_EINVAL, "schedule 4: window %u exceeds the %u steps that fit (D - 1 = %u)", W, Wmax,
+                              v.D - 1);
+    uint32_t cap = queue_cap;
+    if (cap == 0) {
+        const double rate = std::max(10.0, (double)n->cfg.imposed_rate_hz);
+        const double ev = (double)n->N * n->K * rate * n->cfg.dt_ms / 1000.0;
+        cap = (uint32_t)std::min(4096.0, std::max(64.0, 2.0 * ev / ((double)G * G) + 64.0));
+        cap = (cap + 31) / 32 * 32;
+    }
+    if (cap > (1u << 20)) return fail(SNN_EINVAL, "schedule 4: queue capacity %u exceeds 2^20", cap);
+    const uint64_t magic = ((uint64_t)1 << 32) / BQ + (((uint64_t)1 << 32) % BQ ? 1 : 0);
+    for (uint32_t q = 0; q < Q; ++q) {  // the band arithmetic of the kernel, checked for every quad
+        uint32_t b = (uint32_t)(((uint64_t)q * magic) >> 32);
+        if ((uint64_t)b * BQ > q) --b;
+        if (!((uint64_t)b * BQ <= q && q < (uint64_t)(b + 1) * BQ))
+            return fail(SNN_EINVAL, "schedule 4: band arithmetic fails for quad %u", q);
+    }
+    const size_t rec_bytes = (size_t)G * G * cap * sizeof(int2);
+    if (!n->own_rec || rec_bytes != n->own_rec_bytes || n->ogrid != G) {
+        if (n->own_rec) free_block(n, n->own_rec, n->own_rec_bytes);
+        n->own_rec = (int2*)dev_alloc(n, rec_bytes);
+        if (!n->own_rec) return fail(SNN_ENOMEM, "schedule 4: device allocation of %zu bytes of queues failed", rec_bytes);
+        n->own_rec_bytes = rec_bytes;
+    }
+    if (!v.own_cnt || n->ogrid != G) {
+        v.own_cnt = (uint32_t*)dev_alloc(n, (size_t)G * G * 4);
+        v.own_ovf = (uint32_t*)dev_alloc(n, (size_t)G * 4);
+        if (!v.own_cnt || !v.own_ovf) return fail(SNN_ENOMEM, "schedule 4: device allocation of queue counters failed");
+        CUDA_TRY(cudaMemset(v.own_ovf, 0, (size_t)G * 4));
+        CUDA_TRY(cudaMemset(v.own_cnt, 0, (size_t)G * G * 4));
+    }
+    v.own_rec = n->own_rec;
+    v.own_W = W;
+    v.own_BQ = BQ;
+    v.own_cap = cap;
+    v.own_magic = magic;
+    n->ogrid = G;
+    return SNN_OK;
 }
 
 // Bands of target module rows for the persistent delivery.  bands = 0 picks
@@ -848,6 +907,8 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
             }
             if (n->schedule == 3)
                 CUDA_TRY(launch_tiled(n->v, m, n->tgrid, s));
+            else if (n->schedule == 4)
+                CUDA_TRY(launch_owned(n->v, m, n->ogrid, s));
             else
                 CUDA_TRY(launch_persistent(n->v, m, n->pgrid, s));
             if (timed) {
@@ -1124,6 +1185,17 @@ snn_status snn_restore(snn_net* n, const void* host_buf, size_t nbytes, void* st
     return SNN_OK;
 }
 
+snn_status snn_set_window(snn_net* n, uint32_t window, uint32_t queue_cap, uint32_t* window_out,
+                          uint32_t* cap_out, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight uses the queues
+    snn_status st = owned_setup(n, window, queue_cap);
+    if (st != SNN_OK) return st;
+    if (window_out) *window_out = n->v.own_W;
+    if (cap_out) *cap_out = n->v.own_cap;
+    return SNN_OK;
+}
+
 snn_status snn_set_bands(snn_net* n, uint32_t bands, uint32_t* chosen, void* stream) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight reads the tables
@@ -1141,7 +1213,11 @@ snn_status snn_set_resident_state(snn_net* n, int32_t enable, int32_t* resident,
 
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
-    if (schedule < 0 || schedule > 3) return fail(SNN_EINVAL, "schedule must be 0, 1, 2 or 3");
+    if (schedule < 0 || schedule > 4) return fail(SNN_EINVAL, "schedule must be 0, 1, 2, 3 or 4");
+    if (schedule == 4 && n->ogrid == 0) {
+        snn_status st = owned_setup(n, 0, 0);
+        if (st != SNN_OK) return st;
+    }
     if (schedule == 3 && n->cfg.table_layout != SNN_LAYOUT_GROUPED)
         return fail(SNN_EINVAL, "schedule 3 needs a network built with table_layout = SNN_LAYOUT_GROUPED");
     if (schedule == 3 && n->tgrid == 0)

@@ -102,6 +102,15 @@ struct NetView {
     uint32_t band_key_row;    // band_rng is indexed by source module row (1) or source module (0)
     const uint2* band_ids;    // n_bands: neuron ids [x, y) of the sources whose stencil reaches the band
     const uint32_t* band_rng; // keys x n_bands: segment-index entries [j0, j1) of the band, j0 | j1 << 16
+    // owner-windowed delivery (schedule 4): CTA b owns the quads [b BQ, (b + 1) BQ)
+    // and keeps the ring rows of the next own_W steps of its band in shared memory
+    uint32_t own_W;           // window steps (1 <= own_W <= D - 1)
+    uint32_t own_BQ;          // quads per band
+    uint32_t own_cap;         // records per (owner, producer) queue
+    uint64_t own_magic;       // ceil(2^32 / own_BQ): band of quad q = (q * own_magic) >> 32, corrected down
+    int2* own_rec;            // G x G x own_cap records {window index, fixed-point weight}, owner-major
+    uint32_t* own_cnt;        // G x G records queued by producer p for owner b at [b G + p]
+    uint32_t* own_ovf;        // G flags: a producer's queue for this owner overflowed (events went to the ring)
 };
 
 // Parameters of the construction kernels.
@@ -177,6 +186,13 @@ cudaError_t launch_groups(const GroupMeta& gm, int grid, cudaStream_t s);
 int tiled_grid(const NetView& v);  // 0 if the tile does not fit in shared memory
 cudaError_t launch_tiled(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 cudaError_t launch_persistent(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
+// Owner-windowed persistent kernel (schedule 4): the largest window (steps) that
+// fits next to the kernel's other shared memory on `grid` CTAs for bands of BQ
+// quads (0 if none), and the launch.
+uint32_t owned_max_window(const NetView& v, int grid, uint32_t BQ);
+int owned_grid();
+size_t owned_smem_bytes(uint32_t W, uint32_t BQ, int grid);
+cudaError_t launch_owned(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
 // In-disc grid offsets (dx, dy pairs) of the cut-off radius, dx^2 + dy^2 <=
 // R2 = floor((cutoff / spacing)^2), in (dy, dx) raster order (the stencil order

@@ -110,6 +110,7 @@ def load():
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
         "snn_set_bands": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
+        "snn_set_window": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32), vp]),
         "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
                               P(ctypes.c_double), vp]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
@@ -371,6 +372,13 @@ class Network:
     # -- tuning / timing ---------------------------------------------------
     def set_schedule(self, schedule: int, block: int = 0):
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
+
+    def set_window(self, window: int = 0, queue_cap: int = 0):
+        """Schedule 4's delay window (steps kept in shared memory per band) and
+        record-queue capacity; 0 picks the default.  Returns (window, cap)."""
+        w, c = ctypes.c_uint32(), ctypes.c_uint32()
+        check(load().snn_set_window(self._h, int(window), int(queue_cap), ctypes.byref(w), ctypes.byref(c), self._s))
+        return w.value, c.value
 
     def set_bands(self, bands: int = 0) -> int:
         """Banded delivery of schedule 2 (0 = automatic); returns the band count in use."""

@@ -139,7 +139,7 @@ def _compare(net, ref):
     return len(st)
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("name", sorted(SIM_CASES))
 def test_simulation_bit_exact(snn, name, schedule):
     make, steps = SIM_CASES[name]
@@ -302,7 +302,7 @@ def test_full_size_schedules_agree(snn):
     """The 24x24 Gaussian network run 60 steps with each schedule: identical state."""
     cfg = W.gauss_24x24_k1125(seed=3, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped")
     out = []
-    for schedule in (0, 2, 3):
+    for schedule in (0, 2, 3, 4):
         with snn.Network(cfg, raster_capacity=1 << 20) as net:
             net.set_schedule(schedule)
             net.step(60)
@@ -565,7 +565,7 @@ def test_random_descriptions_bit_exact(snn, k):
     cfg = _random_configs()[k]
     ref = oracle.OracleNet(cfg)
     ref.step(120)
-    schedules = [0, 1, 2] + ([3] if cfg.get("table_layout") == "grouped" else [])
+    schedules = [0, 1, 2, 4] + ([3] if cfg.get("table_layout") == "grouped" else [])
     for schedule in schedules:
         with snn.Network(cfg, raster_capacity=1 << 22) as net:
             try:
