@@ -190,7 +190,6 @@ def config_block(cfg, extra=None):
                     % (g, g, g, g, format(n, ","), round(n * 1125 / 1e6)),
         "imposed_rate_hz": cfg["imposed_rate_hz"],
         "ext_drive": "%.0f Hz x %.1f mV Poisson" % (cfg["ext_rate_hz"], cfg["J_ext_mV"]),
-        "timesteps_per_step": TIMESTEPS_PER_STEP,
         "l2": "inputs larger than L2 (129 MB): the %.1f GB synapse table (8 B per synapse, rows padded to "
               "1128) is streamed every step" % (n * 1128 * 8 / 1e9),
         "parallelism": "replicas",
@@ -200,42 +199,77 @@ def config_block(cfg, extra=None):
     return d
 
 
+# CPU part numbers of the Arm implementer (0x41) as /proc/cpuinfo reports them
+_ARM_PARTS = {0xd0c: "Neoverse-N1", 0xd40: "Neoverse-V1", 0xd49: "Neoverse-N2", 0xd4f: "Neoverse-V2",
+              0xd8e: "Neoverse-N3", 0xd84: "Neoverse-V3"}
+
+
 def host_cpu():
-    """The host the CPU baseline ran on: architecture, logical CPUs and model name."""
+    """The host the CPU baseline ran on: architecture, logical CPUs and model
+    (lscpu's model name, else /proc/cpuinfo's model name or Arm part number)."""
     import platform
-    model = ""
+    model = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "processor") and ":" in line and not line.split(":")[1].strip().isdigit():
-                    model = line.split(":", 1)[1].strip()
-                    break
-    except OSError:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
         pass
-    return {"arch": platform.machine(), "logical_cpus": os.cpu_count(), "model": model or None}
+    if not model:
+        impl = part = None
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    key, _, val = line.partition(":")
+                    key, val = key.strip().lower(), val.strip()
+                    if key in ("model name", "cpu model") and val:
+                        model = val
+                        break
+                    if key == "cpu implementer" and impl is None:
+                        impl = val
+                    if key == "cpu part" and part is None:
+                        part = val
+        except OSError:
+            pass
+        if not model and impl and part:
+            try:
+                model = _ARM_PARTS.get(int(part, 16), "part %s" % part) if int(impl, 16) == 0x41 else \
+                    "implementer %s part %s" % (impl, part)
+            except ValueError:
+                model = "implementer %s part %s" % (impl, part)
+    return {"arch": platform.machine(), "logical_cpus": os.cpu_count(), "model": model}
 
 
 # --------------------------------------------------------------------------
-def cpu_oracle_rate(cfg, grid, min_seconds, max_steps, warm_steps=20):
-    """Oracle simulation-phase throughput on a grid x grid patch of the model."""
+ORACLE_SETTLE_STEPS = 100  # simulated steps run before any oracle timing
+
+
+def oracle_sample_desc(cfg, settle, timed_steps, build_s):
+    n = cfg["grid_w"] * cfg["grid_h"] * cfg["neurons_per_module"]
+    return ("oracle (single-threaded C) on the full workload network (%d neurons, K=%d, imposed %.1f Hz): built "
+            "once (%.0f s, not timed), %d settling steps, then %d simulated 1 ms steps timed (a truncated window of "
+            "the 1,000-step bench step; recurrent events / window time), simulation phase only"
+            % (n, cfg["K"], cfg["imposed_rate_hz"], build_s, settle, timed_steps))
+
+
+def cpu_oracle_full(cfg, window_steps, settle=ORACLE_SETTLE_STEPS):
+    """Oracle simulation-phase throughput on the full benchmark network."""
     import oracle
-    from paper_1803_08833_gb300 import workloads as W
-    sample = W.patch(cfg, grid)
-    net = oracle.OracleNet(sample)
-    net.step(warm_steps)
+    t0 = time.perf_counter()
+    net = oracle.OracleNet(cfg)
+    build_s = time.perf_counter() - t0
+    net.step(settle)
     s0 = net.stats()
     t0 = time.perf_counter()
-    steps = 0
-    while steps < max_steps and (time.perf_counter() - t0 < min_seconds or steps < 5):
-        net.step(10)
-        steps += 10
+    net.step(window_steps)
     dt = time.perf_counter() - t0
-    s1 = net.stats()
+    ev = net.stats()["rec_events"] - s0["rec_events"]
     net.close()
-    ev = s1["rec_events"] - s0["rec_events"]
-    return ev / dt, {"steps": steps, "seconds": dt, "events": ev, "neurons": sample["grid_w"] ** 2 * sample[
-        "neurons_per_module"]}
+    return {"value": ev / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": oracle_sample_desc(cfg, settle, window_steps, build_s), "host": host_cpu(),
+            "window_steps": window_steps, "window_s": dt, "events": ev, "build_s": build_s}
 
 
 def run_reference(args):
@@ -244,11 +278,11 @@ def run_reference(args):
         return 0
     cfg = workload()
     import oracle
-    from paper_1803_08833_gb300 import workloads as W
-    grid = 6
-    sample = W.patch(cfg, grid)
-    steps_per = 100
-    net = oracle.OracleNet(sample)
+    steps_per = args.ref_sample_steps
+    t0 = time.perf_counter()
+    net = oracle.OracleNet(cfg)
+    build_s = time.perf_counter() - t0
+    net.step(ORACLE_SETTLE_STEPS)
     for _ in range(args.warmup):
         net.step(steps_per)
     s0 = net.stats()
@@ -257,22 +291,28 @@ def run_reference(args):
         net.step(steps_per)
     dt = time.perf_counter() - t0
     s1 = net.stats()
+    net.close()
     value = (s1["rec_events"] - s0["rec_events"]) / dt
-    desc = ("oracle (single-threaded C) on a %dx%d-module patch of the workload (%d neurons, K=%d, "
-            "imposed %.1f Hz), %d simulated 1 ms steps per bench step, simulation phase only"
-            % (grid, grid, grid * grid * sample["neurons_per_module"], sample["K"], sample["imposed_rate_hz"],
-               steps_per))
+    desc = oracle_sample_desc(cfg, ORACLE_SETTLE_STEPS + args.warmup * steps_per, args.steps * steps_per, build_s)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0 / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config_block(cfg, {"sample": desc}),
+        "data": "synthetic", "config": config_block(cfg),
+        "detail": {"sample": desc, "timesteps_per_step": steps_per,
+                   "note": "each bench step is a bounded sample of %d simulated steps of the same network; the "
+                           "metric is per event, so it compares with the GPU arm's 1,000-step bench steps"
+                           % steps_per},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
                          "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _cpu_baseline_child(cfg, window_steps, q):
+    q.put(cpu_oracle_full(cfg, window_steps))
 
 
 # --------------------------------------------------------------------------
@@ -292,6 +332,16 @@ def run_gpu(args):
     T = args.timesteps
     peak, peak_kind = _peaks()
     stream = torch.cuda.current_stream()
+
+    # the CPU baseline (the oracle on the same network, one core) runs in a
+    # spawned process beside the GPU legs
+    cpu_proc = cpu_q = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        cpu_q = ctx.Queue()
+        cpu_proc = ctx.Process(target=_cpu_baseline_child, args=(cfg, args.cpu_window, cpu_q), daemon=True)
+        cpu_proc.start()
 
     t_build = time.perf_counter()
     net = snn.Network(cfg, raster_capacity=T * 20000)
@@ -385,14 +435,12 @@ def run_gpu(args):
     served = None if args.no_served else run_served(snn, args, stream)
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        rate, info = cpu_oracle_rate(cfg, args.cpu_grid, args.cpu_seconds, 100000)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "oracle (single-threaded C) on a %dx%d-module patch of the workload (%d neurons, "
-                         "K=1125, imposed 7.5 Hz), %d simulated steps after 20 warm-up steps, %.1f s, "
-                         "simulation phase only" % (args.cpu_grid, args.cpu_grid, info["neurons"], info["steps"],
-                                                    info["seconds"]),
-               "host": host_cpu()}
+    if cpu_proc is not None:
+        try:
+            cpu = cpu_q.get(timeout=1800)
+        except Exception as e:  # report, never hang the bench
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": repr(e)}
+        cpu_proc.join(timeout=60)
 
     if rank != 0:
         return 0
@@ -401,7 +449,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_block(cfg, {"build_ms": round(t_build * 1000.0, 1),
+        "config": config_block(cfg),
+        "detail": dict({"build_ms": round(t_build * 1000.0, 1),
                                      "timesteps_per_step": T,
                                      "spikes_per_timestep": spikes / (args.steps * T),
                                      "rate_hz": spikes / (args.steps * T) / net.N * 1000.0,
@@ -752,8 +801,10 @@ def main(argv=None):
     ap.add_argument("--served-seconds", type=float, default=60.0)
     ap.add_argument("--served-chunk", type=int, default=250)
     ap.add_argument("--served-slots", type=int, default=64)
-    ap.add_argument("--cpu-grid", type=int, default=6)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-window", type=int, default=200,
+                    help="simulated steps of the oracle timed on the full network for cpu_baseline")
+    ap.add_argument("--ref-sample-steps", type=int, default=10,
+                    help="simulated steps of the oracle per bench step in --impl reference")
     ap.add_argument("--timing-every", type=int, default=10,
                     help="time the kernels of every n-th simulated step with CUDA events")
     ap.add_argument("--grid", type=int, default=24, help="modules per side (24 = the benchmark workload)")

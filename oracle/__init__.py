@@ -74,6 +74,10 @@ class OrConsts(ctypes.Structure):
     ]
 
 
+class OrConsts64(ctypes.Structure):
+    _fields_ = [("a_m", ctypes.c_double), ("a_c", ctypes.c_double), ("kc", ctypes.c_double)]
+
+
 # names used by workload dictionaries -> oracle field names
 _MAP = {
     "tau_m_ms": "tau_m", "E_mV": "E", "V_th_mV": "V_th", "V_reset_mV": "V_reset",
@@ -147,10 +151,18 @@ def lib():
         L.or_time.restype = ctypes.c_uint32
         L.or_get_state.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4
         L.or_get_state_f64.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2
+        L.or_set_state_f64.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2
+        L.or_get_ring_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.or_constants64.argtypes = [P(OrParams), P(OrConsts64)]
+        L.or_lif_update64.argtypes = [P(OrConsts64), P(OrParams), ctypes.c_uint32, P(ctypes.c_double),
+                                      P(ctypes.c_double), P(ctypes.c_uint8), ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_int]
         L.or_set_state.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 3
         L.or_get_stats.argtypes = [ctypes.c_void_p, u64p, u64p, u64p]
         L.or_gen_rows.argtypes = [P(OrParams), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_void_p,
                                   ctypes.c_void_p, ctypes.c_void_p]
+        L.or_gen_rows_list.argtypes = [P(OrParams), ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64,
+                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.or_gen_rows_v.argtypes = [P(OrParams), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.or_pair_stencil.argtypes = [P(OrParams), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -225,6 +237,29 @@ def lif_update(cfg: dict, V: float, c: float, ref: int, exc: bool, I_fx: int, fo
     return v.value, cf.value, r.value, bool(s)
 
 
+def constants64(cfg: dict) -> dict:
+    """The FP64 mode's propagator constants a_m, a_c, kc (double)."""
+    k = OrConsts64()
+    if lib().or_constants64(ctypes.byref(params(cfg)), ctypes.byref(k)):
+        raise ValueError(lib().or_error().decode())
+    return {"a_m": k.a_m, "a_c": k.a_c, "kc": k.kc}
+
+
+def lif_update64(cfg: dict, V: float, c: float, ref: int, exc: bool, I_mV: float, forced=False):
+    """One neuron update of the FP64 mode (input in mV); returns (V, c, ref, spiked)."""
+    p = params(cfg)
+    k = OrConsts64()
+    if lib().or_constants64(ctypes.byref(p), ctypes.byref(k)):
+        raise ValueError(lib().or_error().decode())
+    ref_steps = constants(cfg)["ref_steps"]
+    v = ctypes.c_double(V)
+    cd = ctypes.c_double(c)
+    r = ctypes.c_uint8(ref)
+    s = lib().or_lif_update64(ctypes.byref(k), ctypes.byref(p), ref_steps, ctypes.byref(v), ctypes.byref(cd),
+                              ctypes.byref(r), int(bool(exc)), float(I_mV), int(bool(forced)))
+    return v.value, cd.value, r.value, bool(s)
+
+
 def gen_rows(cfg: dict, first: int, count: int):
     """Synapse rows [first, first + count) without building the whole network."""
     p = params(cfg)
@@ -253,6 +288,25 @@ def gen_rows_v(cfg: dict, first: int, count: int):
         raise ValueError(lib().or_error().decode())
     n = int(ln[:count].sum())
     return tgt[:n].copy(), w[:n].copy(), d[:n].copy(), ln[:count].copy()
+
+
+def gen_rows_list(cfg: dict, ids):
+    """Rows of the neurons `ids` (any order, either rule), back to back:
+    (targets, weights, delays, row lengths)."""
+    ids = np.ascontiguousarray(ids, np.uint32)
+    p = params(cfg)
+    c = constants(cfg)
+    M = int(cfg["neurons_per_module"])
+    per_row = int(cfg.get("K", 0)) if int(p.conn_rule) == 0 else max(1, c["n_pair_offsets"]) * M
+    cap = max(1, per_row * len(ids))
+    tgt = np.empty(cap, np.uint32)
+    w = np.empty(cap, np.float32)
+    d = np.empty(cap, np.uint8)
+    ln = np.empty(max(1, len(ids)), np.uint32)
+    if lib().or_gen_rows_list(ctypes.byref(p), _ptr(ids), len(ids), cap, _ptr(tgt), _ptr(w), _ptr(d), _ptr(ln)):
+        raise ValueError(lib().or_error().decode())
+    n = int(ln[:len(ids)].sum())
+    return tgt[:n], w[:n], d[:n], ln[:len(ids)].copy()
 
 
 def pair_stencil(cfg: dict):
@@ -387,9 +441,11 @@ class OracleNet:
         if self.fp64:
             V = np.empty(N, np.float64)
             c = np.empty(N, np.float64)
+            ring = np.empty(D * N, np.float64)
             lib().or_get_state(self._h, None, None, _ptr(ref), None)
             lib().or_get_state_f64(self._h, _ptr(V), _ptr(c))
-            return {"V": V, "c": c, "ref": ref}
+            lib().or_get_ring_f64(self._h, _ptr(ring))
+            return {"V": V, "c": c, "ref": ref, "ring": ring.reshape(D, N)}
         V = np.empty(N, np.float32)
         c = np.empty(N, np.float32)
         ring = np.empty(D * N, np.int32)
@@ -397,10 +453,15 @@ class OracleNet:
         return {"V": V, "c": c, "ref": ref, "ring": ring.reshape(D, N)}
 
     def set_state(self, V=None, c=None, ref=None):
-        V = None if V is None else np.ascontiguousarray(V, np.float32)
-        c = None if c is None else np.ascontiguousarray(c, np.float32)
+        dt = np.float64 if self.fp64 else np.float32
+        V = None if V is None else np.ascontiguousarray(V, dt)
+        c = None if c is None else np.ascontiguousarray(c, dt)
         ref = None if ref is None else np.ascontiguousarray(ref, np.uint8)
-        lib().or_set_state(self._h, _ptr(V), _ptr(c), _ptr(ref))
+        if self.fp64:
+            lib().or_set_state_f64(self._h, _ptr(V), _ptr(c))
+            lib().or_set_state(self._h, None, None, _ptr(ref))
+        else:
+            lib().or_set_state(self._h, _ptr(V), _ptr(c), _ptr(ref))
 
     def stats(self):
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

@@ -426,6 +426,39 @@ int or_lif_update(const or_consts* c, const or_params* p, float* V, float* cf, u
     return spike;
 }
 
+int or_constants64(const or_params* p, or_consts64* k) {
+    if (!(p->dt > 0.0f) || !(p->tau_m > 0.0f) || !(p->tau_c > 0.0f)) {
+        set_err("dt, tau_m and tau_c must be positive");
+        return -1;
+    }
+    double dt = (double)p->dt, tm = (double)p->tau_m, tc = (double)p->tau_c;
+    k->a_m = exp(-dt / tm);
+    k->a_c = exp(-dt / tc);
+    k->kc = tc == tm ? (double)p->g_c * dt * k->a_m : (double)p->g_c * (tm * tc / (tc - tm)) * (k->a_c - k->a_m);
+    return 0;
+}
+
+int or_lif_update64(const or_consts64* k, const or_params* p, uint32_t ref_steps, double* V, double* c,
+                    uint8_t* ref, int exc, double I, int forced) {
+    int was_ref = *ref > 0;
+    if (was_ref) {
+        *ref = (uint8_t)(*ref - 1);
+        *V = (double)p->V_reset;
+    } else {
+        /* exact propagator of Eq. 1-2 over dt, then this step's jumps */
+        double E = (double)p->E;
+        *V = ((*V - E) * k->a_m + E) - k->kc * *c + I;
+    }
+    *c = *c * k->a_c;
+    int spike = !was_ref && (*V > (double)p->V_th || forced);
+    if (spike) {
+        *V = (double)p->V_reset;
+        *ref = (uint8_t)ref_steps;
+        if (exc) *c = *c + (double)p->alpha_c;
+    }
+    return spike;
+}
+
 uint32_t or_poisson_count(const or_consts* c, uint32_t u0) {
     uint32_t n = 0;
     for (uint32_t k = 0; k < c->pois_len; ++k)
@@ -459,7 +492,7 @@ struct or_net {
     uint64_t rst_n, rst_cap;
     uint64_t n_spikes, rec, ext;
     uint64_t shuffle_seed;
-    double a_m64, a_c64, kc64;
+    or_consts64 k64;  /* FP64 mode: propagator constants in double */
 };
 
 static int is_exc(const or_net* n, uint32_t i) { return (i % n->M) < n->c.n_exc; }
@@ -725,6 +758,32 @@ int or_gen_rows_v(const or_params* p, uint32_t first, uint32_t count, uint64_t c
     return 0;
 }
 
+int or_gen_rows_list(const or_params* p, const uint32_t* ids, uint32_t count, uint64_t cap, uint32_t* tgt,
+                     float* w, uint8_t* d, uint32_t* len) {
+    or_consts c;
+    if (or_constants(p, &c)) return -1;
+    for (uint32_t r = 0; r < count; ++r)
+        if (ids[r] >= c.N) {
+            set_err("row out of range");
+            return -1;
+        }
+    gen_ctx g;
+    if (gen_init(&g, p, &c, 0, c.N)) return -1;
+    uint64_t used = 0;
+    for (uint32_t r = 0; r < count; ++r) {
+        int64_t n = gen_row(&g, ids[r], cap - used, tgt + used, w + used, NULL, d + used);
+        if (n < 0) {
+            gen_free(&g);
+            set_err("row capacity too small");
+            return -1;
+        }
+        len[r] = (uint32_t)n;
+        used += (uint64_t)n;
+    }
+    gen_free(&g);
+    return 0;
+}
+
 int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
                 uint8_t* d) {
     if (p->conn_rule != 0) {
@@ -809,11 +868,7 @@ or_net* or_create(const or_params* p, int fp64) {
             n->V[i] = or_initial_V(p, i);
         }
     }
-    double dt = (double)p->dt, tm = (double)p->tau_m, tc = (double)p->tau_c;
-    n->a_m64 = exp(-dt / tm);
-    n->a_c64 = exp(-dt / tc);
-    n->kc64 = tc == tm ? (double)p->g_c * dt * n->a_m64
-                       : (double)p->g_c * (tm * tc / (tc - tm)) * (n->a_c64 - n->a_m64);
+    or_constants64(p, &n->k64);
     return n;
 }
 
@@ -890,21 +945,7 @@ static int step_once(or_net* n) {
         if (n->fp64) {
             double I = n->ring64[r] + (double)next * (double)p->J_ext;
             n->ring64[r] = 0.0;
-            int was_ref = n->ref[i] > 0;
-            if (was_ref) {
-                n->ref[i] = (uint8_t)(n->ref[i] - 1);
-                n->V64[i] = (double)p->V_reset;
-            } else {
-                double E = (double)p->E;
-                n->V64[i] = ((n->V64[i] - E) * n->a_m64 + E) - n->kc64 * n->c64[i] + I;
-            }
-            n->c64[i] = n->c64[i] * n->a_c64;
-            spike = !was_ref && (n->V64[i] > (double)p->V_th || forced);
-            if (spike) {
-                n->V64[i] = (double)p->V_reset;
-                n->ref[i] = (uint8_t)c->ref_steps;
-                if (exc) n->c64[i] = n->c64[i] + (double)p->alpha_c;
-            }
+            spike = or_lif_update64(&n->k64, p, c->ref_steps, &n->V64[i], &n->c64[i], &n->ref[i], exc, I, forced);
         } else {
             int64_t I = n->ring[r] + (int64_t)next * c->J_ext_fx;
             n->ring[r] = 0;
@@ -1000,6 +1041,15 @@ void or_get_state(const or_net* n, float* V, float* c, uint8_t* ref, int32_t* ri
 void or_get_state_f64(const or_net* n, double* V, double* c) {
     if (V && n->V64) memcpy(V, n->V64, sizeof(double) * n->N);
     if (c && n->c64) memcpy(c, n->c64, sizeof(double) * n->N);
+}
+
+void or_set_state_f64(or_net* n, const double* V, const double* c) {
+    if (V && n->V64) memcpy(n->V64, V, sizeof(double) * n->N);
+    if (c && n->c64) memcpy(n->c64, c, sizeof(double) * n->N);
+}
+
+void or_get_ring_f64(const or_net* n, double* ring) {
+    if (ring && n->ring64) memcpy(ring, n->ring64, sizeof(double) * (size_t)n->c.D * n->N);
 }
 
 void or_set_state(or_net* n, const float* V, const float* c, const uint8_t* ref) {

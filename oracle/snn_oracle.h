@@ -25,6 +25,10 @@
  *   or_lif_update        pinned: discrete closed-form f-I curve, continuous f-I
  *                        within O(dt), propagator vs numerical ODE solution,
  *                        adaptation steady state
+ *   or_lif_update64      pinned: the same closed forms in double (exact ISI away
+ *   (FP64 mode)          from ties, propagator within 1e-9), and the FP64 step
+ *                        loop against trajectories rebuilt from it and the
+ *                        drive draws, its ring against sums of the FP64 weights
  *   Poisson drive        pinned: table vs Poisson CDF, mean/variance, chi-square
  *   delivery             pinned: order independence, delay/weight arrival trace
  *   whole-network rates  parity unpinned against the paper (its drive is not
@@ -101,6 +105,17 @@ int or_cdf_table(const or_params* p, uint32_t module, uint32_t* thresh,
 
 /* One LIF+SFA update (Eq. 1-2 with the threshold/reset rules).  I_fx is the
  * total input of the step in fixed point.  Returns 1 on a spike. */
+/* FP64 reference mode: the propagator constants of Eq. 1-2 kept in double,
+ * a_m = exp(-dt/tau_m), a_c = exp(-dt/tau_c),
+ * kc = g_c tau_m tau_c / (tau_c - tau_m) (a_c - a_m)  (g_c dt a_m if tau_c = tau_m),
+ * and one neuron update in double with the input I in mV (no fixed point):
+ * the same rules as or_lif_update. */
+typedef struct or_consts64 {
+    double a_m, a_c, kc;
+} or_consts64;
+int or_constants64(const or_params* p, or_consts64* k);
+int or_lif_update64(const or_consts64* k, const or_params* p, uint32_t ref_steps, double* V, double* c,
+                    uint8_t* ref, int exc, double I, int forced);
 int or_lif_update(const or_consts* c, const or_params* p, float* V, float* cf,
                   uint8_t* ref, int exc, int32_t I_fx, int forced);
 uint32_t or_poisson_count(const or_consts* c, uint32_t u0);
@@ -108,6 +123,10 @@ uint32_t or_poisson_count(const or_consts* c, uint32_t u0);
 /* Synapse rows [first, first + count) of the network described by p, without
  * building the rest of it (row i holds entries [i*K, (i+1)*K) of the output,
  * counted from `first`).  For sampled checks of networks too large to build. */
+/* Rows of the neurons ids[0 .. count) back to back (either rule), at most cap
+ * synapses in all; len[r] = length of row r. */
+int or_gen_rows_list(const or_params* p, const uint32_t* ids, uint32_t count, uint64_t cap, uint32_t* tgt,
+                     float* w, uint8_t* d, uint32_t* len);
 int or_gen_rows(const or_params* p, uint32_t first, uint32_t count, uint32_t* tgt, float* w,
                 uint8_t* d);
 /* Initial membrane potential of neuron i, and its external count / forced
@@ -159,6 +178,9 @@ void or_clear_raster(or_net* net);
 uint32_t or_time(const or_net* net);
 void or_get_state(const or_net* net, float* V, float* c, uint8_t* ref, int32_t* ring);
 void or_get_state_f64(const or_net* net, double* V, double* c);
+void or_set_state_f64(or_net* net, const double* V, const double* c);
+/* FP64 mode: the delay ring, D rows of N doubles (row r = inputs of steps with t % D == r) */
+void or_get_ring_f64(const or_net* net, double* ring);
 void or_set_state(or_net* net, const float* V, const float* c, const uint8_t* ref);
 void or_get_stats(const or_net* net, uint64_t* spikes, uint64_t* rec_events, uint64_t* ext_events);
 

@@ -2,18 +2,25 @@
 
 Synapse weights stored in bfloat16 (6 B per synapse instead of 8 B); the input
 still accumulates in exact int32 fixed point.  Reference: the oracle in FP64
-(double state, double weights, no fixed point).  Workload: the exponential
-long-range model (lambda = 290 um, cut-off 1.2 mm, K = 2,250) on a 6x6-module
-patch, under a 5.2 kHz external drive -- the specified 1.5 kHz drive leaves it
-silent, and above ~5.8 kHz it jumps to a saturated ~280 Hz state, so the
-comparison is made inside the low-rate attractor, where the rates depend on
-the recurrent input.  10,000 steps (10 s of simulated time).
+(double state, double weights, no fixed point; pinned in
+test_oracle_fp64.py).  Workload: the exponential long-range model
+(lambda = 290 um, cut-off 1.2 mm, K = 2,250) on a 6x6-module patch, under a
+5.2 kHz external drive -- the specified 1.5 kHz drive leaves it silent, and
+above ~5.8 kHz it jumps to a saturated ~280 Hz state, so the comparison is
+made inside the low-rate attractor, where the rates depend on the recurrent
+input.  10,000 steps (10 s of simulated time) after 500 warm-up steps.
 
-Spiking networks are chaotic, so two correct runs that differ only in rounding
-diverge spike by spike.  The comparison is therefore statistical, and it is
-stated next to the chaos floor: the same statistics between FP32 and FP64 and
-between FP32 and FP32 with one neuron's initial V moved by one ulp.
+Spiking networks are chaotic, so two correct runs that differ in any detail
+diverge spike by spike, and per-neuron rates over 10 s then differ by their
+counting noise.  The comparison is therefore made against the chaos floor:
+the same statistics between the FP64 run and FP64 runs perturbed by one extra
+spike at step 0 (neuron 0, and neuron N / 2), whose rasters are checked to
+have diverged.  A perturbation of one ulp does not serve: the membrane
+contracts between spikes (by a_m = 0.95 per step), so a perturbation that
+flips no threshold comparison dies out and the runs stay identical.
 """
+import multiprocessing as mp
+
 import numpy as np
 import pytest
 
@@ -24,6 +31,35 @@ pytestmark = pytest.mark.gpu
 
 STEPS = 10000
 WARM = 500
+
+
+def _base():
+    return W.patch(W.exp_24x24_k2250(seed=1, weight_dtype="f32", ext_rate_hz=5200.0), 6)
+
+
+def _oracle_fp64_run(kick):
+    """FP64 oracle run; kick = neuron given one extra spike at step 0 (or -1).
+    Returns the per-neuron rates (Hz) and the raster after the warm-up."""
+    cfg = _base()
+    with oracle.OracleNet(cfg, fp64=True) as net:
+        if kick >= 0:
+            V = net.state()["V"]
+            V[kick] = float(cfg["V_th_mV"]) + 5.0  # above threshold: it spikes at step 0
+            net.set_state(V=V)
+        net.step(WARM)
+        net.clear_raster()
+        net.step(STEPS)
+        st, ids = net.raster()
+        return np.bincount(ids, minlength=net.N) / (STEPS / 1000.0), st, ids
+
+
+@pytest.fixture(scope="module")
+def fp64_runs():
+    """Base and two perturbed FP64 oracle runs, in parallel processes started
+    with spawn (no CUDA state is inherited)."""
+    N = _base()["grid_w"] * _base()["grid_h"] * _base()["neurons_per_module"]
+    with mp.get_context("spawn").Pool(3) as pool:
+        return dict(zip(("base", "kick0", "kickN2"), pool.map(_oracle_fp64_run, [-1, 0, N // 2])))
 
 
 @pytest.fixture(scope="module")
@@ -38,17 +74,9 @@ def snn():
     return S
 
 
-def _base():
-    return W.patch(W.exp_24x24_k2250(seed=1, weight_dtype="f32", ext_rate_hz=5200.0), 6)
-
-
-def _rates_gpu(snn, cfg, perturb=False):
+def _rates_gpu(snn, cfg):
     with snn.Network(cfg, raster_capacity=4 << 20) as net:
         net.set_schedule(2)
-        if perturb:
-            V = net.state()["V"]
-            V[0] = np.nextafter(V[0], np.float32(np.inf))
-            net.set_state(V=V)
         net.step(WARM)
         net.clear_raster()
         net.step(STEPS)
@@ -56,38 +84,50 @@ def _rates_gpu(snn, cfg, perturb=False):
         return np.bincount(ids, minlength=net.N) / (STEPS / 1000.0)
 
 
-def _rates_oracle_fp64(cfg):
-    with oracle.OracleNet(cfg, fp64=True) as net:
-        net.step(WARM)
-        net.clear_raster()
-        net.step(STEPS)
-        _, ids = net.raster()
-        return np.bincount(ids, minlength=net.N) / (STEPS / 1000.0)
+def _shared_fraction(a, b):
+    """Fraction of (step, id) spike events of raster a also present in raster b."""
+    ka = set((a[0].astype(np.int64) << 32 | a[1]).tolist())
+    kb = set((b[0].astype(np.int64) << 32 | b[1]).tolist())
+    return len(ka & kb) / max(1, len(ka))
 
 
-def test_bf16_weights_against_fp64_oracle(snn):
+def test_bf16_weights_against_fp64_oracle(fp64_runs, snn):
     cfg = _base()
     M = cfg["neurons_per_module"]
-    r64 = _rates_oracle_fp64(cfg)
+    r64, st64, id64 = fp64_runs["base"]
+    rA, stA, idA = fp64_runs["kick0"]
+    rB, stB, idB = fp64_runs["kickN2"]
     r32 = _rates_gpu(snn, cfg)
     r16 = _rates_gpu(snn, dict(cfg, weight_dtype="bf16"))
-    r32p = _rates_gpu(snn, cfg, perturb=True)
 
     corr = lambda a, b: float(np.corrcoef(a, b)[0, 1])
     mod = lambda r: r.reshape(-1, M).mean(axis=1)
     rel = lambda a, b: float(a.mean() / b.mean() - 1.0)
+    floor_pairs = {"fp64_vs_kick0": corr(rA, r64), "fp64_vs_kickN2": corr(rB, r64), "kick0_vs_kickN2": corr(rA, rB)}
     stats = {
-        "rate_hz": {"fp64": float(r64.mean()), "fp32": float(r32.mean()), "bf16": float(r16.mean())},
+        "rate_hz": {"fp64": float(r64.mean()), "fp32": float(r32.mean()), "bf16": float(r16.mean()),
+                    "fp64_kick0": float(rA.mean()), "fp64_kickN2": float(rB.mean())},
         "mean_rate_rel_err": {"bf16_vs_fp64": rel(r16, r64), "fp32_vs_fp64": rel(r32, r64),
-                              "fp32_vs_fp32_1ulp": rel(r32p, r32)},
+                              "fp64_kick0_vs_fp64": rel(rA, r64), "fp64_kickN2_vs_fp64": rel(rB, r64)},
         "neuron_rate_corr": {"bf16_vs_fp64": corr(r16, r64), "fp32_vs_fp64": corr(r32, r64),
-                             "fp32_vs_fp32_1ulp": corr(r32p, r32)},
-        "module_rate_corr": {"bf16_vs_fp64": corr(mod(r16), mod(r64)), "fp32_vs_fp64": corr(mod(r32), mod(r64))},
+                             "bf16_vs_fp32": corr(r16, r32), **floor_pairs},
+        "module_rate_corr": {"bf16_vs_fp64": corr(mod(r16), mod(r64)), "fp32_vs_fp64": corr(mod(r32), mod(r64)),
+                             "fp64_vs_kick0": corr(mod(rA), mod(r64))},
+        "raster_shared_fraction": {"fp64_vs_kick0": _shared_fraction((st64, id64), (stA, idA)),
+                                   "fp64_vs_kickN2": _shared_fraction((st64, id64), (stB, idB))},
     }
+    floor = min(floor_pairs.values())
+    spread = max(floor_pairs.values()) - floor
+    stats["chaos_floor"] = {"neuron_rate_corr": floor, "spread": spread}
     print("\nprecision", stats)
     assert r64.mean() > 0.5  # the comparison is made in an active state
+    # the perturbed FP64 runs really diverged from the base run (else they are no floor)
+    for k, f in stats["raster_shared_fraction"].items():
+        assert f < 0.5, (k, f)
     # mean population rate of the bf16 path within 1 % of the FP64 run
     assert abs(stats["mean_rate_rel_err"]["bf16_vs_fp64"]) < 0.01
-    # per-neuron rates: as close to FP64 as FP32 itself is (the chaos floor), within 0.02
-    floor = min(stats["neuron_rate_corr"]["fp32_vs_fp64"], stats["neuron_rate_corr"]["fp32_vs_fp32_1ulp"])
-    assert stats["neuron_rate_corr"]["bf16_vs_fp64"] >= min(0.99, floor - 0.02)
+    # per-neuron rates as close to FP64 as FP64 is to itself after one extra
+    # spike: the demonstrated floor, less the spread of its three estimates
+    tol = max(0.005, spread)
+    assert stats["neuron_rate_corr"]["bf16_vs_fp64"] >= floor - tol
+    assert stats["neuron_rate_corr"]["fp32_vs_fp64"] >= floor - tol
