@@ -276,13 +276,14 @@ def run_reference(args):
     rank, ws, local, dist = _dist()
     if rank != 0:
         return 0
-    cfg = workload()
+    cfg = workload(grid=args.grid)
     import oracle
     steps_per = args.ref_sample_steps
+    settle = ORACLE_SETTLE_STEPS if args.ref_settle_steps is None else args.ref_settle_steps
     t0 = time.perf_counter()
     net = oracle.OracleNet(cfg)
     build_s = time.perf_counter() - t0
-    net.step(ORACLE_SETTLE_STEPS)
+    net.step(settle)
     for _ in range(args.warmup):
         net.step(steps_per)
     s0 = net.stats()
@@ -293,7 +294,7 @@ def run_reference(args):
     s1 = net.stats()
     net.close()
     value = (s1["rec_events"] - s0["rec_events"]) / dt
-    desc = oracle_sample_desc(cfg, ORACLE_SETTLE_STEPS + args.warmup * steps_per, args.steps * steps_per, build_s)
+    desc = oracle_sample_desc(cfg, settle + args.warmup * steps_per, args.steps * steps_per, build_s)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000.0 / max(args.steps, 1),
@@ -805,6 +806,8 @@ def main(argv=None):
                     help="simulated steps of the oracle timed on the full network for cpu_baseline")
     ap.add_argument("--ref-sample-steps", type=int, default=10,
                     help="simulated steps of the oracle per bench step in --impl reference")
+    ap.add_argument("--ref-settle-steps", type=int, default=None,
+                    help="untimed oracle steps before the reference arm's warm-up (default %d)" % ORACLE_SETTLE_STEPS)
     ap.add_argument("--timing-every", type=int, default=10,
                     help="time the kernels of every n-th simulated step with CUDA events")
     ap.add_argument("--grid", type=int, default=24, help="modules per side (24 = the benchmark workload)")

@@ -480,6 +480,67 @@ SNN_API snn_status snn_server_stats(snn_server* s, snn_server_stats_t* out);
 SNN_API uint64_t snn_now_ns(void);
 SNN_API void snn_server_destroy(snn_server* s);
 
+/* ---- Spatial decomposition (Sec. II-D) with the two-step spike exchange
+ * (Sec. II-E) and deferred arborization (Sec. II-C).  The paper runs one
+ * network on many processes, each owning a tile of modules; a shard here owns
+ * the module rows [H k / n, H (k + 1) / n) of an n-way split of the grid (its
+ * neurons are one contiguous id range), their state and delay ring, and a
+ * target-side copy of the synapses that the halo sources -- every neuron
+ * within the stencil's row radius of the stripe -- project into it (rows of
+ * the fixed out-degree law drawn exactly as snn_build_network draws them,
+ * restricted to targets in the stripe, draw order kept).  A time step is:
+ *   snn_shard_integrate  the stripe's neurons; the step's spikes (global ids,
+ *                        increasing) and their count are left in the shard's
+ *                        outbox (device memory, snn_shard_outbox) and in its
+ *                        raster;
+ *   exchange             every shard sends its spike count, then its ids, to
+ *                        the shards whose halo covers it (its peers: indexes
+ *                        peer_lo .. peer_hi of snn_shard_info, itself included);
+ *   snn_shard_deliver    the inbound lists (device pointers to ids and to
+ *                        their count, one list per peer, the shard's own
+ *                        outbox included) through the target-side table into
+ *                        the shard's ring; the step ends.
+ * The union of the shards' rasters and states is bit-identical to
+ * snn_build_network's network of the same description.  snn_shards_run runs
+ * all n shards of one decomposition on the current device, exchanging through
+ * the outboxes in place.  Only the fixed out-degree law is supported.
+ * Errors: SNN_EINVAL (pairwise law, index >= n_shards, n_shards > grid_h, a
+ * shard reaching more than 16 shards), SNN_ENOMEM, SNN_ECUDA. */
+typedef struct snn_shard snn_shard;
+typedef struct snn_shard_info_t {
+    uint32_t n_shards, index;
+    uint32_t row0, row1;        /* module rows owned */
+    uint32_t n0, n1;            /* neurons owned [n0, n1) */
+    uint32_t h0, h1;            /* halo sources [h0, h1) whose rows are copied */
+    uint32_t peer_lo, peer_hi;  /* shards whose spikes can reach this one */
+    uint32_t D, t;              /* ring rows; next time step */
+    uint64_t table_synapses;    /* synapses in the target-side copy */
+    uint64_t device_bytes;
+} snn_shard_info_t;
+SNN_API snn_status snn_shard_build(const snn_config* cfg, uint32_t n_shards, uint32_t index, snn_alloc_fn alloc_fn,
+                                   snn_free_fn free_fn, void* alloc_ctx, void* stream, snn_shard** out);
+SNN_API snn_status snn_shard_info(snn_shard* shard, snn_shard_info_t* out);
+/* Async. */
+SNN_API snn_status snn_shard_integrate(snn_shard* shard, void* stream);
+/* Device pointers of the outbox: ids (capacity n1 - n0) and the count. */
+SNN_API snn_status snn_shard_outbox(snn_shard* shard, uint32_t** ids, uint32_t** count);
+/* Async; ids and counts are host arrays of n_lists (<= 16) device pointers. */
+SNN_API snn_status snn_shard_deliver(snn_shard* shard, const uint32_t* const* ids, const uint32_t* const* counts,
+                                     uint32_t n_lists, void* stream);
+/* n_steps steps of shards[0..n) (indexes 0..n-1 of one decomposition, at one
+ * time step, on one device).  Async. */
+SNN_API snn_status snn_shards_run(snn_shard* const* shards, uint32_t n, uint32_t n_steps, void* stream);
+/* The shard's raster ((step, id), ordered) as snn_read_spikes; its state: V,
+ * c, ref of its n1 - n0 neurons and the ring as D rows of n1 - n0 int32;
+ * counters (n_spikes and rec_events count its own spikes, ext_events its own
+ * neurons' drive).  All synchronise `stream`. */
+SNN_API snn_status snn_shard_read_spikes(snn_shard* shard, uint32_t* steps, uint32_t* ids, size_t cap, size_t* n_out,
+                                         void* stream);
+SNN_API snn_status snn_shard_get_state(snn_shard* shard, float* V, float* c, uint8_t* ref, int32_t* ring,
+                                       void* stream);
+SNN_API snn_status snn_shard_stats(snn_shard* shard, snn_stats* out, void* stream);
+SNN_API void snn_shard_destroy(snn_shard* shard);
+
 SNN_API void snn_destroy(snn_net* net);
 SNN_API const char* snn_last_error(void);
 

@@ -432,4 +432,107 @@ cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* r
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Spatial decomposition (Sec. II-D, deferred arborization of Sec. II-C): the
+// target-side copy of a shard.  For the sources [h0, h0 + rows) whose stencil
+// reaches the shard's neurons [n0, n1), the synapses of their rows (the fixed
+// out-degree law, drawn exactly as k_gen_synapses draws them) that target the
+// shard, in draw order: one warp per source row.  Pass 1 counts them.
+__global__ void __launch_bounds__(256) k_shard_count(BuildView b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1,
+                                                     uint32_t* __restrict__ cnt) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;  // warp-uniform
+    const uint32_t i = h0 + r;
+    const uint32_t s = i / b.M;
+    const bool exc = (i - s * b.M) < b.n_exc;
+    const uint32_t* T = b.cdf_T + (size_t)s * b.max_off;
+    const uint32_t* TM = b.cdf_mod + (size_t)s * b.max_off;
+    const uint32_t n = __ldg(b.cdf_n + s);
+    uint32_t c = 0;
+    for (uint32_t k = lane; k < b.K; k += 32) {
+        const Draw d = draw_synapse(b, i, k, exc, T, TM, n);
+        c += (d.tgt >= n0 && d.tgt < n1) ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (lane == 0) cnt[r] = c;
+}
+
+// Pass 2: the kept synapses of row r at [row_ptr[r], row_ptr[r + 1]): target
+// neuron - n0 | delay << 24 and the weight.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_shard_fill(BuildView b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1,
+                                                    const uint64_t* __restrict__ row_ptr, uint32_t* __restrict__ td,
+                                                    void* __restrict__ wout) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= rows) return;  // warp-uniform
+    const uint32_t i = h0 + r;
+    const uint32_t s = i / b.M;
+    const bool exc = (i - s * b.M) < b.n_exc;
+    const uint32_t* T = b.cdf_T + (size_t)s * b.max_off;
+    const uint32_t* TM = b.cdf_mod + (size_t)s * b.max_off;
+    const uint32_t n = __ldg(b.cdf_n + s);
+    uint64_t pos = row_ptr[r];
+    for (uint32_t k0 = 0; k0 < b.K; k0 += 32) {
+        const uint32_t k = k0 + lane;
+        Draw d{0u, 0u, 0u, 0.0f};
+        bool keep = false;
+        if (k < b.K) {
+            d = draw_synapse(b, i, k, exc, T, TM, n);
+            keep = d.tgt >= n0 && d.tgt < n1;
+        }
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) {
+            const uint64_t e = pos + __popc(m & ((1u << lane) - 1u));
+            td[e] = (d.tgt - n0) | (d.d << 24);
+            if (BF16)
+                reinterpret_cast<__nv_bfloat16*>(wout)[e] = __float2bfloat16_rn(d.w);
+            else
+                reinterpret_cast<float*>(wout)[e] = d.w;
+        }
+        pos += __popc(m);
+    }
+}
+
+// V = V_th U[0,1), c = 0, ref = 0 for the neurons [n0, n0 + count) of a shard
+// (the draw of k_init_state, by global neuron id).
+__global__ void k_shard_init(BuildView b, uint32_t n0, uint32_t count, float* __restrict__ V, float* __restrict__ c,
+                             uint8_t* __restrict__ ref) {
+    const uint32_t li = blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= count) return;
+    const U4 u = philox4x32_10(n0 + li, 0u, TAG_INIT, 0u, b.key0, b.key1);
+    V[li] = __fmul_rn(b.V_th, unit24(u.x));
+    c[li] = 0.0f;
+    ref[li] = 0;
+}
+
+cudaError_t launch_shard_count(const BuildView& b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1, uint32_t* cnt,
+                               cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    k_shard_count<<<(rows + 7) / 8, 256, 0, s>>>(b, h0, rows, n0, n1, cnt);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_fill(const BuildView& b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1,
+                              const uint64_t* row_ptr, uint32_t* td, void* w, cudaStream_t s) {
+    if (rows == 0) return cudaSuccess;
+    if (b.w_bf16)
+        k_shard_fill<true><<<(rows + 7) / 8, 256, 0, s>>>(b, h0, rows, n0, n1, row_ptr, td, w);
+    else
+        k_shard_fill<false><<<(rows + 7) / 8, 256, 0, s>>>(b, h0, rows, n0, n1, row_ptr, td, w);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_init(const BuildView& b, uint32_t n0, uint32_t count, float* V, float* c, uint8_t* ref,
+                              cudaStream_t s) {
+    if (count == 0) return cudaSuccess;
+    k_shard_init<<<(count + 255) / 256, 256, 0, s>>>(b, n0, count, V, c, ref);
+    count_launch(1);
+    return cudaGetLastError();
+}
+
 }  // namespace snn

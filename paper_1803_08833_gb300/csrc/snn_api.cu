@@ -577,21 +577,11 @@ snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
     return SNN_OK;
 }
 
-snn_status build_impl(snn_net* n, cudaStream_t s) {
+// The scalar parameters of the construction kernels (device tables are set
+// by the caller); n->max_off must be set.
+void fill_build_view(const snn_net* n, BuildView& b) {
     const snn_config& c = n->cfg;
-    snn_status st = derive(n);
-    if (st != SNN_OK) return st;
-    uint32_t R2 = 0;
-    std::vector<int16_t> off = disc_offsets(c, &R2);
-    n->max_off = (uint32_t)(off.size() / 2);
-
-    NetView& v = n->v;
-    n->pgrid = persistent_grid(v.w_bf16 != 0);
-    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
-    HostTables ht;
-    host_tables(c, &ht);
-
-    BuildView b{};
+    const NetView& v = n->v;
     b.grid_w = c.grid_w;
     b.grid_h = c.grid_h;
     b.n_modules = n->n_modules;
@@ -617,6 +607,24 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
     b.weight_dist = c.weight_dist;
     b.delay_dist = c.delay_dist;
     b.inh_local_only = c.inh_local_only;
+}
+
+snn_status build_impl(snn_net* n, cudaStream_t s) {
+    const snn_config& c = n->cfg;
+    snn_status st = derive(n);
+    if (st != SNN_OK) return st;
+    uint32_t R2 = 0;
+    std::vector<int16_t> off = disc_offsets(c, &R2);
+    n->max_off = (uint32_t)(off.size() / 2);
+
+    NetView& v = n->v;
+    n->pgrid = persistent_grid(v.w_bf16 != 0);
+    const bool pairwise = c.conn_rule == SNN_RULE_PAIRWISE;
+    HostTables ht;
+    host_tables(c, &ht);
+
+    BuildView b{};
+    fill_build_view(n, b);
 
     // construction-only buffers, released at the end of the build
     std::vector<std::pair<void*, size_t>> temps;
@@ -1733,6 +1741,316 @@ void snn_batch_destroy(snn_batch* b) {
             cudaFree(p);
     }
     delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Spatial decomposition (Sec. II-D, II-E; deferred arborization, Sec. II-C).
+
+struct snn_shard {
+    snn_net net;  // description, constants, allocator hook, device blocks
+    uint32_t n_shards = 0, index = 0;
+    uint32_t row0 = 0, row1 = 0, n0 = 0, n1 = 0, h0 = 0, h1 = 0, peer_lo = 0, peer_hi = 0;
+    uint64_t nsyn = 0;
+    uint32_t t = 0;  // next time step
+    ShardView sv{};
+};
+
+namespace {
+
+// Module rows of shard k of n: [H k / n, H (k + 1) / n).
+uint32_t shard_row(uint32_t H, uint32_t n, uint32_t k) { return (uint32_t)((uint64_t)H * k / n); }
+
+snn_status shard_build_impl(snn_shard* sh, cudaStream_t s) {
+    snn_net* n = &sh->net;
+    const snn_config& c = n->cfg;
+    snn_status st = derive(n);
+    if (st != SNN_OK) return st;
+    uint32_t R2 = 0;
+    std::vector<int16_t> off = disc_offsets(c, &R2);
+    n->max_off = (uint32_t)(off.size() / 2);
+    int R = 0;
+    for (size_t o = 1; o < off.size(); o += 2) R = std::max(R, std::abs((int)off[o]));
+    const uint32_t H = c.grid_h, WM = c.grid_w * c.neurons_per_module;
+    sh->row0 = shard_row(H, sh->n_shards, sh->index);
+    sh->row1 = shard_row(H, sh->n_shards, sh->index + 1);
+    sh->n0 = sh->row0 * WM;
+    sh->n1 = sh->row1 * WM;
+    const uint32_t hr0 = (uint32_t)std::max(0, (int)sh->row0 - R);
+    const uint32_t hr1 = std::min(H, sh->row1 + (uint32_t)R);
+    sh->h0 = hr0 * WM;
+    sh->h1 = hr1 * WM;
+    // peers: the shards whose rows overlap the halo (this one included)
+    sh->peer_lo = sh->n_shards;
+    sh->peer_hi = 0;
+    for (uint32_t k = 0; k < sh->n_shards; ++k)
+        if (shard_row(H, sh->n_shards, k) < hr1 && shard_row(H, sh->n_shards, k + 1) > hr0) {
+            sh->peer_lo = std::min(sh->peer_lo, k);
+            sh->peer_hi = std::max(sh->peer_hi, k);
+        }
+    if (sh->peer_hi - sh->peer_lo + 1 > SHARD_MAX_LISTS)
+        return fail(SNN_EINVAL, "shard %u reaches %u shards (at most %u)", sh->index, sh->peer_hi - sh->peer_lo + 1,
+                    SHARD_MAX_LISTS);
+    HostTables ht;
+    host_tables(c, &ht);
+    BuildView b{};
+    fill_build_view(n, b);
+    b.K = n->K;  // the fixed out-degree law
+    b.Kpad = n->Kpad;
+    std::vector<std::pair<void*, size_t>> temps;
+    auto temp = [&](size_t bytes) -> void* {
+        void* p = dev_alloc(n, bytes);
+        if (p) temps.push_back({p, bytes});
+        return p;
+    };
+    if (!ht.wtab.empty()) {
+        float* wt = (float*)temp(ht.wtab.size() * 4);
+        if (!wt) return fail(SNN_ENOMEM, "device allocation of the efficacy table failed");
+        CUDA_TRY(cudaMemcpyAsync(wt, ht.wtab.data(), ht.wtab.size() * 4, cudaMemcpyHostToDevice, s));
+        b.wtab = wt;
+    }
+    if (!ht.dthr.empty()) {
+        uint64_t* dt = (uint64_t*)temp(ht.dthr.size() * 8);
+        if (!dt) return fail(SNN_ENOMEM, "device allocation of the delay table failed");
+        CUDA_TRY(cudaMemcpyAsync(dt, ht.dthr.data(), ht.dthr.size() * 8, cudaMemcpyHostToDevice, s));
+        b.dthr = dt;
+        b.n_dthr = (uint32_t)ht.dthr.size();
+    }
+    // the target-module tables of every source module (as snn_build_network builds them)
+    const size_t tab = (size_t)n->n_modules * n->max_off;
+    b.cdf_T = (uint32_t*)temp(tab * 4);
+    b.cdf_mod = (uint32_t*)temp(tab * 4);
+    b.cdf_n = (uint32_t*)temp((size_t)n->n_modules * 4);
+    b.scratch = (double*)temp(tab * sizeof(double));
+    int16_t* doff = (int16_t*)temp(off.size() * sizeof(int16_t));
+    if (!b.cdf_T || !b.cdf_mod || !b.cdf_n || !b.scratch || !doff)
+        return fail(SNN_ENOMEM, "device allocation of the construction tables failed");
+    CUDA_TRY(cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(int16_t), cudaMemcpyHostToDevice, s));
+    b.offsets = doff;
+    CUDA_TRY(launch_build_cdf(b, s));
+    // the target-side table: halo rows restricted to the shard, counted then filled
+    const uint32_t rows = sh->h1 - sh->h0;
+    uint32_t* dcnt = (uint32_t*)temp((size_t)std::max<uint32_t>(rows, 1) * 4);
+    uint64_t* rp = (uint64_t*)dev_alloc(n, ((size_t)rows + 1) * 8);
+    if (!dcnt || !rp) return fail(SNN_ENOMEM, "device allocation of the shard table index failed");
+    CUDA_TRY(launch_shard_count(b, sh->h0, rows, sh->n0, sh->n1, dcnt, s));
+    std::vector<uint32_t> hc(rows);
+    if (rows) CUDA_TRY(cudaMemcpyAsync(hc.data(), dcnt, (size_t)rows * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<uint64_t> hp((size_t)rows + 1, 0);
+    for (uint32_t r = 0; r < rows; ++r) hp[r + 1] = hp[r] + hc[r];
+    sh->nsyn = hp[rows];
+    CUDA_TRY(cudaMemcpyAsync(rp, hp.data(), hp.size() * 8, cudaMemcpyHostToDevice, s));
+    const size_t wbytes = n->v.w_bf16 ? 2 : 4;
+    uint32_t* td = (uint32_t*)dev_alloc(n, std::max<uint64_t>(sh->nsyn, 1) * 4);
+    void* w = dev_alloc(n, std::max<uint64_t>(sh->nsyn, 1) * wbytes);
+    if (!td || !w) return fail(SNN_ENOMEM, "device allocation of %llu shard synapses failed",
+                               (unsigned long long)sh->nsyn);
+    CUDA_TRY(launch_shard_fill(b, sh->h0, rows, sh->n0, sh->n1, rp, td, w, s));
+    // state, ring, outbox, raster, counters
+    ShardView& sv = sh->sv;
+    sv.n0 = sh->n0;
+    sv.Nl = sh->n1 - sh->n0;
+    sv.Nlpad = (sv.Nl + 255) / 256 * 256;
+    sv.h0 = sh->h0;
+    sv.rows = rows;
+    sv.row_ptr = rp;
+    sv.td = td;
+    sv.w = w;
+    const size_t Np = std::max<uint32_t>(sv.Nlpad, 256);
+    sv.V = (float*)dev_alloc(n, Np * 4);
+    sv.c = (float*)dev_alloc(n, Np * 4);
+    sv.ref = (uint8_t*)dev_alloc(n, Np);
+    sv.ring = (int32_t*)dev_alloc(n, (size_t)n->D * Np * 4);
+    sv.spk_bits = (uint32_t*)dev_alloc(n, Np / 32 * 4);
+    sv.out_ids = (uint32_t*)dev_alloc(n, Np * 4);
+    sv.out_cnt = (uint32_t*)dev_alloc(n, 4);
+    const uint64_t cap = c.raster_capacity ? c.raster_capacity : 1;
+    sv.raster_t = (uint32_t*)dev_alloc(n, cap * 4);
+    sv.raster_id = (uint32_t*)dev_alloc(n, cap * 4);
+    sv.raster_cap = c.raster_capacity;
+    sv.cnt = (ShardCounters*)dev_alloc(n, sizeof(ShardCounters));
+    if (!sv.V || !sv.c || !sv.ref || !sv.ring || !sv.spk_bits || !sv.out_ids || !sv.out_cnt || !sv.raster_t ||
+        !sv.raster_id || !sv.cnt)
+        return fail(SNN_ENOMEM, "device allocation of the shard state failed");
+    CUDA_TRY(launch_shard_init(b, sh->n0, sv.Nl, sv.V, sv.c, sv.ref, s));
+    CUDA_TRY(cudaMemsetAsync(sv.ring, 0, (size_t)n->D * Np * 4, s));
+    CUDA_TRY(cudaMemsetAsync(sv.out_cnt, 0, 4, s));
+    CUDA_TRY(cudaMemsetAsync(sv.cnt, 0, sizeof(ShardCounters), s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // the construction buffers are released next
+    for (auto& tb : temps) free_block(n, tb.first, tb.second);
+    return SNN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+snn_status snn_shard_build(const snn_config* cfg, uint32_t n_shards, uint32_t index, snn_alloc_fn alloc_fn,
+                           snn_free_fn free_fn, void* alloc_ctx, void* stream, snn_shard** out) {
+    if (!out) return fail(SNN_EINVAL, "out is NULL");
+    *out = nullptr;
+    snn_status st = validate(cfg);
+    if (st != SNN_OK) return st;
+    if (cfg->conn_rule != SNN_RULE_FIXED_K)
+        return fail(SNN_EINVAL, "shards are built for the fixed out-degree rule (conn_rule = SNN_RULE_FIXED_K)");
+    if (n_shards == 0 || index >= n_shards || n_shards > cfg->grid_h)
+        return fail(SNN_EINVAL, "need 0 <= index < n_shards <= grid_h (got %u of %u, grid_h %u)", index, n_shards,
+                    cfg->grid_h);
+    if ((alloc_fn == nullptr) != (free_fn == nullptr))
+        return fail(SNN_EINVAL, "alloc_fn and free_fn must both be set or both be NULL");
+    snn_shard* sh = new (std::nothrow) snn_shard();
+    if (!sh) return fail(SNN_ENOMEM, "host allocation failed");
+    sh->net.cfg = *cfg;
+    sh->net.alloc_fn = alloc_fn;
+    sh->net.free_fn = free_fn;
+    sh->net.alloc_ctx = alloc_ctx;
+    cudaGetDevice(&sh->net.device);
+    sh->n_shards = n_shards;
+    sh->index = index;
+    st = shard_build_impl(sh, (cudaStream_t)stream);
+    if (st != SNN_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        release_all(&sh->net);
+        delete sh;
+        return st;
+    }
+    *out = sh;
+    return SNN_OK;
+}
+
+snn_status snn_shard_info(snn_shard* sh, snn_shard_info_t* out) {
+    if (!sh || !out) return fail(SNN_EINVAL, "shard or out is NULL");
+    out->n_shards = sh->n_shards;
+    out->index = sh->index;
+    out->row0 = sh->row0;
+    out->row1 = sh->row1;
+    out->n0 = sh->n0;
+    out->n1 = sh->n1;
+    out->h0 = sh->h0;
+    out->h1 = sh->h1;
+    out->peer_lo = sh->peer_lo;
+    out->peer_hi = sh->peer_hi;
+    out->D = sh->net.D;
+    out->table_synapses = sh->nsyn;
+    out->device_bytes = sh->net.device_bytes;
+    out->t = sh->t;
+    return SNN_OK;
+}
+
+snn_status snn_shard_integrate(snn_shard* sh, void* stream) {
+    if (!sh) return fail(SNN_EINVAL, "shard is NULL");
+    CUDA_TRY(launch_shard_step(sh->net.v, sh->sv, sh->t, (cudaStream_t)stream));
+    return SNN_OK;
+}
+
+snn_status snn_shard_outbox(snn_shard* sh, uint32_t** ids, uint32_t** count) {
+    if (!sh || !ids || !count) return fail(SNN_EINVAL, "shard, ids or count is NULL");
+    *ids = sh->sv.out_ids;
+    *count = sh->sv.out_cnt;
+    return SNN_OK;
+}
+
+snn_status snn_shard_deliver(snn_shard* sh, const uint32_t* const* ids, const uint32_t* const* counts,
+                             uint32_t n_lists, void* stream) {
+    if (!sh) return fail(SNN_EINVAL, "shard is NULL");
+    if (n_lists > SHARD_MAX_LISTS || (n_lists && (!ids || !counts)))
+        return fail(SNN_EINVAL, "at most %u inbound lists, with ids and counts", SHARD_MAX_LISTS);
+    ShardInbound in{};
+    for (uint32_t l = 0; l < n_lists; ++l) {
+        if (!ids[l] || !counts[l]) return fail(SNN_EINVAL, "inbound list %u is NULL", l);
+        in.ids[l] = ids[l];
+        in.cnt[l] = counts[l];
+    }
+    in.n = n_lists;
+    CUDA_TRY(launch_shard_deliver(sh->net.v, sh->sv, in, sh->t, (cudaStream_t)stream));
+    sh->t += 1;
+    return SNN_OK;
+}
+
+snn_status snn_shards_run(snn_shard* const* shards, uint32_t n, uint32_t n_steps, void* stream) {
+    if (!shards || n == 0) return fail(SNN_EINVAL, "no shards");
+    for (uint32_t k = 0; k < n; ++k) {
+        if (!shards[k] || shards[k]->n_shards != n || shards[k]->index != k)
+            return fail(SNN_EINVAL, "shards must be indexes 0..%u of one %u-way decomposition, in order", n - 1, n);
+        if (shards[k]->t != shards[0]->t) return fail(SNN_EINVAL, "shards are at different time steps");
+        if (memcmp(&shards[k]->net.cfg, &shards[0]->net.cfg, sizeof(snn_config)) != 0)
+            return fail(SNN_EINVAL, "shards of different network descriptions");
+    }
+    for (uint32_t step = 0; step < n_steps; ++step) {
+        for (uint32_t k = 0; k < n; ++k) {
+            snn_status st = snn_shard_integrate(shards[k], stream);
+            if (st != SNN_OK) return st;
+        }
+        // one device: the exchange is the peers' outboxes read in place
+        for (uint32_t k = 0; k < n; ++k) {
+            const uint32_t* ids[SHARD_MAX_LISTS];
+            const uint32_t* cnt[SHARD_MAX_LISTS];
+            uint32_t m = 0;
+            for (uint32_t q = shards[k]->peer_lo; q <= shards[k]->peer_hi; ++q, ++m) {
+                ids[m] = shards[q]->sv.out_ids;
+                cnt[m] = shards[q]->sv.out_cnt;
+            }
+            snn_status st = snn_shard_deliver(shards[k], ids, cnt, m, stream);
+            if (st != SNN_OK) return st;
+        }
+    }
+    return SNN_OK;
+}
+
+snn_status snn_shard_read_spikes(snn_shard* sh, uint32_t* steps, uint32_t* ids, size_t cap, size_t* n_out,
+                                 void* stream) {
+    if (!sh || !n_out) return fail(SNN_EINVAL, "shard or n_out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    ShardCounters hc;
+    CUDA_TRY(cudaMemcpyAsync(&hc, sh->sv.cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    uint64_t avail = std::min<uint64_t>(hc.raster_count, sh->sv.raster_cap);
+    const size_t k = (size_t)std::min<uint64_t>(avail, cap);
+    if (k && steps) CUDA_TRY(cudaMemcpyAsync(steps, sh->sv.raster_t, k * 4, cudaMemcpyDeviceToHost, s));
+    if (k && ids) CUDA_TRY(cudaMemcpyAsync(ids, sh->sv.raster_id, k * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *n_out = k;
+    if (hc.raster_count > sh->sv.raster_cap) return fail(SNN_EOVERFLOW, "shard raster overflowed");
+    return SNN_OK;
+}
+
+snn_status snn_shard_get_state(snn_shard* sh, float* V, float* c, uint8_t* ref, int32_t* ring, void* stream) {
+    if (!sh) return fail(SNN_EINVAL, "shard is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const ShardView& sv = sh->sv;
+    if (V) CUDA_TRY(cudaMemcpyAsync(V, sv.V, (size_t)sv.Nl * 4, cudaMemcpyDeviceToHost, s));
+    if (c) CUDA_TRY(cudaMemcpyAsync(c, sv.c, (size_t)sv.Nl * 4, cudaMemcpyDeviceToHost, s));
+    if (ref) CUDA_TRY(cudaMemcpyAsync(ref, sv.ref, sv.Nl, cudaMemcpyDeviceToHost, s));
+    if (ring)
+        CUDA_TRY(cudaMemcpy2DAsync(ring, (size_t)sv.Nl * 4, sv.ring, (size_t)sv.Nlpad * 4, (size_t)sv.Nl * 4,
+                                   sh->net.D, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
+snn_status snn_shard_stats(snn_shard* sh, snn_stats* out, void* stream) {
+    if (!sh || !out) return fail(SNN_EINVAL, "shard or out is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    ShardCounters hc;
+    CUDA_TRY(cudaMemcpyAsync(&hc, sh->sv.cnt, sizeof hc, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    memset(out, 0, sizeof *out);
+    out->steps = sh->t;
+    out->n_spikes = hc.n_spikes;
+    out->rec_events = hc.rec_events;
+    out->ext_events = hc.ext_events;
+    out->raster_count = hc.raster_count;
+    out->raster_capacity = sh->sv.raster_cap;
+    return SNN_OK;
+}
+
+void snn_shard_destroy(snn_shard* sh) {
+    if (!sh) return;
+    cudaDeviceSynchronize();
+    release_all(&sh->net);
+    delete sh;
 }
 
 }  // extern "C"

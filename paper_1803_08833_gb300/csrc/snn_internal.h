@@ -113,6 +113,41 @@ struct NetView {
     uint32_t* own_ovf;        // G flags: a producer's queue for this owner overflowed (events went to the ring)
 };
 
+// One shard of a spatially decomposed network (Sec. II-D): the neurons
+// [n0, n0 + Nl) of a stripe of module rows, their state and delay ring, and the
+// target-side copy of the rows of the halo sources [h0, h0 + rows) restricted
+// to the stripe (deferred arborization, Sec. II-C).
+struct ShardCounters {
+    uint64_t raster_count, n_spikes, rec_events, ext_events;
+};
+struct ShardView {
+    uint32_t n0, Nl, Nlpad;   // first neuron, neurons, ring row stride
+    uint32_t h0, rows;        // halo sources
+    const uint64_t* row_ptr;  // rows + 1
+    const uint32_t* td;       // target - n0 | delay << 24
+    const void* w;            // f32 or bf16
+    float* V;
+    float* c;
+    uint8_t* ref;
+    int32_t* ring;            // D rows of Nlpad
+    uint32_t* spk_bits;       // one bit per neuron of the step
+    uint32_t* out_ids;        // outbox: the step's spikes (global ids, increasing)
+    uint32_t* out_cnt;        // outbox: their count
+    uint32_t* raster_t;
+    uint32_t* raster_id;
+    uint64_t raster_cap;
+    ShardCounters* cnt;
+};
+constexpr uint32_t SHARD_MAX_LISTS = 16;
+struct ShardInbound {  // spike lists delivered into one shard in one step
+    const uint32_t* ids[SHARD_MAX_LISTS];
+    const uint32_t* cnt[SHARD_MAX_LISTS];
+    uint32_t n;
+};
+cudaError_t launch_shard_step(const NetView& v, const ShardView& sv, uint32_t t, cudaStream_t s);
+cudaError_t launch_shard_deliver(const NetView& v, const ShardView& sv, const ShardInbound& in, uint32_t t,
+                                 cudaStream_t s);
+
 // Parameters of the construction kernels.
 struct BuildView {
     uint32_t grid_w, grid_h, n_modules, max_off, M, N, Npad, K, Kpad, n_exc;
@@ -151,6 +186,12 @@ cudaError_t launch_gen_grouped(const BuildView& b, uint32_t* td, void* w, cudaSt
 cudaError_t launch_pair_count(const BuildView& b, cudaStream_t s);
 cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s);
 cudaError_t launch_pair_fill(const BuildView& b, uint32_t* td, void* w, cudaStream_t s);
+cudaError_t launch_shard_count(const BuildView& b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1, uint32_t* cnt,
+                               cudaStream_t s);
+cudaError_t launch_shard_fill(const BuildView& b, uint32_t h0, uint32_t rows, uint32_t n0, uint32_t n1,
+                              const uint64_t* row_ptr, uint32_t* td, void* w, cudaStream_t s);
+cudaError_t launch_shard_init(const BuildView& b, uint32_t n0, uint32_t count, float* V, float* c, uint8_t* ref,
+                              cudaStream_t s);
 cudaError_t launch_init_state(const BuildView& b, float* V, float* c, uint8_t* ref,
                               cudaStream_t s);
 cudaError_t launch_neuron_step(const NetView& v, cudaStream_t s);

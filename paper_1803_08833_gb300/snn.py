@@ -72,6 +72,12 @@ class ServerStats(ctypes.Structure):
                [("active", ctypes.c_uint32), ("queued", ctypes.c_uint32)]
 
 
+class ShardInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("n_shards", "index", "row0", "row1", "n0", "n1", "h0", "h1", "peer_lo", "peer_hi", "D", "t")] + \
+               [("table_synapses", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -109,6 +115,16 @@ def load():
         "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_shard_build": (st, [P(SnnConfig), ctypes.c_uint32, ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, vp, P(vp)]),
+        "snn_shard_info": (st, [vp, P(ShardInfo)]),
+        "snn_shard_integrate": (st, [vp, vp]),
+        "snn_shard_outbox": (st, [vp, P(vp), P(vp)]),
+        "snn_shard_deliver": (st, [vp, P(vp), P(vp), ctypes.c_uint32, vp]),
+        "snn_shards_run": (st, [P(vp), ctypes.c_uint32, ctypes.c_uint32, vp]),
+        "snn_shard_read_spikes": (st, [vp, vp, vp, ctypes.c_size_t, P(ctypes.c_size_t), vp]),
+        "snn_shard_get_state": (st, [vp, vp, vp, vp, vp, vp]),
+        "snn_shard_stats": (st, [vp, P(SnnStats), vp]),
+        "snn_shard_destroy": (None, [vp]),
         "snn_set_bands": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
         "snn_set_window": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32), vp]),
         "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
@@ -489,6 +505,143 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class _DeviceArray:
+    """A 1-D int32 device buffer owned by the library, seen through the CUDA
+    array interface (no copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i4", "data": (int(ptr), False),
+                                         "version": 3}
+
+
+class Shard:
+    """Shard `index` of an n-way decomposition of a network into stripes of
+    module rows (the paper's spatial decomposition), on the current device."""
+
+    def __init__(self, cfg: dict, n_shards: int, index: int, raster_capacity: int = 1 << 20, stream=None):
+        import torch
+        L = load()
+        self.device = torch.cuda.current_device()
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._s = ctypes.c_void_p(self.stream.cuda_stream)
+        self._c = config(cfg, raster_capacity)
+        self._alloc = _TorchAllocator(self.device, self.stream)
+        h = ctypes.c_void_p()
+        check(L.snn_shard_build(ctypes.byref(self._c), int(n_shards), int(index), self._alloc.alloc,
+                                self._alloc.free, None, self._s, ctypes.byref(h)))
+        self._h = h
+        self.raster_capacity = raster_capacity
+
+    def info(self) -> dict:
+        i = ShardInfo()
+        check(load().snn_shard_info(self._h, ctypes.byref(i)))
+        return {f[0]: getattr(i, f[0]) for f in ShardInfo._fields_}
+
+    def integrate(self):
+        check(load().snn_shard_integrate(self._h, self._s))
+
+    def outbox(self):
+        """Device pointers (ids, count) of the step's spikes."""
+        a, b = ctypes.c_void_p(), ctypes.c_void_p()
+        check(load().snn_shard_outbox(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def outbox_tensors(self):
+        """Zero-copy int32 tensor views of the outbox: (ids, capacity n1 - n0;
+        count, 1 entry), for the exchange with other ranks."""
+        import torch
+        ids_p, cnt_p = self.outbox()
+        inf = self.info()
+        return (torch.as_tensor(_DeviceArray(ids_p, max(inf["n1"] - inf["n0"], 1)), device="cuda"),
+                torch.as_tensor(_DeviceArray(cnt_p, 1), device="cuda"))
+
+    def deliver(self, lists):
+        """lists: (ids device pointer, count device pointer) per inbound list."""
+        n = len(lists)
+        ids = (ctypes.c_void_p * max(n, 1))(*[x[0] for x in lists])
+        cnt = (ctypes.c_void_p * max(n, 1))(*[x[1] for x in lists])
+        check(load().snn_shard_deliver(self._h, ids, cnt, n, self._s))
+
+    def read_spikes(self):
+        steps = np.empty(self.raster_capacity, np.uint32)
+        ids = np.empty(self.raster_capacity, np.uint32)
+        n = ctypes.c_size_t()
+        check(load().snn_shard_read_spikes(self._h, _ptr(steps), _ptr(ids), self.raster_capacity, ctypes.byref(n),
+                                           self._s))
+        return steps[: n.value], ids[: n.value]
+
+    def state(self):
+        inf = self.info()
+        Nl = inf["n1"] - inf["n0"]
+        V, c = np.empty(Nl, np.float32), np.empty(Nl, np.float32)
+        ref = np.empty(Nl, np.uint8)
+        ring = np.empty(inf["D"] * Nl, np.int32)
+        check(load().snn_shard_get_state(self._h, _ptr(V), _ptr(c), _ptr(ref), _ptr(ring), self._s))
+        return {"V": V, "c": c, "ref": ref, "ring": ring.reshape(inf["D"], Nl)}
+
+    def stats(self) -> dict:
+        st = SnnStats()
+        check(load().snn_shard_stats(self._h, ctypes.byref(st), self._s))
+        return {f[0]: getattr(st, f[0]) for f in SnnStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().snn_shard_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ShardedNetwork:
+    """All shards of an n-way decomposition on the current device, stepped by
+    snn_shards_run (the exchange reads the peers' outboxes in place); the
+    union state and raster are those of the undivided network."""
+
+    def __init__(self, cfg: dict, n_shards: int, raster_capacity: int = 1 << 20, stream=None):
+        self.cfg = dict(cfg)
+        self.shards = [Shard(cfg, n_shards, k, raster_capacity, stream) for k in range(n_shards)]
+        self._s = self.shards[0]._s
+        self._arr = (ctypes.c_void_p * n_shards)(*[sh._h.value for sh in self.shards])
+
+    def step(self, n: int = 1):
+        check(load().snn_shards_run(self._arr, len(self.shards), int(n), self._s))
+
+    def read_spikes(self):
+        parts = [sh.read_spikes() for sh in self.shards]
+        st = np.concatenate([p[0] for p in parts])
+        ids = np.concatenate([p[1] for p in parts])
+        order = np.lexsort((ids, st))
+        return st[order], ids[order]
+
+    def state(self):
+        parts = [sh.state() for sh in self.shards]
+        return {"V": np.concatenate([p["V"] for p in parts]), "c": np.concatenate([p["c"] for p in parts]),
+                "ref": np.concatenate([p["ref"] for p in parts]),
+                "ring": np.concatenate([p["ring"] for p in parts], axis=1)}
+
+    def stats(self) -> dict:
+        tot = {}
+        for sh in self.shards:
+            for k, v in sh.stats().items():
+                tot[k] = tot.get(k, 0) + v
+        tot["steps"] = self.shards[0].info()["t"]
+        return tot
+
+    def close(self):
+        for sh in self.shards:
+            sh.close()
 
     def __enter__(self):
         return self
