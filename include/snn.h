@@ -120,6 +120,24 @@ typedef struct snn_config {
      * d_exc_hi (renormalised).  Inhibitory delays stay d_inh. */
     int32_t delay_dist;
     float delay_tau_ms;
+    /* Spike-timing dependent plasticity (Sec. II-A: contributions at each
+     * post-synaptic spike and each pre-synaptic arrival, integrated into a
+     * long-term change of every synapse every period; disabled in all of the
+     * paper's measurements, Sec. III-A, which give no rule or parameters).
+     * stdp = 1: pair-based with exponential traces, excitatory synapses only.
+     * At a post-synaptic spike at step t a synapse gains stdp_A_plus times
+     * the sum over its arrivals a < t of exp(-(t - a)/tau_plus); at an arrival
+     * at step t it loses stdp_A_minus times the sum over the post-synaptic
+     * spikes b <= t of exp(-(t - b)/tau_minus).  Each contribution is rounded
+     * to 2^-16 mV and summed exactly (int32); at the end of every
+     * stdp_period_steps steps the sum is added to the weight, clipped to
+     * [0, stdp_w_max], and restarts.  Needs f32 weights and schedule 0 or 1;
+     * no snapshots, batches or serving. */
+    int32_t stdp;
+    float stdp_A_plus, stdp_A_minus;          /* mV */
+    float stdp_tau_plus_ms, stdp_tau_minus_ms;
+    float stdp_w_max;                         /* mV */
+    uint32_t stdp_period_steps;               /* 1000 = the paper's one second */
 } snn_config;
 
 typedef struct snn_stats {
@@ -215,6 +233,13 @@ SNN_API snn_status snn_get_state(snn_net* net, float* V, float* c, uint8_t* ref,
                          uint32_t* t, void* stream);
 SNN_API snn_status snn_set_state(snn_net* net, const float* V, const float* c, const uint8_t* ref,
                          void* stream);
+
+/* STDP state (stdp = 1): the change accumulated by every synapse since the
+ * last period's application (int32, units of 2^-16 mV; rows back to back as
+ * snn_get_table), and the post- and pre-synaptic traces y, x of every neuron
+ * (any pointer may be NULL).  Synchronises `stream`.  Errors: SNN_EINVAL if
+ * the network has no plasticity. */
+SNN_API snn_status snn_get_stdp(snn_net* net, int32_t* delta, float* y, float* x, void* stream);
 
 /* Out-degree of rows [first, first + count) (K each under the fixed rule).
  * Errors: SNN_EINVAL if the rows are out of range. */

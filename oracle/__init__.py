@@ -59,6 +59,9 @@ class OrParams(ctypes.Structure):
         ("inh_local_only", ctypes.c_int32), ("weight_dist", ctypes.c_int32),
         ("w_exc_sd", ctypes.c_float), ("w_inh_sd", ctypes.c_float),
         ("delay_dist", ctypes.c_int32), ("delay_tau_ms", ctypes.c_float),
+        ("stdp", ctypes.c_int32), ("stdp_A_plus", ctypes.c_float), ("stdp_A_minus", ctypes.c_float),
+        ("stdp_tau_plus_ms", ctypes.c_float), ("stdp_tau_minus_ms", ctypes.c_float),
+        ("stdp_w_max", ctypes.c_float), ("stdp_period_steps", ctypes.c_uint32),
     ]
 
 
@@ -151,6 +154,7 @@ def lib():
         L.or_time.restype = ctypes.c_uint32
         L.or_get_state.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 4
         L.or_get_state_f64.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2
+        L.or_get_stdp.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 3
         L.or_set_state_f64.argtypes = [ctypes.c_void_p] + [ctypes.c_void_p] * 2
         L.or_get_ring_f64.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
         L.or_constants64.argtypes = [P(OrParams), P(OrConsts64)]
@@ -462,6 +466,15 @@ class OracleNet:
             lib().or_set_state(self._h, None, None, _ptr(ref))
         else:
             lib().or_set_state(self._h, _ptr(V), _ptr(c), _ptr(ref))
+
+    def stdp(self):
+        """(accumulated change of every synapse in 2^-16 mV, post trace y, pre trace x)."""
+        ns = int(lib().or_n_synapses(self._h))
+        delta = np.zeros(ns, np.int64)
+        y = np.empty(self.N, np.float32)
+        x = np.empty(self.N, np.float32)
+        lib().or_get_stdp(self._h, _ptr(delta), _ptr(y), _ptr(x))
+        return delta, y, x
 
     def stats(self):
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()

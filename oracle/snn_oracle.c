@@ -168,6 +168,11 @@ int or_constants(const or_params* p, or_consts* c) {
         set_err("fx_shift must be in [8, 24]");
         return -1;
     }
+    if (p->stdp && (!(p->stdp_tau_plus_ms > 0.0f) || !(p->stdp_tau_minus_ms > 0.0f) ||
+                    !(p->stdp_w_max >= 0.0f) || p->stdp_period_steps == 0 || p->weight_bf16)) {
+        set_err("stdp needs positive time constants, w_max >= 0, a period >= 1 and f32 weights");
+        return -1;
+    }
     uint64_t N = (uint64_t)p->grid_w * p->grid_h * p->neurons_per_module;
     if (N > 0xFFFFFFF0ull) {
         set_err("too many neurons");
@@ -493,6 +498,17 @@ struct or_net {
     uint64_t n_spikes, rec, ext;
     uint64_t shuffle_seed;
     or_consts64 k64;  /* FP64 mode: propagator constants in double */
+    /* STDP */
+    float sa_p, sa_m;     /* trace decays exp(-dt/tau_plus), exp(-dt/tau_minus) */
+    float* sy;            /* post-synaptic trace of every neuron */
+    float* sx;            /* pre-synaptic trace of every neuron */
+    float* sxh;           /* sx of the last D + 1 steps, row t % (D + 1) */
+    int64_t* sdelta;      /* accumulated change of every synapse, 2^-16 mV */
+    uint64_t* in_ptr;     /* synapses targeting neuron j: in_syn[in_ptr[j] .. in_ptr[j + 1]) */
+    uint64_t* in_syn;
+    uint64_t** arr;       /* arrival lists, one per ring slot (flow step 3) */
+    uint64_t* arr_n;
+    uint64_t* arr_cap;
 };
 
 static int is_exc(const or_net* n, uint32_t i) { return (i % n->M) < n->c.n_exc; }
@@ -502,6 +518,10 @@ void or_destroy(or_net* n) {
     free(n->row_ptr); free(n->tgt); free(n->w); free(n->w64); free(n->d);
     free(n->V); free(n->cf); free(n->V64); free(n->c64); free(n->ref);
     free(n->ring); free(n->ring64); free(n->spk); free(n->rst_t); free(n->rst_id);
+    free(n->sy); free(n->sx); free(n->sxh); free(n->sdelta); free(n->in_ptr); free(n->in_syn);
+    if (n->arr)
+        for (uint32_t k = 0; k < n->c.D; ++k) free(n->arr[k]);
+    free(n->arr); free(n->arr_n); free(n->arr_cap);
     free(n);
 }
 
@@ -814,6 +834,139 @@ void or_drive(const or_params* p, const or_consts* c, uint32_t i, uint32_t t, ui
     *forced = (uint64_t)u[1] < c->imposed_thresh;
 }
 
+/* STDP state: traces, their history, the change accumulators, the arrival
+ * lists and, for the potentiation at a post-synaptic spike, every neuron's
+ * incoming synapses (a target-major index of the CSR). */
+static int stdp_setup(or_net* n) {
+    const or_params* p = &n->p;
+    if (n->fp64) {
+        set_err("stdp is not modelled in the FP64 mode");
+        return -1;
+    }
+    double dt = (double)p->dt;
+    n->sa_p = (float)exp(-dt / (double)p->stdp_tau_plus_ms);
+    n->sa_m = (float)exp(-dt / (double)p->stdp_tau_minus_ms);
+    uint32_t D = n->c.D;
+    n->sy = (float*)calloc(n->N, sizeof(float));
+    n->sx = (float*)calloc(n->N, sizeof(float));
+    n->sxh = (float*)calloc((size_t)(D + 1) * n->N, sizeof(float));
+    n->sdelta = (int64_t*)calloc(n->nsyn, sizeof(int64_t));
+    n->in_ptr = (uint64_t*)calloc((size_t)n->N + 1, sizeof(uint64_t));
+    n->in_syn = (uint64_t*)malloc(sizeof(uint64_t) * (n->nsyn ? n->nsyn : 1));
+    n->arr = (uint64_t**)calloc(D, sizeof(uint64_t*));
+    n->arr_n = (uint64_t*)calloc(D, sizeof(uint64_t));
+    n->arr_cap = (uint64_t*)calloc(D, sizeof(uint64_t));
+    if (!n->sy || !n->sx || !n->sxh || !n->sdelta || !n->in_ptr || !n->in_syn || !n->arr || !n->arr_n || !n->arr_cap) {
+        set_err("out of memory");
+        return -1;
+    }
+    uint64_t total = n->row_ptr[n->N];
+    for (uint64_t e = 0; e < total; ++e) n->in_ptr[n->tgt[e] + 1] += 1;
+    for (uint32_t j = 0; j < n->N; ++j) n->in_ptr[j + 1] += n->in_ptr[j];
+    uint64_t* fill = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n->N + 1));
+    if (!fill) {
+        set_err("out of memory");
+        return -1;
+    }
+    memcpy(fill, n->in_ptr, sizeof(uint64_t) * ((size_t)n->N + 1));
+    for (uint64_t e = 0; e < total; ++e) n->in_syn[fill[n->tgt[e]]++] = e;
+    free(fill);
+    return 0;
+}
+
+static int arrival_push(or_net* n, uint32_t slot, uint64_t e) {
+    if (n->arr_n[slot] == n->arr_cap[slot]) {
+        uint64_t nc = n->arr_cap[slot] ? 2 * n->arr_cap[slot] : 1024;
+        uint64_t* a = (uint64_t*)realloc(n->arr[slot], sizeof(uint64_t) * nc);
+        if (!a) return -1;
+        n->arr[slot] = a;
+        n->arr_cap[slot] = nc;
+    }
+    n->arr[slot][n->arr_n[slot]++] = e;
+    return 0;
+}
+
+static uint32_t source_of(const or_net* n, uint64_t e) {
+    uint32_t lo = 0, hi = n->N;  /* the row holding synapse e: row_ptr[lo] <= e < row_ptr[lo + 1] */
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (n->row_ptr[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* The plasticity of step t, after every neuron has been updated (its spikes
+ * are spk[0 .. nspk)): traces, depression at this step's arrivals, then
+ * potentiation at this step's post-synaptic spikes. */
+static void stdp_step(or_net* n, uint32_t t, uint32_t nspk) {
+    const or_params* p = &n->p;
+    uint32_t D = n->c.D;
+    float scale = ldexpf(1.0f, 16);
+    for (uint32_t i = 0; i < n->N; ++i) {
+        n->sy[i] = n->sy[i] * n->sa_m;
+        n->sx[i] = n->sx[i] * n->sa_p;
+    }
+    for (uint32_t s = 0; s < nspk; ++s) {
+        n->sy[n->spk[s]] = n->sy[n->spk[s]] + 1.0f;
+        n->sx[n->spk[s]] = n->sx[n->spk[s]] + 1.0f;
+    }
+    memcpy(n->sxh + (size_t)(t % (D + 1)) * n->N, n->sx, sizeof(float) * n->N);
+    /* flow step 4: each arrival of this step against the post-synaptic trace,
+     * which includes a spike of this step */
+    uint32_t slot = t % D;
+    for (uint64_t k = 0; k < n->arr_n[slot]; ++k) {
+        uint64_t e = n->arr[slot][k];
+        float c = p->stdp_A_minus * n->sy[n->tgt[e]];
+        n->sdelta[e] -= (int64_t)lrintf(c * scale);
+    }
+    n->arr_n[slot] = 0;
+    /* flow step 1: each post-synaptic spike against the trace of the arrivals
+     * strictly before it: x of the source d + 1 steps ago, decayed one step */
+    for (uint32_t s = 0; s < nspk; ++s) {
+        uint32_t j = n->spk[s];
+        for (uint64_t q = n->in_ptr[j]; q < n->in_ptr[j + 1]; ++q) {
+            uint64_t e = n->in_syn[q];
+            uint32_t i = source_of(n, e);
+            if (!is_exc(n, i)) continue;
+            uint32_t d = n->d[e];
+            if (t < d + 1) continue;  /* no arrival can precede the start */
+            float xa = n->sxh[(size_t)((t - d - 1) % (D + 1)) * n->N + i] * n->sa_p;
+            float c = p->stdp_A_plus * xa;
+            n->sdelta[e] += (int64_t)lrintf(c * scale);
+        }
+    }
+}
+
+/* Every stdp_period_steps: the accumulated changes into the excitatory
+ * weights (each change must fit an int32, the accumulator of the CUDA path). */
+static int stdp_apply(or_net* n) {
+    float inv = ldexpf(1.0f, -16);
+    for (uint32_t i = 0; i < n->N; ++i) {
+        if (!is_exc(n, i)) continue;
+        for (uint64_t e = n->row_ptr[i]; e < n->row_ptr[i + 1]; ++e) {
+            if (n->sdelta[e] > INT32_MAX || n->sdelta[e] < INT32_MIN) {
+                set_err("stdp change overflows int32");
+                return -1;
+            }
+            float w = n->w[e] + (float)n->sdelta[e] * inv;
+            if (w < 0.0f) w = 0.0f;
+            if (w > n->p.stdp_w_max) w = n->p.stdp_w_max;
+            n->w[e] = w;
+            n->sdelta[e] = 0;
+        }
+    }
+    return 0;
+}
+
+void or_get_stdp(const or_net* n, int64_t* delta, float* y, float* x) {
+    if (delta && n->sdelta) memcpy(delta, n->sdelta, sizeof(int64_t) * n->row_ptr[n->N]);
+    if (y && n->sy) memcpy(y, n->sy, sizeof(float) * n->N);
+    if (x && n->sx) memcpy(x, n->sx, sizeof(float) * n->N);
+}
+
 or_net* or_create(const or_params* p, int fp64) {
     or_consts c;
     if (or_constants(p, &c)) return NULL;
@@ -869,6 +1022,10 @@ or_net* or_create(const or_params* p, int fp64) {
         }
     }
     or_constants64(p, &n->k64);
+    if (p->stdp && stdp_setup(n)) {
+        or_destroy(n);
+        return NULL;
+    }
     return n;
 }
 
@@ -915,16 +1072,19 @@ static int raster_push(or_net* n, uint32_t t, uint32_t id) {
     return 0;
 }
 
-static void deliver_one(or_net* n, uint32_t t, uint32_t src, uint32_t k) {
+static int deliver_one(or_net* n, uint32_t t, uint32_t src, uint32_t k) {
     size_t e = (size_t)n->row_ptr[src] + k;
     uint32_t slot = (t + n->d[e]) % n->c.D;
     size_t r = (size_t)slot * n->N + n->tgt[e];
+    /* flow step 3: plastic synapses are also queued for their arrival step */
+    if (n->p.stdp && is_exc(n, src) && arrival_push(n, slot, e)) return -1;
     if (n->fp64) {
         n->ring64[r] += n->w64[e];
     } else {
         float scale = ldexpf(1.0f, (int)n->p.fx_shift);
         n->ring[r] += (int64_t)lrintf(n->w[e] * scale);
     }
+    return 0;
 }
 
 static int step_once(or_net* n) {
@@ -965,6 +1125,7 @@ static int step_once(or_net* n) {
         }
     }
     n->n_spikes += nspk;
+    if (n->p.stdp) stdp_step(n, t, nspk);
     uint64_t total = 0;
     for (uint32_t s = 0; s < nspk; ++s) total += n->row_ptr[n->spk[s] + 1] - n->row_ptr[n->spk[s]];
     n->rec += total;
@@ -973,7 +1134,11 @@ static int step_once(or_net* n) {
     if (n->shuffle_seed == 0) {
         for (uint32_t s = 0; s < nspk; ++s) {
             uint32_t len = (uint32_t)(n->row_ptr[n->spk[s] + 1] - n->row_ptr[n->spk[s]]);
-            for (uint32_t k = 0; k < len; ++k) deliver_one(n, t, n->spk[s], k);
+            for (uint32_t k = 0; k < len; ++k)
+                if (deliver_one(n, t, n->spk[s], k)) {
+                    set_err("out of memory");
+                    return -1;
+                }
         }
     } else {
         /* every (spike, synapse) event in a random order */
@@ -1002,10 +1167,17 @@ static int step_once(or_net* n) {
             src[j] = a;
             syn[j] = b;
         }
-        for (e = 0; e < total; ++e) deliver_one(n, t, src[e], syn[e]);
+        int bad = 0;
+        for (e = 0; e < total; ++e) bad |= deliver_one(n, t, src[e], syn[e]);
         free(src);
         free(syn);
+        if (bad) {
+            set_err("out of memory");
+            return -1;
+        }
     }
+    /* the long-term plasticity of the period that ends with this step */
+    if (n->p.stdp && (t + 1) % n->p.stdp_period_steps == 0 && stdp_apply(n)) return -1;
     n->t = t + 1;
     return 0;
 }

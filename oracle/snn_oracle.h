@@ -31,6 +31,10 @@
  *                        drive draws, its ring against sums of the FP64 weights
  *   Poisson drive        pinned: table vs Poisson CDF, mean/variance, chi-square
  *   delivery             pinned: order independence, delay/weight arrival trace
+ *   STDP (stdp = 1)      pinned: the accumulated change of every synapse against
+ *                        the closed-form pair sum over the raster, weights after
+ *                        a period against the clipped sums, inhibitory synapses
+ *                        and zero amplitudes unchanged
  *   whole-network rates  parity unpinned against the paper (its drive is not
  *                        given and its connection rule differs from this one)
  */
@@ -77,6 +81,21 @@ typedef struct or_params {
     int32_t delay_dist;             /* 0: exc uniform integer in [d_exc_lo, d_exc_hi];
                                        1: exponential of mean delay_tau_ms, truncated to it */
     float delay_tau_ms;
+    /* Spike-timing dependent plasticity (Sec. II-A: contributions at each
+     * post-synaptic spike, flow step 1, and at each pre-synaptic arrival,
+     * flow step 4, integrated into a long-term change of every synapse every
+     * stdp_period_steps; the paper gives no rule and no parameters).  Pair-based
+     * with exponential traces, excitatory synapses only: at a post-synaptic
+     * spike at step t a synapse gains A_plus * sum over its arrivals a < t of
+     * exp(-(t - a)/tau_plus); at an arrival at step t it loses A_minus * sum
+     * over post-synaptic spikes b <= t of exp(-(t - b)/tau_minus).  Each
+     * contribution is rounded to the 2^-16 mV grid and summed exactly; every
+     * period the sum is added to the weight, clipped to [0, w_max]. */
+    int32_t stdp;
+    float stdp_A_plus, stdp_A_minus;          /* mV */
+    float stdp_tau_plus_ms, stdp_tau_minus_ms;
+    float stdp_w_max;                         /* mV */
+    uint32_t stdp_period_steps;               /* 1000 = the paper's one second */
 } or_params;
 
 typedef struct or_consts {
@@ -177,6 +196,10 @@ void or_clear_raster(or_net* net);
 
 uint32_t or_time(const or_net* net);
 void or_get_state(const or_net* net, float* V, float* c, uint8_t* ref, int32_t* ring);
+/* STDP state: the accumulated change of every synapse (2^-16 mV units; CSR
+ * order), the post-synaptic trace y and the pre-synaptic trace x of every
+ * neuron (any pointer may be NULL). */
+void or_get_stdp(const or_net* net, int64_t* delta, float* y, float* x);
 void or_get_state_f64(const or_net* net, double* V, double* c);
 void or_set_state_f64(or_net* net, const double* V, const double* c);
 /* FP64 mode: the delay ring, D rows of N doubles (row r = inputs of steps with t % D == r) */

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsnn.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["snn_api.cu", "build_kernels.cu", "step_kernels.cu", "persistent_kernels.cu", "persistent_tiled.cu", "persistent_owned.cu", "shard_kernels.cu", "cdf_static.cu", "server.cu", "autotune.cu", "batch_kernels.cu"]
+SOURCES = ["snn_api.cu", "build_kernels.cu", "step_kernels.cu", "persistent_kernels.cu", "persistent_tiled.cu", "persistent_owned.cu", "shard_kernels.cu", "stdp_kernels.cu", "cdf_static.cu", "server.cu", "autotune.cu", "batch_kernels.cu"]
 
 
 def nvcc() -> str:

@@ -137,6 +137,7 @@ snn_status snn_server_create(uint64_t budget_bytes, uint32_t chunk_steps, uint32
 snn_status snn_server_submit(snn_server* s, const snn_config* cfg, uint32_t n_steps, uint64_t arrival_ns,
                              uint64_t* request_id) {
     if (!s || !cfg) return sfail(SNN_EINVAL, "server or config is NULL");
+    if (cfg->stdp) return sfail(SNN_EINVAL, "the server runs static synapses (stdp = 0)");
     Pending p;
     p.id = s->next_id++;
     p.cfg = *cfg;

@@ -83,6 +83,8 @@ struct snn_net {
     int pgrid = 0;      // persistent grid (schedule 2)
     int tgrid = 0;      // tiled persistent grid (schedule 3), 0 if unavailable
     int ogrid = 0;      // owner-windowed persistent grid (schedule 4), 0 until set up
+    bool stdp = false;        // spike-timing dependent plasticity (schedules 0 and 1)
+    StdpView sp{};
     int2* own_rec = nullptr;  // schedule 4 record queues and their size
     size_t own_rec_bytes = 0;
     uint32_t pair_n = 0;              // pairwise law: stencil entries
@@ -179,6 +181,13 @@ snn_status validate(const snn_config* c) {
     if (c->weight_dtype != SNN_WEIGHT_F32 && c->weight_dtype != SNN_WEIGHT_BF16)
         return fail(SNN_EINVAL, "weight_dtype must be SNN_WEIGHT_F32 or SNN_WEIGHT_BF16");
     if (c->fx_shift < 8 || c->fx_shift > 24) return fail(SNN_EINVAL, "fx_shift must be in [8, 24]");
+    if (c->stdp != 0 && c->stdp != 1) return fail(SNN_EINVAL, "stdp must be 0 or 1");
+    if (c->stdp &&
+        (!(c->stdp_tau_plus_ms > 0.0f) || !(c->stdp_tau_minus_ms > 0.0f) || !(c->stdp_w_max >= 0.0f) ||
+         !std::isfinite(c->stdp_A_plus) || !std::isfinite(c->stdp_A_minus) || !std::isfinite(c->stdp_w_max) ||
+         c->stdp_period_steps == 0 || c->weight_dtype != SNN_WEIGHT_F32))
+        return fail(SNN_EINVAL, "stdp needs tau_plus, tau_minus > 0, finite amplitudes, w_max >= 0, a period "
+                                ">= 1 and f32 weights");
     if (c->table_layout != SNN_LAYOUT_DRAW && c->table_layout != SNN_LAYOUT_GROUPED)
         return fail(SNN_EINVAL, "table_layout must be SNN_LAYOUT_DRAW or SNN_LAYOUT_GROUPED");
     if (!std::isfinite(c->w_exc_lo) || !std::isfinite(c->w_exc_hi) || !std::isfinite(c->w_inh) ||
@@ -577,6 +586,60 @@ snn_status set_bands(snn_net* n, uint32_t bands, uint32_t* chosen) {
     return SNN_OK;
 }
 
+// Plasticity state of a freshly built table: traces, histories and
+// accumulators at zero, decays from the time constants (FP64, rounded once),
+// and the incoming index (synapses of every target), counted, scanned on the
+// host and filled.
+snn_status stdp_setup(snn_net* n, cudaStream_t s) {
+    const snn_config& c = n->cfg;
+    const NetView& v = n->v;
+    StdpView& p = n->sp;
+    const size_t Np = n->Npad, D = n->D;
+    const size_t nsyn = (size_t)n->N * n->Kpad;
+    p.y = (float*)dev_alloc(n, Np * 4);
+    p.x = (float*)dev_alloc(n, Np * 4);
+    p.xh = (float*)dev_alloc(n, (D + 1) * Np * 4);
+    p.hist = (uint32_t*)dev_alloc(n, D * Np * 4);
+    p.hist_cnt = (uint32_t*)dev_alloc(n, D * 4);
+    p.delta = (int32_t*)dev_alloc(n, nsyn * 4);
+    uint64_t* in_ptr = (uint64_t*)dev_alloc(n, ((size_t)n->N + 1) * 8);
+    uint64_t* cursor = (uint64_t*)dev_alloc(n, ((size_t)n->N + 1) * 8);
+    if (!p.y || !p.x || !p.xh || !p.hist || !p.hist_cnt || !p.delta || !in_ptr || !cursor)
+        return fail(SNN_ENOMEM, "device allocation of the plasticity state failed");
+    CUDA_TRY(cudaMemsetAsync(p.y, 0, Np * 4, s));
+    CUDA_TRY(cudaMemsetAsync(p.x, 0, Np * 4, s));
+    CUDA_TRY(cudaMemsetAsync(p.xh, 0, (D + 1) * Np * 4, s));
+    CUDA_TRY(cudaMemsetAsync(p.hist_cnt, 0, D * 4, s));
+    CUDA_TRY(cudaMemsetAsync(p.delta, 0, nsyn * 4, s));
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, ((size_t)n->N + 1) * 8, s));
+    CUDA_TRY(launch_stdp_index(v, cursor, nullptr, s));  // counts per target
+    std::vector<uint64_t> h((size_t)n->N + 1, 0);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), cursor, (size_t)n->N * 8, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    uint64_t acc = 0;
+    for (size_t j = 0; j <= n->N; ++j) {
+        const uint64_t x = j < n->N ? h[j] : 0;
+        h[j] = acc;
+        acc += x;
+    }
+    uint64_t* in_syn = (uint64_t*)dev_alloc(n, std::max<uint64_t>(acc, 1) * 8);
+    if (!in_syn) return fail(SNN_ENOMEM, "device allocation of the incoming-synapse index failed");
+    CUDA_TRY(cudaMemcpyAsync(in_ptr, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(cursor, h.data(), h.size() * 8, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_stdp_index(v, cursor, in_syn, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // the host vector goes out of scope
+    p.in_ptr = in_ptr;
+    p.in_syn = in_syn;
+    p.a_plus = (float)std::exp(-(double)c.dt_ms / (double)c.stdp_tau_plus_ms);
+    p.a_minus = (float)std::exp(-(double)c.dt_ms / (double)c.stdp_tau_minus_ms);
+    p.A_plus = c.stdp_A_plus;
+    p.A_minus = c.stdp_A_minus;
+    p.w_max = c.stdp_w_max;
+    p.period = c.stdp_period_steps;
+    n->stdp = true;
+    return SNN_OK;
+}
+
 // The scalar parameters of the construction kernels (device tables are set
 // by the caller); n->max_off must be set.
 void fill_build_view(const snn_net* n, BuildView& b) {
@@ -787,6 +850,10 @@ snn_status build_impl(snn_net* n, cudaStream_t s) {
         CUDA_TRY(launch_gen_synapses(b, v.td, v.w, s));
     }
     CUDA_TRY(launch_init_state(b, v.V, v.c, v.ref, s));
+    if (c.stdp) {
+        st = stdp_setup(n, s);
+        if (st != SNN_OK) return st;
+    }
     CUDA_TRY(cudaMemsetAsync(v.ring, 0, (size_t)n->D * n->Npad * 4, s));
     CUDA_TRY(cudaMemsetAsync(v.seg, 0, (size_t)n->Npad * 4, s));
     CUDA_TRY(cudaMemsetAsync(v.st, 0, sizeof(DevState), s));
@@ -935,12 +1002,14 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
             if (st != SNN_OK) return st;
         }
         CUDA_TRY(launch_neuron_step(n->v, s));
+        if (n->stdp) CUDA_TRY(launch_stdp_pre_delivery(n->v, n->sp, s));
         if (timed) {
             snn_status st = timed_end(n->ev_neuron, s, slot);
             if (st == SNN_OK) st = timed_begin(n->ev_deliver, s, &slot);
             if (st != SNN_OK) return st;
         }
         CUDA_TRY(launch_deliver(n->v, n->schedule, n->block, n->grid, s));
+        if (n->stdp) CUDA_TRY(launch_stdp_apply(n->v, n->sp, s));
         if (timed) {
             snn_status st = timed_end(n->ev_deliver, s, slot);
             if (st != SNN_OK) return st;
@@ -1054,6 +1123,29 @@ snn_status snn_get_row_lengths(snn_net* n, uint32_t first, uint32_t count, uint3
     return SNN_OK;
 }
 
+snn_status snn_get_stdp(snn_net* n, int32_t* delta, float* y, float* x, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    if (!n->stdp) return fail(SNN_EINVAL, "the network has no plasticity (stdp = 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (delta) {
+        std::vector<uint32_t> len(n->N);
+        snn_status st = snn_get_row_lengths(n, 0, n->N, len.data(), stream);
+        if (st != SNN_OK) return st;
+        std::vector<int32_t> all((size_t)n->N * n->Kpad);
+        CUDA_TRY(cudaMemcpyAsync(all.data(), n->sp.delta, all.size() * 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        size_t o = 0;
+        for (uint32_t i = 0; i < n->N; ++i) {
+            std::memcpy(delta + o, all.data() + (size_t)i * n->Kpad, (size_t)len[i] * 4);
+            o += len[i];
+        }
+    }
+    if (y) CUDA_TRY(cudaMemcpyAsync(y, n->sp.y, (size_t)n->N * 4, cudaMemcpyDeviceToHost, s));
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, n->sp.x, (size_t)n->N * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SNN_OK;
+}
+
 snn_status snn_construction_tables(const snn_config* cfg, float* wtab, uint64_t* dthr, uint32_t* n_dthr,
                                    int32_t* pair_dx, int32_t* pair_dy, uint64_t* pair_thr, uint32_t cap,
                                    uint32_t* n_pair) {
@@ -1138,6 +1230,7 @@ snn_status snn_set_state(snn_net* n, const float* V, const float* c, const uint8
 }
 
 snn_status snn_snapshot(snn_net* n, void* host_buf, size_t cap, size_t* nbytes, void* stream) {
+    if (n && n->stdp) return fail(SNN_EINVAL, "snapshots do not hold the plastic weights of a network with stdp");
     if (!n || !nbytes) return fail(SNN_EINVAL, "net or n is NULL");
     const size_t N = n->Npad, D = n->D;
     const size_t need = sizeof(SnapshotHeader) + sizeof(DevState) + N * 4 * 2 + N + D * N * 4;
@@ -1163,6 +1256,7 @@ snn_status snn_snapshot(snn_net* n, void* host_buf, size_t cap, size_t* nbytes, 
 }
 
 snn_status snn_restore(snn_net* n, const void* host_buf, size_t nbytes, void* stream) {
+    if (n && n->stdp) return fail(SNN_EINVAL, "snapshots do not hold the plastic weights of a network with stdp");
     if (!n || !host_buf) return fail(SNN_EINVAL, "net or buffer is NULL");
     const size_t N = n->Npad, D = n->D;
     const size_t need = sizeof(SnapshotHeader) + sizeof(DevState) + N * 4 * 2 + N + D * N * 4;
@@ -1222,6 +1316,8 @@ snn_status snn_set_resident_state(snn_net* n, int32_t enable, int32_t* resident,
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     if (schedule < 0 || schedule > 4) return fail(SNN_EINVAL, "schedule must be 0, 1, 2, 3 or 4");
+    if (n->stdp && schedule >= 2)
+        return fail(SNN_EINVAL, "a network with stdp runs the per-step schedules 0 and 1 only");
     if (schedule == 4 && n->ogrid == 0) {
         snn_status st = owned_setup(n, 0, 0);
         if (st != SNN_OK) return st;
@@ -1531,6 +1627,7 @@ snn_status snn_batch_create(snn_net* const* nets, uint32_t n, snn_alloc_fn alloc
         if (!nets[i]) return fail(SNN_EINVAL, "network %u is NULL", i);
         for (uint32_t j = 0; j < i; ++j)
             if (nets[j] == nets[i]) return fail(SNN_EINVAL, "network %u appears twice", i);
+        if (nets[i]->stdp) return fail(SNN_EINVAL, "network %u has stdp, which batches do not run", i);
     }
     snn_batch* b = new (std::nothrow) snn_batch();
     if (!b) return fail(SNN_ENOMEM, "host allocation failed");
@@ -1895,6 +1992,7 @@ snn_status snn_shard_build(const snn_config* cfg, uint32_t n_shards, uint32_t in
     if (st != SNN_OK) return st;
     if (cfg->conn_rule != SNN_RULE_FIXED_K)
         return fail(SNN_EINVAL, "shards are built for the fixed out-degree rule (conn_rule = SNN_RULE_FIXED_K)");
+    if (cfg->stdp) return fail(SNN_EINVAL, "shards run static synapses (stdp = 0)");
     if (n_shards == 0 || index >= n_shards || n_shards > cfg->grid_h)
         return fail(SNN_EINVAL, "need 0 <= index < n_shards <= grid_h (got %u of %u, grid_h %u)", index, n_shards,
                     cfg->grid_h);

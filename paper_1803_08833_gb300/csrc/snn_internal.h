@@ -148,6 +148,24 @@ cudaError_t launch_shard_step(const NetView& v, const ShardView& sv, uint32_t t,
 cudaError_t launch_shard_deliver(const NetView& v, const ShardView& sv, const ShardInbound& in, uint32_t t,
                                  cudaStream_t s);
 
+// Spike-timing dependent plasticity of a network (stdp_kernels.cu).
+struct StdpView {
+    float* y;              // post-synaptic trace, Npad
+    float* x;              // pre-synaptic trace, Npad
+    float* xh;             // x of the last D + 1 steps, row t % (D + 1), stride Npad
+    uint32_t* hist;        // spike ids of the last D steps, row t % D, stride Npad
+    uint32_t* hist_cnt;    // D counts
+    int32_t* delta;        // N x Kpad accumulated changes (2^-16 mV)
+    const uint64_t* in_ptr;  // N + 1: incoming synapses of neuron j at in_syn[in_ptr[j] .. in_ptr[j + 1])
+    const uint64_t* in_syn;  // synapse indices source * Kpad + k
+    float a_plus, a_minus;   // trace decays per step
+    float A_plus, A_minus, w_max;
+    uint32_t period;
+};
+cudaError_t launch_stdp_index(const NetView& v, uint64_t* cnt_or_cursor, uint64_t* in_syn, cudaStream_t s);
+cudaError_t launch_stdp_pre_delivery(const NetView& v, const StdpView& p, cudaStream_t s);
+cudaError_t launch_stdp_apply(const NetView& v, const StdpView& p, cudaStream_t s);
+
 // Parameters of the construction kernels.
 struct BuildView {
     uint32_t grid_w, grid_h, n_modules, max_off, M, N, Npad, K, Kpad, n_exc;

@@ -49,6 +49,9 @@ class SnnConfig(ctypes.Structure):
         ("inh_local_only", ctypes.c_int32), ("weight_dist", ctypes.c_int32),
         ("w_exc_sd", ctypes.c_float), ("w_inh_sd", ctypes.c_float),
         ("delay_dist", ctypes.c_int32), ("delay_tau_ms", ctypes.c_float),
+        ("stdp", ctypes.c_int32), ("stdp_A_plus", ctypes.c_float), ("stdp_A_minus", ctypes.c_float),
+        ("stdp_tau_plus_ms", ctypes.c_float), ("stdp_tau_minus_ms", ctypes.c_float),
+        ("stdp_w_max", ctypes.c_float), ("stdp_period_steps", ctypes.c_uint32),
     ]
 
 
@@ -115,6 +118,7 @@ def load():
         "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_get_stdp": (st, [vp, vp, vp, vp, vp]),
         "snn_shard_build": (st, [P(SnnConfig), ctypes.c_uint32, ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, vp, P(vp)]),
         "snn_shard_info": (st, [vp, P(ShardInfo)]),
         "snn_shard_integrate": (st, [vp, vp]),
@@ -388,6 +392,16 @@ class Network:
     # -- tuning / timing ---------------------------------------------------
     def set_schedule(self, schedule: int, block: int = 0):
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
+
+    def stdp(self):
+        """(accumulated change of every synapse in 2^-16 mV units, rows back to
+        back; post trace y; pre trace x) of a network with plasticity."""
+        ln = self.row_lengths()
+        delta = np.empty(int(ln.astype(np.int64).sum()), np.int32)
+        y = np.empty(self.N, np.float32)
+        x = np.empty(self.N, np.float32)
+        check(load().snn_get_stdp(self._h, _ptr(delta), _ptr(y), _ptr(x), self._s))
+        return delta, y, x
 
     def set_window(self, window: int = 0, queue_cap: int = 0):
         """Schedule 4's delay window (steps kept in shared memory per band) and

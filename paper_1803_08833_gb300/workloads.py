@@ -170,3 +170,20 @@ def swa_48x48(seed=1, K=1100, **kw):
     model itself is not published."""
     lateral = {"kernel": "exp", "sigma_um": 100.0, "lambda_um": 240.0, "cutoff_um": 1200.0}
     return _make(48, 1250, K, lateral, seed, spacing_um=400.0, **kw)
+
+
+# Spike-timing dependent plasticity (Sec. II-A; disabled in all of the paper's
+# measurements, Sec. III-A, and given without a rule or parameters): pair-based
+# with exponential traces of 20 ms on both sides, depression 5 % stronger than
+# potentiation, excitatory weights bounded to [0, 0.5] mV, the long-term
+# change applied every 1,000 steps (the paper's one second).
+STDP = {"stdp": 1, "stdp_A_plus": 0.005, "stdp_A_minus": 0.00525, "stdp_tau_plus_ms": 20.0,
+        "stdp_tau_minus_ms": 20.0, "stdp_w_max": 0.5, "stdp_period_steps": 1000}
+
+
+def plastic(cfg, **kw):
+    """The network `cfg` with STDP switched on (parameters STDP, overridable)."""
+    c = copy.deepcopy(cfg)
+    c.update(STDP)
+    c.update(kw)
+    return c
