@@ -19,6 +19,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libsnn.so")
+# the checked variant (-DSNN_CHECK): device bounds checks on the hot path's
+# indexed writes, which set an error bit instead of writing out of bounds
+LIB_CHECK = os.path.join(PKG, "libsnn_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["snn_api.cu", "build_kernels.cu", "step_kernels.cu", "persistent_kernels.cu", "persistent_tiled.cu", "persistent_owned.cu", "shard_kernels.cu", "stdp_kernels.cu", "cdf_static.cu", "server.cu", "autotune.cu", "batch_kernels.cu"]
 
@@ -30,7 +33,11 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsnn.so")
 
 
-STAMP = os.path.join(BUILD, "flags.txt")
+def _paths(check):
+    """(library, object directory, flag stamp) of the release or checked variant."""
+    if check:
+        return LIB_CHECK, os.path.join(BUILD, "check"), os.path.join(BUILD, "check", "flags.txt")
+    return LIB, BUILD, os.path.join(BUILD, "flags.txt")
 
 
 def _user_flags():
@@ -51,25 +58,28 @@ def _deps():
     return files
 
 
-def stale() -> bool:
-    if not os.path.exists(LIB):
+def stale(check: bool = False) -> bool:
+    lib, _, stamp = _paths(check)
+    if not os.path.exists(lib):
         return True
     try:
-        with open(STAMP) as f:
+        with open(stamp) as f:
             if f.read() != " ".join(_user_flags()):
                 return True
     except OSError:
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, check: bool = False) -> str:
+    """Build libsnn.so (or, with check=True, the checked libsnn_check.so)."""
+    LIB, BUILD, STAMP = _paths(check)
+    if not force and not stale(check):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DSNN_CHECK"] if check else [])
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))

@@ -77,6 +77,7 @@ extern "C" {
 snn_status snn_autotune(snn_net* net, uint32_t trial_steps, const char* cache_path, int32_t* schedule, int32_t* block,
                         double* best_ms_per_step, void* stream) {
     if (!net || trial_steps == 0) return afail(SNN_EINVAL, "net is NULL or trial_steps is 0");
+    snn::NvtxRange range("snn_autotune");
     const std::string key = tune_key(net);
     int s = 0, b = 0;
     if (cache_lookup(cache_path, key, &s, &b) && snn_set_schedule(net, s, b) == SNN_OK) {

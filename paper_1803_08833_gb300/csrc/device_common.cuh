@@ -7,6 +7,16 @@
 
 namespace snn {
 
+// Checked builds (-DSNN_CHECK): bounds checks on the hot path's indexed
+// writes.  A failed check sets ERR_BOUNDS in the network's device state and
+// the access is skipped -- no trap, no fault; the host reports the bit.
+// Release builds compile every check to `true`.
+#ifdef SNN_CHECK
+#define SNN_BOUND(st, cond) ((cond) ? true : (atomicOr(&(st)->err, ERR_BOUNDS), false))
+#else
+#define SNN_BOUND(st, cond) true
+#endif
+
 __device__ __forceinline__ void red_add(int32_t* p, int32_t v) {
     asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -277,7 +287,8 @@ __device__ __forceinline__ void deliver_tasks(const NetView& v, uint64_t tk, uin
                 uint32_t s = slot0 + (tq[q] >> 24);
                 if (s >= v.D) s -= v.D;
                 const float wv = BF16 ? ((q & 1) ? bf16_hi(wq[q >> 1]) : bf16_lo(wq[q >> 1])) : __uint_as_float(wq[q]);
-                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
+                if (SNN_BOUND(v.st, s < v.D && (tq[q] & 0xFFFFFFu) < v.N))
+                    red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
             }
         }
     }
@@ -328,7 +339,8 @@ __device__ __forceinline__ void deliver_tasks_range(const NetView& v, uint64_t t
                 uint32_t s = slot0 + (tq[q] >> 24);
                 if (s >= v.D) s -= v.D;
                 const float wv = BF16 ? ((q & 1) ? bf16_hi(wq[q >> 1]) : bf16_lo(wq[q >> 1])) : __uint_as_float(wq[q]);
-                red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
+                if (SNN_BOUND(v.st, s < v.D && (tq[q] & 0xFFFFFFu) < v.N))
+                    red_add(v.ring + (size_t)s * v.Npad + (tq[q] & 0xFFFFFFu), fx_weight(v, wv));
             }
         }
     }

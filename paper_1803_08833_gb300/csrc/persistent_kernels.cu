@@ -216,7 +216,10 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
             uint32_t pos = (qa << 2) + run + incl - cnt;
 #pragma unroll
             for (int b = 0; b < 4; ++b)
-                if (spk & (1u << b)) v.seg[pos++] = (q << 2) + b;
+                if (spk & (1u << b)) {
+                    if (SNN_BOUND(v.st, pos < (qb << 2))) v.seg[pos] = (q << 2) + b;
+                    ++pos;
+                }
             run += __shfl_sync(0xFFFFFFFFu, incl, 31);
         };
         if (res && qb - qa <= 32u * PF_CHUNKS) {
@@ -315,6 +318,7 @@ __device__ __forceinline__ void run_steps(const NetView& v, uint32_t n_steps, ui
         block_exclusive_scan(v.woff, TW, s_wpre);
         if (reweigh) load_split_weights(v, G, s_wp);
         const uint32_t total = s_wpre[TW];
+        if (threadIdx.x == 0) (void)SNN_BOUND(v.st, total <= v.N);  // at most one spike per neuron and step
         const uint32_t slot0 = t % v.D;
         const uint64_t wa = s_wp[bid], wb = s_wp[bid + 1], wt = s_wp[G];
         uint64_t my_tasks = 0;

@@ -158,14 +158,14 @@ __device__ __forceinline__ void deliver_owned(const NetView& v, uint32_t tk, uin
                 if (d > W) {
                     uint32_t s = slot0 + d;
                     if (s >= v.D) s -= v.D;
-                    red_add_free(v.ring + (size_t)s * v.Npad + tgt, fx[i]);
+                    if (SNN_BOUND(v.st, s < v.D && tgt < v.N)) red_add_free(v.ring + (size_t)s * v.Npad + tgt, fx[i]);
                 } else {
                     const uint32_t qt = tgt >> 2;
                     uint32_t b = (uint32_t)(((uint64_t)qt * v.own_magic) >> 32);
                     if (b * BQ > qt) --b;
                     uint32_t ws = wbase + d;
                     if (ws >= W) ws -= W;
-                    key[i] = b;
+                    key[i] = SNN_BOUND(v.st, b < G && tgt < v.N) ? b : 0xFFFFFFFFu;
                     widx[i] = ws * BN + (tgt - b * BN);
                 }
             }
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(OWN_THREADS, 1) k_run_steps_owned(NetView v, u
                 }
 #pragma unroll
                 for (int u = 0; u < REC_UNROLL; ++u)
-                    if (r[u].x >= 0) atomicAdd(win + r[u].x, r[u].y);
+                    if (r[u].x >= 0 && SNN_BOUND(v.st, (uint32_t)r[u].x < W * BQ * 4)) atomicAdd(win + r[u].x, r[u].y);
             }
         }
         if (s_ovf) {  // some events for this band went to the ring: fold the window's rows in

@@ -197,6 +197,7 @@ static snn_status retire(snn_server* s, Active& a) {
 
 snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued) {
     if (!s) return sfail(SNN_EINVAL, "server is NULL");
+    snn::NvtxRange range("snn_server_tick");
     s->ticks += 1;
     // admission: arrival order, while the footprint fits the budget
     while (!s->queue.empty() && s->active.size() < s->max_slots && s->used + s->queue.front().bytes <= s->budget) {

@@ -58,6 +58,7 @@ struct EventRing {
 
 namespace snn {
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace snn
 
@@ -953,6 +954,7 @@ snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_f
     n->free_fn = free_fn;
     n->alloc_ctx = alloc_ctx;
     cudaGetDevice(&n->device);
+    NvtxRange range("snn_build_network");
     st = build_impl(n, (cudaStream_t)stream);
     if (st != SNN_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -966,6 +968,7 @@ snn_status snn_build_network(const snn_config* cfg, snn_alloc_fn alloc_fn, snn_f
 
 snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
+    NvtxRange range("snn_step");
     cudaStream_t s = (cudaStream_t)stream;
     if (n->schedule >= 2) {
         // one cooperative launch per call (in pieces of at most 2^20 steps)
@@ -980,6 +983,8 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
                 snn_status st = timed_begin(n->ev_persist, s, &slot);
                 if (st != SNN_OK) return st;
             }
+            NvtxRange lr(n->schedule == 3 ? "persistent: target tiles" : n->schedule == 4 ? "persistent: owned windows"
+                                                                                  : "persistent: neuron + delivery phases");
             if (n->schedule == 3)
                 CUDA_TRY(launch_tiled(n->v, m, n->tgrid, s));
             else if (n->schedule == 4)
@@ -1001,15 +1006,21 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
             snn_status st = timed_begin(n->ev_neuron, s, &slot);
             if (st != SNN_OK) return st;
         }
-        CUDA_TRY(launch_neuron_step(n->v, s));
-        if (n->stdp) CUDA_TRY(launch_stdp_pre_delivery(n->v, n->sp, s));
+        {
+            NvtxRange r("neuron phase");
+            CUDA_TRY(launch_neuron_step(n->v, s));
+            if (n->stdp) CUDA_TRY(launch_stdp_pre_delivery(n->v, n->sp, s));
+        }
         if (timed) {
             snn_status st = timed_end(n->ev_neuron, s, slot);
             if (st == SNN_OK) st = timed_begin(n->ev_deliver, s, &slot);
             if (st != SNN_OK) return st;
         }
-        CUDA_TRY(launch_deliver(n->v, n->schedule, n->block, n->grid, s));
-        if (n->stdp) CUDA_TRY(launch_stdp_apply(n->v, n->sp, s));
+        {
+            NvtxRange r("delivery phase");
+            CUDA_TRY(launch_deliver(n->v, n->schedule, n->block, n->grid, s));
+            if (n->stdp) CUDA_TRY(launch_stdp_apply(n->v, n->sp, s));
+        }
         if (timed) {
             snn_status st = timed_end(n->ev_deliver, s, slot);
             if (st != SNN_OK) return st;
@@ -1031,6 +1042,7 @@ snn_status snn_read_spikes(snn_net* n, uint32_t* steps, uint32_t* ids, size_t ca
     if (m && ids) CUDA_TRY(cudaMemcpyAsync(ids, n->v.raster_id, m * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     *n_out = m;
+    if (ds.err & ERR_BOUNDS) return fail(SNN_ECUDA, "a device bounds check failed (error bits 0x%x)", ds.err);
     if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out or a device check failed (error bits 0x%x)", ds.err);
     if (ds.raster_count > n->v.raster_cap)
         return fail(SNN_EOVERFLOW, "raster overflow: %llu spikes recorded, capacity %llu",
@@ -1058,6 +1070,7 @@ snn_status snn_get_stats(snn_net* n, snn_stats* out, void* stream) {
     out->raster_capacity = n->v.raster_cap;
     out->neuron_phase_ns = ds.phase_ns[0];
     out->deliver_phase_ns = ds.phase_ns[1];
+    if (ds.err & ERR_BOUNDS) return fail(SNN_ECUDA, "a device bounds check failed (error bits 0x%x)", ds.err);
     if (ds.err) return fail(SNN_ETIMEOUT, "a device-side wait ran out or a device check failed (error bits 0x%x)", ds.err);
     return SNN_OK;
 }
@@ -1730,6 +1743,7 @@ snn_status snn_batch_waves(snn_batch* b, uint32_t* waves, uint64_t* ring_budget)
 
 snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
     if (!b || !steps) return fail(SNN_EINVAL, "batch or steps is NULL");
+    NvtxRange range("snn_batch_step");
     cudaStream_t s = (cudaStream_t)stream;
     const uint32_t n = (uint32_t)b->nets.size();
     // the pinned staging buffer may still feed the previous call's copy
@@ -2007,6 +2021,7 @@ snn_status snn_shard_build(const snn_config* cfg, uint32_t n_shards, uint32_t in
     cudaGetDevice(&sh->net.device);
     sh->n_shards = n_shards;
     sh->index = index;
+    NvtxRange range("snn_shard_build");
     st = shard_build_impl(sh, (cudaStream_t)stream);
     if (st != SNN_OK) {
         cudaStreamSynchronize((cudaStream_t)stream);
@@ -2076,6 +2091,7 @@ snn_status snn_shards_run(snn_shard* const* shards, uint32_t n, uint32_t n_steps
         if (memcmp(&shards[k]->net.cfg, &shards[0]->net.cfg, sizeof(snn_config)) != 0)
             return fail(SNN_EINVAL, "shards of different network descriptions");
     }
+    NvtxRange range("snn_shards_run");
     for (uint32_t step = 0; step < n_steps; ++step) {
         for (uint32_t k = 0; k < n; ++k) {
             snn_status st = snn_shard_integrate(shards[k], stream);

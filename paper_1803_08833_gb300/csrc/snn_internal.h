@@ -6,9 +6,20 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 struct snn_config;
 
 namespace snn {
+
+// An NVTX range for the lifetime of the object: profilers show the library's
+// phases (construction, steps, launches); free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Philox counter layout (c0, c1, c2, c3) = (a, b, tag, 0).
 constexpr uint32_t TAG_GEN = 0u;    // (neuron i, synapse k): target, weight, delay
@@ -26,6 +37,7 @@ constexpr int PERSIST_THREADS = SNN_PERSIST_THREADS;  // threads per CTA of the 
 constexpr int PERSIST_WARPS = PERSIST_THREADS / 32;
 constexpr uint32_t ERR_BARRIER_TIMEOUT = 1u;         // DevState::err bits
 constexpr uint32_t ERR_ALIGNMENT = 2u;               // a bulk copy address was not 16-byte aligned (skipped)
+constexpr uint32_t ERR_BOUNDS = 4u;                  // a device bounds check failed (checked builds, -DSNN_CHECK)
 constexpr int NEURONS_PER_THREAD = 4;
 constexpr int NEURONS_PER_BLOCK = NEURON_THREADS * NEURONS_PER_THREAD;  // 1024
 constexpr int MAX_POIS = 64;  // Poisson table entries (padded to a power of two)

@@ -138,7 +138,10 @@ __global__ void __launch_bounds__(NEURON_THREADS) k_neuron_step(NetView v) {
     uint32_t* seg = v.seg + (size_t)blockIdx.x * NEURONS_PER_BLOCK;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (spk & (1u << q)) seg[pos++] = base + q;
+        if (spk & (1u << q)) {
+            if (SNN_BOUND(v.st, pos < (uint32_t)NEURONS_PER_BLOCK)) seg[pos] = base + q;
+            ++pos;
+        }
 
     if (tid == 0) {
         v.blk_cnt[blockIdx.x] = btot;

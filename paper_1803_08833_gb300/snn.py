@@ -13,7 +13,8 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libsnn.so")
+# SNN_LIBRARY=check loads the checked build (device bounds checks, -DSNN_CHECK)
+LIB_PATH = os.path.join(_PKG, "libsnn_check.so" if os.environ.get("SNN_LIBRARY") == "check" else "libsnn.so")
 
 SNN_OK, SNN_EINVAL, SNN_ENOMEM, SNN_ECUDA, SNN_EOVERFLOW, SNN_ETIMEOUT, SNN_EBUDGET = 0, -1, -2, -3, -4, -5, -6
 _STATUS = {0: "SNN_OK", -1: "SNN_EINVAL", -2: "SNN_ENOMEM", -3: "SNN_ECUDA", -4: "SNN_EOVERFLOW",
