@@ -570,12 +570,16 @@ def run_batched(snn, args, stream):
 
     with snn.Batch(nets, stream=stream) as batch:
         batch.set_graph(True)
-        ms_batched, ev_batched, launches_batched = timed_batch(batch)
-        waves, ring_budget = batch.waves()
-        cta = batch.groups()
+        # the fixed default: grouped layout, launch shape 0, half the L2 per wave
+        ms_fixed, ev_fixed, _ = timed_batch(batch)
         # the same waves in one global neuron / task space each
         batch.set_mode("global")
         ms_global, ev_global, _ = timed_batch(batch)
+        # the autotuned layout, shape and ring budget (tuning restores every state)
+        tuned = batch.autotune(trial_steps=args.batch_tune_steps)
+        ms_batched, ev_batched, launches_batched = timed_batch(batch)
+        waves, ring_budget = batch.waves()
+        cta = batch.groups()
     # plain: one instance per launch, back to back on the same stream
     e0 = events()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -592,18 +596,25 @@ def run_batched(snn, args, stream):
     v_b = ev_batched / (ms_batched / 1e3)
     v_p = ev_plain / (ms_plain / 1e3)
     v_g = ev_global / (ms_global / 1e3)
+    v_f = ev_fixed / (ms_fixed / 1e3)
     return {"value": v_b, "unit": UNIT, "plain_value": v_p, "speedup_vs_plain": v_b / v_p,
             "global_value": v_g, "speedup_vs_global": v_b / v_g,
+            "fixed_value": v_f, "speedup_vs_fixed": v_b / v_f,
+            "tuned": {"mode": tuned["mode"], "shape": tuned["shape"], "ring_budget_mb": tuned["ring_budget"] / 2 ** 20,
+                      "trial_ms_per_step": tuned["ms_per_step"], "trial_steps": args.batch_tune_steps,
+                      "sweep_ms_per_step": tuned["sweep_ms_per_step"],
+                      "candidates": "layout {groups, global} x shape {2 CTAs/SM x 4 tasks, 1 x 6} x ring "
+                                    "budget {0.35, 0.5, 0.65} of L2, distinct wave plans only"},
             "instances": len(inst), "neurons": neurons, "steps_each": args.batch_steps,
             "ms_batched": ms_batched, "ms_global": ms_global, "ms_plain": ms_plain, "launches": launches_batched,
             "waves": waves, "ring_budget_mb": ring_budget / 2 ** 20,
             "ctas_per_instance": {"min": min(cta), "max": max(cta)},
             "workload": "64 instances, grid side U{4..16} x 1250 neurons, K=1125, Gaussian (even seed, 7.5 Hz) / "
                         "exponential (odd seed, 35 Hz), bf16 weights when seed bit 1 is set, one persistent "
-                        "launch per L2-sized wave of instances (each instance on a group of CTAs of its own, "
-                        "sized by a cost model refined by the warm-up's measured group times), replayed from one "
-                        "CUDA graph, vs one persistent launch per instance (plain) and vs the same waves in one "
-                        "global neuron / task space (global)"}
+                        "launch per L2-sized wave of instances in the autotuned layout, launch shape and ring "
+                        "budget, replayed from one CUDA graph; vs one persistent launch per instance (plain), the "
+                        "fixed default (grouped, shape 0, half the L2; fixed) and the same waves in one global "
+                        "neuron / task space (global)"}
 
 
 def run_precision(snn, args, stream):
@@ -709,7 +720,17 @@ def run_served(snn, args, stream):
     stream_reqs = W.served_stream(seconds=args.served_seconds, rate_hz=20.0, seed=7)
     budget = 150 << 30
     results = []
+    # the batch layout of the ticks: the tuner's choice on a sample of the mix
+    # (the first 16 requests as one batch, states restored after tuning)
+    sample = [snn.Network(cfg, raster_capacity=1 << 10, stream=stream) for _, cfg, _ in stream_reqs[:16]]
+    for n in sample:
+        n.set_schedule(2)
+    with snn.Batch(sample, stream=stream) as b:
+        tuned = b.autotune(trial_steps=100)
+    for n in sample:
+        n.close()
     with snn.Server(budget, chunk_steps=args.served_chunk, max_slots=args.served_slots, stream=stream) as srv:
+        srv.set_batch(tuned["mode"], tuned["shape"], tuned["ring_budget"])
         start = snn.now_ns()
         i = 0
         peak = 0
@@ -753,6 +774,10 @@ def run_served(snn, args, stream):
             "plain": "every 10th request run alone in turn (build, persistent run, destroy): events / total time",
             "gpu_busy_frac": st["busy_ns"] / 1e9 / wall, "peak_active": peak, "launches": st["launches"],
             "budget_gb": 150, "chunk_steps": args.served_chunk,
+            "batch_layout": {"mode": tuned["mode"], "shape": tuned["shape"],
+                             "ring_budget_mb": tuned["ring_budget"] / 2 ** 20,
+                             "tuned_on": "the first 16 requests as one batch, 100 trial steps per candidate",
+                             "sweep_ms_per_step": tuned["sweep_ms_per_step"]},
             "workload": "Poisson arrivals at 20 req/s (seed 7), grid side U{4..32} x 1250 neurons, K U{500..2250}, "
                         "Gaussian or exponential, every network spiking at %.1f Hz (imposed background rate), "
                         "duration U{500..5000} steps, bf16 weights, 150 GB budget, continuous batching in chunks "
@@ -799,6 +824,7 @@ def main(argv=None):
     ap.add_argument("--precision-steps", type=int, default=10000)
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--batch-tune-steps", type=int, default=200, help="trial steps per candidate of the batch tuner")
     ap.add_argument("--served-seconds", type=float, default=60.0)
     ap.add_argument("--served-chunk", type=int, default=250)
     ap.add_argument("--served-slots", type=int, default=64)

@@ -450,6 +450,31 @@ SNN_API snn_status snn_batch_set_graph(snn_batch* b, int32_t enable);
  * SNN_EINVAL (NULL batch, unknown mode). */
 enum { SNN_BATCH_GROUPS = 0, SNN_BATCH_GLOBAL = 1 };
 SNN_API snn_status snn_batch_set_mode(snn_batch* b, int32_t mode);
+/* Launch shape of the waves laid out globally: 0 (default) two CTAs per SM
+ * with four delivery tasks in flight per warp, 1 one CTA per SM with six.
+ * Regroups the waves (synchronises the device).  Errors: SNN_EINVAL. */
+SNN_API snn_status snn_batch_set_shape(snn_batch* b, int32_t shape);
+/* Layout, launch shape and ring budget in one regrouping (as snn_batch_set_mode,
+ * snn_batch_set_shape and snn_batch_set_ring_budget together).  Errors:
+ * SNN_EINVAL. */
+SNN_API snn_status snn_batch_set_layout(snn_batch* b, int32_t mode, int32_t shape, uint64_t ring_budget);
+/* Autotuner of the batch (no counterpart in the paper): times every
+ * combination of layout (SNN_BATCH_GROUPS, SNN_BATCH_GLOBAL), launch shape (0,
+ * 1) and ring budget (0.35, 0.5, 0.65 of the L2) that gives a distinct wave
+ * plan, on trial_steps steps of every network from one snapshot of all their
+ * states (restored after each trial, so tuning changes no result), and keeps
+ * the fastest.  With cache_path != NULL the choice is looked up first and
+ * appended after tuning, keyed by the GPU, the networks' shapes and
+ * trial_steps.  Outputs (may be NULL): the chosen layout, shape and budget,
+ * the measured ms per step (-1 on a cache hit), and trial_ms[12], the ms per
+ * step of every candidate in the order layout x shape x budget (-1 where a
+ * candidate repeated an earlier wave plan, or on a cache hit).  Synchronises
+ * `stream`.  Errors: SNN_EINVAL (NULL batch, trial_steps = 0, a network with
+ * stdp). */
+enum { SNN_BATCH_TUNE_CANDIDATES = 12 };
+SNN_API snn_status snn_batch_autotune(snn_batch* b, uint32_t trial_steps, const char* cache_path, int32_t* mode,
+                                      int32_t* shape, uint64_t* ring_budget, double* best_ms_per_step,
+                                      double* trial_ms, void* stream);
 /* cta (host array of n): the CTAs each network's group had in the last
  * snn_batch_step (0: idle, alone in its wave, or in a global wave). */
 SNN_API snn_status snn_batch_groups(snn_batch* b, uint32_t* cta);
@@ -498,6 +523,10 @@ SNN_API snn_status snn_server_create(uint64_t budget_bytes, uint32_t chunk_steps
                                      snn_server** out);
 SNN_API snn_status snn_server_submit(snn_server* s, const snn_config* cfg, uint32_t n_steps, uint64_t arrival_ns,
                                      uint64_t* request_id);
+/* Layout of every tick's batch (snn_batch_set_layout; e.g. the choice of
+ * snn_batch_autotune on a sample of the request mix); ring_budget 0 keeps the
+ * batch's default.  Errors: SNN_EINVAL. */
+SNN_API snn_status snn_server_set_batch(snn_server* s, int32_t mode, int32_t shape, uint64_t ring_budget);
 SNN_API snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued);
 SNN_API snn_status snn_server_poll(snn_server* s, snn_request_result* out, uint32_t cap, uint32_t* n_out);
 SNN_API snn_status snn_server_stats(snn_server* s, snn_server_stats_t* out);

@@ -14,10 +14,20 @@
 
 namespace snn {
 
-#ifndef SNN_BATCH_MIN_BLOCKS
-#define SNN_BATCH_MIN_BLOCKS 2  // two CTAs per SM: many small networks need more warps than deep unrolling
-#endif
-constexpr int BATCH_UNROLL = 4;  // delivery tasks in flight per warp
+// Launch shapes of the global layout (snn_batch_set_shape): shape 0 runs two
+// CTAs per SM with four delivery tasks in flight per warp (many small
+// networks need more warps than deep unrolling), shape 1 one CTA per SM with
+// six (the single-network persistent kernel's shape).
+template <int SHAPE>
+struct BatchShape;
+template <>
+struct BatchShape<0> {
+    static constexpr int MIN_BLOCKS = 2, UNROLL = 4;
+};
+template <>
+struct BatchShape<1> {
+    static constexpr int MIN_BLOCKS = 1, UNROLL = 6;
+};
 
 // Neuron id of spike jl of network k: the (network, warp) segment by binary
 // search over the network's part of the segment prefix, then the warp's
@@ -52,7 +62,10 @@ __device__ __forceinline__ uint32_t upper_slot(const uint32_t* pre, uint32_t n, 
     return lo;
 }
 
-__global__ void __launch_bounds__(PERSIST_THREADS, SNN_BATCH_MIN_BLOCKS) k_run_batch(BatchMeta bm, uint32_t n_steps) {
+template <int SHAPE>
+__global__ void __launch_bounds__(PERSIST_THREADS, BatchShape<SHAPE>::MIN_BLOCKS)
+    k_run_batch(BatchMeta bm, uint32_t n_steps) {
+    constexpr int BATCH_UNROLL = BatchShape<SHAPE>::UNROLL;  // delivery tasks in flight per warp
     extern __shared__ __align__(16) uint32_t smem[];
     const uint32_t n = bm.n, NW = bm.n_seg;
     const uint32_t G = gridDim.x, TW = G * PERSIST_WARPS;
@@ -228,38 +241,40 @@ static size_t batch_smem(uint32_t n, uint32_t n_seg) {
     return (size_t)n * 16 + (size_t)(4 * (n + 1) + 2 * n + n_seg + 1 + PERSIST_THREADS) * sizeof(uint32_t);
 }
 
-int batch_grid(uint32_t n, uint32_t n_seg_bound) {
+static const void* batch_fn(int shape) {
+    return shape == 1 ? (const void*)k_run_batch<1> : (const void*)k_run_batch<0>;
+}
+
+int batch_grid(uint32_t n, uint32_t n_seg_bound, int shape) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = batch_smem(n, n_seg_bound);
+    const void* fn = batch_fn(shape);
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void*)k_run_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     int fit = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, (const void*)k_run_batch, PERSIST_THREADS, smem) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, PERSIST_THREADS, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return fit * sms;
 }
 
-cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, cudaStream_t s) {
+cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, int shape, cudaStream_t s) {
     const size_t smem = batch_smem(bm.n, bm.n_seg);
+    const void* fn = batch_fn(shape);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)k_run_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     BatchMeta m = bm;
     uint32_t ns = n_steps;
     void* args[] = {&m, &ns};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_run_batch, dim3(grid), dim3(PERSIST_THREADS), args,
-                                                smem, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(PERSIST_THREADS), args, smem, s);
     count_launch(1);
     return e;
 }

@@ -65,6 +65,8 @@ snn_status sfail(snn_status s, const std::string& m) {
 struct snn_server {
     uint64_t budget = 0, used = 0;
     uint32_t chunk = 0, max_slots = 0;
+    int32_t batch_mode = SNN_BATCH_GROUPS, batch_shape = 0;  // layout of every tick's batch
+    uint64_t batch_budget = 0;                                // its ring budget (0: the batch's default)
     snn_alloc_fn alloc_fn = nullptr;
     snn_free_fn free_fn = nullptr;
     void* alloc_ctx = nullptr;
@@ -131,6 +133,16 @@ snn_status snn_server_create(uint64_t budget_bytes, uint32_t chunk_steps, uint32
         return sfail(SNN_ECUDA, "cudaStreamCreateWithFlags failed");
     }
     *out = s;
+    return SNN_OK;
+}
+
+snn_status snn_server_set_batch(snn_server* s, int32_t mode, int32_t shape, uint64_t ring_budget) {
+    if (!s) return sfail(SNN_EINVAL, "server is NULL");
+    if ((mode != SNN_BATCH_GROUPS && mode != SNN_BATCH_GLOBAL) || (shape != 0 && shape != 1))
+        return sfail(SNN_EINVAL, "unknown batch layout or shape");
+    s->batch_mode = mode;
+    s->batch_shape = shape;
+    s->batch_budget = ring_budget;
     return SNN_OK;
 }
 
@@ -229,7 +241,15 @@ snn_status snn_server_tick(snn_server* s, uint32_t* n_active, uint32_t* n_queued
         snn_batch* b = nullptr;
         snn_status e = snn_batch_create(nets.data(), (uint32_t)nets.size(), s->alloc_fn, s->free_fn, s->alloc_ctx, &b);
         if (e != SNN_OK) return e;
-        e = snn_batch_step(b, steps.data(), s->stream);
+        // a non-default layout regroups the waves once (set_mode and set_shape
+        // each regroup; the budget call regroups for both)
+        if (s->batch_mode != SNN_BATCH_GROUPS || s->batch_shape != 0 || s->batch_budget) {
+            uint64_t bud = 0;
+            uint32_t waves = 0;
+            snn_batch_waves(b, &waves, &bud);
+            e = snn_batch_set_layout(b, s->batch_mode, s->batch_shape, s->batch_budget ? s->batch_budget : bud);
+        }
+        if (e == SNN_OK) e = snn_batch_step(b, steps.data(), s->stream);
         // while the batch runs: retire the networks that finished in the previous tick
         for (auto& a : s->finished) retire(s, a);
         s->finished.clear();

@@ -1412,6 +1412,7 @@ struct BatchWave {
     GroupMeta gmeta{};
     uint32_t first = 0, count = 0;
     int grid = 0;
+    int shape = 0;  // global waves: launch shape of k_run_batch
     bool grouped = false;
     uint32_t stage_off = 0;  // grouped: offset of the wave's CTA prefix in the staging words
 };
@@ -1433,6 +1434,7 @@ struct snn_batch {
     std::vector<double> work;   // per network: estimated CTA-microseconds of one step
     std::vector<uint32_t> last_cta, last_steps;  // CTAs and steps of each network's group in the last call
     int32_t mode = SNN_BATCH_GROUPS;
+    int32_t shape = 0;  // launch shape of global waves (batch_kernels.cu)
     int ggrid = 0;  // grouped kernel's grid
     uint64_t ring_budget = 0;
     bool use_graph = false;
@@ -1564,7 +1566,7 @@ snn_status build_wave(snn_batch* b, uint32_t first, uint32_t count, BatchWave* w
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = batch_grid(count, (uint32_t)(8 * PERSIST_WARPS * sms) + count);
+    const int grid = batch_grid(count, (uint32_t)(8 * PERSIST_WARPS * sms) + count, b->shape);
     if (grid <= 0) return fail(SNN_EINVAL, "the batch kernel does not fit on this device (%u networks)", count);
     // global quad offsets; first and last warp overlapping each network
     const uint64_t TW = (uint64_t)grid * PERSIST_WARPS;
@@ -1625,6 +1627,7 @@ snn_status build_wave(snn_batch* b, uint32_t first, uint32_t count, BatchWave* w
     w->first = first;
     w->count = count;
     w->grid = grid;
+    w->shape = b->shape;
     return SNN_OK;
 }
 
@@ -1702,6 +1705,174 @@ snn_status snn_batch_set_ring_budget(snn_batch* b, uint64_t bytes) {
     }
     b->stage_len = stage;
     return SNN_OK;
+}
+
+// Autotuner of a batch: every (layout, launch shape, ring budget) candidate is
+// timed on `trial_steps` steps of every network from one snapshot of all of
+// their states (a first call refines the grouped layout's cost model, the
+// second is timed), the states are restored after each, and the fastest is
+// kept.  Candidates that give the same wave plan as an earlier one are not
+// run again.  The choice is cached in a text file keyed by the GPU and the
+// networks' shapes.
+snn_status snn_batch_autotune(snn_batch* b, uint32_t trial_steps, const char* cache_path, int32_t* mode_out,
+                              int32_t* shape_out, uint64_t* budget_out, double* best_ms, double* trial_ms,
+                              void* stream) {
+    if (trial_ms)
+        for (int k = 0; k < SNN_BATCH_TUNE_CANDIDATES; ++k) trial_ms[k] = -1.0;
+    if (!b || trial_steps == 0) return fail(SNN_EINVAL, "batch is NULL or trial_steps is 0");
+    NvtxRange range("snn_batch_autotune");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint32_t n = (uint32_t)b->nets.size();
+    for (snn_net* net : b->nets)
+        if (net->stdp) return fail(SNN_EINVAL, "a network of the batch has stdp");
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, dev);
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the networks' shapes
+    auto mix = [&](uint64_t x) {
+        for (int k = 0; k < 8; ++k) {
+            h ^= (x >> (8 * k)) & 0xFF;
+            h *= 1099511628211ull;
+        }
+    };
+    for (snn_net* net : b->nets) {
+        mix(net->N);
+        mix(net->K);
+        mix(net->D);
+        mix((uint64_t)net->v.w_bf16 | (uint64_t)net->cfg.conn_rule << 8 | (uint64_t)net->v.n_bands << 16);
+        mix((uint64_t)std::llround(net->cfg.imposed_rate_hz * 1000.0));
+    }
+    char key[320];
+    std::string gpu(prop.name);
+    for (char& ch : gpu)
+        if (ch == ' ') ch = '_';
+    snprintf(key, sizeof key, "batch:%s:%u:%016llx:%u", gpu.c_str(), n, (unsigned long long)h, trial_steps);
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "r")) {
+            char k2[320];
+            int m = 0, sh = 0;
+            unsigned long long bud = 0;
+            bool hit = false;
+            while (fscanf(f, "%319s %d %d %llu", k2, &m, &sh, &bud) == 4)
+                if (strcmp(k2, key) == 0) hit = true, b->mode = m, b->shape = sh, b->ring_budget = bud;
+            fclose(f);
+            if (hit) {
+                snn_status st = snn_batch_set_ring_budget(b, b->ring_budget);
+                if (st != SNN_OK) return st;
+                if (mode_out) *mode_out = b->mode;
+                if (shape_out) *shape_out = b->shape;
+                if (budget_out) *budget_out = b->ring_budget;
+                if (best_ms) *best_ms = -1.0;
+                return SNN_OK;
+            }
+        }
+    }
+    // one snapshot of every network, restored after every trial; the trials
+    // record no spikes (each raster counter parked at its capacity) and the
+    // recorded rasters are kept
+    std::vector<std::vector<char>> snap(n);
+    std::vector<uint64_t> rcount(n);
+    for (uint32_t i = 0; i < n; ++i) {
+        size_t bytes = 0;
+        snn_status st = snn_snapshot(b->nets[i], nullptr, 0, &bytes, stream);
+        if (st != SNN_OK) return st;
+        snap[i].resize(bytes);
+        st = snn_snapshot(b->nets[i], snap[i].data(), bytes, &bytes, stream);
+        if (st != SNN_OK) return st;
+        DevState ds;
+        std::memcpy(&ds, snap[i].data() + sizeof(SnapshotHeader), sizeof ds);
+        rcount[i] = ds.raster_count;
+    }
+    auto restore = [&](bool last) -> snn_status {
+        for (uint32_t i = 0; i < n; ++i) {
+            snn_status st = snn_restore(b->nets[i], snap[i].data(), snap[i].size(), stream);
+            if (st != SNN_OK) return st;
+            CUDA_TRY(snn_set_raster_count(b->nets[i], last ? rcount[i] : b->nets[i]->v.raster_cap, s));
+        }
+        return SNN_OK;
+    };
+    if (snn_status st0 = restore(false); st0 != SNN_OK) return st0;
+    const int32_t mode0 = b->mode, shape0 = b->shape;
+    const uint64_t budget0 = b->ring_budget;
+    const double fracs[] = {0.35, 0.5, 0.65};
+    std::vector<uint32_t> warm(n, std::max(trial_steps / 4, 1u)), trial(n, trial_steps);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best = 1e300;
+    int32_t bm = mode0, bs = shape0;
+    uint64_t bb = budget0;
+    std::vector<std::vector<uint64_t>> seen;
+    snn_status st = SNN_OK;
+    int cand = -1;
+    for (int32_t m : {SNN_BATCH_GROUPS, SNN_BATCH_GLOBAL}) {
+        for (int32_t sh : {0, 1}) {
+            for (double fr : fracs) {
+                ++cand;
+                const uint64_t bud = l2 > 0 ? (uint64_t)(fr * l2) : (64ull << 20);
+                b->mode = m;
+                b->shape = sh;
+                st = snn_batch_set_ring_budget(b, bud);
+                if (st != SNN_OK) break;
+                std::vector<uint64_t> plan;  // the waves (first, count, layout, shape) this candidate gives
+                for (const BatchWave& w : b->waves)
+                    plan.push_back((uint64_t)w.first | (uint64_t)w.count << 24 | (uint64_t)w.grouped << 48 |
+                                   (uint64_t)(w.grouped ? 0 : w.shape) << 49);
+                if (std::find(seen.begin(), seen.end(), plan) != seen.end()) continue;
+                seen.push_back(plan);
+                if ((st = snn_batch_step(b, warm.data(), stream)) != SNN_OK || (st = restore(false)) != SNN_OK) break;
+                CUDA_TRY(cudaStreamSynchronize(s));
+                CUDA_TRY(cudaEventRecord(e0, s));
+                if ((st = snn_batch_step(b, trial.data(), stream)) != SNN_OK) break;
+                CUDA_TRY(cudaEventRecord(e1, s));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if ((st = restore(false)) != SNN_OK) break;
+                if (trial_ms) trial_ms[cand] = ms / trial_steps;
+                if (ms < best) best = ms, bm = m, bs = sh, bb = bud;
+            }
+            if (st != SNN_OK) break;
+        }
+        if (st != SNN_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (snn_status st1 = restore(true); st == SNN_OK) st = st1;  // the rasters as they were
+    if (st != SNN_OK) return st;
+    b->mode = bm;
+    b->shape = bs;
+    st = snn_batch_set_ring_budget(b, bb);
+    if (st != SNN_OK) return st;
+    if (cache_path) {
+        if (FILE* f = fopen(cache_path, "a")) {
+            fprintf(f, "%s %d %d %llu\n", key, (int)bm, (int)bs, (unsigned long long)bb);
+            fclose(f);
+        }
+    }
+    if (mode_out) *mode_out = bm;
+    if (shape_out) *shape_out = bs;
+    if (budget_out) *budget_out = bb;
+    if (best_ms) *best_ms = best / trial_steps;
+    return SNN_OK;
+}
+
+snn_status snn_batch_set_layout(snn_batch* b, int32_t mode, int32_t shape, uint64_t ring_budget) {
+    if (!b || ring_budget == 0) return fail(SNN_EINVAL, "batch is NULL or the budget is 0");
+    if (mode != SNN_BATCH_GLOBAL && mode != SNN_BATCH_GROUPS) return fail(SNN_EINVAL, "unknown batch mode %d", (int)mode);
+    if (shape != 0 && shape != 1) return fail(SNN_EINVAL, "unknown batch shape %d", (int)shape);
+    b->mode = mode;
+    b->shape = shape;
+    return snn_batch_set_ring_budget(b, ring_budget);
+}
+
+snn_status snn_batch_set_shape(snn_batch* b, int32_t shape) {
+    if (!b) return fail(SNN_EINVAL, "batch is NULL");
+    if (shape != 0 && shape != 1) return fail(SNN_EINVAL, "unknown batch shape %d", (int)shape);
+    b->shape = shape;
+    return snn_batch_set_ring_budget(b, b->ring_budget);
 }
 
 snn_status snn_batch_set_mode(snn_batch* b, int32_t mode) {
@@ -1789,7 +1960,7 @@ snn_status snn_batch_step(snn_batch* b, const uint32_t* steps, void* stream) {
                 if (e == cudaSuccess) e = launch_groups(w.gmeta, w.grid, q);
             } else {
                 e = cudaMemsetAsync(&w.meta.bst->bar_count, 0, sizeof(uint32_t), q);
-                if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, q);
+                if (e == cudaSuccess) e = launch_batch(w.meta, key[k], w.grid, w.shape, q);
             }
             if (e != cudaSuccess) return e;
         }

@@ -241,8 +241,8 @@ struct BatchMeta {
     uint32_t barrier_extra;
     uint32_t n, n_seg, Qtot;
 };
-int batch_grid(uint32_t n, uint32_t n_seg_bound);
-cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, cudaStream_t s);
+int batch_grid(uint32_t n, uint32_t n_seg_bound, int shape);
+cudaError_t launch_batch(const BatchMeta& bm, uint32_t n_steps, int grid, int shape, cudaStream_t s);
 // Grouped batched execution: network k on its own CTAs [gcta[k], gcta[k+1]).
 struct GroupMeta {
     const NetView* views;   // n

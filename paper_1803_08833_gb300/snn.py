@@ -119,6 +119,11 @@ def load():
         "snn_get_dims": (st, [vp, P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32),
                               P(ctypes.c_uint64)]),
         "snn_set_schedule": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "snn_batch_set_shape": (st, [vp, ctypes.c_int32]),
+        "snn_batch_set_layout": (st, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64]),
+        "snn_server_set_batch": (st, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64]),
+        "snn_batch_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
+                                    P(ctypes.c_uint64), P(ctypes.c_double), P(ctypes.c_double), vp]),
         "snn_get_stdp": (st, [vp, vp, vp, vp, vp]),
         "snn_shard_build": (st, [P(SnnConfig), ctypes.c_uint32, ctypes.c_uint32, ALLOC_FN, FREE_FN, vp, vp, P(vp)]),
         "snn_shard_info": (st, [vp, P(ShardInfo)]),
@@ -486,6 +491,24 @@ class Batch:
     def set_ring_budget(self, nbytes: int):
         check(load().snn_batch_set_ring_budget(self._h, int(nbytes)))
 
+    def set_shape(self, shape: int):
+        check(load().snn_batch_set_shape(self._h, int(shape)))
+
+    def autotune(self, trial_steps: int = 100, cache_path=None):
+        """Times every (layout, launch shape, ring budget) candidate and keeps
+        the fastest; returns {mode, shape, ring_budget, ms_per_step}."""
+        m, sh, bud, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_double()
+        trials = (ctypes.c_double * 12)()
+        cp = cache_path.encode() if cache_path else None
+        check(load().snn_batch_autotune(self._h, int(trial_steps), cp, ctypes.byref(m), ctypes.byref(sh),
+                                        ctypes.byref(bud), ctypes.byref(ms), trials, self._s))
+        sweep = {}
+        for k, t in enumerate(trials):
+            if t >= 0:
+                sweep["%s/shape%d/%.2fL2" % (("groups", "global")[k // 6], (k // 3) % 2, (0.35, 0.5, 0.65)[k % 3])] = t
+        return {"mode": "global" if m.value == 1 else "groups", "shape": sh.value, "ring_budget": bud.value,
+                "ms_per_step": ms.value, "sweep_ms_per_step": sweep}
+
     def set_mode(self, mode: str):
         """'groups' (default: every network of a wave on CTAs of its own) or
         'global' (one neuron and task space for the whole wave)."""
@@ -700,6 +723,10 @@ class Server:
         check(load().snn_server_create(int(budget_bytes), int(chunk_steps), int(max_slots), self._alloc.alloc,
                                        self._alloc.free, None, self._s, ctypes.byref(h)))
         self._h = h
+
+    def set_batch(self, mode: str = "groups", shape: int = 0, ring_budget: int = 0):
+        """Layout of every tick's batch (e.g. a batch tuner's choice)."""
+        check(load().snn_server_set_batch(self._h, 1 if mode == "global" else 0, int(shape), int(ring_budget)))
 
     def submit(self, cfg: dict, steps: int, arrival_ns: int = 0, raster_capacity: int = 1 << 16) -> int:
         c = config(cfg, raster_capacity)

@@ -205,3 +205,49 @@ def test_grouped_batch_of_both_laws_and_weight_types(snn):
     for net, ref in zip(nets, refs):
         _check(net, ref)
         net.close()
+
+
+@pytest.mark.parametrize("shape", [0, 1])
+def test_global_layout_launch_shapes_equal_the_oracle(snn, shape):
+    """Both launch shapes of the global layout (2 CTAs per SM x 4 tasks in
+    flight, 1 CTA per SM x 6) give the oracle's results."""
+    cfgs = _cases()
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    with snn.Batch(nets) as batch:
+        batch.set_mode("global")
+        batch.set_shape(shape)
+        batch.set_graph(True)
+        for steps in ([40, 40, 40, 40, 40, 40], [7, 0, 19, 3, 11, 5]):
+            batch.step(steps)
+            for r, n in zip(refs, steps):
+                r.step(n)
+    for net, ref in zip(nets, refs):
+        _check(net, ref)
+        net.close()
+
+
+def test_autotuned_batch_changes_no_result(snn, tmp_path):
+    """The tuner runs every candidate layout, shape and ring budget from one
+    snapshot and restores it: afterwards the batch continues exactly as the
+    oracle does; a second call finds the choice in the cache."""
+    cfgs = _cases()
+    nets = [snn.Network(c, raster_capacity=1 << 20) for c in cfgs]
+    refs = [oracle.OracleNet(c) for c in cfgs]
+    cache = str(tmp_path / "tune.txt")
+    with snn.Batch(nets) as batch:
+        batch.step([15] * len(nets))
+        for r in refs:
+            r.step(15)
+        got = batch.autotune(trial_steps=20, cache_path=cache)
+        assert got["mode"] in ("groups", "global") and got["shape"] in (0, 1) and got["ms_per_step"] > 0
+        again = batch.autotune(trial_steps=20, cache_path=cache)
+        assert again["ms_per_step"] == -1.0 and (again["mode"], again["shape"], again["ring_budget"]) == \
+            (got["mode"], got["shape"], got["ring_budget"])
+        batch.set_graph(True)
+        batch.step([30, 10, 30, 0, 30, 25])
+        for r, n in zip(refs, [30, 10, 30, 0, 30, 25]):
+            r.step(n)
+    for net, ref in zip(nets, refs):
+        _check(net, ref)
+        net.close()

@@ -108,3 +108,26 @@ def test_pairwise_requests_in_the_mix(snn):
     assert mixed[0]["n_spikes"] == len(st) and mixed[0]["rec_events"] == ref.stats()["rec_events"]
     assert mixed[0]["raster_hash"] == _fnv([st, ids])
     assert mixed[0]["state_hash"] == _fnv([ref.state()["V"]])
+
+
+def test_server_batch_layout_changes_no_result(snn):
+    """Every tick's batch in the global layout, launch shape 1, a small ring
+    budget: each request's result equals the default layout's."""
+    import paper_1803_08833_gb300.workloads as W
+    reqs = [(W.small(grid=2, M=120, K=77, seed=5, imposed_rate_hz=30.0), 90),
+            (W.small(grid=3, M=80, K=150, lateral="exp", seed=6, imposed_rate_hz=35.0), 140),
+            (W.small(grid=2, M=64, K=30, seed=7, imposed_rate_hz=20.0), 60)]
+    out = []
+    for layout in (None, ("global", 1, 1 << 20)):
+        with snn.Server(1 << 32, chunk_steps=25, max_slots=8) as srv:
+            if layout:
+                srv.set_batch(*layout)
+            for cfg, steps in reqs:
+                srv.submit(cfg, steps, raster_capacity=1 << 16)
+            res = []
+            while len(res) < len(reqs):
+                srv.tick()
+                res += srv.poll()
+            out.append(sorted((r["request_id"], r["raster_hash"], r["state_hash"], r["n_spikes"]) for r in res))
+    assert out[0] == out[1]
+    assert all(r[3] > 0 for r in out[0])
