@@ -51,9 +51,9 @@ ALG_NEURON_BYTES = 26
 BYTES_PER_EVENT = {"f32": 8, "bf16": 6}
 # neuron update, schedule 2: the ring slot read and cleared; V, c (f32) and ref
 # (u8) stay in shared memory for the whole launch (read and written back once
-# per launch).  Schedule 4: the state is read and written every step (18 B) and
-# the ring row entering the delay window is read and cleared (8 B).
-NEURON_BYTES = {2: 2 * 4, 3: 2 * 4 + 18, 4: 18 + 8}
+# per launch).  Schedules 4 and 5: the state is read and written every step (18 B)
+# and one ring row is read and cleared (8 B).
+NEURON_BYTES = {2: 2 * 4, 3: 2 * 4 + 18, 4: 18 + 8, 5: 18 + 8}
 # random 4-byte red.global.add.s32 into an L2-resident buffer (4-60 MB), measured on
 # GB300 by `bench.py --calibrate`: the rate that bounds the push delivery, one
 # reduction per recurrent synaptic event
@@ -329,7 +329,7 @@ def run_gpu(args):
     _barrier(dist)
     torch.cuda.set_device(local)
     schedule = 2 if args.schedule is None else args.schedule
-    cfg = workload(seed=1 + rank, grid=args.grid, K=args.K, layout="grouped" if schedule == 3 else "draw")
+    cfg = workload(seed=1 + rank, grid=args.grid, K=args.K, layout="grouped" if schedule in (3, 5) else "draw")
     T = args.timesteps
     peak, peak_kind = _peaks()
     stream = torch.cuda.current_stream()
@@ -393,7 +393,7 @@ def run_gpu(args):
     traffic = None
     packed = None
     if pl > 0:  # persistent schedule: one launch = T steps of neuron update + delivery
-        kname = {3: "k_run_steps_tiled", 4: "k_run_steps_owned"}.get(schedule, "k_run_steps")
+        kname = {3: "k_run_steps_tiled", 4: "k_run_steps_owned", 5: "k_run_steps_pull"}.get(schedule, "k_run_steps")
         kernel = "%s<f32> (persistent: neuron update + delivery, %d steps per launch)" % (kname, T)
         launches_timed = pl
         launch_s = pms / pl / 1000.0

@@ -286,6 +286,17 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  *      bounded like those of schedule 2.  Errors: SNN_EINVAL if no window
  *      row fits in shared memory, SNN_ENOMEM for the queues (G x G x cap x
  *      8 bytes, G = SMs).
+ *   5: as 4 (bands of ceil(N / SMs) neurons, a delay window of W steps per
+ *      band in shared memory, snn_set_pull_window), but pulled: after the
+ *      neuron phase every CTA reads, from the row of each spike whose source
+ *      module's stencil reaches its band, the one contiguous range of
+ *      synapses that targets the band's modules (the rows are grouped by
+ *      target module), adds the events of delay <= W into its window with
+ *      shared-memory atomics and those of longer delay into the ring with L2
+ *      reductions.  One grid barrier per step.  Needs table_layout =
+ *      SNN_LAYOUT_GROUPED with K <= 8188 synapses per row.  Errors:
+ *      SNN_EINVAL (no grouped rows, K too large, or no window row fits in
+ *      shared memory), SNN_ENOMEM.
  * All schedules give bit-identical results.  block: threads per block of the
  * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
@@ -302,6 +313,15 @@ SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t bloc
  * 2^20), SNN_ENOMEM. */
 SNN_API snn_status snn_set_window(snn_net* net, uint32_t window, uint32_t queue_cap, uint32_t* window_out,
                                   uint32_t* cap_out, void* stream);
+
+/* Delay window of schedule 5 (no counterpart in the paper; the window holds
+ * the band's part of the delay queues of flow step 3, Sec. II-A): window =
+ * steps each band keeps in shared memory (0 = the most that fit, at most
+ * D - 1); events of a longer delay go through the ring in global memory, so
+ * any window gives the same results.  *window_out (may be NULL) receives the
+ * window in use.  Synchronises `stream`.  Errors: SNN_EINVAL (layout not
+ * grouped, window too large), SNN_ENOMEM. */
+SNN_API snn_status snn_set_pull_window(snn_net* net, uint32_t window, uint32_t* window_out, void* stream);
 
 /* Banded delivery of schedule 2 (no counterpart in the paper, whose processes
  * each own a tile of the grid): the target module rows are split into `bands`

@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libsnn.so")
 # indexed writes, which set an error bit instead of writing out of bounds
 LIB_CHECK = os.path.join(PKG, "libsnn_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["snn_api.cu", "build_kernels.cu", "step_kernels.cu", "persistent_kernels.cu", "persistent_tiled.cu", "persistent_owned.cu", "shard_kernels.cu", "stdp_kernels.cu", "cdf_static.cu", "server.cu", "autotune.cu", "batch_kernels.cu"]
+SOURCES = ["snn_api.cu", "build_kernels.cu", "step_kernels.cu", "persistent_kernels.cu", "persistent_tiled.cu", "persistent_owned.cu", "persistent_pull.cu", "shard_kernels.cu", "stdp_kernels.cu", "cdf_static.cu", "server.cu", "autotune.cu", "batch_kernels.cu"]
 
 
 def nvcc() -> str:

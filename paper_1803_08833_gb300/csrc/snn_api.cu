@@ -84,6 +84,8 @@ struct snn_net {
     int pgrid = 0;      // persistent grid (schedule 2)
     int tgrid = 0;      // tiled persistent grid (schedule 3), 0 if unavailable
     int ogrid = 0;      // owner-windowed persistent grid (schedule 4), 0 until set up
+    int plgrid = 0;     // pulled windowed persistent grid (schedule 5), 0 until set up
+    size_t pull_runs_bytes = 0;
     bool stdp = false;        // spike-timing dependent plasticity (schedules 0 and 1)
     StdpView sp{};
     int2* own_rec = nullptr;  // schedule 4 record queues and their size
@@ -491,6 +493,73 @@ snn_status owned_setup(snn_net* n, uint32_t window, uint32_t queue_cap) {
     v.own_cap = cap;
     v.own_magic = magic;
     n->ogrid = G;
+    return SNN_OK;
+}
+
+// Pulled windowed delivery (schedule 5): bands of ceil(Q / G) quads, one per
+// CTA of a grid of one CTA per SM, each with its table of runs (source module,
+// stencil entries of the band's target modules); a window of `window` steps
+// (0 = the largest that fits in shared memory, at most D - 1).  Needs the
+// grouped layout (rows ordered by target module) with K synapses per row.
+snn_status pull_setup(snn_net* n, uint32_t window) {
+    NetView& v = n->v;
+    if (n->cfg.table_layout != SNN_LAYOUT_GROUPED || v.row_len || !v.segidx)
+        return fail(SNN_EINVAL, "schedule 5 needs a network built with table_layout = SNN_LAYOUT_GROUPED and K "
+                                "synapses per row");
+    if (n->K > pull_k_max()) return fail(SNN_EINVAL, "schedule 5: K = %u exceeds %u", n->K, pull_k_max());
+    const int G = owned_grid();
+    if (G <= 0) return fail(SNN_ECUDA, "schedule 5: no multiprocessor count");
+    const uint32_t Q = n->Npad / 4;
+    const uint32_t BQ = (Q + (uint32_t)G - 1) / (uint32_t)G;
+    uint32_t R2 = 0;
+    const std::vector<int16_t> off = disc_offsets(n->cfg, &R2);
+    std::vector<uint2> runs;
+    std::vector<uint32_t> ptr;
+    const uint32_t R_max = pull_build_runs(n->N, n->M, n->cfg.grid_w, n->cfg.grid_h, off, (uint32_t)G, BQ, Q, runs, ptr);
+    for (const uint2& r : runs)  // the kernel's reads of the segment index stay in the row
+        if ((r.y & 0xFFFFu) >= (r.y >> 16) || (r.y >> 16) > n->max_off || r.x >= n->n_modules)
+            return fail(SNN_EINVAL, "schedule 5: run table entry out of range");
+    const uint32_t Wmax = pull_max_window(v, G, BQ, R_max);
+    if (Wmax == 0)
+        return fail(SNN_EINVAL, "schedule 5: a delay window row of %u neurons per CTA does not fit in shared memory",
+                    BQ * 4);
+    const uint32_t W = window == 0 ? Wmax : window;
+    if (W > Wmax) return fail(SNN_EINVAL, "schedule 5: window %u exceeds the %u steps that fit (D - 1 = %u)", W, Wmax,
+                              v.D - 1);
+    cudaStream_t s = 0;
+    if (n->plgrid != G || !v.pull_seg) {
+        const size_t warps = (size_t)G * pull_warps();
+        struct Req {
+            void** p;
+            size_t bytes;
+        } reqs[] = {
+            {(void**)&v.pull_seg, (size_t)n->Npad * 2 * 4},
+            {(void**)&v.pull_segmod, (size_t)n->Npad * 2 * 4},
+            {(void**)&v.pull_mcnt, (size_t)n->n_modules * 3 * 4},
+            {(void**)&v.pull_woff, warps * 2 * 4},
+            {(void**)&v.pull_run_ptr, (size_t)(G + 1) * 4},
+        };
+        for (auto& r : reqs) {
+            *r.p = dev_alloc(n, r.bytes);
+            if (!*r.p) return fail(SNN_ENOMEM, "schedule 5: device allocation of %zu bytes failed", r.bytes);
+        }
+        CUDA_TRY(cudaMemsetAsync(v.pull_seg, 0, (size_t)n->Npad * 2 * 4, s));
+        CUDA_TRY(cudaMemsetAsync(v.pull_segmod, 0, (size_t)n->Npad * 2 * 4, s));
+    }
+    if (v.pull_runs) free_block(n, (void*)v.pull_runs, n->pull_runs_bytes);
+    v.pull_runs = nullptr;
+    n->pull_runs_bytes = std::max<size_t>(runs.size(), 1) * sizeof(uint2);
+    uint2* druns = (uint2*)dev_alloc(n, n->pull_runs_bytes);
+    if (!druns) return fail(SNN_ENOMEM, "schedule 5: device allocation of the run table failed");
+    if (!runs.empty())
+        CUDA_TRY(cudaMemcpyAsync(druns, runs.data(), runs.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((void*)v.pull_run_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
+    v.pull_runs = druns;
+    v.pull_W = W;
+    v.pull_BQ = BQ;
+    v.pull_R_max = R_max;
+    n->plgrid = G;
     return SNN_OK;
 }
 
@@ -983,12 +1052,16 @@ snn_status snn_step(snn_net* n, uint32_t n_steps, void* stream) {
                 snn_status st = timed_begin(n->ev_persist, s, &slot);
                 if (st != SNN_OK) return st;
             }
-            NvtxRange lr(n->schedule == 3 ? "persistent: target tiles" : n->schedule == 4 ? "persistent: owned windows"
-                                                                                  : "persistent: neuron + delivery phases");
+            NvtxRange lr(n->schedule == 3   ? "persistent: target tiles"
+                         : n->schedule == 4 ? "persistent: owned windows"
+                         : n->schedule == 5 ? "persistent: pulled windows"
+                                            : "persistent: neuron + delivery phases");
             if (n->schedule == 3)
                 CUDA_TRY(launch_tiled(n->v, m, n->tgrid, s));
             else if (n->schedule == 4)
                 CUDA_TRY(launch_owned(n->v, m, n->ogrid, s));
+            else if (n->schedule == 5)
+                CUDA_TRY(launch_pull(n->v, m, n->plgrid, s));
             else
                 CUDA_TRY(launch_persistent(n->v, m, n->pgrid, s));
             if (timed) {
@@ -1311,6 +1384,15 @@ snn_status snn_set_window(snn_net* n, uint32_t window, uint32_t queue_cap, uint3
     return SNN_OK;
 }
 
+snn_status snn_set_pull_window(snn_net* n, uint32_t window, uint32_t* window_out, void* stream) {
+    if (!n) return fail(SNN_EINVAL, "net is NULL");
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight uses the run table
+    snn_status st = pull_setup(n, window);
+    if (st != SNN_OK) return st;
+    if (window_out) *window_out = n->v.pull_W;
+    return SNN_OK;
+}
+
 snn_status snn_set_bands(snn_net* n, uint32_t bands, uint32_t* chosen, void* stream) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight reads the tables
@@ -1328,11 +1410,15 @@ snn_status snn_set_resident_state(snn_net* n, int32_t enable, int32_t* resident,
 
 snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
-    if (schedule < 0 || schedule > 4) return fail(SNN_EINVAL, "schedule must be 0, 1, 2, 3 or 4");
+    if (schedule < 0 || schedule > 5) return fail(SNN_EINVAL, "schedule must be 0, 1, 2, 3, 4 or 5");
     if (n->stdp && schedule >= 2)
         return fail(SNN_EINVAL, "a network with stdp runs the per-step schedules 0 and 1 only");
     if (schedule == 4 && n->ogrid == 0) {
         snn_status st = owned_setup(n, 0, 0);
+        if (st != SNN_OK) return st;
+    }
+    if (schedule == 5 && n->plgrid == 0) {
+        snn_status st = pull_setup(n, 0);
         if (st != SNN_OK) return st;
     }
     if (schedule == 3 && n->cfg.table_layout != SNN_LAYOUT_GROUPED)

@@ -123,6 +123,19 @@ struct NetView {
     int2* own_rec;            // G x G x own_cap records {window index, fixed-point weight}, owner-major
     uint32_t* own_cnt;        // G x G records queued by producer p for owner b at [b G + p]
     uint32_t* own_ovf;        // G flags: a producer's queue for this owner overflowed (events went to the ring)
+    // pulled windowed delivery (schedule 5, grouped layout): CTA b owns the quads
+    // [b BQ, (b + 1) BQ), keeps the input of its band for the next pull_W steps in
+    // shared memory and pulls, from every spiking row, the range of synapses
+    // whose target modules overlap the band
+    uint32_t pull_W;          // window steps (1 <= pull_W <= D - 1)
+    uint32_t pull_BQ;         // quads per band
+    uint32_t pull_R_max;      // most runs of one band
+    const uint2* pull_runs;   // runs of all bands: {source module, stencil entries j0 | j1 << 16}
+    const uint32_t* pull_run_ptr;  // G + 1: runs of band b at [ptr[b], ptr[b + 1])
+    uint32_t* pull_seg;       // 2 x Npad: spikes per warp in id order (by step parity)
+    uint32_t* pull_segmod;    // 2 x Npad: spikes of module m at [m M, m M + count) (by step parity)
+    uint32_t* pull_mcnt;      // 3 x n_modules spike counts (by step mod 3)
+    uint32_t* pull_woff;      // 2 x G x warps per CTA: spikes per warp (by step parity)
 };
 
 // One shard of a spatially decomposed network (Sec. II-D): the neurons
@@ -264,6 +277,13 @@ uint32_t owned_max_window(const NetView& v, int grid, uint32_t BQ);
 int owned_grid();
 size_t owned_smem_bytes(uint32_t W, uint32_t BQ, int grid);
 cudaError_t launch_owned(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
+uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const std::vector<int16_t>& off,
+                         uint32_t G, uint32_t BQ, uint32_t Q, std::vector<uint2>& runs, std::vector<uint32_t>& ptr);
+uint32_t pull_max_window(const NetView& v, int grid, uint32_t BQ, uint32_t R_max);
+size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max);
+uint32_t pull_warps();
+uint32_t pull_k_max();
+cudaError_t launch_pull(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
 // In-disc grid offsets (dx, dy pairs) of the cut-off radius, dx^2 + dy^2 <=
 // R2 = floor((cutoff / spacing)^2), in (dy, dx) raster order (the stencil order

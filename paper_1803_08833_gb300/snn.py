@@ -137,6 +137,7 @@ def load():
         "snn_shard_destroy": (None, [vp]),
         "snn_set_bands": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
         "snn_set_window": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32), vp]),
+        "snn_set_pull_window": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
         "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
                               P(ctypes.c_double), vp]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
@@ -415,6 +416,13 @@ class Network:
         w, c = ctypes.c_uint32(), ctypes.c_uint32()
         check(load().snn_set_window(self._h, int(window), int(queue_cap), ctypes.byref(w), ctypes.byref(c), self._s))
         return w.value, c.value
+
+    def set_pull_window(self, window: int = 0) -> int:
+        """Schedule 5's delay window (steps kept in shared memory per band);
+        0 picks the most that fit.  Returns the window in use."""
+        w = ctypes.c_uint32()
+        check(load().snn_set_pull_window(self._h, int(window), ctypes.byref(w), self._s))
+        return w.value
 
     def set_bands(self, bands: int = 0) -> int:
         """Banded delivery of schedule 2 (0 = automatic); returns the band count in use."""

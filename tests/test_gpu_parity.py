@@ -139,12 +139,12 @@ def _compare(net, ref):
     return len(st)
 
 
-@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("schedule", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name", sorted(SIM_CASES))
 def test_simulation_bit_exact(snn, name, schedule):
     make, steps = SIM_CASES[name]
     cfg = make()
-    if schedule == 3:
+    if schedule in (3, 5):
         cfg["table_layout"] = "grouped"
     with snn.Network(cfg, raster_capacity=1 << 22) as net:
         net.set_schedule(schedule)
@@ -302,7 +302,7 @@ def test_full_size_schedules_agree(snn):
     """The 24x24 Gaussian network run 60 steps with each schedule: identical state."""
     cfg = W.gauss_24x24_k1125(seed=3, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped")
     out = []
-    for schedule in (0, 2, 3, 4):
+    for schedule in (0, 2, 3, 4, 5):
         with snn.Network(cfg, raster_capacity=1 << 20) as net:
             net.set_schedule(schedule)
             net.step(60)
