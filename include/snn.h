@@ -286,8 +286,8 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  *      bounded like those of schedule 2.  Errors: SNN_EINVAL if no window
  *      row fits in shared memory, SNN_ENOMEM for the queues (G x G x cap x
  *      8 bytes, G = SMs).
- *   5: as 4 (bands of ceil(N / SMs) neurons, a delay window of W steps per
- *      band in shared memory, snn_set_pull_window), but pulled: after the
+ *   5: as 4 (one band of neurons per SM, a delay window of W steps per band
+ *      in shared memory, snn_set_pull_window), but pulled: after the
  *      neuron phase every CTA reads, from the row of each spike whose source
  *      module's stencil reaches its band, the one contiguous range of
  *      synapses that targets the band's modules (the rows are grouped by
@@ -314,14 +314,21 @@ SNN_API snn_status snn_set_schedule(snn_net* net, int32_t schedule, int32_t bloc
 SNN_API snn_status snn_set_window(snn_net* net, uint32_t window, uint32_t queue_cap, uint32_t* window_out,
                                   uint32_t* cap_out, void* stream);
 
-/* Delay window of schedule 5 (no counterpart in the paper; the window holds
- * the band's part of the delay queues of flow step 3, Sec. II-A): window =
- * steps each band keeps in shared memory (0 = the most that fit, at most
- * D - 1); events of a longer delay go through the ring in global memory, so
- * any window gives the same results.  *window_out (may be NULL) receives the
- * window in use.  Synchronises `stream`.  Errors: SNN_EINVAL (layout not
- * grouped, window too large), SNN_ENOMEM. */
-SNN_API snn_status snn_set_pull_window(snn_net* net, uint32_t window, uint32_t* window_out, void* stream);
+/* Bands and delay window of schedule 5 (no counterpart in the paper; the
+ * window holds the band's part of the delay queues of flow step 3, Sec. II-A).
+ * band_mode 1: every CTA owns ceil(N / SMs) neurons (rounded to 4), so a band
+ * also reads the synapses of the modules it shares with its neighbours and
+ * skips those targets; 2: band boundaries only at module boundaries that fall
+ * on a multiple of 4 neurons (every 4 / gcd(M, 4)-th module), so a band reads
+ * only its own synapses but bands differ in size; 0: 2 where its largest band
+ * is no larger than a band of mode 1 plus one module, else 1.  window = steps
+ * each band keeps in shared memory (0 = the most that fit, at most D - 1);
+ * events of a longer delay go through the ring in global memory.  Every
+ * choice gives the same results.  Outputs (may be NULL): the window and the
+ * band mode in use.  Synchronises `stream`.  Errors: SNN_EINVAL (layout not
+ * grouped, band_mode not 0-2, window too large), SNN_ENOMEM. */
+SNN_API snn_status snn_set_pull_window(snn_net* net, uint32_t window, int32_t band_mode, uint32_t* window_out,
+                                       int32_t* mode_out, void* stream);
 
 /* Banded delivery of schedule 2 (no counterpart in the paper, whose processes
  * each own a tile of the grid): the target module rows are split into `bands`

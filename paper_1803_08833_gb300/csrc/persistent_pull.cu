@@ -42,6 +42,7 @@
 #include "grid_common.cuh"
 
 #include <algorithm>
+#include <numeric>
 #include <vector>
 
 namespace snn {
@@ -64,18 +65,18 @@ static_assert(PULL_PIECES < 1024u && (uint64_t)PULL_PIECES * ((PULL_K_MAX + 3) /
 // Shared memory other than the window, in 32-bit words: per-warp spike
 // offsets (TW + 1), drawn-ahead drives, the staged pieces (row, start | length
 // << 16, quad prefix), the band's runs (source module, j0 | j1 << 16, spike
-// prefix), the compaction of a batch, the per-delay destinations of a step;
-// padded to 16 B.
+// prefix), the compaction of a batch, the per-delay destinations of a step,
+// the first quad of every band (G + 1); padded to 16 B.
 __host__ __device__ constexpr uint32_t pull_aux_words(uint32_t G, uint32_t R_max) {
     return ((G * PULL_WARPS + 1) + PULL_DRV * PULL_THREADS + 3 * PULL_PIECES + 1 + 2 * R_max + (R_max + 1) +
-            (PULL_PIECES + 1) + 256 + 3) &
+            (PULL_PIECES + 1) + 256 + (G + 1) + 3) &
            ~3u;
 }
 
 // Neuron id of spike j of the step: its warp by binary search over the
 // per-warp prefix, then that warp's staging segment of `seg`.
 __device__ __forceinline__ uint32_t pull_spike_id(const uint32_t* seg, const uint32_t* s_wpre, uint32_t TW,
-                                                  uint32_t BQ, uint32_t Q, uint32_t j) {
+                                                  const uint32_t* s_bq, uint32_t j) {
     uint32_t lo = 0, hi = TW;
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -85,7 +86,7 @@ __device__ __forceinline__ uint32_t pull_spike_id(const uint32_t* seg, const uin
             hi = mid;
     }
     const uint32_t b = lo / PULL_WARPS, w = lo - b * PULL_WARPS;
-    const uint32_t q0 = min(b * BQ, Q), q1 = min(q0 + BQ, Q);
+    const uint32_t q0 = s_bq[b], q1 = s_bq[b + 1];
     const uint32_t qa = q0 + (q1 - q0) * w / PULL_WARPS;
     return __ldcg(seg + ((size_t)qa << 2) + (j - s_wpre[lo]));
 }
@@ -230,8 +231,8 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     const uint32_t G = gridDim.x, bid = blockIdx.x, tid = threadIdx.x;
     const uint32_t TW = G * PULL_WARPS;
     const uint32_t Q = v.Npad >> 2, M = v.M, nm = v.n_modules, D = v.D;
-    const uint32_t W = v.pull_W, BQ = v.pull_BQ, BN = BQ << 2;
-    const uint32_t q0 = min(bid * BQ, Q), q1 = min(q0 + BQ, Q), nq = q1 - q0;  // this CTA's band of quads
+    const uint32_t W = v.pull_W, BQ = v.pull_BQ, BN = BQ << 2;  // BQ: quads of the largest band
+    const uint32_t q0 = v.pull_bq[bid], q1 = v.pull_bq[bid + 1], nq = q1 - q0;  // this CTA's band of quads
     const uint32_t n0 = q0 << 2, nband = nq << 2;                              // its neurons [n0, n0 + nband)
     const uint32_t rbase = v.pull_run_ptr[bid], nr = v.pull_run_ptr[bid + 1] - rbase;
     int4* win4 = reinterpret_cast<int4*>(smem);  // W rows of BQ quads
@@ -246,6 +247,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     uint32_t* s_rpre = s_rj + v.pull_R_max;             //   spike prefix (R_max + 1)
     uint32_t* s_tmp = s_rpre + v.pull_R_max + 1;        // compaction of a batch (PULL_PIECES + 1)
     uint32_t* s_dtab = s_tmp + PULL_PIECES + 1;         // per delay d: where the events of this step go (256)
+    uint32_t* s_bq = s_dtab + 256;                      // first quad of every band (G + 1)
     __shared__ uint32_t s_t0;
     __shared__ unsigned long long s_rc0;
     __shared__ uint32_t s_ext[PULL_WARPS];
@@ -263,6 +265,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
         s_rj[r] = x.y;
     }
     for (uint32_t x = tid; x < W * BQ; x += PULL_THREADS) win4[x] = make_int4(0, 0, 0, 0);
+    for (uint32_t b = tid; b <= G; b += PULL_THREADS) s_bq[b] = v.pull_bq[b];
     for (uint32_t m = bid * PULL_THREADS + tid; m < 3 * nm; m += G * PULL_THREADS) v.pull_mcnt[m] = 0;
     bool ok = grid_barrier(v, G, gen);  // (starts with a CTA barrier) the module counters are clear everywhere
     const uint32_t t0 = s_t0;
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
         block_exclusive_scan(woff, TW, s_wpre);  // ends with a CTA barrier
         const uint32_t total = s_wpre[TW];
         for (uint32_t j = bid + G * tid; j < total; j += G * PULL_THREADS) {
-            const uint32_t id = pull_spike_id(seg, s_wpre, TW, BQ, Q, j);
+            const uint32_t id = pull_spike_id(seg, s_wpre, TW, s_bq, j);
             const uint64_t r = rc + j;
             if (r < v.raster_cap) {
                 v.raster_t[r] = t;
@@ -528,14 +531,15 @@ size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max) {
 uint32_t pull_warps() { return PULL_WARPS; }
 uint32_t pull_k_max() { return PULL_K_MAX; }
 
-// The runs of every band (CTA b owns the quads [b BQ, (b + 1) BQ) of Q): for
+// The runs of every band (band b = the quads [bq[b], bq[b + 1]) of Q): for
 // each source module whose in-grid stencil reaches a module the band's
 // neurons touch, the stencil entries [j0, j1) of those target modules.  The
 // stencil offsets are in (dy, dx) raster order, so the in-grid entries of a
 // source are in increasing target module order and [j0, j1) is contiguous.
 // Returns R_max, the most runs of one band.
 uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const std::vector<int16_t>& off,
-                         uint32_t G, uint32_t BQ, uint32_t Q, std::vector<uint2>& runs, std::vector<uint32_t>& ptr) {
+                         const std::vector<uint32_t>& bq, std::vector<uint2>& runs, std::vector<uint32_t>& ptr) {
+    const uint32_t G = (uint32_t)bq.size() - 1;
     runs.clear();
     ptr.assign(G + 1, 0);
     int R = 0;  // row radius of the stencil
@@ -543,8 +547,7 @@ uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const
     uint32_t R_max = 0;
     for (uint32_t b = 0; b < G; ++b) {
         ptr[b] = (uint32_t)runs.size();
-        const uint32_t q0 = std::min(b * BQ, Q), q1 = std::min(q0 + BQ, Q);
-        const uint32_t n0 = q0 * 4, n1 = std::min(q1 * 4, N);
+        const uint32_t n0 = bq[b] * 4, n1 = std::min(bq[b + 1] * 4, N);
         if (n1 <= n0) continue;
         const uint32_t m_lo = n0 / M, m_hi = (n1 - 1) / M;
         const int y_lo = std::max(0, (int)(m_lo / gw) - R), y_hi = std::min((int)gh - 1, (int)(m_hi / gw) + R);
@@ -565,6 +568,30 @@ uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const
     }
     ptr[G] = (uint32_t)runs.size();
     return R_max;
+}
+
+// The bands: G contiguous ranges of quads, bq[0] = 0 and bq[G] = ceil(N / 4)
+// (the padding quads up to Q hold no neuron, receive nothing and are left
+// alone).  Uniform: ceil(N / 4 / G) quads each.  Module-aligned: every boundary
+// falls on a module boundary that is also a quad boundary (every u-th module,
+// u = 4 / gcd(M, 4)), the units of u modules split as evenly as possible; a
+// band then reads no synapse of a module it does not own.
+std::vector<uint32_t> pull_bands(uint32_t N, uint32_t M, uint32_t Q, uint32_t G, bool aligned) {
+    Q = std::min(Q, (N + 3) / 4);
+    std::vector<uint32_t> bq(G + 1, Q);
+    bq[0] = 0;
+    if (!aligned) {
+        const uint32_t BQ = (Q + G - 1) / G;
+        for (uint32_t b = 1; b < G; ++b) bq[b] = std::min(b * BQ, Q);
+        return bq;
+    }
+    const uint32_t u = 4 / std::gcd(M, 4u);
+    const uint32_t nm = (N + M - 1) / M, U = (nm + u - 1) / u;
+    for (uint32_t b = 1; b < G; ++b) {
+        const uint64_t unit = (uint64_t)U * b / G;
+        bq[b] = (uint32_t)std::min<uint64_t>(unit * u * M / 4, Q);
+    }
+    return bq;
 }
 
 uint32_t pull_max_window(const NetView& v, int grid, uint32_t BQ, uint32_t R_max) {

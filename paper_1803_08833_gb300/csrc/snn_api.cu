@@ -86,6 +86,7 @@ struct snn_net {
     int ogrid = 0;      // owner-windowed persistent grid (schedule 4), 0 until set up
     int plgrid = 0;     // pulled windowed persistent grid (schedule 5), 0 until set up
     size_t pull_runs_bytes = 0;
+    int pull_mode = 0;  // schedule 5 bands in use: 1 uniform, 2 module-aligned
     bool stdp = false;        // spike-timing dependent plasticity (schedules 0 and 1)
     StdpView sp{};
     int2* own_rec = nullptr;  // schedule 4 record queues and their size
@@ -496,30 +497,49 @@ snn_status owned_setup(snn_net* n, uint32_t window, uint32_t queue_cap) {
     return SNN_OK;
 }
 
-// Pulled windowed delivery (schedule 5): bands of ceil(Q / G) quads, one per
-// CTA of a grid of one CTA per SM, each with its table of runs (source module,
-// stencil entries of the band's target modules); a window of `window` steps
-// (0 = the largest that fits in shared memory, at most D - 1).  Needs the
-// grouped layout (rows ordered by target module) with K synapses per row.
-snn_status pull_setup(snn_net* n, uint32_t window) {
+// Pulled windowed delivery (schedule 5): one band of quads per CTA of a grid
+// of one CTA per SM, each with its table of runs (source module, stencil
+// entries of the band's target modules); a window of `window` steps (0 = the
+// largest that fits in shared memory, at most D - 1).  band_mode 1: bands of
+// ceil(Q / G) quads; 2: bands on module boundaries (a band then reads only
+// synapses it owns, but bands differ in size by up to u modules); 0: 2 if its
+// largest band is at most a uniform band plus one module (the synapses a
+// uniform band reads beyond its own) and fits in shared memory, else 1.  Needs
+// the grouped layout (rows ordered by target module) with K synapses per row.
+snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     NetView& v = n->v;
     if (n->cfg.table_layout != SNN_LAYOUT_GROUPED || v.row_len || !v.segidx)
         return fail(SNN_EINVAL, "schedule 5 needs a network built with table_layout = SNN_LAYOUT_GROUPED and K "
                                 "synapses per row");
     if (n->K > pull_k_max()) return fail(SNN_EINVAL, "schedule 5: K = %u exceeds %u", n->K, pull_k_max());
+    if (band_mode < 0 || band_mode > 2) return fail(SNN_EINVAL, "schedule 5: band_mode must be 0, 1 or 2");
     const int G = owned_grid();
     if (G <= 0) return fail(SNN_ECUDA, "schedule 5: no multiprocessor count");
     const uint32_t Q = n->Npad / 4;
-    const uint32_t BQ = (Q + (uint32_t)G - 1) / (uint32_t)G;
     uint32_t R2 = 0;
     const std::vector<int16_t> off = disc_offsets(n->cfg, &R2);
-    std::vector<uint2> runs;
-    std::vector<uint32_t> ptr;
-    const uint32_t R_max = pull_build_runs(n->N, n->M, n->cfg.grid_w, n->cfg.grid_h, off, (uint32_t)G, BQ, Q, runs, ptr);
+    struct Plan {
+        std::vector<uint32_t> bq, ptr;
+        std::vector<uint2> runs;
+        uint32_t BQ = 0, R_max = 0, Wmax = 0;
+    } plan[2];
+    for (int k = 0; k < 2; ++k) {
+        if (band_mode != 0 && band_mode != k + 1) continue;
+        Plan& p = plan[k];
+        p.bq = pull_bands(n->N, n->M, Q, (uint32_t)G, k == 1);
+        for (int b = 0; b < G; ++b) p.BQ = std::max(p.BQ, p.bq[b + 1] - p.bq[b]);
+        p.R_max = pull_build_runs(n->N, n->M, n->cfg.grid_w, n->cfg.grid_h, off, p.bq, p.runs, p.ptr);
+        p.Wmax = p.BQ ? pull_max_window(v, G, p.BQ, p.R_max) : 0;
+    }
+    int pick = band_mode == 2 ? 1 : 0;
+    if (band_mode == 0 && plan[1].Wmax > 0 && (uint64_t)plan[1].BQ * 4 <= (uint64_t)plan[0].BQ * 4 + n->M) pick = 1;
+    Plan& p = plan[pick];
+    const uint32_t BQ = p.BQ, R_max = p.R_max, Wmax = p.Wmax;
+    std::vector<uint2>& runs = p.runs;
+    std::vector<uint32_t>& ptr = p.ptr;
     for (const uint2& r : runs)  // the kernel's reads of the segment index stay in the row
         if ((r.y & 0xFFFFu) >= (r.y >> 16) || (r.y >> 16) > n->max_off || r.x >= n->n_modules)
             return fail(SNN_EINVAL, "schedule 5: run table entry out of range");
-    const uint32_t Wmax = pull_max_window(v, G, BQ, R_max);
     if (Wmax == 0)
         return fail(SNN_EINVAL, "schedule 5: a delay window row of %u neurons per CTA does not fit in shared memory",
                     BQ * 4);
@@ -538,6 +558,7 @@ snn_status pull_setup(snn_net* n, uint32_t window) {
             {(void**)&v.pull_mcnt, (size_t)n->n_modules * 3 * 4},
             {(void**)&v.pull_woff, warps * 2 * 4},
             {(void**)&v.pull_run_ptr, (size_t)(G + 1) * 4},
+            {(void**)&v.pull_bq, (size_t)(G + 1) * 4},
         };
         for (auto& r : reqs) {
             *r.p = dev_alloc(n, r.bytes);
@@ -554,12 +575,14 @@ snn_status pull_setup(snn_net* n, uint32_t window) {
     if (!runs.empty())
         CUDA_TRY(cudaMemcpyAsync(druns, runs.data(), runs.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync((void*)v.pull_run_ptr, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync((void*)v.pull_bq, p.bq.data(), p.bq.size() * 4, cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors go out of scope
     v.pull_runs = druns;
     v.pull_W = W;
     v.pull_BQ = BQ;
     v.pull_R_max = R_max;
     n->plgrid = G;
+    n->pull_mode = pick + 1;
     return SNN_OK;
 }
 
@@ -1384,12 +1407,14 @@ snn_status snn_set_window(snn_net* n, uint32_t window, uint32_t queue_cap, uint3
     return SNN_OK;
 }
 
-snn_status snn_set_pull_window(snn_net* n, uint32_t window, uint32_t* window_out, void* stream) {
+snn_status snn_set_pull_window(snn_net* n, uint32_t window, int32_t band_mode, uint32_t* window_out,
+                               int32_t* mode_out, void* stream) {
     if (!n) return fail(SNN_EINVAL, "net is NULL");
     CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));  // no launch in flight uses the run table
-    snn_status st = pull_setup(n, window);
+    snn_status st = pull_setup(n, window, band_mode);
     if (st != SNN_OK) return st;
     if (window_out) *window_out = n->v.pull_W;
+    if (mode_out) *mode_out = n->pull_mode;
     return SNN_OK;
 }
 
@@ -1418,7 +1443,7 @@ snn_status snn_set_schedule(snn_net* n, int32_t schedule, int32_t block) {
         if (st != SNN_OK) return st;
     }
     if (schedule == 5 && n->plgrid == 0) {
-        snn_status st = pull_setup(n, 0);
+        snn_status st = pull_setup(n, 0, 0);
         if (st != SNN_OK) return st;
     }
     if (schedule == 3 && n->cfg.table_layout != SNN_LAYOUT_GROUPED)

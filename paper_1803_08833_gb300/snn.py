@@ -137,7 +137,7 @@ def load():
         "snn_shard_destroy": (None, [vp]),
         "snn_set_bands": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
         "snn_set_window": (st, [vp, ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_uint32), P(ctypes.c_uint32), vp]),
-        "snn_set_pull_window": (st, [vp, ctypes.c_uint32, P(ctypes.c_uint32), vp]),
+        "snn_set_pull_window": (st, [vp, ctypes.c_uint32, ctypes.c_int32, P(ctypes.c_uint32), P(ctypes.c_int32), vp]),
         "snn_autotune": (st, [vp, ctypes.c_uint32, ctypes.c_char_p, P(ctypes.c_int32), P(ctypes.c_int32),
                               P(ctypes.c_double), vp]),
         "snn_set_timing": (st, [vp, ctypes.c_int32]),
@@ -417,11 +417,15 @@ class Network:
         check(load().snn_set_window(self._h, int(window), int(queue_cap), ctypes.byref(w), ctypes.byref(c), self._s))
         return w.value, c.value
 
-    def set_pull_window(self, window: int = 0) -> int:
-        """Schedule 5's delay window (steps kept in shared memory per band);
-        0 picks the most that fit.  Returns the window in use."""
-        w = ctypes.c_uint32()
-        check(load().snn_set_pull_window(self._h, int(window), ctypes.byref(w), self._s))
+    def set_pull_window(self, window: int = 0, band_mode: int = 0) -> int:
+        """Schedule 5's delay window (steps kept in shared memory per band; 0
+        picks the most that fit) and bands (0 automatic, 1 uniform, 2 on module
+        boundaries).  Returns the window in use (the band mode in use is
+        `pull_band_mode`)."""
+        w, m = ctypes.c_uint32(), ctypes.c_int32()
+        check(load().snn_set_pull_window(self._h, int(window), int(band_mode), ctypes.byref(w), ctypes.byref(m),
+                                         self._s))
+        self.pull_band_mode = m.value
         return w.value
 
     def set_bands(self, bands: int = 0) -> int:

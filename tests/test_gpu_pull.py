@@ -69,21 +69,26 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("band_mode", [1, 2])
 @pytest.mark.parametrize("window", [0, 1, 2, 5])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_windows_equal_oracle(snn, name, window):
+def test_windows_equal_oracle(snn, name, window, band_mode):
     """Window 1 sends every event of delay > 1 to the ring; the default keeps
-    most of them in shared memory."""
+    most of them in shared memory.  Band mode 1 splits modules between bands
+    (M = 250, 333, 77 leave modules inside quads), mode 2 cuts only at module
+    boundaries on a multiple of 4 neurons (every module for M = 1000, every
+    second for M = 250 and 120, every fourth for M = 333 and 77)."""
     make, steps = CASES[name]
     cfg = make()
     ref = oracle.OracleNet(cfg)
     ref.step(steps)
     with snn.Network(cfg, raster_capacity=1 << 22) as net:
         net.set_schedule(5)
-        wmax = net.set_pull_window(0)
+        wmax = net.set_pull_window(0, band_mode)
+        assert net.pull_band_mode == band_mode
         if window > wmax:
             pytest.skip("window %d does not fit (max %d)" % (window, wmax))
-        assert net.set_pull_window(window) == (window or wmax)
+        assert net.set_pull_window(window, band_mode) == (window or wmax)
         net.step(steps // 3)
         net.step(1)
         net.step(steps - steps // 3 - 1)
@@ -114,21 +119,25 @@ def test_switching_schedules_and_snapshot(snn):
         _compare(net, ref)
 
 
-@pytest.mark.parametrize("make", [
-    lambda: W.gauss_24x24_k1125(seed=5, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped"),
-    lambda: W.exp_24x24_k2250(seed=4, imposed_rate_hz=W.PAPER_RATE_EXP_HZ, table_layout="grouped"),
-], ids=["gauss_24x24_k1125", "exp_24x24_k2250_bf16"])
-def test_full_size_schedule_5_equals_schedule_2(snn, make):
+@pytest.mark.parametrize("make,band_mode", [
+    (lambda: W.gauss_24x24_k1125(seed=5, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped"), 0),
+    (lambda: W.gauss_24x24_k1125(seed=5, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped"), 1),
+    (lambda: W.exp_24x24_k2250(seed=4, imposed_rate_hz=W.PAPER_RATE_EXP_HZ, table_layout="grouped"), 0),
+], ids=["gauss_24x24_k1125", "gauss_24x24_k1125_uniform_bands", "exp_24x24_k2250_bf16"])
+def test_full_size_schedule_5_equals_schedule_2(snn, make, band_mode):
     """The 24x24 benchmark networks (720,000 neurons, 810 M and 1.6 G synapses)
     at the paper's rates, 200 steps in two calls: schedule 5 with its default
-    window equals schedule 2 in raster, state, ring and counters."""
+    window equals schedule 2 in raster, state, ring and counters.  The
+    automatic bands of these networks are module-aligned (2 or 4 modules of
+    1,250 neurons against 4,740 neurons per uniform band)."""
     cfg = make()
     out = []
     for sched in (2, 5):
         with snn.Network(cfg, raster_capacity=1 << 24) as net:
             net.set_schedule(sched)
             if sched == 5:
-                assert net.set_pull_window(0) >= 6  # most delays stay in shared memory on a GB300
+                assert net.set_pull_window(0, band_mode) >= 6  # most delays stay in shared memory on a GB300
+                assert net.pull_band_mode == (band_mode or 2)
             net.step(120)
             net.step(80)
             st = net.state()
@@ -172,3 +181,5 @@ def test_schedule_5_argument_errors(snn):
         wmax = net.set_pull_window(0)
         with pytest.raises(snn.SnnError, match="window"):
             net.set_pull_window(wmax + 1)
+        with pytest.raises(snn.SnnError, match="band_mode"):
+            net.set_pull_window(0, 3)
