@@ -13,8 +13,8 @@
 //   N  the band's neurons (flow steps 4-6, Sec. II-A): the input of step t is
 //      window row t mod W plus ring row t mod D, both cleared after the read;
 //      spikes are staged in id order per warp (for the raster) and appended to
-//      their module's list, and the whole row of each (target | delay words,
-//      weights) is prefetched into L2 with one bulk prefetch per array;
+//      their module's list (counted by the module's owner in shared memory
+//      when the bands are module-aligned);
 //   -- grid barrier --
 //   D  (flow steps 2-3) every CTA writes the raster entries of every G-th
 //      spike; then it walks its band's runs: for every source module whose
@@ -59,6 +59,7 @@ constexpr int PULL_DRV = 4;                     // chunks per thread whose next-
 constexpr uint32_t PULL_PIECES = PULL_THREADS;  // (spike, run) pieces staged per batch: one per thread
 constexpr int PULL_UNROLL = SNN_PULL_UNROLL;    // chunks of 32 quads in flight per warp
 constexpr uint32_t PULL_K_MAX = 8188;           // longest row: a piece spans at most 2^11 quads
+constexpr uint32_t PULL_MODS_MAX = 64;          // modules of a band counted in shared memory
 static_assert(PULL_PIECES < 1024u && (uint64_t)PULL_PIECES * ((PULL_K_MAX + 3) / 4 + 1) < (1u << 22),
               "the compaction key of a batch holds 10 bits of rank and 22 bits of quads");
 
@@ -89,11 +90,6 @@ __device__ __forceinline__ uint32_t pull_spike_id(const uint32_t* seg, const uin
     const uint32_t q0 = s_bq[b], q1 = s_bq[b + 1];
     const uint32_t qa = q0 + (q1 - q0) * w / PULL_WARPS;
     return __ldcg(seg + ((size_t)qa << 2) + (j - s_wpre[lo]));
-}
-
-// The whole of [p, p + bytes) into L2 (bulk prefetch; p and bytes 16-byte aligned).
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // The L2 line holding p.
@@ -253,12 +249,18 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     __shared__ uint32_t s_ext[PULL_WARPS];
     __shared__ unsigned long long s_rec[PULL_WARPS];
     __shared__ uint32_t s_pois[MAX_POIS];
+    __shared__ uint32_t s_mc[PULL_MODS_MAX];  // module-aligned bands: spikes per module of the band this step
     load_poisson_table(v, s_pois);
     uint32_t gen = 0;
     if (tid == 0) {
         s_t0 = v.st->t;
         s_rc0 = v.st->raster_count;
     }
+    // With module-aligned bands every module has one owner, which counts its
+    // spikes in shared memory and publishes the count before the barrier.
+    const bool own_mods = v.pull_aligned != 0;
+    const uint32_t m_lo = n0 / M, nmb = nband ? (n0 + nband - 1) / M - m_lo + 1 : 0u;
+    for (uint32_t m = tid; m < PULL_MODS_MAX; m += PULL_THREADS) s_mc[m] = 0;
     for (uint32_t r = tid; r < nr; r += PULL_THREADS) {
         const uint2 x = v.pull_runs[rbase + r];
         s_rsrc[r] = x.x;
@@ -276,7 +278,6 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     int4* ring4 = reinterpret_cast<int4*>(v.ring);
     const uint32_t Q4 = v.Npad >> 2;  // int4 per ring row
     const uint32_t Kpad = v.Kpad, stride = v.seg_stride;
-    const uint32_t wbytes = Kpad * (BF16 ? 2u : 4u);  // bytes of a row of weights
     const uint64_t pol = evict_normal_policy();
 
     uint64_t rc = s_rc0;
@@ -343,10 +344,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
                         const uint32_t id = (q << 2) + b;
                         if (SNN_BOUND(v.st, pos < (qb << 2))) seg[pos] = id;
                         ++pos;
-                        // the whole row into L2 now, in two bulk reads, while the other bands finish
-                        prefetch_l2(v.td + (size_t)id * Kpad, Kpad * 4u);
-                        prefetch_l2(static_cast<const char*>(v.w) + (size_t)id * wbytes, wbytes);
-                        prefetch_line(v.segidx + (size_t)id * stride);
+                        prefetch_line(v.segidx + (size_t)id * stride);  // read by the bands in the next phase
                     }
                 run += __shfl_sync(0xFFFFFFFFu, incl, 31);
                 if (__any_sync(0xFFFFFFFFu, spk != 0)) {  // module lists: one atomic per module and bit
@@ -359,7 +357,14 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
                         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
                         const uint32_t leader = __ffs(peers) - 1;
                         uint32_t base = 0;
-                        if (has && lane == leader) base = atomicAdd(mcnt + mb, (uint32_t)__popc(peers));
+                        if (has && lane == leader) {
+                            if (own_mods)
+                                base = SNN_BOUND(v.st, mb - m_lo < nmb && nmb <= PULL_MODS_MAX)
+                                           ? atomicAdd(s_mc + (mb - m_lo), (uint32_t)__popc(peers))
+                                           : M;
+                            else
+                                base = atomicAdd(mcnt + mb, (uint32_t)__popc(peers));
+                        }
                         base = __shfl_sync(0xFFFFFFFFu, base, leader);
                         const uint32_t at = base + __popc(peers & lt_mask);
                         if (has && SNN_BOUND(v.st, mb < nm && at < M)) segm[(size_t)mb * M + at] = (q << 2) + b;
@@ -368,6 +373,13 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             }
         }
         if (lane == 0) woff[wg] = run;
+        if (own_mods) {  // the band's module counts, published (and cleared for the next step)
+            __syncthreads();
+            for (uint32_t m = tid; m < nmb; m += PULL_THREADS) {
+                mcnt[m_lo + m] = s_mc[m];
+                s_mc[m] = 0;
+            }
+        }
         if (!grid_barrier(v, G, gen)) break;
         if (bid == 0 && tid == 0) {
             const uint64_t now = global_ns();
@@ -393,18 +405,10 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             const uint32_t ws = (wslot + d) % W, rs = (slot0 + d) % D;
             s_dtab[d] = d <= W ? ws * BN : 0x80000000u | rs;
         }
+        // the runs' spike counts and the per-warp spike counts: loads in flight together
+        for (uint32_t r = tid; r < nr; r += PULL_THREADS) s_rpre[r] = __ldcg(mcnt + s_rsrc[r]);
         block_exclusive_scan(woff, TW, s_wpre);  // ends with a CTA barrier
         const uint32_t total = s_wpre[TW];
-        for (uint32_t j = bid + G * tid; j < total; j += G * PULL_THREADS) {
-            const uint32_t id = pull_spike_id(seg, s_wpre, TW, s_bq, j);
-            const uint64_t r = rc + j;
-            if (r < v.raster_cap) {
-                v.raster_t[r] = t;
-                v.raster_id[r] = id;
-            }
-        }
-        for (uint32_t r = tid; r < nr; r += PULL_THREADS) s_rpre[r] = __ldcg(mcnt + s_rsrc[r]);
-        __syncthreads();
         block_scan_inplace(s_rpre, nr);  // s_rpre[nr] = pieces of the step
         const uint32_t P = s_rpre[nr];
         // piece p: spike (p - s_rpre[r]) of run r's source module; its range [a, a + len) of the row
@@ -419,12 +423,21 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             a = __ldg(sg + (jj & 0xFFFFu));
             len = __ldg(sg + (jj >> 16)) - a;
         };
-        // pieces are loaded two batches ahead (the row id) and one ahead (its range)
+        // pieces are loaded two batches ahead (the row id) and one ahead (its
+        // range); the raster entries are written while the first loads are in flight
         uint32_t idA = 0, aA = 0, lA = 0, idB = 0, rB = 0;
         {
             uint32_t rA = 0;
             if (tid < P) idA = piece_id(tid, rA);
             if (PULL_PIECES + tid < P) idB = piece_id(PULL_PIECES + tid, rB);
+            for (uint32_t j = bid + G * tid; j < total; j += G * PULL_THREADS) {
+                const uint32_t id = pull_spike_id(seg, s_wpre, TW, s_bq, j);
+                const uint64_t r = rc + j;
+                if (r < v.raster_cap) {
+                    v.raster_t[r] = t;
+                    v.raster_id[r] = id;
+                }
+            }
             if (tid < P) piece_range(idA, rA, aA, lA);
         }
         for (uint32_t pb = 0; pb < P; pb += PULL_PIECES) {
@@ -529,6 +542,7 @@ size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max) {
 }
 
 uint32_t pull_warps() { return PULL_WARPS; }
+uint32_t pull_mods_max() { return PULL_MODS_MAX; }
 uint32_t pull_k_max() { return PULL_K_MAX; }
 
 // The runs of every band (band b = the quads [bq[b], bq[b + 1]) of Q): for

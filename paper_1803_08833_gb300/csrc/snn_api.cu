@@ -581,6 +581,14 @@ snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     v.pull_W = W;
     v.pull_BQ = BQ;
     v.pull_R_max = R_max;
+    v.pull_aligned = 0;
+    if (pick == 1) {  // every module in one band: counted by its owner when no band holds too many
+        uint32_t most = 0;
+        for (int b = 0; b < G; ++b)
+            if (p.bq[b + 1] > p.bq[b])
+                most = std::max(most, (std::min(p.bq[b + 1] * 4, n->N) - 1) / n->M - p.bq[b] * 4 / n->M + 1);
+        v.pull_aligned = most <= pull_mods_max() ? 1u : 0u;
+    }
     n->plgrid = G;
     n->pull_mode = pick + 1;
     return SNN_OK;

@@ -130,6 +130,7 @@ struct NetView {
     uint32_t pull_W;          // window steps (1 <= pull_W <= D - 1)
     uint32_t pull_BQ;         // quads of the largest band (the window row)
     const uint32_t* pull_bq;  // G + 1: band b = the quads [pull_bq[b], pull_bq[b + 1])
+    uint32_t pull_aligned;    // bands on module boundaries, at most pull_mods_max() modules each
     uint32_t pull_R_max;      // most runs of one band
     const uint2* pull_runs;   // runs of all bands: {source module, stencil entries j0 | j1 << 16}
     const uint32_t* pull_run_ptr;  // G + 1: runs of band b at [ptr[b], ptr[b + 1])
@@ -284,6 +285,7 @@ std::vector<uint32_t> pull_bands(uint32_t N, uint32_t M, uint32_t Q, uint32_t G,
 uint32_t pull_max_window(const NetView& v, int grid, uint32_t BQ, uint32_t R_max);
 size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max);
 uint32_t pull_warps();
+uint32_t pull_mods_max();
 uint32_t pull_k_max();
 cudaError_t launch_pull(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
