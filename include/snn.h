@@ -360,7 +360,8 @@ SNN_API snn_status snn_set_resident_state(snn_net* net, int32_t enable, int32_t*
 
 /* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
  * per delivery block, 2, 3 if the network has the grouped layout and its
- * tile fits, 4 if a delay window fits) for trial_steps steps from the same snapshot of the dynamic
+ * tile fits, 4 if a delay window fits, 5 if the network has the grouped
+ * layout and fixed out-degree) for trial_steps steps from the same snapshot of the dynamic
  * state, times each with CUDA events, restores the state (the raster and the
  * counters are as before the call) and selects the fastest.  If cache_path
  * is not NULL the choice is looked up there first and appended after

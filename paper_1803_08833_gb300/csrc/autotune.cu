@@ -96,7 +96,7 @@ snn_status snn_autotune(snn_net* net, uint32_t trial_steps, const char* cache_pa
     std::vector<char> snap(n);
     e = snn_snapshot(net, snap.data(), n, &n, stream);
     if (e != SNN_OK) return e;
-    const int cand[][2] = {{0, 128}, {0, 256}, {1, 128}, {1, 256}, {2, 0}, {3, 0}, {4, 0}};
+    const int cand[][2] = {{0, 128}, {0, 256}, {1, 128}, {1, 256}, {2, 0}, {3, 0}, {4, 0}, {5, 0}};
     cudaEvent_t a, z;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess)
         return afail(SNN_ECUDA, "cudaEventCreate failed");

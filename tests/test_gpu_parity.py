@@ -371,7 +371,7 @@ def test_autotune_leaves_the_simulation_unchanged(snn, tmp_path):
     with snn.Network(cfg) as net:
         net.step(20)
         sched, block, ms = net.autotune(trial_steps=15, cache_path=cache)
-        assert sched in (0, 1, 2, 3) and ms > 0
+        assert sched in (0, 1, 2, 3, 4, 5) and ms > 0
         net.step(30)
         ref = oracle.OracleNet(cfg)
         ref.step(50)
