@@ -380,7 +380,20 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
                 s_mc[m] = 0;
             }
         }
-        if (!grid_barrier(v, G, gen)) break;
+        // split barrier: arrive, then do what needs nobody else's data -- this
+        // step's per-delay destinations and the next step's external drive --
+        // while the other CTAs finish, then wait
+        grid_arrive(v.st, gen);
+        // d <= W: word offset of window row (t + d) mod W; else 2^31 | ring row (t + d) mod D
+        for (uint32_t d = tid; d < 256; d += PULL_THREADS) {
+            const uint32_t ws = (wslot + d) % W, rs = (slot0 + d) % D;
+            s_dtab[d] = d <= W ? ws * BN : 0x80000000u | rs;
+        }
+        ndrv = 0;
+        if (step + 1 < n_steps)
+            for (; ndrv < nd_max; ++ndrv)
+                s_drv[ndrv * PULL_THREADS + tid] = quad_drive(v, s_pois, (qa + lane + 32 * ndrv) << 2, t + 1);
+        if (!grid_wait(v.st, G + v.barrier_extra, v.wait_limit_ns, gen)) break;
         if (bid == 0 && tid == 0) {
             const uint64_t now = global_ns();
             ph_n += now - stamp;
@@ -388,22 +401,10 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
         }
 
         // ---- phase D: raster of every G-th spike, then the band's pieces
-        ndrv = 0;
-        const bool next = step + 1 < n_steps;
-        auto draw_next = [&]() {
-            if (next && ndrv < nd_max) {
-                s_drv[ndrv * PULL_THREADS + tid] = quad_drive(v, s_pois, (qa + lane + 32 * ndrv) << 2, t + 1);
-                ++ndrv;
-            }
-        };
+        auto no_hook = []() {};
         {
             uint32_t* mclr = v.pull_mcnt + (size_t)((t + 2u) % 3u) * nm;  // the counters of step t - 1
             for (uint32_t m = bid * PULL_THREADS + tid; m < nm; m += G * PULL_THREADS) mclr[m] = 0;
-        }
-        // d <= W: word offset of window row (t + d) mod W; else 2^31 | ring row (t + d) mod D
-        for (uint32_t d = tid; d < 256; d += PULL_THREADS) {
-            const uint32_t ws = (wslot + d) % W, rs = (slot0 + d) % D;
-            s_dtab[d] = d <= W ? ws * BN : 0x80000000u | rs;
         }
         // the runs' spike counts and the per-warp spike counts: loads in flight together
         for (uint32_t r = tid; r < nr; r += PULL_THREADS) s_rpre[r] = __ldcg(mcnt + s_rsrc[r]);
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
                 uint32_t pp = pull_slot(s_pre, np, c0 << 5);
                 for (uint32_t c = c0; c < c1;)
                     pull_chunks<BF16>(v, c, c1, pp, np, Qt, s_pid, s_pa, s_pre, s_dtab, win, n0, nband, W, BN, lane,
-                                      pol, draw_next);
+                                      pol, no_hook);
             }
             __syncthreads();  // the staged batch is read by every warp before the next is written
             idA = idB;
@@ -476,7 +477,6 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             idB = idC;
             rB = rC;
         }
-        while (ndrv < nd_max && next) draw_next();
         rc += total;
         spikes += total;
         __syncthreads();  // every event of the step is in the window before N(t + 1) reads it
