@@ -7,7 +7,7 @@
 //   k_gen_synapses per (neuron, 4 synapses): Philox draws -> target module by
 //                  inverse CDF, target neuron, weight, delay; 16 B vector stores
 //                  of target | delay << 24 and of the weights.
-//   k_pair_count / k_pair_rows / k_pair_fill
+//   k_pair_count / k_pair_rows / k_pair_fill / k_pair_attr
 //                  the pairwise law of Sec. III-B: per (neuron, stencil entry)
 //                  the connection draws of every candidate target, counted,
 //                  turned into row offsets, then written.
@@ -262,11 +262,13 @@ __global__ void __launch_bounds__(256) k_gen_grouped(BuildView b, uint32_t* __re
 // in (o, j) order; the k-th takes its efficacy and delay from Philox
 // (i, k, GEN).
 
-// Candidates of (i, o) that connect; with `out`, writes them from row offset
-// `start` on.  Returns the count.
-template <bool WRITE, bool BF16>
+// Candidates of (i, o) that connect; with WRITE, writes their targets from
+// row offset `start` on (k_pair_attr adds the delays and efficacies, one
+// thread per synapse, so that no lane of the candidate loop waits on another
+// lane's draws).  Returns the count.
+template <bool WRITE>
 __device__ __forceinline__ uint32_t pair_entry(const BuildView& b, uint32_t i, uint32_t o, uint32_t start,
-                                               uint32_t* __restrict__ td, void* __restrict__ wout) {
+                                               uint32_t* __restrict__ td) {
     const uint32_t s = i / b.M, a = i - s * b.M;
     const bool exc = a < b.n_exc;
     const int dx = __ldg(b.pair_dx + o), dy = __ldg(b.pair_dy + o);
@@ -285,19 +287,7 @@ __device__ __forceinline__ uint32_t pair_entry(const BuildView& b, uint32_t i, u
         for (int q = 0; q < 4; ++q) {
             const uint32_t j = (g << 2) + q;
             if (j >= b.M || (local && j == a) || (uint64_t)uw[q] >= thr) continue;
-            if (WRITE) {
-                const uint32_t k = start + n;
-                const U4 v = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
-                float w;
-                uint32_t d;
-                syn_attr(b, exc, v.z, v.w, w, d);
-                const size_t e = (size_t)i * b.Kpad + k;
-                td[e] = (base + j) | (d << 24);
-                if (BF16)
-                    reinterpret_cast<__nv_bfloat16*>(wout)[e] = __float2bfloat16_rn(w);
-                else
-                    reinterpret_cast<float*>(wout)[e] = w;
-            }
+            if (WRITE) td[(size_t)i * b.Kpad + start + n] = base + j;
             ++n;
         }
     }
@@ -308,7 +298,7 @@ __global__ void __launch_bounds__(256) k_pair_count(BuildView b) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
-    const uint32_t n = pair_entry<false, false>(b, i, o, 0u, nullptr, nullptr);
+    const uint32_t n = pair_entry<false>(b, i, o, 0u, nullptr);
     b.pair_cnt[(size_t)i * (b.pair_n + 1) + o] = (uint16_t)min(n, 0xFFFFu);
 }
 
@@ -340,12 +330,41 @@ __global__ void __launch_bounds__(256) k_pair_rows(BuildView b) {
     }
 }
 
-template <bool BF16>
-__global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __restrict__ td, void* __restrict__ wout) {
+__global__ void __launch_bounds__(256) k_pair_fill(BuildView b, uint32_t* __restrict__ td) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)b.N * b.pair_n) return;
     const uint32_t i = (uint32_t)(gid / b.pair_n), o = (uint32_t)(gid - (uint64_t)i * b.pair_n);
-    pair_entry<true, BF16>(b, i, o, b.pair_cnt[(size_t)i * (b.pair_n + 1) + o], td, wout);
+    pair_entry<true>(b, i, o, b.pair_cnt[(size_t)i * (b.pair_n + 1) + o], td);
+}
+
+// Efficacy and delay of synapse k of row i from Philox (i, k, GEN), added to
+// the target k_pair_fill wrote; four synapses per thread, rows of row_len[i].
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_pair_attr(BuildView b, uint32_t* __restrict__ td, void* __restrict__ wout) {
+    const uint32_t groups = b.Kpad >> 2;
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)b.N * groups) return;
+    const uint32_t i = (uint32_t)(gid / groups);
+    const uint32_t k0 = (uint32_t)(gid - (uint64_t)i * groups) << 2;
+    const uint32_t len = b.row_len[i];
+    if (k0 >= len) return;
+    const bool exc = (i % b.M) < b.n_exc;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t k = k0 + q;
+        if (k < len) {
+            const U4 u = philox4x32_10(i, k, TAG_GEN, 0u, b.key0, b.key1);
+            float w;
+            uint32_t d;
+            syn_attr(b, exc, u.z, u.w, w, d);
+            const size_t e = (size_t)i * b.Kpad + k;
+            td[e] |= d << 24;
+            if (BF16)
+                reinterpret_cast<__nv_bfloat16*>(wout)[e] = __float2bfloat16_rn(w);
+            else
+                reinterpret_cast<float*>(wout)[e] = w;
+        }
+    }
 }
 
 __global__ void k_init_state(BuildView b, float* __restrict__ V, float* __restrict__ c,
@@ -418,11 +437,16 @@ cudaError_t launch_pair_rows(const BuildView& b, cudaStream_t s) {
 
 cudaError_t launch_pair_fill(const BuildView& b, uint32_t* td, void* w, cudaStream_t s) {
     if (b.N == 0 || b.pair_n == 0) return cudaSuccess;
-    if (b.w_bf16)
-        k_pair_fill<true><<<pair_blocks(b), 256, 0, s>>>(b, td, w);
-    else
-        k_pair_fill<false><<<pair_blocks(b), 256, 0, s>>>(b, td, w);
-    count_launch(1);
+    k_pair_fill<<<pair_blocks(b), 256, 0, s>>>(b, td);
+    const uint64_t threads = (uint64_t)b.N * (b.Kpad >> 2);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (threads) {
+        if (b.w_bf16)
+            k_pair_attr<true><<<blocks, 256, 0, s>>>(b, td, w);
+        else
+            k_pair_attr<false><<<blocks, 256, 0, s>>>(b, td, w);
+    }
+    count_launch(threads ? 2 : 1);
     return cudaGetLastError();
 }
 
