@@ -5,17 +5,19 @@
 // event, and L2 takes scattered 8-byte stores at about the same sector rate
 // (k_run_steps_owned, which queued near events as records, measured that).
 // Here no event is written to L2 unless its delay is longer than the window.
-// Every CTA owns a band of quads [b BQ, (b + 1) BQ) for the whole launch and
-// keeps in shared memory a window of W rows: row (t + d) mod W collects the
-// input its band receives at step t + d from events of delay d <= W.  Events of
-// longer delay go to the delay ring in global memory as before.  One step t:
+// Every CTA owns a band of quads for the whole launch (uniform bands, or bands
+// cut only at module boundaries) and keeps in shared memory a window of W rows
+// of the band: row (t + d) mod W collects the input its band receives at step
+// t + d from events of delay d <= W.  Events of longer delay go to the delay
+// ring in global memory as before.  One step t:
 //
 //   N  the band's neurons (flow steps 4-6, Sec. II-A): the input of step t is
 //      window row t mod W plus ring row t mod D, both cleared after the read;
 //      spikes are staged in id order per warp (for the raster) and appended to
 //      their module's list (counted by the module's owner in shared memory
 //      when the bands are module-aligned);
-//   -- grid barrier --
+//   -- grid barrier, split: between arriving and waiting each CTA fills the
+//      step's per-delay destinations and draws the next step's external drive --
 //   D  (flow steps 2-3) every CTA writes the raster entries of every G-th
 //      spike; then it walks its band's runs: for every source module whose
 //      stencil reaches the band, the spikes of that module and, in each
@@ -140,12 +142,11 @@ __device__ __forceinline__ uint32_t pull_piece_quads(uint32_t a, uint32_t len) {
 // target lies in the band [n0, n0 + nband) add their weight where s_dtab[d]
 // says: window row (t + d) mod W if d <= W, else ring row (t + d) mod D.
 // Advances c and pp past the chunks delivered.
-template <bool BF16, class Hook>
+template <bool BF16>
 __device__ __forceinline__ void pull_chunks(const NetView& v, uint32_t& c, uint32_t cend, uint32_t& pp,
                                             uint32_t np, uint32_t Qt, const uint32_t* s_pid, const uint32_t* s_pa,
                                             const uint32_t* s_pre, const uint32_t* s_dtab, int32_t* win, uint32_t n0,
-                                            uint32_t nband, uint32_t W, uint32_t BN, uint32_t lane, uint64_t pol,
-                                            Hook hook) {
+                                            uint32_t nband, uint32_t W, uint32_t BN, uint32_t lane, uint64_t pol) {
     uint4 tg[PULL_UNROLL], wr[PULL_UNROLL];
     uint32_t vm[PULL_UNROLL];                    // the lane's synapses of its piece: bit q for synapse q of the quad
     const uint32_t le_mask = (2u << lane) - 1u;  // lanes <= this one (all 32 for lane 31)
@@ -190,7 +191,6 @@ __device__ __forceinline__ void pull_chunks(const NetView& v, uint32_t& c, uint3
             }
         }
     }
-    hook();
     // the events: every quantity computed for all 4 synapses, the adds predicated
 #pragma unroll
     for (int u = 0; u < PULL_UNROLL; ++u) {
@@ -401,7 +401,6 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
         }
 
         // ---- phase D: raster of every G-th spike, then the band's pieces
-        auto no_hook = []() {};
         {
             uint32_t* mclr = v.pull_mcnt + (size_t)((t + 2u) % 3u) * nm;  // the counters of step t - 1
             for (uint32_t m = bid * PULL_THREADS + tid; m < nm; m += G * PULL_THREADS) mclr[m] = 0;
@@ -468,7 +467,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
                 uint32_t pp = pull_slot(s_pre, np, c0 << 5);
                 for (uint32_t c = c0; c < c1;)
                     pull_chunks<BF16>(v, c, c1, pp, np, Qt, s_pid, s_pa, s_pre, s_dtab, win, n0, nband, W, BN, lane,
-                                      pol, no_hook);
+                                      pol);
             }
             __syncthreads();  // the staged batch is read by every warp before the next is written
             idA = idB;
