@@ -36,7 +36,7 @@ def snn():
     return S
 
 
-def _step_by_step(snn, cfg, steps, min_bands, warm=2, n_sample=3000, seed=0):
+def _step_by_step(snn, cfg, steps, min_bands, warm=2, n_sample=3000, seed=0, schedule=2):
     rng = np.random.default_rng(seed)
     k = oracle.constants(cfg)
     M = cfg["neurons_per_module"]
@@ -44,7 +44,7 @@ def _step_by_step(snn, cfg, steps, min_bands, warm=2, n_sample=3000, seed=0):
     with snn.Network(cfg, raster_capacity=1 << 24) as net:
         bands = net.set_bands(0)
         assert bands >= min_bands, bands
-        net.set_schedule(2)
+        net.set_schedule(schedule)
         N, D = net.N, net.D
         sample = np.unique(np.concatenate([rng.integers(0, N, n_sample), [0, M - 1, N // 2, N - 1]]))
         exc = (sample % M) < k["n_exc"]
@@ -90,6 +90,15 @@ def test_48x48_fixed_law_banded_steps_equal_oracle(snn):
     print("\n48x48 fixed law: %d bands, %d sampled spikes checked" % (bands, sp))
 
 
+def test_48x48_fixed_law_pulled_windows_steps_equal_oracle(snn):
+    """Schedule 5 at 2.88 M neurons: bands of 14-16 modules (20,000 neurons),
+    so only 2 steps of window fit in shared memory and most events take the
+    far path through the ring; every step still equals the oracle's."""
+    cfg = W.gauss_48x48_k1125(seed=9, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped")
+    _, sp = _step_by_step(snn, cfg, steps=4, min_bands=1, schedule=5)
+    print("\n48x48 fixed law, schedule 5: %d sampled spikes checked" % sp)
+
+
 def test_48x48_pairwise_law_banded_steps_equal_oracle(snn):
     cfg = W.pairwise(grid=48, seed=7, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ)
     bands, sp = _step_by_step(snn, cfg, steps=3, min_bands=2)
@@ -100,5 +109,8 @@ def test_96x96_fixed_law_banded_steps_equal_oracle(snn):
     """11.5 M neurons, 12.96 G synapses (104 GB of table), the ring (968 MB)
     eight times the L2: 13 bands on a GB300."""
     cfg = W.gauss_96x96_k1125(seed=8, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped")
+    with snn.Network(cfg, raster_capacity=1 << 10) as net:  # a band of 76,000 neurons: no window row fits
+        with pytest.raises(snn.SnnError, match="does not fit in shared memory"):
+            net.set_schedule(5)
     bands, sp = _step_by_step(snn, cfg, steps=2, min_bands=8)
     print("\n96x96 fixed law: %d bands, %d sampled spikes checked" % (bands, sp))
