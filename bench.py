@@ -356,7 +356,16 @@ def run_gpu(args):
     net = snn.Network(cfg, raster_capacity=T * 20000)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t_build
-    net.set_schedule(schedule, args.block)
+    try:
+        net.set_schedule(schedule, args.block)
+    except snn.SnnError as e:
+        if args.schedule is not None:
+            raise
+        # the default pulled windows need a window row of each SM's band in shared memory
+        # (up to ~50,000 neurons per SM on a GB300); larger networks run the push kernel
+        _log("schedule 5 unavailable here (%s); using schedule 2" % e)
+        schedule = 2
+        net.set_schedule(schedule, args.block)
     net.set_timing(args.timing_every)
 
     for _ in range(args.warmup):
