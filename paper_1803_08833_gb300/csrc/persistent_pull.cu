@@ -32,10 +32,11 @@
 //      reduction (d > W).
 //
 // There is one grid barrier per step.  A CTA may start N(t + 1) while others
-// are still in D(t): its window is its own, ring row t + 1 received its last
-// far event in D(t - W) at the latest, and the spike lists are kept by step
-// parity (the module counters by step mod 3, so that each can be cleared two
-// steps after its use while nobody reads or writes it).
+// are still in D(t): every event a CTA delivers targets its own band, so its
+// window and its band's columns of the ring are written by it alone, and the
+// spike lists are kept by step parity (the module counters by step mod 3, so
+// that each can be cleared two steps after its use while nobody reads or
+// writes it).
 //
 // The window starts empty and is added back into the ring at the end of a
 // launch, so between calls the ring holds exactly what the push delivery
