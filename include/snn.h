@@ -512,6 +512,20 @@ SNN_API snn_status snn_batch_groups(snn_batch* b, uint32_t* cta);
  * sum to ctas when any network runs) minimising the largest
  * steps[i] (8 + work[i] / cta[i]).  Errors: SNN_EINVAL (NULL arrays, n = 0,
  * n > ctas, a work that is negative or not finite). */
+/* The bands and run tables of schedule 5, host only (no counterpart in the
+ * paper): for a description and `sms` CTAs (one per SM), band_mode 1 (uniform
+ * bands of ceil(N / 4 / sms) quads) or 2 (module-aligned bands).  Writes bq
+ * (sms + 1 entries: band b owns the quads [bq[b], bq[b + 1]), bq[sms] =
+ * ceil(N / 4)), run_ptr (sms + 1: the runs of band b are [run_ptr[b],
+ * run_ptr[b + 1])) and runs (pairs {source module, j0 | j1 << 16}: the band
+ * reads, from each spike of that source module, the stencil entries [j0, j1)
+ * of the source's in-grid stencil, the ones whose target modules overlap the
+ * band) and *n_runs.  Errors: SNN_EINVAL (NULL arrays, sms = 0, band_mode not
+ * 1 or 2, an empty grid, N >= 2^24), SNN_EOVERFLOW (more than cap runs; *n_runs,
+ * bq and run_ptr are set, so a second call can size runs). */
+SNN_API snn_status snn_plan_pull_bands(const snn_config* cfg, uint32_t sms, int32_t band_mode, uint32_t* bq,
+                                       uint32_t* run_ptr, uint32_t* runs, uint32_t cap, uint32_t* n_runs);
+
 SNN_API snn_status snn_plan_groups(const uint32_t* steps, const double* work, uint32_t n, uint32_t ctas,
                                    uint32_t* cta);
 /* CUDA-event time (ms) and count of the batch launches since creation. */

@@ -2012,6 +2012,34 @@ snn_status snn_plan_groups(const uint32_t* steps, const double* work, uint32_t n
     return SNN_OK;
 }
 
+snn_status snn_plan_pull_bands(const snn_config* cfg, uint32_t sms, int32_t band_mode, uint32_t* bq,
+                               uint32_t* run_ptr, uint32_t* runs, uint32_t cap, uint32_t* n_runs) {
+    if (!cfg || !bq || !run_ptr || !n_runs) return fail(SNN_EINVAL, "cfg, bq, run_ptr and n_runs must be set");
+    if (sms == 0) return fail(SNN_EINVAL, "sms must be at least 1");
+    if (band_mode != 1 && band_mode != 2) return fail(SNN_EINVAL, "band_mode must be 1 or 2");
+    if (cfg->grid_w == 0 || cfg->grid_h == 0 || cfg->neurons_per_module == 0)
+        return fail(SNN_EINVAL, "empty grid");
+    const uint64_t N64 = (uint64_t)cfg->grid_w * cfg->grid_h * cfg->neurons_per_module;
+    if (N64 >= (1ull << 24)) return fail(SNN_EINVAL, "more than 2^24 neurons");
+    const uint32_t N = (uint32_t)N64, M = cfg->neurons_per_module;
+    uint32_t R2 = 0;
+    const std::vector<int16_t> off = disc_offsets(*cfg, &R2);
+    const std::vector<uint32_t> b = pull_bands(N, M, (N + 3) / 4, sms, band_mode == 2);
+    std::vector<uint2> r;
+    std::vector<uint32_t> ptr;
+    pull_build_runs(N, M, cfg->grid_w, cfg->grid_h, off, b, r, ptr);
+    std::copy(b.begin(), b.end(), bq);
+    std::copy(ptr.begin(), ptr.end(), run_ptr);
+    *n_runs = (uint32_t)r.size();
+    if (r.size() > cap || (!runs && !r.empty()))
+        return fail(SNN_EOVERFLOW, "%zu runs do not fit in %u", r.size(), cap);
+    for (size_t i = 0; i < r.size(); ++i) {
+        runs[2 * i] = r[i].x;
+        runs[2 * i + 1] = r[i].y;
+    }
+    return SNN_OK;
+}
+
 snn_status snn_batch_groups(snn_batch* b, uint32_t* cta) {
     if (!b || !cta) return fail(SNN_EINVAL, "batch or cta is NULL");
     std::copy(b->last_cta.begin(), b->last_cta.end(), cta);

@@ -156,6 +156,8 @@ def load():
         "snn_batch_set_mode": (st, [vp, ctypes.c_int32]),
         "snn_batch_groups": (st, [vp, P(ctypes.c_uint32)]),
         "snn_plan_groups": (st, [vp, vp, ctypes.c_uint32, ctypes.c_uint32, vp]),
+        "snn_plan_pull_bands": (st, [P(SnnConfig), ctypes.c_uint32, ctypes.c_int32, vp, vp, vp, ctypes.c_uint32,
+                                     P(ctypes.c_uint32)]),
         "snn_batch_time": (st, [vp, P(ctypes.c_double), P(ctypes.c_uint64)]),
         "snn_batch_destroy": (None, [vp]),
         "snn_estimate_bytes": (ctypes.c_uint64, [P(SnnConfig)]),
@@ -706,6 +708,25 @@ class ShardedNetwork:
 def now_ns() -> int:
     """The library's host monotonic clock (time base of request arrivals)."""
     return int(load().snn_now_ns())
+
+
+def plan_pull_bands(cfg: dict, sms: int, band_mode: int):
+    """Schedule 5's bands and run tables for a description (host only):
+    (bq, run_ptr, runs) with runs an (n, 2) array of {source module,
+    j0 | j1 << 16}; band b owns the quads [bq[b], bq[b + 1])."""
+    L = load()
+    c = config(cfg)
+    bq = np.zeros(sms + 1, np.uint32)
+    ptr = np.zeros(sms + 1, np.uint32)
+    n = ctypes.c_uint32()
+    st_ = L.snn_plan_pull_bands(ctypes.byref(c), int(sms), int(band_mode), _ptr(bq), _ptr(ptr), None, 0,
+                                ctypes.byref(n))
+    if st_ not in (SNN_OK, SNN_EOVERFLOW):
+        check(st_)
+    runs = np.zeros((max(1, n.value), 2), np.uint32)
+    check(L.snn_plan_pull_bands(ctypes.byref(c), int(sms), int(band_mode), _ptr(bq), _ptr(ptr), _ptr(runs),
+                                max(1, n.value), ctypes.byref(n)))
+    return bq, ptr, runs[:n.value]
 
 
 def plan_groups(steps, work, ctas: int):
