@@ -293,10 +293,12 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  *      synapses that targets the band's modules (the rows are grouped by
  *      target module), adds the events of delay <= W into its window with
  *      shared-memory atomics and those of longer delay into the ring with L2
- *      reductions.  One grid barrier per step.  Needs table_layout =
- *      SNN_LAYOUT_GROUPED with K <= 8188 synapses per row.  Errors:
- *      SNN_EINVAL (no grouped rows, K too large, or no window row fits in
- *      shared memory), SNN_ENOMEM.
+ *      reductions.  One grid barrier per step.  Needs rows grouped by target
+ *      module -- table_layout = SNN_LAYOUT_GROUPED under the fixed out-degree
+ *      law, any layout under the per-pair law (its rows are grouped by
+ *      stencil offset) -- of at most 8188 synapses.  Errors: SNN_EINVAL (no
+ *      grouped rows, a row too long, or no window row fits in shared
+ *      memory), SNN_ENOMEM.
  * All schedules give bit-identical results.  block: threads per block of the
  * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */
@@ -325,7 +327,7 @@ SNN_API snn_status snn_set_window(snn_net* net, uint32_t window, uint32_t queue_
  * each band keeps in shared memory (0 = the most that fit, at most D - 1);
  * events of a longer delay go through the ring in global memory.  Every
  * choice gives the same results.  Outputs (may be NULL): the window and the
- * band mode in use.  Synchronises `stream`.  Errors: SNN_EINVAL (layout not
+ * band mode in use.  Synchronises `stream`.  Errors: SNN_EINVAL (rows not
  * grouped, band_mode not 0-2, window too large), SNN_ENOMEM. */
 SNN_API snn_status snn_set_pull_window(snn_net* net, uint32_t window, int32_t band_mode, uint32_t* window_out,
                                        int32_t* mode_out, void* stream);
@@ -360,9 +362,9 @@ SNN_API snn_status snn_set_resident_state(snn_net* net, int32_t enable, int32_t*
 
 /* Autotuner: runs every applicable schedule (0 and 1 at 128 and 256 threads
  * per delivery block, 2, 3 if the network has the grouped layout and its
- * tile fits, 4 if a delay window fits, 5 if the network has the grouped
- * layout and fixed out-degree) for trial_steps steps from the same snapshot of the dynamic
- * state, times each with CUDA events, restores the state (the raster and the
+ * tile fits, 4 if a delay window fits, 5 if the rows are grouped by target
+ * module: the grouped layout, or the per-pair law) for trial_steps steps
+ * from the same snapshot of the dynamic state, times each with CUDA events, restores the state (the raster and the
  * counters are as before the call) and selects the fastest.  If cache_path
  * is not NULL the choice is looked up there first and appended after
  * tuning; the key holds the network's shape, weight type, layout, rates and

@@ -550,9 +550,13 @@ uint32_t pull_k_max() { return PULL_K_MAX; }
 // neurons touch, the stencil entries [j0, j1) of those target modules.  The
 // stencil offsets are in (dy, dx) raster order, so the in-grid entries of a
 // source are in increasing target module order and [j0, j1) is contiguous.
-// Returns R_max, the most runs of one band.
+// Entries are numbered over the in-grid offsets only (the fixed law's segment
+// index), or, with all_entries, over every offset (the per-pair law's rows,
+// whose out-of-grid entries are empty segments).  Returns R_max, the most
+// runs of one band.
 uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const std::vector<int16_t>& off,
-                         const std::vector<uint32_t>& bq, std::vector<uint2>& runs, std::vector<uint32_t>& ptr) {
+                         const std::vector<uint32_t>& bq, std::vector<uint2>& runs, std::vector<uint32_t>& ptr,
+                         bool all_entries) {
     const uint32_t G = (uint32_t)bq.size() - 1;
     runs.clear();
     ptr.assign(G + 1, 0);
@@ -570,7 +574,13 @@ uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const
                 uint32_t j = 0, j0 = 0, j1 = 0;
                 for (size_t o = 0; o < off.size(); o += 2) {
                     const int tx = (int)sx + off[o], ty = sy + off[o + 1];
-                    if (tx < 0 || ty < 0 || tx >= (int)gw || ty >= (int)gh) continue;
+                    if (tx < 0 || ty < 0 || tx >= (int)gw || ty >= (int)gh) {
+                        if (all_entries) {  // an empty segment: inside the range if a later entry is
+                            if (j0 == j) j0 = j + 1;
+                            ++j;
+                        }
+                        continue;
+                    }
                     const uint32_t tm = (uint32_t)ty * gw + (uint32_t)tx;
                     if (tm < m_lo) j0 = j + 1;
                     if (tm <= m_hi) j1 = j + 1;

@@ -506,18 +506,40 @@ snn_status owned_setup(snn_net* n, uint32_t window, uint32_t queue_cap) {
 // largest band is at most a uniform band plus one module (the synapses a
 // uniform band reads beyond its own) and fits in shared memory, else 1.  Needs
 // the grouped layout (rows ordered by target module) with K synapses per row.
+// The stencil the rows' segment index follows, as (dx, dy) pairs in its order,
+// and whether every offset numbers an entry (per-pair law) or only the in-grid
+// ones (fixed out-degree law).
+std::vector<int16_t> pull_stencil(const snn_config& c, bool* all_entries) {
+    std::vector<int16_t> off;
+    if (c.conn_rule == SNN_RULE_PAIRWISE) {
+        HostTables ht;
+        host_tables(c, &ht);
+        for (size_t k = 0; k < ht.pdx.size(); ++k) {
+            off.push_back((int16_t)ht.pdx[k]);
+            off.push_back((int16_t)ht.pdy[k]);
+        }
+        *all_entries = true;
+    } else {
+        uint32_t R2 = 0;
+        off = disc_offsets(c, &R2);
+        *all_entries = false;
+    }
+    return off;
+}
+
 snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     NetView& v = n->v;
-    if (n->cfg.table_layout != SNN_LAYOUT_GROUPED || v.row_len || !v.segidx)
-        return fail(SNN_EINVAL, "schedule 5 needs a network built with table_layout = SNN_LAYOUT_GROUPED and K "
-                                "synapses per row");
+    const bool pairwise = n->cfg.conn_rule == SNN_RULE_PAIRWISE;
+    if (!v.segidx || (!pairwise && (n->cfg.table_layout != SNN_LAYOUT_GROUPED || v.row_len)))
+        return fail(SNN_EINVAL, "schedule 5 needs rows grouped by target module: table_layout = "
+                                "SNN_LAYOUT_GROUPED, or the per-pair law");
     if (n->K > pull_k_max()) return fail(SNN_EINVAL, "schedule 5: K = %u exceeds %u", n->K, pull_k_max());
     if (band_mode < 0 || band_mode > 2) return fail(SNN_EINVAL, "schedule 5: band_mode must be 0, 1 or 2");
     const int G = owned_grid();
     if (G <= 0) return fail(SNN_ECUDA, "schedule 5: no multiprocessor count");
     const uint32_t Q = n->Npad / 4;
-    uint32_t R2 = 0;
-    const std::vector<int16_t> off = disc_offsets(n->cfg, &R2);
+    bool all_entries = false;
+    const std::vector<int16_t> off = pull_stencil(n->cfg, &all_entries);
     struct Plan {
         std::vector<uint32_t> bq, ptr;
         std::vector<uint2> runs;
@@ -528,7 +550,7 @@ snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
         Plan& p = plan[k];
         p.bq = pull_bands(n->N, n->M, Q, (uint32_t)G, k == 1);
         for (int b = 0; b < G; ++b) p.BQ = std::max(p.BQ, p.bq[b + 1] - p.bq[b]);
-        p.R_max = pull_build_runs(n->N, n->M, n->cfg.grid_w, n->cfg.grid_h, off, p.bq, p.runs, p.ptr);
+        p.R_max = pull_build_runs(n->N, n->M, n->cfg.grid_w, n->cfg.grid_h, off, p.bq, p.runs, p.ptr, all_entries);
         p.Wmax = p.BQ ? pull_max_window(v, G, p.BQ, p.R_max) : 0;
     }
     int pick = band_mode == 2 ? 1 : 0;
@@ -538,7 +560,7 @@ snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     std::vector<uint2>& runs = p.runs;
     std::vector<uint32_t>& ptr = p.ptr;
     for (const uint2& r : runs)  // the kernel's reads of the segment index stay in the row
-        if ((r.y & 0xFFFFu) >= (r.y >> 16) || (r.y >> 16) > n->max_off || r.x >= n->n_modules)
+        if ((r.y & 0xFFFFu) >= (r.y >> 16) || (r.y >> 16) >= v.seg_stride || r.x >= n->n_modules)
             return fail(SNN_EINVAL, "schedule 5: run table entry out of range");
     if (Wmax == 0)
         return fail(SNN_EINVAL, "schedule 5: a delay window row of %u neurons per CTA does not fit in shared memory",
@@ -2022,12 +2044,12 @@ snn_status snn_plan_pull_bands(const snn_config* cfg, uint32_t sms, int32_t band
     const uint64_t N64 = (uint64_t)cfg->grid_w * cfg->grid_h * cfg->neurons_per_module;
     if (N64 >= (1ull << 24)) return fail(SNN_EINVAL, "more than 2^24 neurons");
     const uint32_t N = (uint32_t)N64, M = cfg->neurons_per_module;
-    uint32_t R2 = 0;
-    const std::vector<int16_t> off = disc_offsets(*cfg, &R2);
+    bool all_entries = false;
+    const std::vector<int16_t> off = pull_stencil(*cfg, &all_entries);
     const std::vector<uint32_t> b = pull_bands(N, M, (N + 3) / 4, sms, band_mode == 2);
     std::vector<uint2> r;
     std::vector<uint32_t> ptr;
-    pull_build_runs(N, M, cfg->grid_w, cfg->grid_h, off, b, r, ptr);
+    pull_build_runs(N, M, cfg->grid_w, cfg->grid_h, off, b, r, ptr, all_entries);
     std::copy(b.begin(), b.end(), bq);
     std::copy(ptr.begin(), ptr.end(), run_ptr);
     *n_runs = (uint32_t)r.size();

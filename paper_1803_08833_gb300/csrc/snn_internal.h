@@ -280,7 +280,8 @@ int owned_grid();
 size_t owned_smem_bytes(uint32_t W, uint32_t BQ, int grid);
 cudaError_t launch_owned(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t pull_build_runs(uint32_t N, uint32_t M, uint32_t gw, uint32_t gh, const std::vector<int16_t>& off,
-                         const std::vector<uint32_t>& bq, std::vector<uint2>& runs, std::vector<uint32_t>& ptr);
+                         const std::vector<uint32_t>& bq, std::vector<uint2>& runs, std::vector<uint32_t>& ptr,
+                         bool all_entries);
 std::vector<uint32_t> pull_bands(uint32_t N, uint32_t M, uint32_t Q, uint32_t G, bool aligned);
 uint32_t pull_max_window(const NetView& v, int grid, uint32_t BQ, uint32_t R_max);
 size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max);

@@ -8,8 +8,8 @@ modules (the grouped layout orders each row by target module).  Near events
 go into the window, far ones into the ring; one grid barrier per step.  None
 of that may change a result: spike raster, V, c, refractory counters, the
 whole ring and the counters must equal the oracle bit for bit, for any
-window, both lateral kernels, ragged bands and modules, and across launches,
-snapshots and schedule switches.
+window, both lateral kernels, both connection laws, ragged bands and modules,
+and across launches, snapshots and schedule switches.
 """
 import numpy as np
 import pytest
@@ -66,6 +66,10 @@ CASES = {
                                            grid_h=9, cutoff_um=120.0)), 120),
     # external drive only, at the specified 4x4 network's size
     "drive": (lambda: _grouped(W.gauss_4x4_k1000(seed=2, ext_rate_hz=5000.0)), 200),
+    # the per-pair law (rows of variable length, grouped by stencil offset by construction)
+    "pairwise_gauss": (lambda: W.pairwise(grid=4, M=150, seed=6, imposed_rate_hz=30.0), 100),
+    "pairwise_exp_bf16": (lambda: dict(W.pairwise(grid=5, M=90, lateral="exp", seed=8, weight_dtype="bf16",
+                                                  imposed_rate_hz=35.0), grid_h=3), 100),
 }
 
 
@@ -123,7 +127,8 @@ def test_switching_schedules_and_snapshot(snn):
     (lambda: W.gauss_24x24_k1125(seed=5, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped"), 0),
     (lambda: W.gauss_24x24_k1125(seed=5, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ, table_layout="grouped"), 1),
     (lambda: W.exp_24x24_k2250(seed=4, imposed_rate_hz=W.PAPER_RATE_EXP_HZ, table_layout="grouped"), 0),
-], ids=["gauss_24x24_k1125", "gauss_24x24_k1125_uniform_bands", "exp_24x24_k2250_bf16"])
+    (lambda: W.pairwise(grid=24, seed=3, imposed_rate_hz=W.PAPER_RATE_GAUSS_HZ), 0),
+], ids=["gauss_24x24_k1125", "gauss_24x24_k1125_uniform_bands", "exp_24x24_k2250_bf16", "pairwise_24x24_gauss"])
 def test_full_size_schedule_5_equals_schedule_2(snn, make, band_mode):
     """The 24x24 benchmark networks (720,000 neurons, 810 M and 1.6 G synapses)
     at the paper's rates, 200 steps in two calls: schedule 5 with its default
@@ -171,9 +176,6 @@ def test_schedule_5_bounded_barrier_wait_reports_timeout(snn):
 
 def test_schedule_5_argument_errors(snn):
     with snn.Network(W.small(grid=2, M=64, K=10, seed=1)) as net:  # draw-order rows
-        with pytest.raises(snn.SnnError, match="GROUPED"):
-            net.set_schedule(5)
-    with snn.Network(W.pairwise(grid=3, M=30, seed=2)) as net:  # ragged rows
         with pytest.raises(snn.SnnError, match="GROUPED"):
             net.set_schedule(5)
     with snn.Network(_grouped(W.small(grid=2, M=64, K=10, seed=1))) as net:

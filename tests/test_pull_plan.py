@@ -22,6 +22,9 @@ def snn():
 
 CASES = {
     "gauss_24x24_M1250": W.gauss_24x24_k1125(seed=1),
+    # the per-pair law: its rows number every stencil offset, out-of-grid ones as empty segments
+    "pairwise_gauss_12x12_M1250": W.pairwise(grid=12, seed=1),
+    "pairwise_exp_5x7_M90": dict(W.pairwise(grid=5, M=90, lateral="exp", seed=2), grid_h=7),
     "exp_6x6_M120": W.small(grid=6, M=120, K=400, lateral="exp", seed=5),
     "ragged_3x2_M333": dict(W.small(grid=3, M=333, K=37, seed=9), grid_h=2),
     "short_cutoff_7x9_M77": dict(W.small(grid=7, M=77, K=60, seed=12), grid_h=9, cutoff_um=120.0),
@@ -29,19 +32,37 @@ CASES = {
 }
 
 
+def _entry_modules(cfg, s):
+    """Target module of every segment-index entry of source module s (-1: an
+    out-of-grid entry, an empty segment): the fixed law's entries are its
+    in-grid stencil modules (the oracle's target table), the per-pair law's
+    are all offsets of the oracle's pair stencil."""
+    if cfg.get("conn_rule") == "pairwise":
+        gw, gh = cfg["grid_w"], cfg["grid_h"]
+        dx, dy = oracle.pair_stencil(cfg)[:2]
+        tx, ty = s % gw + dx, s // gw + dy
+        inside = (tx >= 0) & (ty >= 0) & (tx < gw) & (ty < gh)
+        return np.where(inside, ty * gw + tx, -1)
+    return np.asarray(oracle.cdf_table(cfg, s)[1]).astype(np.int64)
+
+
 def _brute_runs(cfg, n0, n1):
-    """Runs of the band of neurons [n0, n1): (source module, j0, j1)."""
+    """Runs of the band of neurons [n0, n1): (source module, j0, j1), the
+    entries from the first to the last whose target module the band touches."""
     M = cfg["neurons_per_module"]
     nm = cfg["grid_w"] * cfg["grid_h"]
     m_lo, m_hi = n0 // M, (n1 - 1) // M
     out = []
     for s in range(nm):
-        TM = np.asarray(oracle.cdf_table(cfg, s)[1])
+        TM = _entry_modules(cfg, s)
         hit = np.nonzero((TM >= m_lo) & (TM <= m_hi))[0]
         if len(hit) == 0:
             continue
-        assert np.all(np.diff(hit) == 1), "the band's entries of a source must be contiguous"
-        out.append((s, int(hit[0]), int(hit[-1]) + 1))
+        j0, j1 = int(hit[0]), int(hit[-1]) + 1
+        inner = TM[j0:j1]
+        # in between only the band's modules, or empty segments
+        assert np.all((inner == -1) | ((inner >= m_lo) & (inner <= m_hi))), "non-contiguous entries"
+        out.append((s, j0, j1))
     return out
 
 
