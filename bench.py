@@ -69,12 +69,11 @@ NCU_TRAFFIC = {
         "bytes_per_event": 8.39,
         "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
                    "376.9 MB DRAM read+write for 44.9 M recurrent events, scaled to a launch by its events"},
-    5: {"kernel": "k_run_steps_pull", "source_sha256": "052b1d4bf9ea4c14ada1a072cb94c12eca37776669fe71386fb71e6da4d3b07f",
-        "bytes_per_event": 9.58,
+    5: {"kernel": "k_run_steps_pull", "source_sha256": "6a22c8d0169c811c45070b9b6ebac19a82c7a76166cbeae82624af887e5902d8",
+        "bytes_per_event": 9.57,
         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 16x16 Gaussian patch (320,000 "
-                   "neurons, K=1125, module-aligned bands as at 24x24), one 30-step launch: 778.1 MB DRAM "
-                   "read+write for 81.2 M recurrent events (777.8 MB on the capture of this source), "
-                   "scaled to a launch by its events"},
+                   "neurons, K=1125, module-aligned bands as at 24x24), one 30-step launch: 777.4 MB DRAM "
+                   "read+write for 81.2 M recurrent events, scaled to a launch by its events"},
 }
 KERNEL_SOURCES = {2: "persistent_kernels.cu", 5: "persistent_pull.cu"}
 
