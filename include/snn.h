@@ -296,9 +296,11 @@ SNN_API snn_status snn_get_dims(snn_net* net, uint32_t* N, uint32_t* K, uint32_t
  *      reductions.  One grid barrier per step.  Needs rows grouped by target
  *      module -- table_layout = SNN_LAYOUT_GROUPED under the fixed out-degree
  *      law, any layout under the per-pair law (its rows are grouped by
- *      stencil offset) -- of at most 8188 synapses.  Errors: SNN_EINVAL (no
- *      grouped rows, a row too long, or no window row fits in shared
- *      memory), SNN_ENOMEM.
+ *      stencil offset) -- of at most 8188 synapses.  The band's neuron state
+ *      stays in the SM's tensor memory for the launch (bands of at most
+ *      28,672 neurons).  Errors: SNN_EINVAL (no grouped rows, a row too
+ *      long, no window row fits in shared memory, or the band's state does
+ *      not fit in tensor memory), SNN_ENOMEM.
  * All schedules give bit-identical results.  block: threads per block of the
  * delivery kernel for schedules 0 and 1 (multiple of 32 in [32, 256], 0 =
  * default); ignored by schedule 2.  Errors: SNN_EINVAL. */

@@ -12,12 +12,18 @@
 // ring in global memory as before.  One step t:
 //
 //   N  the band's neurons (flow steps 4-6, Sec. II-A): the input of step t is
-//      window row t mod W plus ring row t mod D, both cleared after the read;
-//      spikes are staged in id order per warp (for the raster) and appended to
-//      their module's list (counted by the module's owner in shared memory
-//      when the bands are module-aligned);
+//      window row t mod W; the neuron state (V, c, refractory counters) stays
+//      in the SM's tensor memory for the whole launch, so the phase reads
+//      nothing from global memory; spikes are staged in id order per warp (for
+//      the raster) and appended to their module's list (counted by the
+//      module's owner in shared memory when the bands are module-aligned);
 //   -- grid barrier, split: between arriving and waiting each CTA fills the
-//      step's per-delay destinations and draws the next step's external drive --
+//      step's per-delay destinations, draws the next step's external drive and
+//      starts copying its band's slice of ring row (t + W) mod D into window
+//      row t mod W (the row N(t) has consumed): every far event of step t + W
+//      has a delay > W, so it came from a step < t and the slice is final.
+//      The copy lands before D(t) adds the events of delay W into that row,
+//      and the slice is then cleared in the ring --
 //   D  (flow steps 2-3) every CTA writes the raster entries of every G-th
 //      spike; then it walks its band's runs: for every source module whose
 //      stencil reaches the band, the spikes of that module and, in each
@@ -38,9 +44,11 @@
 // that each can be cleared two steps after its use while nobody reads or
 // writes it).
 //
-// The window starts empty and is added back into the ring at the end of a
-// launch, so between calls the ring holds exactly what the push delivery
-// would hold.  Integer sums: results are bit-identical to every other schedule.
+// At the start of a launch the window takes ring rows t0 .. t0 + W - 1 of the
+// band (cleared there) and the state moves into tensor memory; at the end the
+// window is added back into the ring and the state written back, so between
+// calls the ring and the state hold exactly what the push delivery would hold.
+// Integer sums: results are bit-identical to every other schedule.
 // Every barrier wait is bounded (grid_common.cuh).
 #include "grid_common.cuh"
 
@@ -128,6 +136,66 @@ __device__ __forceinline__ uint64_t evict_normal_policy() {
 // of four) that hold them: quads (a >> 2) .. ((a + len - 1) >> 2) of the row,
 // so every quad is one 16-byte vector (rows start 32-byte aligned and hold
 // Kpad >= a + len entries: a vector never leaves its row).
+// Tensor memory (128 lanes x 512 columns of 32 bits per SM, Blackwell) holds
+// the band's neuron state for a launch.  Warp w reaches the lanes 32 (w mod 4)
+// .. 32 (w mod 4) + 31; lane i of chunk k of the warp is the quad of its lane i,
+// with V and c in 8 columns (8-aligned) and the refractory bytes in one:
+// columns 8 (MC (w / 4) + k) .. + 7 and 32 MC + MC (w / 4) + k, MC = chunks per
+// warp (36 MC columns in all).  Loads and stores wait for completion inside
+// the same asm statement, so no register is read before its data arrived.
+__device__ __forceinline__ void tmem_alloc(uint32_t* s_dst, uint32_t ncols) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n\t"
+        "tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::"r"((uint32_t)__cvta_generic_to_shared(s_dst)),
+        "r"(ncols)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld9(uint32_t a8, uint32_t a1, uint32_t (&r)[9]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%9];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x1.b32 {%8}, [%10];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8])
+        : "r"(a8), "r"(a1)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st9(uint32_t a8, uint32_t a1, const uint32_t (&r)[9]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%2, %3, %4, %5, %6, %7, %8, %9};\n\t"
+        "tcgen05.st.sync.aligned.32x32b.x1.b32 [%1], {%10};\n\t"
+        "tcgen05.wait::st.sync.aligned;" ::"r"(a8),
+        "r"(a1), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8])
+        : "memory");
+}
+// The quad's state as 9 words: V (4), c (4), refractory bytes.
+__device__ __forceinline__ void state_words(const float4& V, const float4& C, uint32_t R, uint32_t (&r)[9]) {
+    r[0] = __float_as_uint(V.x);
+    r[1] = __float_as_uint(V.y);
+    r[2] = __float_as_uint(V.z);
+    r[3] = __float_as_uint(V.w);
+    r[4] = __float_as_uint(C.x);
+    r[5] = __float_as_uint(C.y);
+    r[6] = __float_as_uint(C.z);
+    r[7] = __float_as_uint(C.w);
+    r[8] = R;
+}
+
+// 16 bytes global -> shared without registers (L2 only), and the wait for
+// every such copy this thread issued.
+__device__ __forceinline__ void cp_async16(void* s_dst, const void* g_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(s_dst)),
+                 "l"(g_src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t pull_piece_quads(uint32_t a, uint32_t len) {
     return len ? ((a + len + 3) >> 2) - (a >> 2) : 0u;
 }
@@ -251,6 +319,7 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     __shared__ unsigned long long s_rec[PULL_WARPS];
     __shared__ uint32_t s_pois[MAX_POIS];
     __shared__ uint32_t s_mc[PULL_MODS_MAX];  // module-aligned bands: spikes per module of the band this step
+    __shared__ uint32_t s_tmem;               // tensor memory of the band's state
     load_poisson_table(v, s_pois);
     uint32_t gen = 0;
     if (tid == 0) {
@@ -270,14 +339,45 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     for (uint32_t x = tid; x < W * BQ; x += PULL_THREADS) win4[x] = make_int4(0, 0, 0, 0);
     for (uint32_t b = tid; b <= G; b += PULL_THREADS) s_bq[b] = v.pull_bq[b];
     for (uint32_t m = bid * PULL_THREADS + tid; m < 3 * nm; m += G * PULL_THREADS) v.pull_mcnt[m] = 0;
-    bool ok = grid_barrier(v, G, gen);  // (starts with a CTA barrier) the module counters are clear everywhere
-    const uint32_t t0 = s_t0;
     const uint32_t lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     const uint32_t wg = bid * PULL_WARPS + warp;
     const uint32_t qa = q0 + nq * warp / PULL_WARPS, qb = q0 + nq * (warp + 1) / PULL_WARPS;
+    // the band's state into tensor memory: this warp's chunks of 32 quads
+    const uint32_t MC = v.pull_tmem_chunks, tcols = v.pull_tmem_cols;
+    if (warp == 0) tmem_alloc(&s_tmem, tcols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tm_lane = s_tmem + (((warp & 3u) * 32u) << 16);
+    const uint32_t tm_vc = tm_lane + 8u * MC * (warp >> 2), tm_r = tm_lane + 32u * MC + MC * (warp >> 2);
+    {
+        uint32_t k = 0;
+        for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
+            const uint32_t q = qc + lane;
+            uint32_t w9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (q < qb) {
+                QuadIn in;
+                load_state(v, q << 2, in);
+                state_words(in.V, in.C, in.R, w9);
+            }
+            __syncwarp();
+            if (SNN_BOUND(v.st, k < MC)) tmem_st9(tm_vc + 8u * k, tm_r + k, w9);
+        }
+    }
+    bool ok = grid_barrier(v, G, gen);  // (starts with a CTA barrier) the module counters are clear everywhere
+    const uint32_t t0 = s_t0;
     int4* ring4 = reinterpret_cast<int4*>(v.ring);
     const uint32_t Q4 = v.Npad >> 2;  // int4 per ring row
+    // the window takes the band's ring rows of steps t0 .. t0 + W - 1 (final:
+    // their far events came from earlier launches), cleared in the ring
+    for (uint32_t x = tid; x < W * nq; x += PULL_THREADS) {
+        const uint32_t k = x / nq, lq = x - k * nq;
+        int4* g = ring4 + (size_t)((t0 + k) % D) * Q4 + q0 + lq;
+        win4[(size_t)((t0 + k) % W) * BQ + lq] = __ldcg(g);
+        *g = make_int4(0, 0, 0, 0);
+    }
+    __syncthreads();
     const uint32_t Kpad = v.Kpad, stride = v.seg_stride;
     const uint64_t pol = evict_normal_policy();
 
@@ -303,34 +403,32 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
         uint32_t* segm = v.pull_segmod + (size_t)par * v.Npad;  // spikes of module m at [m M, m M + mcnt[m])
         uint32_t* mcnt = v.pull_mcnt + (size_t)(t % 3u) * nm;
         uint32_t* woff = v.pull_woff + (size_t)par * TW;
-        // ---- phase N: input = window row + ring row, both cleared; spikes staged
+        // ---- phase N: input = window row t mod W (the ring's far events of the
+        // step were folded into it W steps ago); state in tensor memory; spikes staged
         uint32_t run = 0;
         {
-            QuadIn nx;
-            int4 nF = make_int4(0, 0, 0, 0);
-            auto load_in = [&](uint32_t q, uint32_t k, QuadIn& in, int4& F) {
-                load_state(v, q << 2, in);
-                F = __ldcg(ring4 + (size_t)slot0 * Q4 + q);
-                in.drive = drive_of(k, t);
-            };
-            if (qa + lane < qb) load_in(qa + lane, 0, nx, nF);
             uint32_t k = 0;
             for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
                 const uint32_t q = qc + lane;
-                QuadIn cur = nx;
-                const int4 cF = nF;
-                if (q + 32 < qb) load_in(q + 32, k + 1, nx, nF);
+                uint32_t w9[9];
+                __syncwarp();
+                tmem_ld9(tm_vc + 8u * k, tm_r + k, w9);
                 uint32_t spk = 0;
                 if (q < qb) {
-                    int4* wp = win4 + (size_t)wslot * BQ + (q - q0);
-                    const int4 a = *wp;
-                    cur.I = make_int4(a.x + cF.x, a.y + cF.y, a.z + cF.z, a.w + cF.w);
-                    *wp = make_int4(0, 0, 0, 0);  // the row now collects step t + W
-                    ring4[(size_t)slot0 * Q4 + q] = make_int4(0, 0, 0, 0);
+                    QuadIn cur;
+                    cur.V = make_float4(__uint_as_float(w9[0]), __uint_as_float(w9[1]), __uint_as_float(w9[2]),
+                                        __uint_as_float(w9[3]));
+                    cur.C = make_float4(__uint_as_float(w9[4]), __uint_as_float(w9[5]), __uint_as_float(w9[6]),
+                                        __uint_as_float(w9[7]));
+                    cur.R = w9[8];
+                    cur.drive = drive_of(k, t);
+                    cur.I = win4[(size_t)wslot * BQ + (q - q0)];
                     QuadOut o;
                     spk = integrate_quad<false>(v, q << 2, 0u, cur, ext, rec, o);
-                    store_state(v, q << 2, o);
+                    state_words(o.V, o.C, o.R, w9);
                 }
+                __syncwarp();
+                tmem_st9(tm_vc + 8u * k, tm_r + k, w9);
                 const uint32_t cnt = __popc(spk);
                 uint32_t incl = cnt;
 #pragma unroll
@@ -390,6 +488,10 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             const uint32_t ws = (wslot + d) % W, rs = (slot0 + d) % D;
             s_dtab[d] = d <= W ? ws * BN : 0x80000000u | rs;
         }
+        // ring row (t + W) mod D of the band into window row t mod W (waited for
+        // before the first event of delay W lands there, cleared in the ring then)
+        int4* fold = ring4 + (size_t)((t + W) % D) * Q4 + q0;
+        for (uint32_t x = tid; x < nq; x += PULL_THREADS) cp_async16(win4 + (size_t)wslot * BQ + x, fold + x);
         ndrv = 0;
         if (step + 1 < n_steps)
             for (; ndrv < nd_max; ++ndrv)
@@ -441,6 +543,9 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             }
             if (tid < P) piece_range(idA, rA, aA, lA);
         }
+        // the fold has landed (visible to the CTA after the batch's first barrier)
+        cp_async_wait_all();
+        for (uint32_t x = tid; x < nq; x += PULL_THREADS) fold[x] = make_int4(0, 0, 0, 0);
         for (uint32_t pb = 0; pb < P; pb += PULL_PIECES) {
             const uint32_t nb = min(PULL_PIECES, P - pb);
             // the batch's non-empty pieces, compacted: (rank << 22) | quads, scanned
@@ -489,7 +594,9 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     }
 
     // ---- epilogue: the window back into the ring (rows te .. te + W - 1: no
-    // other CTA's far reduction of the last step lands there), counters
+    // other CTA's far reduction of the last step lands there), the state back
+    // from tensor memory, counters
+    cp_async_wait_all();  // a step left by a barrier timeout may have a fold in flight
     __syncthreads();
     {
         const uint32_t te = t0 + done;
@@ -501,6 +608,28 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
             ring4[g] = make_int4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w);
         }
     }
+    {
+        uint32_t k = 0;
+        for (uint32_t qc = qa; qc < qb; qc += 32, ++k) {
+            const uint32_t q = qc + lane;
+            uint32_t w9[9];
+            tmem_ld9(tm_vc + 8u * k, tm_r + k, w9);
+            if (q < qb) {
+                QuadOut o;
+                o.V = make_float4(__uint_as_float(w9[0]), __uint_as_float(w9[1]), __uint_as_float(w9[2]),
+                                  __uint_as_float(w9[3]));
+                o.C = make_float4(__uint_as_float(w9[4]), __uint_as_float(w9[5]), __uint_as_float(w9[6]),
+                                  __uint_as_float(w9[7]));
+                o.R = w9[8];
+                store_state(v, q << 2, o);
+            }
+            __syncwarp();
+        }
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_dealloc(s_tmem, tcols);
     uint32_t e = ext;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -544,6 +673,21 @@ size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max) {
 uint32_t pull_warps() { return PULL_WARPS; }
 uint32_t pull_mods_max() { return PULL_MODS_MAX; }
 uint32_t pull_k_max() { return PULL_K_MAX; }
+
+// Tensor-memory columns for bands of at most BQ quads (0: more than the 512 of
+// an SM), and the chunks of 32 quads per warp they hold: a warp's share of a
+// band is at most ceil(BQ / warps) quads, 9 columns per chunk, four warps per
+// lane quarter.
+uint32_t pull_tmem_cols(uint32_t BQ, uint32_t* chunks) {
+    const uint32_t per_warp = (BQ + PULL_WARPS - 1) / PULL_WARPS;
+    const uint32_t mc = std::max(1u, (per_warp + 31) / 32);
+    *chunks = mc;
+    const uint32_t need = 4u * 9u * mc;
+    if (need > 512u) return 0;
+    uint32_t cols = 32;
+    while (cols < need) cols <<= 1;
+    return cols;
+}
 
 // The runs of every band (band b = the quads [bq[b], bq[b + 1]) of Q): for
 // each source module whose in-grid stencil reaches a module the band's
@@ -660,6 +804,12 @@ cudaError_t launch_pull(const NetView& v, uint32_t n_steps, int grid, cudaStream
     const size_t smem = pull_smem_bytes(v.pull_W, v.pull_BQ, grid, v.pull_R_max);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // CTAs sharing an SM share its 512 tensor-memory columns: an allocation
+    // waiting for another CTA's columns would wait at the grid barrier forever
+    int fit = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, fn, PULL_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (fit < 1 || (uint64_t)fit * v.pull_tmem_cols > 512u || v.pull_tmem_cols < 32u) return cudaErrorInvalidConfiguration;
     NetView vv = v;
     uint32_t ns = n_steps;
     void* args[] = {&vv, &ns};

@@ -568,6 +568,10 @@ snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     const uint32_t W = window == 0 ? Wmax : window;
     if (W > Wmax) return fail(SNN_EINVAL, "schedule 5: window %u exceeds the %u steps that fit (D - 1 = %u)", W, Wmax,
                               v.D - 1);
+    uint32_t tchunks = 0;
+    const uint32_t tcols = pull_tmem_cols(BQ, &tchunks);
+    if (tcols == 0)
+        return fail(SNN_EINVAL, "schedule 5: the state of a band of %u neurons does not fit in tensor memory", BQ * 4);
     cudaStream_t s = 0;
     if (n->plgrid != G || !v.pull_seg) {
         const size_t warps = (size_t)G * pull_warps();
@@ -603,6 +607,8 @@ snn_status pull_setup(snn_net* n, uint32_t window, int32_t band_mode) {
     v.pull_W = W;
     v.pull_BQ = BQ;
     v.pull_R_max = R_max;
+    v.pull_tmem_chunks = tchunks;
+    v.pull_tmem_cols = tcols;
     v.pull_aligned = 0;
     if (pick == 1) {  // every module in one band: counted by its owner when no band holds too many
         uint32_t most = 0;

@@ -132,6 +132,8 @@ struct NetView {
     const uint32_t* pull_bq;  // G + 1: band b = the quads [pull_bq[b], pull_bq[b + 1])
     uint32_t pull_aligned;    // bands on module boundaries, at most pull_mods_max() modules each
     uint32_t pull_R_max;      // most runs of one band
+    uint32_t pull_tmem_chunks;  // chunks of 32 quads per warp whose state is in tensor memory
+    uint32_t pull_tmem_cols;    // tensor-memory columns allocated per CTA (a power of 2, 32 .. 512)
     const uint2* pull_runs;   // runs of all bands: {source module, stencil entries j0 | j1 << 16}
     const uint32_t* pull_run_ptr;  // G + 1: runs of band b at [ptr[b], ptr[b + 1])
     uint32_t* pull_seg;       // 2 x Npad: spikes per warp in id order (by step parity)
@@ -288,6 +290,7 @@ size_t pull_smem_bytes(uint32_t W, uint32_t BQ, int grid, uint32_t R_max);
 uint32_t pull_warps();
 uint32_t pull_mods_max();
 uint32_t pull_k_max();
+uint32_t pull_tmem_cols(uint32_t BQ, uint32_t* chunks);
 cudaError_t launch_pull(const NetView& v, uint32_t n_steps, int grid, cudaStream_t s);
 uint32_t persistent_resident_quads(const NetView& v, int grid);  // 0: the state cannot stay in shared memory
 // In-disc grid offsets (dx, dy pairs) of the cut-off radius, dx^2 + dy^2 <=

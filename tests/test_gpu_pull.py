@@ -174,6 +174,21 @@ def test_schedule_5_bounded_barrier_wait_reports_timeout(snn):
         _compare(net2, ref)
 
 
+def test_schedule_5_refuses_bands_beyond_tensor_memory(snn):
+    """The band's neuron state stays in tensor memory (512 columns per SM: at
+    most 7,168 quads a band on 16 warps).  100 x 100 modules of 440 neurons
+    give bands of 29,040 (aligned) or 28,948 (uniform) neurons: a window row
+    still fits in shared memory, the state does not, and the schedule is
+    refused with the network left usable."""
+    cfg = _grouped(W.small(grid=100, M=440, K=10, seed=4, imposed_rate_hz=20.0))
+    with snn.Network(cfg) as net:
+        with pytest.raises(snn.SnnError, match="tensor memory"):
+            net.set_schedule(5)
+        net.set_schedule(2)
+        net.step(3)
+        assert net.stats()["steps"] == 3
+
+
 def test_schedule_5_argument_errors(snn):
     with snn.Network(W.small(grid=2, M=64, K=10, seed=1)) as net:  # draw-order rows
         with pytest.raises(snn.SnnError, match="GROUPED"):
