@@ -371,11 +371,15 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     const uint32_t Q4 = v.Npad >> 2;  // int4 per ring row
     // the window takes the band's ring rows of steps t0 .. t0 + W - 1 (final:
     // their far events came from earlier launches), cleared in the ring
+    // (all copies in flight at once; each cleared once it has landed)
     for (uint32_t x = tid; x < W * nq; x += PULL_THREADS) {
         const uint32_t k = x / nq, lq = x - k * nq;
-        int4* g = ring4 + (size_t)((t0 + k) % D) * Q4 + q0 + lq;
-        win4[(size_t)((t0 + k) % W) * BQ + lq] = __ldcg(g);
-        *g = make_int4(0, 0, 0, 0);
+        cp_async16(win4 + (size_t)((t0 + k) % W) * BQ + lq, ring4 + (size_t)((t0 + k) % D) * Q4 + q0 + lq);
+    }
+    cp_async_wait_all();
+    for (uint32_t x = tid; x < W * nq; x += PULL_THREADS) {
+        const uint32_t k = x / nq, lq = x - k * nq;
+        ring4[(size_t)((t0 + k) % D) * Q4 + q0 + lq] = make_int4(0, 0, 0, 0);
     }
     __syncthreads();
     const uint32_t Kpad = v.Kpad, stride = v.seg_stride;
@@ -599,13 +603,27 @@ __global__ void __launch_bounds__(PULL_THREADS, 1) k_run_steps_pull(NetView v, u
     cp_async_wait_all();  // a step left by a barrier timeout may have a fold in flight
     __syncthreads();
     {
-        const uint32_t te = t0 + done;
-        for (uint32_t x = tid; x < W * nq; x += PULL_THREADS) {
-            const uint32_t k = x / nq, lq = x - k * nq;
-            const size_t g = (size_t)((te + k) % D) * Q4 + q0 + lq;
-            const int4 a = __ldcg(ring4 + g);
-            const int4 c = win4[(size_t)((te + k) % W) * BQ + lq];
-            ring4[g] = make_int4(a.x + c.x, a.y + c.y, a.z + c.z, a.w + c.w);
+        const uint32_t te = t0 + done, nx = W * nq;
+        for (uint32_t x0 = 0; x0 < nx; x0 += 8 * PULL_THREADS) {  // eight ring loads in flight per thread
+            int4 a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t x = x0 + u * PULL_THREADS + tid;
+                if (x < nx) {
+                    const uint32_t k = x / nq, lq = x - k * nq;
+                    a[u] = __ldcg(ring4 + (size_t)((te + k) % D) * Q4 + q0 + lq);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t x = x0 + u * PULL_THREADS + tid;
+                if (x < nx) {
+                    const uint32_t k = x / nq, lq = x - k * nq;
+                    const int4 c = win4[(size_t)((te + k) % W) * BQ + lq];
+                    ring4[(size_t)((te + k) % D) * Q4 + q0 + lq] =
+                        make_int4(a[u].x + c.x, a[u].y + c.y, a[u].z + c.z, a[u].w + c.w);
+                }
+            }
         }
     }
     {
