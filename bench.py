@@ -69,11 +69,13 @@ NCU_TRAFFIC = {
         "bytes_per_event": 8.39,
         "capture": "ncu --set full, 12x12 Gaussian patch (180,000 neurons, K=1125), one 30-step launch: "
                    "376.9 MB DRAM read+write for 44.9 M recurrent events, scaled to a launch by its events"},
-    5: {"kernel": "k_run_steps_pull", "source_sha256": "6a22c8d0169c811c45070b9b6ebac19a82c7a76166cbeae82624af887e5902d8",
-        "bytes_per_event": 9.57,
+    5: {"kernel": "k_run_steps_pull", "source_sha256": "21c6397f6a2eddcc4eed07e53a1a027d1d2cb080cccc1dbcfce389a977c85ae5",
+        "bytes_per_event": 9.31,
         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum, 16x16 Gaussian patch (320,000 "
-                   "neurons, K=1125, module-aligned bands as at 24x24), one 30-step launch: 777.4 MB DRAM "
-                   "read+write for 81.2 M recurrent events, scaled to a launch by its events"},
+                   "neurons, K=1125, module-aligned bands as at 24x24), one 300-step launch: 7,486.9 MB DRAM "
+                   "read+write for 804.0 M recurrent events (a 30-step launch: 819.5 MB for 81.2 M, so ~70 MB "
+                   "per launch are fixed -- the window filled from and returned to the ring -- and 9.22 B per "
+                   "event), scaled to a launch by its events"},
 }
 KERNEL_SOURCES = {2: "persistent_kernels.cu", 5: "persistent_pull.cu"}
 
