@@ -29,6 +29,10 @@ CASES = {
     "ragged_3x2_M333": dict(W.small(grid=3, M=333, K=37, seed=9), grid_h=2),
     "short_cutoff_7x9_M77": dict(W.small(grid=7, M=77, K=60, seed=12), grid_h=9, cutoff_um=120.0),
     "spec_4x4_M1000": W.gauss_4x4_k1000(seed=1),
+    # one module: every band's runs come from it alone
+    "single_module_1x1_M50": W.small(grid=1, M=50, K=20, seed=3),
+    # the per-pair law with modules split inside quads
+    "pairwise_ragged_3x4_M43": dict(W.pairwise(grid=3, M=43, seed=7), grid_h=4),
 }
 
 
@@ -66,7 +70,7 @@ def _brute_runs(cfg, n0, n1):
     return out
 
 
-@pytest.mark.parametrize("sms", [152, 7, 1])
+@pytest.mark.parametrize("sms", [152, 7, 1, 1000])
 @pytest.mark.parametrize("band_mode", [1, 2])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_bands_and_runs_equal_brute_force(snn, name, band_mode, sms):
@@ -87,6 +91,8 @@ def test_bands_and_runs_equal_brute_force(snn, name, band_mode, sms):
         units = -(-(N // M) // u)
         assert sizes.max() * 4 <= -(-units // sms) * u * M + 3
     assert ptr[0] == 0 and ptr[-1] == len(runs) and np.all(np.diff(ptr.astype(np.int64)) >= 0)
+    if sms > Q:  # more SMs than quads: the trailing bands are empty
+        assert np.count_nonzero(sizes) <= Q
     step = max(1, sms // 12)  # the brute force over every source is slow in Python: a spread of bands
     for b in list(range(0, sms, step)) + [sms - 1]:
         n0, n1 = int(bq[b]) * 4, min(int(bq[b + 1]) * 4, N)
