@@ -402,7 +402,8 @@ class Network:
     def set_schedule(self, schedule: int, block: int = 0):
         """0/1: two launches per step; 2: persistent push kernel; 3: target
         tiles; 4: owned windows with record queues; 5: owned windows filled by
-        pulling row ranges (grouped layout).  Results are identical."""
+        pulling row ranges (rows grouped by target module: the grouped layout,
+        or the per-pair law).  Results are identical."""
         check(load().snn_set_schedule(self._h, int(schedule), int(block)))
 
     def stdp(self):
